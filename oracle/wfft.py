@@ -1,0 +1,61 @@
+"""Sec. 2.3, Eq. (3): spatial derivatives by FFT with the 16th-order modified wavenumber.
+
+Readings:
+* Eq. (3) is circular as printed (k_x on both sides). It is read as
+      k_eff(k) = (2/dx) * sum_{n=0}^{7} c_n phi^(2n+1),  phi = sin(k dx / 2),
+  with k = 2 pi m / (N dx) for the DFT index m in [-N/2, N/2), the truncated Maclaurin
+  series of arcsin(phi) / (dx/2); the same per axis with dy for k_y.
+* The Nyquist index m = -N/2 gets a first-derivative multiplier of 0, so that the
+  derivative of a real field stays real.
+* Every derivative used by the model is one inverse transform of a spectrum times a
+  product of first-derivative multipliers d(m) = i k_eff(m) (second derivatives are
+  d^2, mixed ones d_x d_y). The window of the "windowed" FFT is not specified in the
+  paper; no window is applied (W = 1), i.e. the operator is Eq. (3) as printed.
+"""
+import numpy as np
+
+# Eq. (3): the eight coefficients as printed.
+C_KEFF = np.array([1.0, 1.0 / 6.0, 3.0 / 40.0, 5.0 / 112.0, 35.0 / 1152.0,
+                   63.0 / 2816.0, 231.0 / 13312.0, 143.0 / 10240.0])
+
+
+def dft_indices(N):
+    """DFT index m of each FFT output position, in [-N/2, N/2)."""
+    return np.rint(np.fft.fftfreq(N) * N).astype(np.int64)
+
+
+def keff(m, N, dx):
+    """Eq. (3): modified wavenumber of DFT index m on an N-point axis of spacing dx."""
+    phi = np.sin(np.pi * np.asarray(m, dtype=np.float64) / N)
+    s = np.zeros_like(phi)
+    for n, c in enumerate(C_KEFF):
+        s = s + c * phi ** (2 * n + 1)
+    return (2.0 / dx) * s
+
+
+def deriv_multiplier(N, dx):
+    """d(m) = i k_eff(m) per FFT position, zero at the Nyquist index."""
+    m = dft_indices(N)
+    d = 1j * keff(m, N, dx)
+    if N % 2 == 0:
+        d[m == -N // 2] = 0.0
+    return d
+
+
+def spectral_deriv(h, ox, oy, dx, dy):
+    """Spectral derivative d^(ox) / dx^(ox) d^(oy) / dy^(oy) of a real field h of shape (ny, nx)."""
+    ny, nx = h.shape
+    mult = deriv_multiplier(nx, dx)[None, :] ** ox * deriv_multiplier(ny, dy)[:, None] ** oy
+    return np.fft.ifft2(mult * np.fft.fft2(h)).real
+
+
+def dft_deriv_matrix(N, dx, order=1):
+    """Brute-force real N x N matrix of the same operator along one axis, built from the DFT
+    sums (no FFT): D[a, b] = (1/N) sum_m d(m)^order exp(2 pi i m (a - b) / N)."""
+    m = dft_indices(N)
+    d = deriv_multiplier(N, dx) ** order
+    a = np.arange(N)
+    D = np.zeros((N, N), dtype=np.complex128)
+    for j in range(N):
+        D += d[j] * np.exp(2j * np.pi * m[j] * (a[:, None] - a[None, :]) / N)
+    return (D / N).real

@@ -1,0 +1,93 @@
+"""Pins of the oracle's spatial-derivative scheme (Sec. 2.3, Eq. (3)) against mathematics
+that does not go through the oracle's own formula."""
+import numpy as np
+import pytest
+import sympy
+
+from oracle.wfft import C_KEFF, keff, deriv_multiplier, spectral_deriv, dft_deriv_matrix, dft_indices
+
+
+def test_keff_coefficients_are_arcsin_series():
+    # Eq. (3): the eight printed fractions are the Maclaurin coefficients of arcsin.
+    x = sympy.symbols("x")
+    ser = sympy.series(sympy.asin(x), x, 0, 17).removeO()
+    for n, c in enumerate(C_KEFF):
+        exact = ser.coeff(x, 2 * n + 1)
+        assert c == pytest.approx(float(exact), rel=0, abs=1e-17)
+
+
+def test_keff_is_sixteenth_order():
+    # k - k_eff ~ c_8 phi^17: the log-log slope of the error between two moderate phi is ~17.
+    N, dx = 4096, 1.0
+    m = np.array([N * np.arcsin(0.5) / np.pi, N * np.arcsin(0.4) / np.pi])  # phi = 0.5, 0.4
+    k = 2.0 * np.pi * m / (N * dx)
+    err = k - keff(m, N, dx)
+    assert np.all(err > 0)
+    slope = np.log(err[0] / err[1]) / np.log(0.5 / 0.4)
+    assert 17.0 <= slope <= 18.5
+    # at phi = 1 the truncated series sums to 1.37..., i.e. k_eff/k = 0.8724 at Nyquist
+    assert keff(N // 2, N, dx) / (np.pi / dx) == pytest.approx(0.8724, abs=5e-5)
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 64), (64, 32), (32, 128)])
+def test_low_mode_derivatives_match_calculus(nx, ny):
+    # smooth band-limited field: the spectral derivative equals the analytic one, since
+    # k_eff(k) = k to machine precision for modes m <= 2 when N >= 32 (c_8 phi^16 < 1e-15).
+    dx, dy = 0.013, 0.021
+    x = np.arange(nx)[None, :] * dx
+    y = np.arange(ny)[:, None] * dy
+    Lx, Ly = nx * dx, ny * dy
+    a, b = 2 * np.pi / Lx, 2 * np.pi / Ly
+    h = 1.3 + np.sin(a * x) * np.cos(2 * b * y) + 0.4 * np.cos(2 * a * x + 0.3)
+    hx = a * np.cos(a * x) * np.cos(2 * b * y) - 0.8 * a * np.sin(2 * a * x + 0.3)
+    hy = -2 * b * np.sin(a * x) * np.sin(2 * b * y)
+    hxx = -a * a * np.sin(a * x) * np.cos(2 * b * y) - 1.6 * a * a * np.cos(2 * a * x + 0.3)
+    hxy = -2 * a * b * np.cos(a * x) * np.sin(2 * b * y)
+    hyy = -4 * b * b * np.sin(a * x) * np.cos(2 * b * y)
+    for (ox, oy), ref in {(1, 0): hx, (0, 1): hy, (2, 0): hxx, (1, 1): hxy, (0, 2): hyy}.items():
+        got = spectral_deriv(h, ox, oy, dx, dy)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_high_mode_eigenvalue_and_nyquist():
+    # derivative of a pure mode is k_eff(m) times the quadrature mode; Nyquist mode -> 0
+    N, dx = 32, 0.1
+    x = np.arange(N)
+    for m in (5, 11, 15):
+        h = np.sin(2 * np.pi * m * x / N)[None, :].repeat(2, axis=0)
+        got = spectral_deriv(h, 1, 0, dx, 1.0)
+        phi = np.sin(np.pi * m / N)
+        # eigenvalue bracketed by the truncation of the arcsin series (all terms positive)
+        ke = got[0] / np.cos(2 * np.pi * m * x / N)
+        ke = ke[np.abs(np.cos(2 * np.pi * m * x / N)) > 0.5]
+        assert np.ptp(ke) < 1e-10 * abs(ke[0])
+        assert (2 / dx) * phi <= ke[0] <= (2 / dx) * np.arcsin(phi)
+    nyq = np.cos(np.pi * x)[None, :].repeat(2, axis=0)
+    assert np.max(np.abs(spectral_deriv(nyq, 1, 0, dx, 1.0))) < 1e-12
+    assert np.max(np.abs(spectral_deriv(np.full((4, N), 3.0), 1, 0, dx, 1.0))) < 1e-12
+
+
+def test_multiplier_is_odd_and_purely_imaginary():
+    for N in (2, 4, 8, 64, 128):
+        d = deriv_multiplier(N, 0.5)
+        m = dft_indices(N)
+        assert np.all(d.real == 0)
+        for j in range(N):
+            jj = np.where(m == -m[j])[0]
+            if len(jj):
+                assert abs(d[jj[0]] + d[j]) <= 1e-15 * abs(d[j]) or (m[j] == -N // 2 and d[j] == 0)
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 8), (16, 4), (4, 32), (2, 8)])
+def test_fft_derivative_matches_brute_force_dft(nx, ny):
+    rng = np.random.default_rng(7)
+    h = rng.standard_normal((ny, nx))
+    dx, dy = 0.3, 0.7
+    for ox, oy in [(1, 0), (0, 1), (2, 0), (0, 2), (1, 1)]:
+        ref = h
+        if ox:
+            ref = ref @ dft_deriv_matrix(nx, dx, ox).T
+        if oy:
+            ref = dft_deriv_matrix(ny, dy, oy) @ ref
+        got = spectral_deriv(h, ox, oy, dx, dy)
+        assert np.allclose(got, ref, rtol=0, atol=1e-11 * max(1.0, np.abs(ref).max()))
