@@ -1,0 +1,140 @@
+/*
+ * lbm_d2v16.h -- C ABI of the GB300 (sm_103a) library for the D2V16-FFT-TLB thermal
+ * liquid-vapour lattice Boltzmann kinetic model of Gan, Xu, Zhang, Wang, Yu and Yang
+ * ("Lattice Boltzmann kinetic modeling and simulation of thermal liquid-vapor system").
+ *
+ * The library advances the 16 discrete distributions f_i of the Kataoka-Tsutahara
+ * D2V16 velocity model on a doubly periodic nx x ny grid by the two-stage Runge-Kutta
+ * scheme of Sec. 2.3 applied to Eq. (1), with the forcing term I_i of Eq. (2) and
+ * spatial derivatives by FFT with the 16th-order modified wavenumber of Eq. (3).
+ * All device memory of a simulation is owned by its handle; every host buffer
+ * passed in or out is owned by the caller.
+ *
+ * Layouts. A scalar field is row-major [ny][nx] (x fastest), float64. The 16 distributions
+ * are [16][ny][nx]. Velocity i (0-based) is: 0..3 -> (1,0),(0,1),(-1,0),(0,-1);
+ * 4..7 -> 6x the same; 8..11 -> (s,s),(-s,s),(-s,-s),(s,-s) with s = sqrt2;
+ * 12..15 -> the same with s = 3/sqrt2. eta_i = eta0 on 0..3 and 0 elsewhere (Sec. 2.1).
+ *
+ * Errors. Every int-returning call returns LBM_OK (0) or a negative LBM_ERR_* code;
+ * lbm_strerror() gives a message, lbm_last_error() a detailed one for the calling thread.
+ * A call that fails leaves the handle usable unless it returns LBM_ERR_CUDA, after which
+ * the CUDA context may be unusable (sticky errors).
+ *
+ * Streams. All device work of a handle is issued on the stream given to lbm_create
+ * (NULL = the legacy default stream). Calls with host buffers synchronise that stream;
+ * calls with device buffers are asynchronous on it.
+ */
+#ifndef LBM_D2V16_H
+#define LBM_D2V16_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)       /* invalid argument (sizes, params, NULL pointers) */
+#define LBM_ERR_NOMEM (-2)     /* device allocation failed */
+#define LBM_ERR_CUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define LBM_ERR_NONFINITE (-4) /* a NaN or Inf was found in the state */
+#define LBM_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define LBM_ERR_STATE (-6)     /* call out of order (e.g. lbm_step before lbm_init) */
+#define LBM_ERR_UNSUPPORTED (-7) /* size or precision not supported by this build */
+
+/* precision of the hot path */
+#define LBM_FP64 0   /* every step in float64 (the plain method) */
+#define LBM_MIXED 1  /* f-field storage, its FFTs and the update in float32; see DESIGN notes */
+
+/* test hooks: switch terms of Eq. (1) off */
+#define LBM_FLAG_NO_ADVECTION 1 /* drop v_i . grad f_i */
+#define LBM_FLAG_NO_COLLISION 2 /* drop -(f_i - f_i^eq)/tau */
+#define LBM_FLAG_NO_FORCE 4     /* drop I_i (and skip the macroscopic derivative chain) */
+
+typedef struct lbm_params {
+    double tau;   /* relaxation time (Eq. (1)) */
+    double dt;    /* time step of the Runge-Kutta scheme (Sec. 2.3) */
+    double dx;    /* grid spacing along x (Eq. (3)) */
+    double dy;    /* grid spacing along y */
+    double K;     /* surface-tension coefficient (Lambda, C) */
+    double H;     /* M = K + H T (Sec. 2.2) */
+    double q;     /* heat-flux coefficient of C_q */
+    double zeta;  /* bulk viscosity in B and C */
+    double b;     /* total degrees of freedom (Sec. 2.1) */
+    double eta0;  /* extra-degree-of-freedom parameter of velocities 0..3 (Sec. 2.1: 2.5) */
+    int precision; /* LBM_FP64 or LBM_MIXED */
+    int flags;     /* LBM_FLAG_* bits, 0 for the full model */
+} lbm_params;
+
+typedef struct lbm_ctx *lbm_handle;
+
+/* Fills *p with the phase-separation set of Sec. 3.2 (tau = dt = 1e-4, dx = dy = 1/256,
+ * K = 5e-6, H = 0, zeta = 0) with q = -0.004 and b = 2 (Sec. 3.1), eta0 = 2.5, FP64. */
+void lbm_default_params(lbm_params *p);
+
+/* Creates a simulation on the current CUDA device. nx, ny: powers of two, 2 <= n <= 4096
+ * (LBM_ERR_ARG otherwise; LBM_ERR_UNSUPPORTED when the row kernels' shared memory cannot
+ * hold a row, e.g. nx = 4096 in LBM_FP64). params is copied. stream: a cudaStream_t or NULL.
+ * On success *out owns all device memory of the simulation. */
+int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handle *out);
+
+/* Sets f_i := f_i^eq(rho, u, T) at every node (the initial state of Sec. 3's runs) and
+ * resets the step counter. Host buffers, [ny][nx] float64 each; T > 0 and 0 < rho < 3. */
+int lbm_init(lbm_handle h, const double *rho, const double *ux, const double *uy, const double *T);
+
+/* Same as lbm_init with device buffers (asynchronous on the handle's stream). */
+int lbm_init_device(lbm_handle h, const double *rho, const double *ux, const double *uy,
+                    const double *T);
+
+/* Advances n >= 0 full Runge-Kutta steps (Sec. 2.3), asynchronously on the stream. */
+int lbm_step(lbm_handle h, int n);
+
+/* Moments rho, u_x, u_y, T of the current f (Sec. 2.1) into host buffers [ny][nx].
+ * Synchronises the stream. Any pointer may be NULL to skip that field. */
+int lbm_moments(lbm_handle h, double *rho, double *ux, double *uy, double *T);
+
+/* Same into device buffers (asynchronous). */
+int lbm_moments_device(lbm_handle h, double *rho, double *ux, double *uy, double *T);
+
+/* Copies the 16 distributions to / from host memory, [16][ny][nx] float64. lbm_set_f
+ * replaces the state (LBM_MIXED rounds to float32) and resets nothing else. */
+int lbm_get_f(lbm_handle h, double *f16);
+int lbm_set_f(lbm_handle h, const double *f16);
+
+/* Global diagnostics (host out[6]): total mass, x and y momentum, total energy
+ * sum(e_T) dx dy with e_T = rho T - 9 rho^2/8 + K |grad rho|^2 / 2 + rho u^2 / 2 (Sec. 2.2),
+ * max |u|, and the number of steps taken. Synchronises the stream. */
+int lbm_diagnostics(lbm_handle h, double out[6]);
+
+/* Waits for all work of the handle; returns LBM_ERR_CUDA if a kernel failed. */
+int lbm_synchronize(lbm_handle h);
+
+/* Frees all device memory of the handle (synchronises first). NULL is ignored. */
+void lbm_destroy(lbm_handle h);
+
+/* Static message of an error code; lbm_last_error(): last detailed message of this thread. */
+const char *lbm_strerror(int code);
+const char *lbm_last_error(void);
+
+/* Maxwell construction of the van der Waals fluid P = 3 rho T/(3 - rho) - 9 rho^2/8
+ * (Sec. 3.1): coexisting liquid and vapour densities at 0 < T < 1 (host only). */
+int lbm_maxwell(double T, double *rho_l, double *rho_v);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around every launch
+ * while enabled. lbm_timing_read returns, for kernel class k (LBM_K_*), the summed device
+ * time in ms and the launch count since the last lbm_timing(h, 1). Reading synchronises. */
+#define LBM_K_COL 0    /* column-pass derivative kernels (f and macroscopic fields) */
+#define LBM_K_MACRO 1  /* row pass of the macroscopic chain (fluxes, x-derivatives) */
+#define LBM_K_FLUX 2   /* column pass of the flux divergences */
+#define LBM_K_UPDATE 3 /* fused row pass: x-derivatives of f, f^eq, I_i, BGK, RK stage, moments */
+#define LBM_K_COUNT 4
+int lbm_timing(lbm_handle h, int enable);
+int lbm_timing_read(lbm_handle h, int kernel, double *ms, long long *launches);
+
+/* Device bytes held by the handle. */
+size_t lbm_device_bytes(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_D2V16_H */

@@ -1,0 +1,205 @@
+"""Python binding of the D2V16-FFT-TLB CUDA library (C ABI in include/lbm_d2v16.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+The shared library is built in-tree by `paper_1403_3746_gb300.build.build()`; importing
+this module does not build it, and every call fails loudly if it is missing.
+
+Host arrays are numpy float64 (C-contiguous, shape (ny, nx) for fields and (16, ny, nx)
+for the distributions). Device arrays are torch CUDA float64 tensors of the same shapes.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as LIB_PATH
+
+LBM_OK = 0
+LBM_FP64 = 0
+LBM_MIXED = 1
+LBM_FLAG_NO_ADVECTION = 1
+LBM_FLAG_NO_COLLISION = 2
+LBM_FLAG_NO_FORCE = 4
+KERNELS = {"col": 0, "macro": 1, "flux": 2, "update": 3}
+
+_lib = None
+
+
+class LbmError(RuntimeError):
+    pass
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("K", ctypes.c_double), ("H", ctypes.c_double),
+                ("q", ctypes.c_double), ("zeta", ctypes.c_double), ("b", ctypes.c_double),
+                ("eta0", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "lbm_default_params": (None, [ctypes.POINTER(lbm_params)]),
+    "lbm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(lbm_params), _P,
+                                  ctypes.POINTER(_P)]),
+    "lbm_init": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "lbm_init_device": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "lbm_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lbm_moments": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "lbm_moments_device": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "lbm_get_f": (ctypes.c_int, [_P, _P]),
+    "lbm_set_f": (ctypes.c_int, [_P, _P]),
+    "lbm_diagnostics": (ctypes.c_int, [_P, _D]),
+    "lbm_synchronize": (ctypes.c_int, [_P]),
+    "lbm_destroy": (None, [_P]),
+    "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_maxwell": (ctypes.c_int, [ctypes.c_double, _D, _D]),
+    "lbm_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lbm_timing_read": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm_device_bytes": (ctypes.c_size_t, [_P]),
+}
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LbmError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_1403_3746_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != LBM_OK:
+        L = lib()
+        raise LbmError(f"{L.lbm_strerror(rc).decode()} ({rc}): {L.lbm_last_error().decode()}")
+
+
+def default_params(**kw):
+    """lbm_params with the library defaults (phase-separation set), overridden by kw."""
+    p = lbm_params()
+    lib().lbm_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def maxwell(T):
+    """Coexisting (rho_liquid, rho_vapour) of the van der Waals fluid at temperature T."""
+    rl, rv = ctypes.c_double(), ctypes.c_double()
+    _check(lib().lbm_maxwell(float(T), ctypes.byref(rl), ctypes.byref(rv)))
+    return rl.value, rv.value
+
+
+def _host(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t, shape):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("device arrays must be contiguous float64 CUDA tensors")
+    if tuple(t.shape) != shape:
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Simulation:
+    """One D2V16 simulation on an nx x ny periodic grid (lbm_create .. lbm_destroy)."""
+
+    def __init__(self, nx, ny, params=None, stream=None):
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = params if params is not None else default_params()
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream) if isinstance(stream, int) else (stream or ctypes.c_void_p())
+        _check(lib().lbm_create(self.nx, self.ny, ctypes.byref(self.params), s, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+    def init(self, rho, ux, uy, T):
+        """f := f^eq(rho, u, T); host numpy arrays or CUDA float64 tensors of shape (ny, nx)."""
+        if type(rho).__module__.startswith("torch"):
+            ps = [_dev_ptr(a, self.shape) for a in (rho, ux, uy, T)]
+            _check(lib().lbm_init_device(self._h, *ps))
+        else:
+            arrs = [_host(a, self.shape) for a in (rho, ux, uy, T)]
+            _check(lib().lbm_init(self._h, *[_ptr(a) for a in arrs]))
+
+    def step(self, n=1):
+        _check(lib().lbm_step(self._h, int(n)))
+
+    def synchronize(self):
+        _check(lib().lbm_synchronize(self._h))
+
+    def moments(self):
+        """(rho, u_x, u_y, T) as host numpy arrays."""
+        out = [np.empty(self.shape) for _ in range(4)]
+        _check(lib().lbm_moments(self._h, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def moments_device(self, rho, ux, uy, T):
+        ps = [_dev_ptr(a, self.shape) if a is not None else ctypes.c_void_p() for a in (rho, ux, uy, T)]
+        _check(lib().lbm_moments_device(self._h, *ps))
+
+    def get_f(self):
+        f = np.empty((16,) + self.shape)
+        _check(lib().lbm_get_f(self._h, _ptr(f)))
+        return f
+
+    def set_f(self, f):
+        f = _host(f, (16,) + self.shape)
+        _check(lib().lbm_set_f(self._h, _ptr(f)))
+
+    def diagnostics(self):
+        """dict(mass, px, py, energy, umax, steps)."""
+        out = (ctypes.c_double * 6)()
+        _check(lib().lbm_diagnostics(self._h, out))
+        return dict(zip(("mass", "px", "py", "energy", "umax", "steps"), list(out)))
+
+    def timing(self, enable=True):
+        _check(lib().lbm_timing(self._h, 1 if enable else 0))
+
+    def timing_read(self, kernel):
+        ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+        _check(lib().lbm_timing_read(self._h, KERNELS.get(kernel, kernel), ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
+    def device_bytes(self):
+        return int(lib().lbm_device_bytes(self._h))

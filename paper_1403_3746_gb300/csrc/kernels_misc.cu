@@ -1,0 +1,208 @@
+// Setup, readout and diagnostic kernels (not on the per-step hot path).
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// f_i := f_i^eq(rho, u, T) at every node (the initial state of Sec. 3's runs), then the
+// moments of the stored f (so that the first stage uses the moments of f itself).
+template <typename F>
+__global__ void init_feq_kernel(const __grid_constant__ InitArgs a) {
+    F *f = reinterpret_cast<F *>(a.f);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.n;
+         g += (long long)gridDim.x * blockDim.x) {
+        const double rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
+        const double u2 = ux * ux + uy * uy, b = a.b;
+        const double e = (b + 2.0) * T + u2, gq = (b + 4.0) * T + u2;
+        const double m[16] = {rho,
+                              rho * ux,
+                              rho * uy,
+                              rho * (b * T + u2),
+                              rho * (T + ux * ux),
+                              rho * ux * uy,
+                              rho * (T + uy * uy),
+                              rho * ux * e,
+                              rho * uy * e,
+                              rho * ux * (3.0 * T + ux * ux),
+                              rho * uy * (T + ux * ux),
+                              rho * ux * (T + uy * uy),
+                              rho * uy * (3.0 * T + uy * uy),
+                              rho * (T * e + gq * ux * ux),
+                              rho * gq * ux * uy,
+                              rho * (T * e + gq * uy * uy)};
+        double mr = 0, mjx = 0, mjy = 0, mE = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            double fe = 0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * m[j];
+            const F fs = (F)fe;
+            f[i * a.n + g] = fs;
+            const double fd = (double)fs;
+            mr += fd;
+            mjx += vel_x(i) * fd;
+            mjy += vel_y(i) * fd;
+            mE += a.psi[i] * fd;
+        }
+        const double ir = 1.0 / mr, nux = mjx * ir, nuy = mjy * ir;
+        a.mrho[g] = mr;
+        a.mux[g] = nux;
+        a.muy[g] = nuy;
+        a.mT[g] = (mE * ir - (nux * nux + nuy * nuy)) / b;
+    }
+}
+
+// Sec. 2.1 moments of a stored f.
+template <typename F>
+__global__ void moments_kernel(const __grid_constant__ MomArgs a) {
+    const F *f = reinterpret_cast<const F *>(a.f);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.n;
+         g += (long long)gridDim.x * blockDim.x) {
+        double mr = 0, mjx = 0, mjy = 0, mE = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const double fd = (double)f[i * a.n + g];
+            mr += fd;
+            mjx += vel_x(i) * fd;
+            mjy += vel_y(i) * fd;
+            mE += a.psi[i] * fd;
+        }
+        const double ir = 1.0 / mr, nux = mjx * ir, nuy = mjy * ir;
+        if (a.rho) a.rho[g] = mr;
+        if (a.ux) a.ux[g] = nux;
+        if (a.uy) a.uy[g] = nuy;
+        if (a.T) a.T[g] = (mE * ir - (nux * nux + nuy * nuy)) / a.b;
+    }
+}
+
+// Per-block partial sums of mass, x/y momentum, e_T (Sec. 2.2) and the max of |u|^2.
+__global__ void __launch_bounds__(256) diag_kernel(const __grid_constant__ DiagArgs a) {
+    __shared__ double red[5][256];
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, mx = 0;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.n;
+         g += (long long)gridDim.x * blockDim.x) {
+        const double rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
+        const double rx = a.rx[g], ry = a.ry[g];
+        const double u2 = ux * ux + uy * uy;
+        s0 += rho;
+        s1 += rho * ux;
+        s2 += rho * uy;
+        s3 += rho * T - 1.125 * rho * rho + 0.5 * a.K * (rx * rx + ry * ry) + 0.5 * rho * u2;
+        mx = fmax(mx, u2);
+    }
+    const int t = threadIdx.x;
+    red[0][t] = s0; red[1][t] = s1; red[2][t] = s2; red[3][t] = s3; red[4][t] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            red[0][t] += red[0][t + w];
+            red[1][t] += red[1][t + w];
+            red[2][t] += red[2][t + w];
+            red[3][t] += red[3][t + w];
+            red[4][t] = fmax(red[4][t], red[4][t + w]);
+        }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int k = 0; k < 5; ++k) a.partial[blockIdx.x * 5 + k] = red[k][0];
+}
+
+// tw[k] = exp(-2 pi i k / n), evaluated in float64 with sincospi (exact argument scaling),
+// rounded once for the float32 table.
+__global__ void twiddle_kernel(double2 *tw64, float2 *tw32, int n) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)k / (double)n, &s, &c);
+        tw64[k] = make_double2(c, s);
+        tw32[k] = make_float2((float)c, (float)s);
+    }
+}
+
+template <typename F>
+__global__ void convert_out_kernel(const F *f, double *out, long long n) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
+         g += (long long)gridDim.x * blockDim.x)
+        out[g] = (double)f[g];
+}
+template <typename F>
+__global__ void convert_in_kernel(const double *in, F *f, long long n) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
+         g += (long long)gridDim.x * blockDim.x)
+        f[g] = (F)in[g];
+}
+
+// Generic spectral x-derivative of up to 4 fields (paired into complex lines).
+template <typename R>
+__global__ void __launch_bounds__(256) row_deriv_kernel(const __grid_constant__ RowDerivArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *s = reinterpret_cast<R *>(smem_raw);
+    const int nx = a.nx, Rw = a.rows, log2n = a.ax.log2n, L2 = 2 * nx;
+    const int nodes = Rw * nx, nl = (a.nin + 1) / 2;
+    const size_t g0 = (size_t)blockIdx.x * nodes;
+    for (int idx = threadIdx.x; idx < 2 * nl * nodes; idx += blockDim.x) {
+        const int k = idx / nodes, rem = idx - k * nodes;
+        const int r = rem >> log2n, x = rem & (nx - 1);
+        s[((k >> 1) * Rw + r) * L2 + (k & 1) * nx + x] = k < a.nin ? a.in[k][g0 + rem] : R(0);
+    }
+    __syncthreads();
+    const LineSet<R> X{s, nl * Rw, L2, 1, nx};
+    fft_forward<R, false>(X, log2n, a.ax.tw);
+    spec_mul<R, false>(X, X, log2n, 1, R(1), a.ax.k1, a.ax.k2);
+    __syncthreads();
+    fft_inverse<R, false>(X, log2n, a.ax.tw);
+    for (int idx = threadIdx.x; idx < a.nin * nodes; idx += blockDim.x) {
+        const int k = idx / nodes, rem = idx - k * nodes;
+        const int r = rem >> log2n, x = rem & (nx - 1);
+        a.out[k][g0 + rem] = s[((k >> 1) * Rw + r) * L2 + (k & 1) * nx + x];
+    }
+}
+
+static inline int grid_for(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+template <typename F> cudaError_t launch_init(const InitArgs &a, cudaStream_t s) {
+    init_feq_kernel<F><<<grid_for(a.n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename F> cudaError_t launch_moments(const MomArgs &a, cudaStream_t s) {
+    moments_kernel<F><<<grid_for(a.n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_diag(const DiagArgs &a, int blocks, cudaStream_t s) {
+    diag_kernel<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_twiddles(double2 *tw64, float2 *tw32, int n, cudaStream_t s) {
+    twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw64, tw32, n);
+    return cudaGetLastError();
+}
+template <typename F> cudaError_t launch_convert_out(const F *f, double *out, long long n, cudaStream_t s) {
+    convert_out_kernel<F><<<grid_for(n), 256, 0, s>>>(f, out, n);
+    return cudaGetLastError();
+}
+template <typename F> cudaError_t launch_convert_in(const double *in, F *f, long long n, cudaStream_t s) {
+    convert_in_kernel<F><<<grid_for(n), 256, 0, s>>>(in, f, n);
+    return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_row_deriv(const RowDerivArgs<R> &a, int threads, size_t smem, cudaStream_t s) {
+    cudaError_t e =
+        cudaFuncSetAttribute(row_deriv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    row_deriv_kernel<R><<<a.ny / a.rows, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_init<double>(const InitArgs &, cudaStream_t);
+template cudaError_t launch_init<float>(const InitArgs &, cudaStream_t);
+template cudaError_t launch_moments<double>(const MomArgs &, cudaStream_t);
+template cudaError_t launch_moments<float>(const MomArgs &, cudaStream_t);
+template cudaError_t launch_convert_out<double>(const double *, double *, long long, cudaStream_t);
+template cudaError_t launch_convert_out<float>(const float *, double *, long long, cudaStream_t);
+template cudaError_t launch_convert_in<double>(const double *, double *, long long, cudaStream_t);
+template cudaError_t launch_convert_in<float>(const double *, float *, long long, cudaStream_t);
+template cudaError_t launch_row_deriv<double>(const RowDerivArgs<double> &, int, size_t, cudaStream_t);
+template cudaError_t launch_row_deriv<float>(const RowDerivArgs<float> &, int, size_t, cudaStream_t);
+
+}  // namespace lbm

@@ -1,0 +1,695 @@
+// C ABI of the D2V16-FFT-TLB library: simulation contexts, host-side tables and the
+// orchestration of the four kernel passes of each Runge-Kutta stage (Sec. 2.3).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU_TRY(expr)                                                                                   \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess) return fail(LBM_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));      \
+    } while (0)
+
+bool is_pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
+int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+// Position p of a digit-reversed spectrum (radix-4 DIF stages, then one radix-2 stage when
+// log2 N is odd) holds DFT index freq(p).
+int freq_of(int p, int l2) {
+    if (l2 == 0) return 0;
+    if (l2 == 1) return p;
+    const int S = 1 << (l2 - 2);
+    return (p >> (l2 - 2)) + 4 * freq_of(p & (S - 1), l2 - 2);
+}
+
+// Eq. (3): k_eff = (2/d) sum_{n=0}^{7} c_n phi^(2n+1), phi = sin(pi m / N).
+double keff(int m, int N, double d) {
+    static const double c[8] = {1.0, 1.0 / 6.0, 3.0 / 40.0, 5.0 / 112.0, 35.0 / 1152.0,
+                                63.0 / 2816.0, 231.0 / 13312.0, 143.0 / 10240.0};
+    const double phi = std::sin(M_PI * (double)m / (double)N);
+    double s = 0.0, pw = phi;
+    for (int n = 0; n < 8; ++n) {
+        s += c[n] * pw;
+        pw *= phi * phi;
+    }
+    return 2.0 / d * s;
+}
+
+// Inverse of the 16x16 matrix whose rows are the moment functionals
+// 1; v_x, v_y; psi; v_x v_x, v_x v_y, v_y v_y; psi v_x, psi v_y; v_x^3, v_x^2 v_y, v_x v_y^2, v_y^3;
+// psi v_x^2, psi v_x v_y, psi v_y^2 (psi = v^2 + eta^2) evaluated on the 16 velocities.
+bool moment_inverse(double eta0, double out[256]) {
+    double a[16][32];
+    for (int i = 0; i < 16; ++i) {
+        const double vx = vel_x(i), vy = vel_y(i);
+        const double psi = vel_sq(i) + (i < 4 ? eta0 * eta0 : 0.0);
+        const double row[16] = {1.0,         vx,          vy,          psi,         vx * vx,     vx * vy,
+                                vy * vy,     psi * vx,    psi * vy,    vx * vx * vx, vx * vx * vy, vx * vy * vy,
+                                vy * vy * vy, psi * vx * vx, psi * vx * vy, psi * vy * vy};
+        for (int r = 0; r < 16; ++r) a[r][i] = row[r];
+    }
+    for (int r = 0; r < 16; ++r)
+        for (int j = 0; j < 16; ++j) a[r][16 + j] = (r == j) ? 1.0 : 0.0;
+    for (int col = 0; col < 16; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 16; ++r)
+            if (std::fabs(a[r][col]) > std::fabs(a[piv][col])) piv = r;
+        if (std::fabs(a[piv][col]) < 1e-12) return false;
+        if (piv != col)
+            for (int j = 0; j < 32; ++j) std::swap(a[piv][j], a[col][j]);
+        const double inv = 1.0 / a[col][col];
+        for (int j = 0; j < 32; ++j) a[col][j] *= inv;
+        for (int r = 0; r < 16; ++r)
+            if (r != col && a[r][col] != 0.0) {
+                const double f = a[r][col];
+                for (int j = 0; j < 32; ++j) a[r][j] -= f * a[col][j];
+            }
+    }
+    for (int r = 0; r < 16; ++r)
+        for (int j = 0; j < 16; ++j) out[r * 16 + j] = a[r][16 + j];
+    return true;
+}
+
+int col_width(int nx, int ny, size_t esize, int tiles) {
+    int W = (int)(128 / esize);
+    if (W > nx) W = nx;
+    while (W > 2 && (size_t)ny * W * esize * tiles > 112 * 1024) W >>= 1;
+    return W;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, lx = 0, ly = 0;
+    long long n = 0;  // nodes
+    lbm_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool mixed = false;
+    size_t fsize = 8;
+
+    char *slab = nullptr;
+    size_t slab_bytes = 0;
+    void *f0 = nullptr, *f1 = nullptr, *Ay = nullptr;
+    double *rho = nullptr, *ux = nullptr, *uy = nullptr, *T = nullptr;
+    double *ry = nullptr, *ryy = nullptr, *uxy = nullptr, *uyy = nullptr, *Ty = nullptr;
+    double *Qy = nullptr, *Sxy = nullptr, *Syy = nullptr, *divu = nullptr;
+    double *dQx = nullptr, *dSxx = nullptr, *dSxy = nullptr, *Cnum = nullptr;
+    double *dQy = nullptr, *dSxyy = nullptr, *dSyy = nullptr, *ddivuy = nullptr;
+    double *partial = nullptr;
+    int diag_blocks = 0;
+    // per-axis tables
+    double2 *tw64x = nullptr, *tw64y = nullptr;
+    float2 *tw32x = nullptr, *tw32y = nullptr;
+    double *k1x = nullptr, *k2x = nullptr, *k1y = nullptr, *k2y = nullptr;
+    float *k1x32 = nullptr, *k2x32 = nullptr, *k1y32 = nullptr, *k2y32 = nullptr;
+    double minv[256];
+
+    // launch geometry
+    int colW_f = 2, colW_m = 2;
+    size_t col_smem_f = 0, col_smem_m = 0;
+    int rows = 1;
+    size_t macro_smem = 0, upd_smem = 0, rowd_smem = 0;
+
+    bool initialized = false;
+    long long steps = 0;
+
+    // per-launch timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_cls;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+struct LaunchTimer {
+    lbm_ctx *c;
+    size_t slot = (size_t)-1;
+    LaunchTimer(lbm_ctx *cc, int cls) : c(cc) {
+        if (!c->timing) return;
+        if (c->ev_used + 2 > c->ev.size()) {
+            if (c->ev.size() >= (1u << 20)) return;
+            for (int k = 0; k < 256; ++k) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+                c->ev.push_back(e);
+                c->ev_cls.push_back(0);
+            }
+        }
+        slot = c->ev_used;
+        c->ev_used += 2;
+        c->ev_cls[slot] = cls;
+        cudaEventRecord(c->ev[slot], c->stream);
+    }
+    ~LaunchTimer() {
+        if (slot != (size_t)-1) cudaEventRecord(c->ev[slot + 1], c->stream);
+    }
+};
+
+template <typename R> Axis<R> axis(const lbm_ctx *c, bool xdir);
+template <> Axis<double> axis<double>(const lbm_ctx *c, bool xdir) {
+    return xdir ? Axis<double>{c->tw64x, c->k1x, c->k2x, c->lx} : Axis<double>{c->tw64y, c->k1y, c->k2y, c->ly};
+}
+template <> Axis<float> axis<float>(const lbm_ctx *c, bool xdir) {
+    return xdir ? Axis<float>{c->tw32x, c->k1x32, c->k2x32, c->lx}
+                : Axis<float>{c->tw32y, c->k1y32, c->k2y32, c->ly};
+}
+
+// one Runge-Kutta stage: K_COL, K_MACRO, K_FLUX, K_UPDATE
+template <typename F>
+int run_stage(lbm_ctx *c, int stage) {
+    const lbm_params &p = c->p;
+    const bool adv = !(p.flags & LBM_FLAG_NO_ADVECTION);
+    const bool frc = !(p.flags & LBM_FLAG_NO_FORCE);
+    const size_t plane = (size_t)c->n;
+    F *f0 = static_cast<F *>(c->f0), *f1 = static_cast<F *>(c->f1);
+    F *Ay = static_cast<F *>(c->Ay);
+    const F *fs = stage == 0 ? f0 : f1;
+
+    if (adv) {
+        ColArgs<F> a{};
+        a.nx = c->nx;
+        a.ny = c->ny;
+        a.W = c->colW_f;
+        a.log2W = ilog2(c->colW_f);
+        a.ay = axis<F>(c, false);
+        for (int k = 0; k < 12; ++k) {
+            const int i = yfield(k);
+            a.jobs[k] = ColJob<F>{fs + i * plane, Ay + k * plane, nullptr, 1, 1, (F)vel_y(i), F(0)};
+        }
+        LaunchTimer t(c, LBM_K_COL);
+        CU_TRY(launch_col<F>(a, 12, 256, c->col_smem_f, c->stream));
+    }
+    if (frc) {
+        {
+            ColArgs<double> a{};
+            a.nx = c->nx;
+            a.ny = c->ny;
+            a.W = c->colW_m;
+            a.log2W = ilog2(c->colW_m);
+            a.ay = axis<double>(c, false);
+            a.jobs[0] = ColJob<double>{c->rho, c->ry, c->ryy, 1, 2, 1.0, 1.0};
+            a.jobs[1] = ColJob<double>{c->ux, c->uxy, nullptr, 1, 1, 1.0, 0.0};
+            a.jobs[2] = ColJob<double>{c->uy, c->uyy, nullptr, 1, 1, 1.0, 0.0};
+            a.jobs[3] = ColJob<double>{c->T, c->Ty, nullptr, 1, 1, 1.0, 0.0};
+            LaunchTimer t(c, LBM_K_COL);
+            CU_TRY(launch_col<double>(a, 4, 256, c->col_smem_m, c->stream));
+        }
+        {
+            MacroArgs<double> a{};
+            a.rho = c->rho; a.ux = c->ux; a.uy = c->uy; a.T = c->T;
+            a.ry = c->ry; a.ryy = c->ryy; a.uxy = c->uxy; a.uyy = c->uyy; a.Ty = c->Ty;
+            a.Qy = c->Qy; a.Sxy = c->Sxy; a.Syy = c->Syy; a.divu = c->divu;
+            a.dQx = c->dQx; a.dSxx = c->dSxx; a.dSxy = c->dSxy; a.Cnum = c->Cnum;
+            a.nx = c->nx; a.ny = c->ny; a.rows = c->rows;
+            a.ax = axis<double>(c, true);
+            a.K = p.K; a.H = p.H; a.q = p.q; a.zeta = p.zeta;
+            LaunchTimer t(c, LBM_K_MACRO);
+            CU_TRY(launch_macro<double>(a, 256, c->macro_smem, c->stream));
+        }
+        {
+            ColArgs<double> a{};
+            a.nx = c->nx;
+            a.ny = c->ny;
+            a.W = c->colW_m;
+            a.log2W = ilog2(c->colW_m);
+            a.ay = axis<double>(c, false);
+            a.jobs[0] = ColJob<double>{c->Qy, c->dQy, nullptr, 1, 1, 1.0, 0.0};
+            a.jobs[1] = ColJob<double>{c->Sxy, c->dSxyy, nullptr, 1, 1, 1.0, 0.0};
+            a.jobs[2] = ColJob<double>{c->Syy, c->dSyy, nullptr, 1, 1, 1.0, 0.0};
+            a.jobs[3] = ColJob<double>{c->divu, c->ddivuy, nullptr, 1, 1, 1.0, 0.0};
+            LaunchTimer t(c, LBM_K_FLUX);
+            CU_TRY(launch_col<double>(a, 4, 256, c->col_smem_m, c->stream));
+        }
+    }
+    {
+        UpdateArgs<F, double> a{};
+        a.fs = fs;
+        a.fbase = f0;
+        a.fout = stage == 0 ? f1 : f0;
+        a.Ay = Ay;
+        a.rho = c->rho; a.ux = c->ux; a.uy = c->uy; a.T = c->T;
+        a.ry = c->ry; a.dQx = c->dQx; a.dSxx = c->dSxx; a.dSxy = c->dSxy; a.Cnum = c->Cnum;
+        a.dQy = c->dQy; a.dSxyy = c->dSxyy; a.dSyy = c->dSyy; a.ddivuy = c->ddivuy;
+        a.nx = c->nx; a.ny = c->ny; a.rows = c->rows;
+        a.ax = axis<F>(c, true);
+        a.tau_inv = 1.0 / p.tau;
+        a.h = stage == 0 ? 0.5 * p.dt : p.dt;
+        a.K = p.K;
+        a.b = p.b;
+        a.eta2 = p.eta0 * p.eta0;
+        a.flags = p.flags;
+        for (int k = 0; k < 256; ++k) a.minv[k] = (F)c->minv[k];
+        LaunchTimer t(c, LBM_K_UPDATE);
+        CU_TRY((launch_update<F, double>(a, 256, c->upd_smem, c->stream)));
+    }
+    return LBM_OK;
+}
+
+int check_params(const lbm_params *p) {
+    if (!p) return fail(LBM_ERR_ARG, "params is NULL");
+    const double v[] = {p->tau, p->dt, p->dx, p->dy, p->K, p->H, p->q, p->zeta, p->b, p->eta0};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(LBM_ERR_ARG, "non-finite parameter");
+    if (p->tau <= 0 || p->dt <= 0 || p->dx <= 0 || p->dy <= 0 || p->b <= 0)
+        return fail(LBM_ERR_ARG, "tau, dt, dx, dy and b must be positive");
+    if (p->precision != LBM_FP64 && p->precision != LBM_MIXED)
+        return fail(LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_MIXED");
+    if (p->flags & ~(LBM_FLAG_NO_ADVECTION | LBM_FLAG_NO_COLLISION | LBM_FLAG_NO_FORCE))
+        return fail(LBM_ERR_ARG, "unknown flag bits");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->tau = 1e-4;
+    p->dt = 1e-4;
+    p->dx = 1.0 / 256.0;
+    p->dy = 1.0 / 256.0;
+    p->K = 5e-6;
+    p->H = 0.0;
+    p->q = -0.004;
+    p->zeta = 0.0;
+    p->b = 2.0;
+    p->eta0 = 2.5;
+    p->precision = LBM_FP64;
+    p->flags = 0;
+}
+
+const char *lbm_strerror(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_NOMEM: return "device allocation failed";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_NONFINITE: return "non-finite value in the state";
+        case LBM_ERR_TIMEOUT: return "device wait timed out";
+        case LBM_ERR_STATE: return "call out of order";
+        case LBM_ERR_UNSUPPORTED: return "unsupported size or precision";
+        default: return "unknown error";
+    }
+}
+
+const char *lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handle *out) {
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!is_pow2(nx) || !is_pow2(ny) || nx > 4096 || ny > 4096)
+        return fail(LBM_ERR_ARG, "nx=%d, ny=%d: each must be a power of two in [2, 4096]", nx, ny);
+    int rc = check_params(params);
+    if (rc) return rc;
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(LBM_ERR_NOMEM, "host allocation failed");
+    c->nx = nx;
+    c->ny = ny;
+    c->lx = ilog2(nx);
+    c->ly = ilog2(ny);
+    c->n = (long long)nx * ny;
+    c->p = *params;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->mixed = params->precision == LBM_MIXED;
+    c->fsize = c->mixed ? 4 : 8;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return fail(LBM_ERR_CUDA, "no CUDA device");
+    }
+    if (!moment_inverse(params->eta0, c->minv)) {
+        delete c;
+        return fail(LBM_ERR_ARG, "moment matrix is singular for eta0=%g", params->eta0);
+    }
+
+    // launch geometry
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    c->colW_f = col_width(nx, ny, c->fsize, 1);
+    c->colW_m = col_width(nx, ny, 8, 2);
+    c->col_smem_f = (size_t)ny * c->colW_f * c->fsize;
+    c->col_smem_m = (size_t)ny * c->colW_m * 8 * 2;
+    int rows = 512 / nx;
+    if (rows < 1) rows = 1;
+    if (rows > ny) rows = ny;
+    c->rows = rows;
+    c->upd_smem = (size_t)12 * rows * nx * c->fsize;
+    c->macro_smem = (size_t)10 * rows * nx * 8;
+    c->rowd_smem = (size_t)2 * rows * nx * 8;
+    const size_t need = std::max(std::max(c->upd_smem, c->macro_smem), std::max(c->col_smem_f, c->col_smem_m));
+    if (need > (size_t)smem_optin) {
+        delete c;
+        return fail(LBM_ERR_UNSUPPORTED, "nx=%d ny=%d needs %zu B of shared memory per block (device: %d)", nx,
+                    ny, need, smem_optin);
+    }
+
+    // device memory: one slab, 256-byte aligned pieces
+    const size_t plane_d = (size_t)c->n * 8, plane_f = (size_t)c->n * c->fsize;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    c->diag_blocks = (int)std::min<long long>(1024, (c->n + 255) / 256);
+    size_t off = 0;
+    std::vector<std::pair<void **, size_t>> parts;
+    parts.push_back({&c->f0, 16 * plane_f});
+    parts.push_back({&c->f1, 16 * plane_f});
+    parts.push_back({&c->Ay, 12 * plane_f});
+    double **macro[] = {&c->rho, &c->ux,   &c->uy,   &c->T,    &c->ry,   &c->ryy,  &c->uxy, &c->uyy,
+                        &c->Ty,  &c->Qy,   &c->Sxy,  &c->Syy,  &c->divu, &c->dQx,  &c->dSxx, &c->dSxy,
+                        &c->Cnum, &c->dQy, &c->dSxyy, &c->dSyy, &c->ddivuy};
+    for (double **m : macro) parts.push_back({reinterpret_cast<void **>(m), plane_d});
+    parts.push_back({reinterpret_cast<void **>(&c->partial), (size_t)c->diag_blocks * 5 * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->tw64x), (size_t)nx * 16});
+    parts.push_back({reinterpret_cast<void **>(&c->tw64y), (size_t)ny * 16});
+    parts.push_back({reinterpret_cast<void **>(&c->tw32x), (size_t)nx * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->tw32y), (size_t)ny * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->k1x), (size_t)nx * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->k2x), (size_t)nx * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->k1y), (size_t)ny * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->k2y), (size_t)ny * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->k1x32), (size_t)nx * 4});
+    parts.push_back({reinterpret_cast<void **>(&c->k2x32), (size_t)nx * 4});
+    parts.push_back({reinterpret_cast<void **>(&c->k1y32), (size_t)ny * 4});
+    parts.push_back({reinterpret_cast<void **>(&c->k2y32), (size_t)ny * 4});
+    for (auto &pp : parts) off += al(pp.second);
+    if (cudaMalloc(&c->slab, off) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(LBM_ERR_NOMEM, "cudaMalloc of %zu bytes failed", off);
+    }
+    c->slab_bytes = off;
+    off = 0;
+    for (auto &pp : parts) {
+        *pp.first = c->slab + off;
+        off += al(pp.second);
+    }
+
+    // tables: twiddles on the device (sincospi), multipliers on the host (Eq. (3))
+    cudaError_t e = launch_twiddles(c->tw64x, c->tw32x, nx, c->stream);
+    if (e == cudaSuccess) e = launch_twiddles(c->tw64y, c->tw32y, ny, c->stream);
+    for (int ax = 0; ax < 2 && e == cudaSuccess; ++ax) {
+        const int N = ax == 0 ? nx : ny, l2 = ax == 0 ? c->lx : c->ly;
+        const double d = ax == 0 ? params->dx : params->dy;
+        std::vector<double> k1(N), k2(N);
+        std::vector<float> k1f(N), k2f(N);
+        for (int pos = 0; pos < N; ++pos) {
+            const int k = freq_of(pos, l2);
+            const int m = k < N / 2 ? k : k - N;
+            const double ke = (2 * m == -N) ? 0.0 : keff(m, N, d);
+            k1[pos] = ke / N;
+            k2[pos] = -ke * ke / N;
+            k1f[pos] = (float)k1[pos];
+            k2f[pos] = (float)k2[pos];
+        }
+        double *dk1 = ax == 0 ? c->k1x : c->k1y, *dk2 = ax == 0 ? c->k2x : c->k2y;
+        float *fk1 = ax == 0 ? c->k1x32 : c->k1y32, *fk2 = ax == 0 ? c->k2x32 : c->k2y32;
+        e = cudaMemcpy(dk1, k1.data(), N * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dk2, k2.data(), N * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(fk1, k1f.data(), N * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(fk2, k2f.data(), N * 4, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(c->slab);
+        delete c;
+        return fail(LBM_ERR_CUDA, "table setup: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaFree(c->slab);
+    delete c;
+}
+
+static int init_common(lbm_ctx *c, const double *rho, const double *ux, const double *uy, const double *T) {
+    InitArgs a{};
+    a.rho = rho; a.ux = ux; a.uy = uy; a.T = T;
+    a.f = c->f0;
+    a.mrho = c->rho; a.mux = c->ux; a.muy = c->uy; a.mT = c->T;
+    a.n = c->n;
+    a.b = c->p.b;
+    for (int k = 0; k < 256; ++k) a.minv[k] = c->minv[k];
+    for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
+    CU_TRY(c->mixed ? launch_init<float>(a, c->stream) : launch_init<double>(a, c->stream));
+    c->initialized = true;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_handle c, const double *rho, const double *ux, const double *uy, const double *T) {
+    if (!c || !rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "NULL argument");
+    for (long long g = 0; g < c->n; ++g) {
+        if (!(rho[g] > 0.0 && rho[g] < 3.0) || !(T[g] > 0.0) || !std::isfinite(T[g]) || !std::isfinite(ux[g]) ||
+            !std::isfinite(uy[g]))
+            return fail(LBM_ERR_ARG, "node %lld: need 0 < rho < 3, T > 0 and finite u", g);
+    }
+    const size_t bytes = (size_t)c->n * 8;
+    // stage through the flux scratch fields (free between steps)
+    CU_TRY(cudaMemcpyAsync(c->Qy, rho, bytes, cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemcpyAsync(c->Sxy, ux, bytes, cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemcpyAsync(c->Syy, uy, bytes, cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemcpyAsync(c->divu, T, bytes, cudaMemcpyHostToDevice, c->stream));
+    int rc = init_common(c, c->Qy, c->Sxy, c->Syy, c->divu);
+    if (rc) return rc;
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_init_device(lbm_handle c, const double *rho, const double *ux, const double *uy, const double *T) {
+    if (!c || !rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "NULL argument");
+    return init_common(c, rho, ux, uy, T);
+}
+
+int lbm_step(lbm_handle c, int n) {
+    if (!c || n < 0) return fail(LBM_ERR_ARG, "bad handle or n < 0");
+    if (!c->initialized) return fail(LBM_ERR_STATE, "lbm_step before lbm_init / lbm_set_f");
+    for (int s = 0; s < n; ++s) {
+        for (int st = 0; st < 2; ++st) {
+            int rc = c->mixed ? run_stage<float>(c, st) : run_stage<double>(c, st);
+            if (rc) return rc;
+        }
+        ++c->steps;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments_device(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
+    const size_t bytes = (size_t)c->n * 8;
+    if (rho) CU_TRY(cudaMemcpyAsync(rho, c->rho, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (ux) CU_TRY(cudaMemcpyAsync(ux, c->ux, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (uy) CU_TRY(cudaMemcpyAsync(uy, c->uy, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (T) CU_TRY(cudaMemcpyAsync(T, c->T, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
+    const size_t bytes = (size_t)c->n * 8;
+    if (rho) CU_TRY(cudaMemcpyAsync(rho, c->rho, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (ux) CU_TRY(cudaMemcpyAsync(ux, c->ux, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (uy) CU_TRY(cudaMemcpyAsync(uy, c->uy, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (T) CU_TRY(cudaMemcpyAsync(T, c->T, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_get_f(lbm_handle c, double *f16) {
+    if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
+    const size_t cnt = (size_t)16 * c->n;
+    if (!c->mixed) {
+        CU_TRY(cudaMemcpyAsync(f16, c->f0, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
+        CU_TRY(cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+    std::vector<float> tmp(cnt);
+    CU_TRY(cudaMemcpyAsync(tmp.data(), c->f0, cnt * 4, cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < cnt; ++k) f16[k] = (double)tmp[k];
+    return LBM_OK;
+}
+
+int lbm_set_f(lbm_handle c, const double *f16) {
+    if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
+    const size_t cnt = (size_t)16 * c->n;
+    for (size_t k = 0; k < cnt; ++k)
+        if (!std::isfinite(f16[k])) return fail(LBM_ERR_NONFINITE, "f16[%zu] is not finite", k);
+    if (!c->mixed) {
+        CU_TRY(cudaMemcpyAsync(c->f0, f16, cnt * 8, cudaMemcpyHostToDevice, c->stream));
+        CU_TRY(cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> tmp(cnt);
+        for (size_t k = 0; k < cnt; ++k) tmp[k] = (float)f16[k];
+        CU_TRY(cudaMemcpyAsync(c->f0, tmp.data(), cnt * 4, cudaMemcpyHostToDevice, c->stream));
+        CU_TRY(cudaStreamSynchronize(c->stream));
+    }
+    MomArgs a{};
+    a.f = c->f0;
+    a.rho = c->rho; a.ux = c->ux; a.uy = c->uy; a.T = c->T;
+    a.n = c->n;
+    a.b = c->p.b;
+    for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
+    CU_TRY(c->mixed ? launch_moments<float>(a, c->stream) : launch_moments<double>(a, c->stream));
+    c->initialized = true;
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_handle c, double out[6]) {
+    if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
+    // d_y rho into ry, d_x rho into dQx (stage scratch, rebuilt by the next stage)
+    ColArgs<double> ca{};
+    ca.nx = c->nx;
+    ca.ny = c->ny;
+    ca.W = c->colW_m;
+    ca.log2W = ilog2(c->colW_m);
+    ca.ay = axis<double>(c, false);
+    ca.jobs[0] = ColJob<double>{c->rho, c->ry, nullptr, 1, 1, 1.0, 0.0};
+    CU_TRY(launch_col<double>(ca, 1, 256, c->col_smem_m, c->stream));
+    RowDerivArgs<double> ra{};
+    ra.in[0] = c->rho;
+    ra.out[0] = c->dQx;
+    ra.nin = 1;
+    ra.nx = c->nx;
+    ra.ny = c->ny;
+    ra.rows = c->rows;
+    ra.ax = axis<double>(c, true);
+    CU_TRY(launch_row_deriv<double>(ra, 256, c->rowd_smem, c->stream));
+    DiagArgs da{};
+    da.rho = c->rho; da.ux = c->ux; da.uy = c->uy; da.T = c->T;
+    da.rx = c->dQx; da.ry = c->ry;
+    da.partial = c->partial;
+    da.n = c->n;
+    da.K = c->p.K;
+    da.cell = c->p.dx * c->p.dy;
+    CU_TRY(launch_diag(da, c->diag_blocks, c->stream));
+    std::vector<double> part((size_t)c->diag_blocks * 5);
+    CU_TRY(cudaMemcpyAsync(part.data(), c->partial, part.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    double s[4] = {0, 0, 0, 0}, mx = 0;
+    for (int b = 0; b < c->diag_blocks; ++b) {
+        for (int k = 0; k < 4; ++k) s[k] += part[b * 5 + k];
+        mx = std::max(mx, part[b * 5 + 4]);
+    }
+    const double cell = c->p.dx * c->p.dy;
+    out[0] = s[0] * cell;
+    out[1] = s[1] * cell;
+    out[2] = s[2] * cell;
+    out[3] = s[3] * cell;
+    out[4] = std::sqrt(mx);
+    out[5] = (double)c->steps;
+    for (int k = 0; k < 5; ++k)
+        if (!std::isfinite(out[k])) return fail(LBM_ERR_NONFINITE, "diagnostic %d is not finite", k);
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_handle c) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_timing(lbm_handle c, int enable) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    c->timing = enable != 0;
+    c->ev_used = 0;
+    return LBM_OK;
+}
+
+int lbm_timing_read(lbm_handle c, int kernel, double *ms, long long *launches) {
+    if (!c || !ms || !launches || kernel < 0 || kernel >= LBM_K_COUNT) return fail(LBM_ERR_ARG, "bad argument");
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    double tot = 0;
+    long long cnt = 0;
+    for (size_t s = 0; s + 1 < c->ev_used; s += 2) {
+        if (c->ev_cls[s] != kernel) continue;
+        float t = 0;
+        CU_TRY(cudaEventElapsedTime(&t, c->ev[s], c->ev[s + 1]));
+        tot += t;
+        ++cnt;
+    }
+    *ms = tot;
+    *launches = cnt;
+    return LBM_OK;
+}
+
+size_t lbm_device_bytes(lbm_handle c) { return c ? c->slab_bytes : 0; }
+
+// Maxwell construction (Sec. 3.1) in chemical-potential form: equal pressure and equal
+// mu(rho) = T ln(rho/(3 - rho)) + 3T/(3 - rho) - 9 rho/4 on the two outer branches of the
+// van der Waals isotherm, by nested bisection on the saturation pressure.
+int lbm_maxwell(double T, double *rho_l, double *rho_v) {
+    if (!rho_l || !rho_v) return fail(LBM_ERR_ARG, "NULL output");
+    if (!(T > 0.0 && T < 1.0)) return fail(LBM_ERR_ARG, "need 0 < T < 1 (T=%g)", T);
+    auto P = [T](double r) { return 3.0 * r * T / (3.0 - r) - 1.125 * r * r; };
+    auto mu = [T](double r) { return T * std::log(r / (3.0 - r)) + 3.0 * T / (3.0 - r) - 2.25 * r; };
+    // spinodals: dP/drho = 0 <=> 4T = rho (3 - rho)^2, one root in (0,1), one in (1,3)
+    auto sp = [T](double lo, double hi, bool rising) {
+        for (int it = 0; it < 200; ++it) {
+            const double m = 0.5 * (lo + hi);
+            const double g = m * (3.0 - m) * (3.0 - m) - 4.0 * T;
+            if ((g < 0) == rising) lo = m; else hi = m;
+        }
+        return 0.5 * (lo + hi);
+    };
+    const double sv = sp(0.0, 1.0, true), sl = sp(1.0, 3.0, false);
+    // root of P(rho) = Ps on a monotone branch
+    auto branch = [&](double lo, double hi, double Ps, bool increasing) {
+        for (int it = 0; it < 200; ++it) {
+            const double m = 0.5 * (lo + hi);
+            if ((P(m) < Ps) == increasing) lo = m; else hi = m;
+        }
+        return 0.5 * (lo + hi);
+    };
+    double plo = std::max(P(sl), 0.0), phi = P(sv);
+    double rl = 0, rv = 0;
+    for (int it = 0; it < 200; ++it) {
+        const double Ps = 0.5 * (plo + phi);
+        rv = branch(1e-300, sv, Ps, true);
+        rl = branch(sl, 3.0 - 1e-15, Ps, true);
+        // d(mu_l - mu_v)/dPs = 1/rho_l - 1/rho_v < 0: a positive difference means Ps is too low
+        if (mu(rl) - mu(rv) > 0) plo = Ps; else phi = Ps;
+    }
+    *rho_l = rl;
+    *rho_v = rv;
+    return LBM_OK;
+}
+
+}  // extern "C"

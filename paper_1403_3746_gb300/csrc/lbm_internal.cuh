@@ -1,0 +1,153 @@
+// Internal declarations of the D2V16-FFT-TLB CUDA library (sm_103a).
+//
+// One Runge-Kutta stage (Sec. 2.3) is four kernel passes over HBM-resident fields:
+//   K_COL     column pass: y-derivatives of 12 f_i (those with v_iy != 0) and of the
+//             moments rho, u_x, u_y, T (d_y rho, d_yy rho, d_y u_x, d_y u_y, d_y T)
+//   K_MACRO   row pass: x-derivatives of the moments, van der Waals pressure, stress
+//             Lambda, the fluxes S and Q, the x-halves of div S and div Q, and the part
+//             of C known at this point
+//   K_FLUX    column pass: y-halves of div S, div Q and d_y(div u)
+//   K_UPDATE  row pass: x-derivatives of 12 f_i, f^eq, I_i (Eq. (2)), BGK, the stage
+//             combination, and the moments of the new f for the next stage
+// With no spectral window the 2D derivative multiplier i (v_x k_x + v_y k_y) splits
+// exactly into a row operator and a column operator, so every derivative is one line
+// transform pair along one axis.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_line.cuh"
+#include "lbm_d2v16.h"
+
+namespace lbm {
+
+// D2V16 velocities (0-based), Sec. 2.1 (values: see the header comment of lbm_d2v16.h).
+#define LBM_SQ2 1.4142135623730950488016887
+#define LBM_D3S2 2.1213203435596425732025331  // 3/sqrt(2)
+__host__ __device__ __forceinline__ double vel_x(int i) {
+    switch (i) {
+        case 0: return 1.0;  case 2: return -1.0;
+        case 4: return 6.0;  case 6: return -6.0;
+        case 8: return LBM_SQ2;  case 9: return -LBM_SQ2;  case 10: return -LBM_SQ2;  case 11: return LBM_SQ2;
+        case 12: return LBM_D3S2; case 13: return -LBM_D3S2; case 14: return -LBM_D3S2; case 15: return LBM_D3S2;
+        default: return 0.0;
+    }
+}
+__host__ __device__ __forceinline__ double vel_y(int i) {
+    switch (i) {
+        case 1: return 1.0;  case 3: return -1.0;
+        case 5: return 6.0;  case 7: return -6.0;
+        case 8: return LBM_SQ2;  case 9: return LBM_SQ2;  case 10: return -LBM_SQ2;  case 11: return -LBM_SQ2;
+        case 12: return LBM_D3S2; case 13: return LBM_D3S2; case 14: return -LBM_D3S2; case 15: return -LBM_D3S2;
+        default: return 0.0;
+    }
+}
+// |v_i|^2 (without eta)
+__host__ __device__ __forceinline__ double vel_sq(int i) {
+    return i < 4 ? 1.0 : (i < 8 ? 36.0 : (i < 12 ? 4.0 : 9.0));
+}
+// fields with v_x != 0, in the order of the 12 real rows of the update kernel's shared tile:
+// row k holds field XF(k); complex line p packs rows 2p (real part) and 2p+1 (imag part)
+__host__ __device__ __forceinline__ int xfield(int k) { return k < 4 ? 2 * k : k + 4; }
+__host__ __device__ __forceinline__ int xslot(int i) { return i < 8 ? ((i & 1) ? -1 : i / 2) : i - 4; }
+// fields with v_y != 0 and their slot in the 12-field column-pass output Ay
+__host__ __device__ __forceinline__ int yfield(int k) { return k < 4 ? 2 * k + 1 : k + 4; }
+__host__ __device__ __forceinline__ int yslot(int i) { return i < 8 ? ((i & 1) ? i / 2 : -1) : i - 4; }
+
+// twiddles and derivative multipliers of one axis (digit-reversed order, see fft_line.cuh)
+template <typename R> struct Axis {
+    const typename cplx<R>::T *tw;  // exp(-2 pi i k/N), k < N
+    const R *k1;                    // k_eff(m(p)) / N, 0 at Nyquist
+    const R *k2;                    // -k_eff(m(p))^2 / N, 0 at Nyquist
+    int log2n;
+};
+
+// ---- column derivative pass -------------------------------------------------------
+template <typename F> struct ColJob {
+    const F *in;
+    F *out0, *out1;  // out1 may be NULL
+    int order0, order1;
+    F c0, c1;  // outputs are c * d^order / dy^order (in)
+};
+#define LBM_MAX_COLJOBS 16
+template <typename F> struct ColArgs {
+    ColJob<F> jobs[LBM_MAX_COLJOBS];
+    int nx, ny, W, log2W;
+    Axis<F> ay;
+};
+
+// ---- row pass of the macroscopic chain ---------------------------------------------
+template <typename M> struct MacroArgs {
+    const M *rho, *ux, *uy, *T;               // moments of the stage's f
+    const M *ry, *ryy, *uxy, *uyy, *Ty;       // d_y rho, d_yy rho, d_y u_x, d_y u_y, d_y T
+    M *Qy, *Sxy, *Syy, *divu;                 // inputs of the flux column pass
+    M *dQx, *dSxx, *dSxy, *Cnum;              // d_x Q_x, d_x S_xx, d_x S_xy, partial numerator of C
+    int nx, ny, rows;
+    Axis<M> ax;
+    double K, H, q, zeta;
+};
+
+// ---- fused update row pass -----------------------------------------------------------
+template <typename F, typename M> struct UpdateArgs {
+    const F *fs;     // f of this stage (derivatives, BGK, f^eq moments)
+    const F *fbase;  // f^n (the stage starts from it)
+    F *fout;         // f^{n+1/2} or f^{n+1}; may alias fbase (same node, same thread)
+    const F *Ay;     // 12 fields v_iy d_y f_i
+    M *rho, *ux, *uy, *T;  // in: moments of fs; out: moments of fout
+    const M *ry, *dQx, *dSxx, *dSxy, *Cnum, *dQy, *dSxyy, *dSyy, *ddivuy;
+    int nx, ny, rows;
+    Axis<F> ax;
+    double tau_inv, h, K, b, eta2;  // eta2 = eta0^2 (velocities 0..3)
+    int flags;
+    F minv[256];  // inverse of the 16x16 moment matrix, row-major
+};
+
+struct InitArgs {
+    const double *rho, *ux, *uy, *T;  // inputs
+    void *f;                          // [16][ny][nx] F
+    double *mrho, *mux, *muy, *mT;    // moments of the stored f
+    long long n;
+    double b;
+    double minv[256];
+    double psi[16];
+};
+
+struct MomArgs {
+    const void *f;
+    double *rho, *ux, *uy, *T;
+    long long n;
+    double psi[16];
+    double b;
+};
+
+struct DiagArgs {
+    const double *rho, *ux, *uy, *T, *rx, *ry;
+    double *partial;  // [blocks][5]
+    long long n;
+    double K, cell;
+};
+
+template <typename R> struct RowDerivArgs {
+    const R *in[4];
+    R *out[4];
+    int nin;  // 1..4 inputs (paired two per complex line)
+    int nx, ny, rows;
+    Axis<R> ax;
+};
+
+// launchers (kernels_*.cu); all return cudaGetLastError() of the launch
+template <typename F> cudaError_t launch_col(const ColArgs<F> &a, int njobs, int threads, size_t smem,
+                                             cudaStream_t s);
+template <typename M> cudaError_t launch_macro(const MacroArgs<M> &a, int threads, size_t smem, cudaStream_t s);
+template <typename F, typename M>
+cudaError_t launch_update(const UpdateArgs<F, M> &a, int threads, size_t smem, cudaStream_t s);
+template <typename R>
+cudaError_t launch_row_deriv(const RowDerivArgs<R> &a, int threads, size_t smem, cudaStream_t s);
+template <typename F> cudaError_t launch_init(const InitArgs &a, cudaStream_t s);
+template <typename F> cudaError_t launch_moments(const MomArgs &a, cudaStream_t s);
+cudaError_t launch_diag(const DiagArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_twiddles(double2 *tw64, float2 *tw32, int n, cudaStream_t s);
+template <typename F> cudaError_t launch_convert_out(const F *f, double *out, long long n, cudaStream_t s);
+template <typename F> cudaError_t launch_convert_in(const double *in, F *f, long long n, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,75 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds, loads, exports every
+entry point its header declares, and its host-only logic is right."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1403_3746_gb300 as lbm
+from paper_1403_3746_gb300 import build as lbm_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    lbm_build.build()
+    return lbm.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_default_params_are_the_phase_separation_set(L):
+    p = lbm.default_params()
+    assert (p.tau, p.dt, p.dx, p.dy, p.K, p.H, p.q, p.zeta, p.b, p.eta0) == \
+        (1e-4, 1e-4, 1 / 256, 1 / 256, 5e-6, 0.0, -0.004, 0.0, 2.0, 2.5)
+    assert p.precision == lbm.LBM_FP64 and p.flags == 0
+
+
+def test_maxwell_matches_oracle_construction(L):
+    # the library solves equal pressure + equal chemical potential; the oracle the equal-area rule
+    from oracle.maxwell import coexistence
+    for T in (0.8, 0.85, 0.9, 0.95, 0.99):
+        rl, rv = lbm.maxwell(T)
+        ol, ov = coexistence(T)
+        assert rl == pytest.approx(ol, rel=1e-11) and rv == pytest.approx(ov, rel=1e-10)
+    with pytest.raises(lbm.LbmError):
+        lbm.maxwell(1.2)
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 8), (8, 0), (8, 6), (8192, 8), (1, 8)])
+def test_create_rejects_bad_sizes_before_touching_the_device(L, nx, ny):
+    p = lbm.default_params()
+    h = ctypes.c_void_p()
+    assert L.lbm_create(nx, ny, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert not h.value
+
+
+@pytest.mark.parametrize("field,value", [("tau", 0.0), ("dt", -1.0), ("dx", float("nan")),
+                                         ("precision", 7), ("flags", 64)])
+def test_create_rejects_bad_params(L, field, value):
+    p = lbm.default_params(**{field: value})
+    h = ctypes.c_void_p()
+    assert L.lbm_create(16, 16, ctypes.byref(p), None, ctypes.byref(h)) == -1
+
+
+def test_error_strings(L):
+    assert L.lbm_strerror(0) == b"ok"
+    assert L.lbm_strerror(-7).startswith(b"unsupported")
+    assert L.lbm_strerror(-99) == b"unknown error"
