@@ -1,0 +1,338 @@
+"""Benchmark of one D2V16-FFT-TLB Runge-Kutta step (all four passes of both stages).
+
+Workload: a static circular droplet (R = 128, tanh interface of width 2, Maxwell
+coexistence densities at T = 0.9) on a 1024 x 1024 periodic grid, with the
+phase-separation parameter set (tau = dt = 1e-4, dx = dy = 1/256, K = 5e-6, q = -0.004).
+Synthetic, seeded inputs; the metric is MLUPS (lattice-node updates per second, one
+update = one full two-stage step), headline = the FP32-spectral path (LBM_MIXED), with
+the plain FP64 path measured beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: W untimed steps, then K steps each between CUDA events on the library's stream,
+with a 256 MiB buffer written between steps (outside the events) to flush the 126 MB L2.
+Under torchrun every rank runs its own replica (no data-path collective: a single grid
+does not shard without an all-to-all, see the design notes); value = all ranks' node
+updates / the slowest rank's time. One JSON line is printed by rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 1024
+WORKLOAD = "droplet R=128 on 1024x1024 periodic grid, T=0.9, phase-separation parameter set"
+PARAMS = dict(tau=1e-4, dt=1e-4, dx=1.0 / 256, dy=1.0 / 256, K=5e-6, q=-0.004)
+T0, RADIUS = 0.9, 128
+# algorithmic bytes per node and launch, in units of the path's element size
+# (col 34, macro 17, flux 8; update 61 in stage 1 and 77 in stage 2: mean 69)
+ELEMS_PER_NODE = {"col": 34, "macro": 17, "flux": 8, "update": 69}
+ELEMS_PER_NODE_STEP = 2 * (34 + 17 + 8) + 61 + 77  # 256
+KERNEL_NAMES = {"col": "col_deriv_kernel", "macro": "macro_row_kernel", "flux": "col_deriv_kernel",
+                "update": "update_row_kernel"}
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (no tensor path for this work)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1403_3746_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key, precision):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d[f"{precision}:{kernel_key}"]
+        if e.get("source_digest") != source_digest():
+            return None
+        return e["dram_bytes_per_launch_full_size"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                try:
+                    rows.append(f)
+                except Exception:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_fields(lbm, synthetic, n=N_GRID, radius=RADIUS):
+    rl, rv = lbm.maxwell(T0)
+    return synthetic.droplet(n, n, radius, rl, rv, T0, width=2.0)
+
+
+def time_path(lbm, torch, precision, steps, warmup, fields, stream):
+    p = lbm.default_params(precision=precision, **PARAMS)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with lbm.Simulation(N_GRID, N_GRID, p, stream=stream.cuda_stream) as sim:
+        sim.init(*fields)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                sim.step(1)
+                flush.fill_(1.0)
+            stream.synchronize()
+            sim.timing(True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for a, b in ev:
+                a.record(stream)
+                sim.step(1)
+                b.record(stream)
+                flush.fill_(float(len(ev)))
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        kern = {k: sim.timing_read(k) for k in ELEMS_PER_NODE}
+        sim.timing(False)
+        diag = sim.diagnostics()
+    return step_ms, kern, wall, diag
+
+
+def e2e_path(lbm, torch, precision, steps, fields):
+    """Through the C ABI with host buffers: init from pinned host memory, every step
+    lbm_step + lbm_diagnostics (device->host read of the step's diagnostics), and the
+    final moments read back to pinned host memory."""
+    p = lbm.default_params(precision=precision, **PARAMS)
+    pinned = [torch.empty((N_GRID, N_GRID), dtype=torch.float64, pin_memory=True).numpy() for _ in range(8)]
+    for dst, src in zip(pinned[:4], fields):
+        dst[...] = src
+    with lbm.Simulation(N_GRID, N_GRID, p) as sim:
+        sim.init(*pinned[:4])
+        sim.step(2)
+        sim.synchronize()
+        t0 = time.perf_counter()
+        sim.init(*pinned[:4])
+        for _ in range(steps):
+            sim.step(1)
+            sim.diagnostics()
+        out = sim.moments()
+        for dst, src in zip(pinned[4:], out):
+            dst[...] = src
+        wall = time.perf_counter() - t0
+    n = N_GRID * N_GRID
+    return {"value": n * steps / wall / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": 4 * n * 8 / steps, "d2h_bytes_per_step": 6 * 8 + 4 * n * 8 / steps,
+            "note": "init from pinned host + per step lbm_step and lbm_diagnostics + final moments"}
+
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle, synthetic
+from oracle.dvm import D2V16
+from oracle.model import init_feq, rk2_step
+n, steps, warm = {n}, {steps}, {warm}
+rl, rv = oracle.coexistence({T0})
+fields = synthetic.droplet(n, n, {radius}, rl, rv, {T0}, width=2.0)
+p = oracle.Params(**{params!r})
+d = D2V16(p.eta0)
+f = init_feq(d, *fields, p)
+for _ in range(warm):
+    f = rk2_step(d, f, p)
+ts = []
+for _ in range(steps):
+    t = time.perf_counter(); f = rk2_step(d, f, p); ts.append(time.perf_counter() - t)
+print(json.dumps({{"step_s": ts}}))
+"""
+
+
+def run_oracle(n, steps, warm, radius):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, n=n, steps=steps, warm=warm, T0=T0, radius=radius, params=PARAMS)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["step_s"]
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_main(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    # the oracle on host cores; each step is one RK2 step of a 256 x 256 sample of the workload
+    n, radius = 256, RADIUS // 4
+    ts = run_oracle(n, args.steps, args.warmup, radius)
+    total = sum(ts)
+    v = n * n * len(ts) / total / 1e6
+    line = {"metric": "MLUPS of D2V16 RK2 step at 1024^2", "value": v, "unit": "MLUPS",
+            "impl": "reference", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(ts), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{n}x{n} crop, R={radius}", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(ts)} RK2 steps of a {n}x{n} droplet (R={radius}), numpy FP64, 1 thread"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import torch
+    import paper_1403_3746_gb300 as lbm
+    from paper_1403_3746_gb300 import build as lbm_build
+    import synthetic
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if not os.path.exists(lbm_build.LIB):
+        lbm_build.build()
+    lbm.lib()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    fields = make_fields(lbm, synthetic)
+    hbm, peak_kind = peaks()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        step_ms, kern, wall, diag = time_path(lbm, torch, lbm.LBM_MIXED, args.steps, args.warmup, fields, stream)
+    clocks = clk.summary()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n = N_GRID * N_GRID
+    value = world * n * args.steps / (total_ms * 1e-3) / 1e6
+
+    # FP64 path on the same workload (plain method)
+    k64 = args.fp64_steps or max(3, args.steps // 10)
+    step64, kern64, _, _ = time_path(lbm, torch, lbm.LBM_FP64, k64, min(args.warmup, 3), fields, stream)
+    fp64_mlups = n * k64 / (sum(step64) * 1e-3) / 1e6
+
+    dom = max(kern, key=lambda k: kern[k][0])
+    ms, cnt = kern[dom]
+    per_launch_s = ms * 1e-3 / max(cnt, 1)
+    alg_bytes = ELEMS_PER_NODE[dom] * 4 * n
+    achieved = alg_bytes / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom] + "<float>", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": ncu_traffic(dom, "mixed"),
+                "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                "step_frac": ELEMS_PER_NODE_STEP * 4 * n / (total_ms * 1e-3 / args.steps) / 1e9 / hbm}
+    launches = sum(c for _, c in kern.values())
+    e2e = e2e_path(lbm, torch, lbm.LBM_MIXED, max(10, args.steps // 4), fields) if rank == 0 else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ts = run_oracle(N_GRID, 2, 0, RADIUS)
+        cpu = {"value": n * len(ts) / sum(ts) / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{len(ts)} RK2 steps of the 1024x1024 droplet, numpy FP64, 1 thread"}
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": "MLUPS of D2V16 RK2 step at 1024^2", "value": value, "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (moment sums compensated)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "LBM_MIXED", "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "fp64_path": {"value": fp64_mlups, "unit": "MLUPS", "steps": k64,
+                          "ms_per_step": sum(step64) / k64,
+                          "kernels_ms_per_step": {k: v[0] / k64 for k, v in kern64.items()},
+                          "bound": "alu (fp64)", "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS},
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
+            "roofline": roofline, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clocks, "wall_s_timed_loop": wall,
+            "check": {"mass": diag["mass"], "umax": diag["umax"]},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

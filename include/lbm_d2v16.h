@@ -62,6 +62,8 @@ typedef struct lbm_params {
     double zeta;  /* bulk viscosity in B and C */
     double b;     /* total degrees of freedom (Sec. 2.1) */
     double eta0;  /* extra-degree-of-freedom parameter of velocities 0..3 (Sec. 2.1: 2.5) */
+    double win_alpha; /* window of the windowed FFT: W(m) = exp(-win_alpha (|m|/(N/2))^win_p) */
+    double win_p;     /* along each derivative's axis; win_alpha = 0 (default): W = 1, Eq. (3) */
     int precision; /* LBM_FP64 or LBM_MIXED */
     int flags;     /* LBM_FLAG_* bits, 0 for the full model */
 } lbm_params;
@@ -69,7 +71,8 @@ typedef struct lbm_params {
 typedef struct lbm_ctx *lbm_handle;
 
 /* Fills *p with the phase-separation set of Sec. 3.2 (tau = dt = 1e-4, dx = dy = 1/256,
- * K = 5e-6, H = 0, zeta = 0) with q = -0.004 and b = 2 (Sec. 3.1), eta0 = 2.5, FP64. */
+ * K = 5e-6, H = 0, zeta = 0) with q = -0.004 and b = 2 (Sec. 3.1), eta0 = 2.5, no window
+ * (win_alpha = 0, win_p = 36), FP64, no flags. */
 void lbm_default_params(lbm_params *p);
 
 /* Creates a simulation on the current CUDA device. nx, ny: powers of two, 2 <= n <= 4096

@@ -13,8 +13,8 @@ from .wfft import spectral_deriv
 
 def diagnostics(dvm, f, p):
     rho, ux, uy, T = moments(dvm, f, p.b)
-    rx = spectral_deriv(rho, 1, 0, p.dx, p.dy)
-    ry = spectral_deriv(rho, 0, 1, p.dx, p.dy)
+    rx = spectral_deriv(rho, 1, 0, p.dx, p.dy, p.win_alpha, p.win_p)
+    ry = spectral_deriv(rho, 0, 1, p.dx, p.dy, p.win_alpha, p.win_p)
     u2 = ux * ux + uy * uy
     eT = rho * T - 9.0 / 8.0 * rho * rho + 0.5 * p.K * (rx * rx + ry * ry) + 0.5 * rho * u2
     cell = p.dx * p.dy

@@ -54,6 +54,8 @@ class Params:
     zeta: float = 0.0
     b: float = 2.0
     eta0: float = 2.5
+    win_alpha: float = 0.0
+    win_p: float = 36.0
     force: bool = True
     collide: bool = True
     advect: bool = True
@@ -83,7 +85,7 @@ def forcing_terms(dvm, rho, ux, uy, T, fe, p):
     """Eq. (2) and the coefficient definitions after it. Returns I (16, ny, nx) and a dict
     of the intermediate fields (A, B_x, B_y, C, C_q, ...)."""
     def D(h, ox, oy):
-        return spectral_deriv(h, ox, oy, p.dx, p.dy)
+        return spectral_deriv(h, ox, oy, p.dx, p.dy, p.win_alpha, p.win_p)
 
     # spatial derivatives of the macroscopic fields
     rx, ry = D(rho, 1, 0), D(rho, 0, 1)
@@ -134,8 +136,8 @@ def advection(dvm, f, p):
     """v_i . grad f_i for all 16 fields (Eq. (1) left side), by the FFT scheme of Eq. (3)."""
     out = np.empty_like(f)
     for i in range(16):
-        out[i] = dvm.vx[i] * spectral_deriv(f[i], 1, 0, p.dx, p.dy) \
-            + dvm.vy[i] * spectral_deriv(f[i], 0, 1, p.dx, p.dy)
+        out[i] = dvm.vx[i] * spectral_deriv(f[i], 1, 0, p.dx, p.dy, p.win_alpha, p.win_p) \
+            + dvm.vy[i] * spectral_deriv(f[i], 0, 1, p.dx, p.dy, p.win_alpha, p.win_p)
     return out
 
 

@@ -8,9 +8,12 @@ Readings:
 * The Nyquist index m = -N/2 gets a first-derivative multiplier of 0, so that the
   derivative of a real field stays real.
 * Every derivative used by the model is one inverse transform of a spectrum times a
-  product of first-derivative multipliers d(m) = i k_eff(m) (second derivatives are
-  d^2, mixed ones d_x d_y). The window of the "windowed" FFT is not specified in the
-  paper; no window is applied (W = 1), i.e. the operator is Eq. (3) as printed.
+  product of first-derivative multipliers d(m) = i W(m) k_eff(m) of the two axes
+  (second derivatives are d^2, mixed ones d_x d_y): compositions of first derivatives.
+* The window W of the "windowed" FFT scheme is not specified in the paper. It is read
+  as a per-axis exponential filter W(m) = exp(-alpha (|m|/(N/2))^p) (Hou and Li, J.
+  Comput. Phys. 226 (2007): alpha = 36, p = 36) applied with each first derivative
+  along that derivative's own axis; alpha = 0 (W = 1) is Eq. (3) exactly.
 """
 import numpy as np
 
@@ -33,19 +36,29 @@ def keff(m, N, dx):
     return (2.0 / dx) * s
 
 
-def deriv_multiplier(N, dx):
-    """d(m) = i k_eff(m) per FFT position, zero at the Nyquist index."""
+def window(N, alpha, p):
+    """Spectral window W(m) = exp(-alpha (|m| / (N/2))^p) of the windowed FFT scheme
+    (exponential filter; alpha = 0 gives W = 1)."""
+    m = np.abs(dft_indices(N)).astype(np.float64)
+    if alpha == 0.0:
+        return np.ones(N)
+    return np.exp(-alpha * (m / (N / 2.0)) ** p)
+
+
+def deriv_multiplier(N, dx, alpha=0.0, p=36.0):
+    """d(m) = i W(m) k_eff(m) per FFT position, zero at the Nyquist index."""
     m = dft_indices(N)
-    d = 1j * keff(m, N, dx)
+    d = 1j * keff(m, N, dx) * window(N, alpha, p)
     if N % 2 == 0:
         d[m == -N // 2] = 0.0
     return d
 
 
-def spectral_deriv(h, ox, oy, dx, dy):
-    """Spectral derivative d^(ox) / dx^(ox) d^(oy) / dy^(oy) of a real field h of shape (ny, nx)."""
+def spectral_deriv(h, ox, oy, dx, dy, alpha=0.0, p=36.0):
+    """Spectral derivative d^(ox) / dx^(ox) d^(oy) / dy^(oy) of a real field h of shape (ny, nx):
+    the composition of the first-derivative operators of each axis."""
     ny, nx = h.shape
-    mult = deriv_multiplier(nx, dx)[None, :] ** ox * deriv_multiplier(ny, dy)[:, None] ** oy
+    mult = deriv_multiplier(nx, dx, alpha, p)[None, :] ** ox * deriv_multiplier(ny, dy, alpha, p)[:, None] ** oy
     return np.fft.ifft2(mult * np.fft.fft2(h)).real
 
 

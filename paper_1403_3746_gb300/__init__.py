@@ -33,7 +33,8 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double),
                 ("dy", ctypes.c_double), ("K", ctypes.c_double), ("H", ctypes.c_double),
                 ("q", ctypes.c_double), ("zeta", ctypes.c_double), ("b", ctypes.c_double),
-                ("eta0", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("eta0", ctypes.c_double), ("win_alpha", ctypes.c_double), ("win_p", ctypes.c_double),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -44,10 +44,10 @@ __global__ void init_feq_kernel(const __grid_constant__ InitArgs a) {
             mE += a.psi[i] * fd;
         }
         const double ir = 1.0 / mr, nux = mjx * ir, nuy = mjy * ir;
-        a.mrho[g] = mr;
-        a.mux[g] = nux;
-        a.muy[g] = nuy;
-        a.mT[g] = (mE * ir - (nux * nux + nuy * nuy)) / b;
+        static_cast<F *>(a.mrho)[g] = (F)mr;
+        static_cast<F *>(a.mux)[g] = (F)nux;
+        static_cast<F *>(a.muy)[g] = (F)nuy;
+        static_cast<F *>(a.mT)[g] = (F)((mE * ir - (nux * nux + nuy * nuy)) / b);
     }
 }
 
@@ -67,21 +67,25 @@ __global__ void moments_kernel(const __grid_constant__ MomArgs a) {
             mE += a.psi[i] * fd;
         }
         const double ir = 1.0 / mr, nux = mjx * ir, nuy = mjy * ir;
-        if (a.rho) a.rho[g] = mr;
-        if (a.ux) a.ux[g] = nux;
-        if (a.uy) a.uy[g] = nuy;
-        if (a.T) a.T[g] = (mE * ir - (nux * nux + nuy * nuy)) / a.b;
+        static_cast<F *>(a.rho)[g] = (F)mr;
+        static_cast<F *>(a.ux)[g] = (F)nux;
+        static_cast<F *>(a.uy)[g] = (F)nuy;
+        static_cast<F *>(a.T)[g] = (F)((mE * ir - (nux * nux + nuy * nuy)) / a.b);
     }
 }
 
 // Per-block partial sums of mass, x/y momentum, e_T (Sec. 2.2) and the max of |u|^2.
+template <typename R>
 __global__ void __launch_bounds__(256) diag_kernel(const __grid_constant__ DiagArgs a) {
     __shared__ double red[5][256];
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0, mx = 0;
+    const R *prho = static_cast<const R *>(a.rho), *pux = static_cast<const R *>(a.ux);
+    const R *puy = static_cast<const R *>(a.uy), *pT = static_cast<const R *>(a.T);
+    const R *prx = static_cast<const R *>(a.rx), *pry = static_cast<const R *>(a.ry);
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.n;
          g += (long long)gridDim.x * blockDim.x) {
-        const double rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
-        const double rx = a.rx[g], ry = a.ry[g];
+        const double rho = prho[g], ux = pux[g], uy = puy[g], T = pT[g];
+        const double rx = prx[g], ry = pry[g];
         const double u2 = ux * ux + uy * uy;
         s0 += rho;
         s1 += rho * ux;
@@ -169,8 +173,8 @@ template <typename F> cudaError_t launch_moments(const MomArgs &a, cudaStream_t 
     moments_kernel<F><<<grid_for(a.n), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_diag(const DiagArgs &a, int blocks, cudaStream_t s) {
-    diag_kernel<<<blocks, 256, 0, s>>>(a);
+template <typename R> cudaError_t launch_diag(const DiagArgs &a, int blocks, cudaStream_t s) {
+    diag_kernel<R><<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_twiddles(double2 *tw64, float2 *tw32, int n, cudaStream_t s) {
@@ -186,11 +190,11 @@ template <typename F> cudaError_t launch_convert_in(const double *in, F *f, long
     return cudaGetLastError();
 }
 template <typename R>
-cudaError_t launch_row_deriv(const RowDerivArgs<R> &a, int threads, size_t smem, cudaStream_t s) {
+cudaError_t launch_row_deriv(const RowDerivArgs<R> &a, size_t smem, cudaStream_t s) {
     cudaError_t e =
         cudaFuncSetAttribute(row_deriv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    row_deriv_kernel<R><<<a.ny / a.rows, threads, smem, s>>>(a);
+    row_deriv_kernel<R><<<a.ny / a.rows, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -202,7 +206,9 @@ template cudaError_t launch_convert_out<double>(const double *, double *, long l
 template cudaError_t launch_convert_out<float>(const float *, double *, long long, cudaStream_t);
 template cudaError_t launch_convert_in<double>(const double *, double *, long long, cudaStream_t);
 template cudaError_t launch_convert_in<float>(const double *, float *, long long, cudaStream_t);
-template cudaError_t launch_row_deriv<double>(const RowDerivArgs<double> &, int, size_t, cudaStream_t);
-template cudaError_t launch_row_deriv<float>(const RowDerivArgs<float> &, int, size_t, cudaStream_t);
+template cudaError_t launch_row_deriv<double>(const RowDerivArgs<double> &, size_t, cudaStream_t);
+template cudaError_t launch_row_deriv<float>(const RowDerivArgs<float> &, size_t, cudaStream_t);
+template cudaError_t launch_diag<double>(const DiagArgs &, int, cudaStream_t);
+template cudaError_t launch_diag<float>(const DiagArgs &, int, cudaStream_t);
 
 }  // namespace lbm

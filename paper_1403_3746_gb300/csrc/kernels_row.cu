@@ -2,6 +2,8 @@
 //
 // A CTA owns `rows` consecutive rows (rows * nx nodes); each row segment is read and
 // written with coalesced accesses, and threads map to consecutive x in the node loops.
+// Template parameter R is the arithmetic and storage type of the path (double for
+// LBM_FP64, float for LBM_MIXED).
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -16,15 +18,15 @@ namespace lbm {
 // Then per node: P^w, Lambda, S, Q, div u, the partial numerator of C; and a second
 // transform pair gives d_x Q_x, d_x S_xx (line A) and d_x S_xy (line B).
 // ---------------------------------------------------------------------------------------
-template <typename M>
-__global__ void __launch_bounds__(256) macro_row_kernel(const __grid_constant__ MacroArgs<M> a) {
+template <typename R>
+__global__ void __launch_bounds__(256) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    M *s = reinterpret_cast<M *>(smem_raw);
-    const int nx = a.nx, R = a.rows, log2n = a.ax.log2n;
+    R *s = reinterpret_cast<R *>(smem_raw);
+    const int nx = a.nx, NR = a.rows, log2n = a.ax.log2n;
     const int L2 = 2 * nx;
-    const int nodes = R * nx;
+    const int nodes = NR * nx;
     const size_t g0 = (size_t)blockIdx.x * nodes;
-    M *sA = s, *sB = s + R * L2, *sC = s + 2 * R * L2, *sA2 = s + 3 * R * L2, *sB2 = s + 4 * R * L2;
+    R *sA = s, *sB = s + NR * L2, *sC = s + 2 * NR * L2, *sA2 = s + 3 * NR * L2, *sB2 = s + 4 * NR * L2;
 
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int r = idx >> log2n, x = idx & (nx - 1);
@@ -35,69 +37,69 @@ __global__ void __launch_bounds__(256) macro_row_kernel(const __grid_constant__ 
         sB[o] = a.ux[g];
         sB[o + nx] = a.uyy[g];
         sC[o] = a.uy[g];
-        sC[o + nx] = M(0);
+        sC[o + nx] = R(0);
     }
     __syncthreads();
-    const LineSet<M> ABC{s, 3 * R, L2, 1, nx};
-    fft_forward<M, false>(ABC, log2n, a.ax.tw);
-    spec_mul<M, false>(LineSet<M>{sA2, R, L2, 1, nx}, LineSet<M>{sA, R, L2, 1, nx}, log2n, 2, M(1), a.ax.k1,
+    const LineSet<R> ABC{s, 3 * NR, L2, 1, nx};
+    fft_forward<R, false>(ABC, log2n, a.ax.tw);
+    spec_mul<R, false>(LineSet<R>{sA2, NR, L2, 1, nx}, LineSet<R>{sA, NR, L2, 1, nx}, log2n, 2, R(1), a.ax.k1,
                        a.ax.k2);
-    spec_mul<M, false>(LineSet<M>{sB2, R, L2, 1, nx}, LineSet<M>{sB, R, L2, 1, nx}, log2n, 2, M(1), a.ax.k1,
+    spec_mul<R, false>(LineSet<R>{sB2, NR, L2, 1, nx}, LineSet<R>{sB, NR, L2, 1, nx}, log2n, 2, R(1), a.ax.k1,
                        a.ax.k2);
     __syncthreads();
-    spec_mul<M, false>(ABC, ABC, log2n, 1, M(1), a.ax.k1, a.ax.k2);
+    spec_mul<R, false>(ABC, ABC, log2n, 1, R(1), a.ax.k1, a.ax.k2);
     __syncthreads();
-    fft_inverse<M, false>(LineSet<M>{s, 5 * R, L2, 1, nx}, log2n, a.ax.tw);
+    fft_inverse<R, false>(LineSet<R>{s, 5 * NR, L2, 1, nx}, log2n, a.ax.tw);
 
-    const double K = a.K, H = a.H, q = a.q, zeta = a.zeta;
+    const R K = a.K, H = a.H, q = a.q, zeta = a.zeta;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int r = idx >> log2n, x = idx & (nx - 1);
         const size_t g = g0 + idx;
         const int o = r * L2 + x;
-        const double rx = sA[o], Tx = sA[o + nx], rxx = sA2[o];
-        const double dux_dx = sB[o], dxduyy = sB[o + nx], dxxux = sB2[o];
-        const double duy_dx = sC[o];
-        const double rho = a.rho[g], T = a.T[g];
-        const double ry = a.ry[g], ryy = a.ryy[g], dux_dy = a.uxy[g], duy_dy = a.uyy[g], Ty = a.Ty[g];
+        const R rx = sA[o], Tx = sA[o + nx], rxx = sA2[o];
+        const R dux_dx = sB[o], dxduyy = sB[o + nx], dxxux = sB2[o];
+        const R duy_dx = sC[o];
+        const R rho = a.rho[g], T = a.T[g];
+        const R ry = a.ry[g], ryy = a.ryy[g], dux_dy = a.uxy[g], duy_dy = a.uyy[g], Ty = a.Ty[g];
 
-        const double lap = rxx + ryy;
-        const double divu = dux_dx + duy_dy;
-        const double ddivu_x = dxxux + dxduyy;  // d_x (div u)
+        const R lap = rxx + ryy;
+        const R divu = dux_dx + duy_dy;
+        const R ddivu_x = dxxux + dxduyy;  // d_x (div u)
         // van der Waals EOS (Sec. 2.2)
-        const double rT = rho * T;
-        const double Pw = 3.0 * rT / (3.0 - rho) - 1.125 * rho * rho;
+        const R rT = rho * T;
+        const R Pw = R(3) * rT / (R(3) - rho) - R(1.125) * rho * rho;
         // Lambda with M = K + H T and grad(M/T) = -K grad T / T^2
-        const double Mc = K + H * T;
-        const double iT2 = 1.0 / (T * T);
-        const double gx = -K * Tx * iT2, gy = -K * Ty * iT2;
-        const double grr = rx * rx + ry * ry;
-        const double iso = Mc * (rho * lap + 0.5 * grr) + rT * (rx * gx + ry * gy);
-        const double Lxx = Mc * rx * rx - iso, Lxy = Mc * rx * ry, Lyy = Mc * ry * ry - iso;
-        const double Pn = Pw - rT - zeta * divu;
-        const double Sxx = Pn + Lxx, Sxy = Lxy, Syy = Pn + Lyy;
-        const double qrT = q * rT;
-        const double Qx = qrT * Tx, Qy = qrT * Ty;
+        const R Mc = K + H * T;
+        const R iT2 = R(1) / (T * T);
+        const R gx = -K * Tx * iT2, gy = -K * Ty * iT2;
+        const R grr = rx * rx + ry * ry;
+        const R iso = Mc * (rho * lap + R(0.5) * grr) + rT * (rx * gx + ry * gy);
+        const R Lxx = Mc * rx * rx - iso, Lxy = Mc * rx * ry, Lyy = Mc * ry * ry - iso;
+        const R Pn = Pw - rT - zeta * divu;
+        const R Sxx = Pn + Lxx, Sxy = Lxy, Syy = Pn + Lyy;
+        const R qrT = q * rT;
+        const R Qx = qrT * Tx, Qy = qrT * Ty;
         // numerator of C without the -K rho d_y rho d_y(div u) term (needs the flux pass)
-        const double L_gradu = Lxx * dux_dx + Lxy * (duy_dx + dux_dy) + Lyy * duy_dy;
-        const double r_gradu_r = rx * (dux_dx * rx + duy_dx * ry) + ry * (dux_dy * rx + duy_dy * ry);
-        const double Cnum = (Pw - rT) * divu + L_gradu - zeta * divu * divu + 1.125 * rho * rho * divu +
-                            K * (-0.5 * grr * divu - rho * rx * ddivu_x - r_gradu_r);
-        a.Qy[g] = (M)Qy;
-        a.Sxy[g] = (M)Sxy;
-        a.Syy[g] = (M)Syy;
-        a.divu[g] = (M)divu;
-        a.Cnum[g] = (M)Cnum;
-        sA[o] = (M)Qx;
-        sA[o + nx] = (M)Sxx;
-        sB[o] = (M)Sxy;
-        sB[o + nx] = M(0);
+        const R L_gradu = Lxx * dux_dx + Lxy * (duy_dx + dux_dy) + Lyy * duy_dy;
+        const R r_gradu_r = rx * (dux_dx * rx + duy_dx * ry) + ry * (dux_dy * rx + duy_dy * ry);
+        const R Cnum = (Pw - rT) * divu + L_gradu - zeta * divu * divu + R(1.125) * rho * rho * divu +
+                       K * (-R(0.5) * grr * divu - rho * rx * ddivu_x - r_gradu_r);
+        a.Qy[g] = Qy;
+        a.Sxy[g] = Sxy;
+        a.Syy[g] = Syy;
+        a.divu[g] = divu;
+        a.Cnum[g] = Cnum;
+        sA[o] = Qx;
+        sA[o + nx] = Sxx;
+        sB[o] = Sxy;
+        sB[o + nx] = R(0);
     }
     __syncthreads();
-    const LineSet<M> AB{s, 2 * R, L2, 1, nx};
-    fft_forward<M, false>(AB, log2n, a.ax.tw);
-    spec_mul<M, false>(AB, AB, log2n, 1, M(1), a.ax.k1, a.ax.k2);
+    const LineSet<R> AB{s, 2 * NR, L2, 1, nx};
+    fft_forward<R, false>(AB, log2n, a.ax.tw);
+    spec_mul<R, false>(AB, AB, log2n, 1, R(1), a.ax.k1, a.ax.k2);
     __syncthreads();
-    fft_inverse<M, false>(AB, log2n, a.ax.tw);
+    fft_inverse<R, false>(AB, log2n, a.ax.tw);
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int r = idx >> log2n, x = idx & (nx - 1);
         const size_t g = g0 + idx;
@@ -107,6 +109,69 @@ __global__ void __launch_bounds__(256) macro_row_kernel(const __grid_constant__ 
         a.dSxy[g] = sB[o];
     }
 }
+
+// ---------------------------------------------------------------------------------------
+// Moment sums of the new f (Sec. 2.1): rho = sum f, j = sum f v, E = sum f psi.
+// float64 path: plain sums. float32 path: each sum is accumulated with error-free
+// transformations (Knuth's TwoSum and the FMA-based TwoProduct, as in the compensated
+// dot product "Dot2" of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)), so the
+// sums of the stored float32 values are as accurate as in twice the working precision;
+// the irrational weights sqrt2 and 3/sqrt2 enter as float32 pairs (hi + lo).
+// ---------------------------------------------------------------------------------------
+template <typename R> struct MomentSums;
+
+template <> struct MomentSums<double> {
+    double r = 0, jx = 0, jy = 0, E = 0;
+    __device__ __forceinline__ void add(int i, double f, double psi_hi, double) {
+        r += f;
+        if (vel_x(i) != 0.0) jx += vel_x(i) * f;
+        if (vel_y(i) != 0.0) jy += vel_y(i) * f;
+        E += psi_hi * f;
+    }
+    __device__ __forceinline__ void finish(double b, double &rho, double &ux, double &uy, double &T) const {
+        rho = r;
+        const double ir = 1.0 / r;
+        ux = jx * ir;
+        uy = jy * ir;
+        T = (E * ir - (ux * ux + uy * uy)) / b;
+    }
+};
+
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+__device__ __forceinline__ void dot2_acc(float &s, float &c, float f, float wh, float wl) {
+    const float p = f * wh;
+    const float e = fmaf(f, wh, -p);  // exact: f*wh = p + e
+    two_sum_acc(s, c, p);
+    c += fmaf(f, wl, e);
+}
+
+template <> struct MomentSums<float> {
+    float rs = 0, rc = 0, xs = 0, xc = 0, ys = 0, yc = 0, es = 0, ec = 0;
+    __device__ __forceinline__ void add(int i, float f, float psi_hi, float psi_lo) {
+        two_sum_acc(rs, rc, f);
+        if (vel_x(i) != 0.0) {
+            const float wh = (float)vel_x(i), wl = (float)(vel_x(i) - (double)(float)vel_x(i));
+            dot2_acc(xs, xc, f, wh, wl);
+        }
+        if (vel_y(i) != 0.0) {
+            const float wh = (float)vel_y(i), wl = (float)(vel_y(i) - (double)(float)vel_y(i));
+            dot2_acc(ys, yc, f, wh, wl);
+        }
+        dot2_acc(es, ec, f, psi_hi, psi_lo);
+    }
+    __device__ __forceinline__ void finish(float b, float &rho, float &ux, float &uy, float &T) const {
+        rho = rs + rc;
+        const float jx = xs + xc, jy = ys + yc, E = es + ec;
+        ux = jx / rho;
+        uy = jy / rho;
+        T = (E / rho - (ux * ux + uy * uy)) / b;
+    }
+};
 
 // ---------------------------------------------------------------------------------------
 // Fused update row pass: Eq. (1) right-hand side and one Runge-Kutta stage (Sec. 2.3).
@@ -140,13 +205,13 @@ __device__ __forceinline__ void equilibrium_moments(R rho, R ux, R uy, R T, R b,
     m[15] = rho * (T * e + gq * uy * uy);
 }
 
-template <typename F, typename M>
-__global__ void __launch_bounds__(256) update_row_kernel(const __grid_constant__ UpdateArgs<F, M> a) {
+template <typename R, bool MOMENT_SPACE>
+__global__ void __launch_bounds__(256) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    F *s = reinterpret_cast<F *>(smem_raw);
-    const int nx = a.nx, R = a.rows, log2n = a.ax.log2n;
+    R *s = reinterpret_cast<R *>(smem_raw);
+    const int nx = a.nx, NR = a.rows, log2n = a.ax.log2n;
     const int L2 = 2 * nx;
-    const int nodes = R * nx;
+    const int nodes = NR * nx;
     const size_t plane = (size_t)nx * a.ny;
     const size_t g0 = (size_t)blockIdx.x * nodes;
     const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
@@ -157,91 +222,120 @@ __global__ void __launch_bounds__(256) update_row_kernel(const __grid_constant__
         for (int idx = threadIdx.x; idx < 12 * nodes; idx += blockDim.x) {
             const int k = idx / nodes, rem = idx - k * nodes;
             const int r = rem >> log2n, x = rem & (nx - 1);
-            s[((k >> 1) * R + r) * L2 + (k & 1) * nx + x] = a.fs[xfield(k) * plane + g0 + rem];
+            s[((k >> 1) * NR + r) * L2 + (k & 1) * nx + x] = a.fs[xfield(k) * plane + g0 + rem];
         }
         __syncthreads();
-        const LineSet<F> X{s, 6 * R, L2, 1, nx};
-        fft_forward<F, false>(X, log2n, a.ax.tw);
-        spec_mul<F, false>(X, X, log2n, 1, F(1), a.ax.k1, a.ax.k2);
+        const LineSet<R> X{s, 6 * NR, L2, 1, nx};
+        fft_forward<R, false>(X, log2n, a.ax.tw);
+        spec_mul<R, false>(X, X, log2n, 1, R(1), a.ax.k1, a.ax.k2);
         __syncthreads();
-        fft_inverse<F, false>(X, log2n, a.ax.tw);
+        fft_inverse<R, false>(X, log2n, a.ax.tw);
     }
 
-    const double b = a.b, K = a.K, tau_inv = a.tau_inv, h = a.h;
+    const R b = a.b, K = a.K, tau_inv = a.tau_inv, h = a.h;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int r = idx >> log2n, x = idx & (nx - 1);
         const size_t g = g0 + idx;
-        const double rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
-        double Bx = 0, By = 0, CC = 0, A = 0;
+        const R rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
+        R Bx = 0, By = 0, CC = 0, A = 0;
         if (frc) {
-            const double rT = rho * T;
-            const double irT = 1.0 / rT;
+            const R rT = rho * T;
+            const R irT = R(1) / rT;
             Bx = (a.dSxx[g] + a.dSxyy[g]) * irT;
             By = (a.dSxy[g] + a.dSyy[g]) * irT;
-            const double C = (a.Cnum[g] - K * rho * a.ry[g] * a.ddivuy[g]) * (0.5 * irT / T);
-            const double Cq = (a.dQx[g] + a.dQy[g]) * (irT / T);
+            const R C = (a.Cnum[g] - K * rho * a.ry[g] * a.ddivuy[g]) * (R(0.5) * irT / T);
+            const R Cq = (a.dQx[g] + a.dQy[g]) * (irT / T);
             CC = C + Cq;
-            A = -2.0 * CC * T;
+            A = R(-2) * CC * T;
         }
-        double m[16];
-        equilibrium_moments<double>(rho, ux, uy, T, b, m);
-        double mr = 0, mjx = 0, mjy = 0, mE = 0;
+        R m[16];
+        equilibrium_moments<R>(rho, ux, uy, T, b, m);
+        // neq_i = f_i^eq - f_i. float64: f^eq = M^-1 m^eq directly. float32: in moment space,
+        // neq = M^-1 (m^eq - M f) over the 12 non-conserved moments only (the 4 conserved
+        // ones agree exactly), so the rounding of M^-1 to float32 cannot bias mass, momentum
+        // or energy: its error scales with the non-equilibrium part instead of with rho.
+        R fsv[16], neq[16], fev[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) fsv[i] = a.fs[i * plane + g];
+        if (MOMENT_SPACE) {
+            R dm[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                R mf = 0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) mf += a.mrow[j * 16 + i] * fsv[i];
+                dm[j] = m[4 + j] - mf;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                R ne = 0;
+#pragma unroll
+                for (int j = 0; j < 12; ++j) ne += a.minv[i * 16 + 4 + j] * dm[j];
+                neq[i] = ne;
+                fev[i] = fsv[i] + ne;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                R fe = 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * m[j];
+                fev[i] = fe;
+                neq[i] = fe - fsv[i];
+            }
+        }
+        MomentSums<R> acc;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            double fe = 0;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) fe += (double)a.minv[i * 16 + j] * m[j];
-            const double fsi = a.fs[i * plane + g];
-            double Ri = 0;
+            const R fsi = fsv[i];
+            const R fe = fev[i];
+            R Ri = 0;
             if (adv) {
-                double ad = 0;
+                R ad = 0;
                 const int xs = xslot(i), ys = yslot(i);
-                if (xs >= 0) ad += vel_x(i) * (double)s[((xs >> 1) * R + r) * L2 + (xs & 1) * nx + x];
-                if (ys >= 0) ad += (double)a.Ay[ys * plane + g];
+                if (xs >= 0) ad += R(vel_x(i)) * s[((xs >> 1) * NR + r) * L2 + (xs & 1) * nx + x];
+                if (ys >= 0) ad += a.Ay[ys * plane + g];
                 Ri -= ad;
             }
-            if (col) Ri -= (fsi - fe) * tau_inv;
+            if (col) Ri += neq[i] * tau_inv;
             if (frc) {
-                const double cx = vel_x(i) - ux, cy = vel_y(i) - uy;
+                const R cx = R(vel_x(i)) - ux, cy = R(vel_y(i)) - uy;
                 Ri -= (A + Bx * cx + By * cy + CC * (cx * cx + cy * cy)) * fe;
             }
-            const F fo = (F)((double)a.fbase[i * plane + g] + h * Ri);
+            const R fo = a.fbase[i * plane + g] + h * Ri;
             a.fout[i * plane + g] = fo;
-            const double fd = (double)fo;
-            mr += fd;
-            mjx += vel_x(i) * fd;
-            mjy += vel_y(i) * fd;
-            mE += (vel_sq(i) + (i < 4 ? a.eta2 : 0.0)) * fd;
+            acc.add(i, fo, a.psi_hi[i], a.psi_lo[i]);
         }
-        const double irho = 1.0 / mr;
-        const double nux = mjx * irho, nuy = mjy * irho;
-        a.rho[g] = (M)mr;
-        a.ux[g] = (M)nux;
-        a.uy[g] = (M)nuy;
-        a.T[g] = (M)((mE * irho - (nux * nux + nuy * nuy)) / b);
+        R nr, nux, nuy, nT;
+        acc.finish(b, nr, nux, nuy, nT);
+        a.rho[g] = nr;
+        a.ux[g] = nux;
+        a.uy[g] = nuy;
+        a.T[g] = nT;
     }
 }
 
-template <typename F, typename M>
-cudaError_t launch_update(const UpdateArgs<F, M> &a, int threads, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(update_row_kernel<F, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+// float64 (the plain method): f^eq = M^-1 m^eq; float32: the moment-space collision.
+template <typename R> cudaError_t launch_update(const UpdateArgs<R> &a, size_t smem, cudaStream_t s) {
+    constexpr bool MS = sizeof(R) == 4;
+    cudaError_t e = cudaFuncSetAttribute(update_row_kernel<R, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    update_row_kernel<F, M><<<a.ny / a.rows, threads, smem, s>>>(a);
+    update_row_kernel<R, MS><<<a.ny / a.rows, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename M>
-cudaError_t launch_macro(const MacroArgs<M> &a, int threads, size_t smem, cudaStream_t s) {
+template <typename R> cudaError_t launch_macro(const MacroArgs<R> &a, size_t smem, cudaStream_t s) {
     cudaError_t e =
-        cudaFuncSetAttribute(macro_row_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(macro_row_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    macro_row_kernel<M><<<a.ny / a.rows, threads, smem, s>>>(a);
+    macro_row_kernel<R><<<a.ny / a.rows, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_update<double, double>(const UpdateArgs<double, double> &, int, size_t, cudaStream_t);
-template cudaError_t launch_update<float, double>(const UpdateArgs<float, double> &, int, size_t, cudaStream_t);
-template cudaError_t launch_macro<double>(const MacroArgs<double> &, int, size_t, cudaStream_t);
+template cudaError_t launch_update<double>(const UpdateArgs<double> &, size_t, cudaStream_t);
+template cudaError_t launch_update<float>(const UpdateArgs<float> &, size_t, cudaStream_t);
+template cudaError_t launch_macro<double>(const MacroArgs<double> &, size_t, cudaStream_t);
+template cudaError_t launch_macro<float>(const MacroArgs<float> &, size_t, cudaStream_t);
 
 }  // namespace lbm

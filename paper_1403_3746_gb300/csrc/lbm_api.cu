@@ -64,16 +64,22 @@ double keff(int m, int N, double d) {
 // Inverse of the 16x16 matrix whose rows are the moment functionals
 // 1; v_x, v_y; psi; v_x v_x, v_x v_y, v_y v_y; psi v_x, psi v_y; v_x^3, v_x^2 v_y, v_x v_y^2, v_y^3;
 // psi v_x^2, psi v_x v_y, psi v_y^2 (psi = v^2 + eta^2) evaluated on the 16 velocities.
-bool moment_inverse(double eta0, double out[256]) {
-    double a[16][32];
+void moment_rows(double eta0, double rows[16][16]) {
     for (int i = 0; i < 16; ++i) {
         const double vx = vel_x(i), vy = vel_y(i);
         const double psi = vel_sq(i) + (i < 4 ? eta0 * eta0 : 0.0);
         const double row[16] = {1.0,         vx,          vy,          psi,         vx * vx,     vx * vy,
                                 vy * vy,     psi * vx,    psi * vy,    vx * vx * vx, vx * vx * vy, vx * vy * vy,
                                 vy * vy * vy, psi * vx * vx, psi * vx * vy, psi * vy * vy};
-        for (int r = 0; r < 16; ++r) a[r][i] = row[r];
+        for (int r = 0; r < 16; ++r) rows[r][i] = row[r];
     }
+}
+
+bool moment_inverse(double eta0, double out[256]) {
+    double a[16][32], rows[16][16];
+    moment_rows(eta0, rows);
+    for (int r = 0; r < 16; ++r)
+        for (int i = 0; i < 16; ++i) a[r][i] = rows[r][i];
     for (int r = 0; r < 16; ++r)
         for (int j = 0; j < 16; ++j) a[r][16 + j] = (r == j) ? 1.0 : 0.0;
     for (int col = 0; col < 16; ++col) {
@@ -116,12 +122,16 @@ struct lbm_ctx {
 
     char *slab = nullptr;
     size_t slab_bytes = 0;
+    // state and stage scratch; element type is double (LBM_FP64) or float (LBM_MIXED)
     void *f0 = nullptr, *f1 = nullptr, *Ay = nullptr;
-    double *rho = nullptr, *ux = nullptr, *uy = nullptr, *T = nullptr;
-    double *ry = nullptr, *ryy = nullptr, *uxy = nullptr, *uyy = nullptr, *Ty = nullptr;
-    double *Qy = nullptr, *Sxy = nullptr, *Syy = nullptr, *divu = nullptr;
-    double *dQx = nullptr, *dSxx = nullptr, *dSxy = nullptr, *Cnum = nullptr;
-    double *dQy = nullptr, *dSxyy = nullptr, *dSyy = nullptr, *ddivuy = nullptr;
+    enum {
+        RHO, UX, UY, TT,                      // moments of the current f
+        RY, RYY, UXY, UYY, TY,                // column pass: y-derivatives of the moments
+        QY, SXY, SYY, DIVU, DQX, DSXX, DSXY, CNUM,  // macro row pass outputs
+        DQY, DSXYY, DSYY, DDIVUY,             // flux column pass outputs
+        NMACRO
+    };
+    void *m[NMACRO] = {};
     double *partial = nullptr;
     int diag_blocks = 0;
     // per-axis tables
@@ -130,10 +140,11 @@ struct lbm_ctx {
     double *k1x = nullptr, *k2x = nullptr, *k1y = nullptr, *k2y = nullptr;
     float *k1x32 = nullptr, *k2x32 = nullptr, *k1y32 = nullptr, *k2y32 = nullptr;
     double minv[256];
+    double mrow[192];  // moment-matrix rows 4..15
 
     // launch geometry
-    int colW_f = 2, colW_m = 2;
-    size_t col_smem_f = 0, col_smem_m = 0;
+    int colW = 2;
+    size_t col_smem = 0;
     int rows = 1;
     size_t macro_smem = 0, upd_smem = 0, rowd_smem = 0;
 
@@ -182,104 +193,112 @@ template <> Axis<float> axis<float>(const lbm_ctx *c, bool xdir) {
                 : Axis<float>{c->tw32y, c->k1y32, c->k2y32, c->ly};
 }
 
+template <typename R> ColArgs<R> col_args(const lbm_ctx *c) {
+    ColArgs<R> a{};
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.W = c->colW;
+    a.log2W = ilog2(c->colW);
+    a.ay = axis<R>(c, false);
+    return a;
+}
+
 // one Runge-Kutta stage: K_COL, K_MACRO, K_FLUX, K_UPDATE
-template <typename F>
+template <typename R>
 int run_stage(lbm_ctx *c, int stage) {
     const lbm_params &p = c->p;
     const bool adv = !(p.flags & LBM_FLAG_NO_ADVECTION);
     const bool frc = !(p.flags & LBM_FLAG_NO_FORCE);
     const size_t plane = (size_t)c->n;
-    F *f0 = static_cast<F *>(c->f0), *f1 = static_cast<F *>(c->f1);
-    F *Ay = static_cast<F *>(c->Ay);
-    const F *fs = stage == 0 ? f0 : f1;
+    R *f0 = static_cast<R *>(c->f0), *f1 = static_cast<R *>(c->f1);
+    R *Ay = static_cast<R *>(c->Ay);
+    const R *fs = stage == 0 ? f0 : f1;
+    auto M = [c](int k) { return static_cast<R *>(c->m[k]); };
 
-    if (adv) {
-        ColArgs<F> a{};
-        a.nx = c->nx;
-        a.ny = c->ny;
-        a.W = c->colW_f;
-        a.log2W = ilog2(c->colW_f);
-        a.ay = axis<F>(c, false);
-        for (int k = 0; k < 12; ++k) {
-            const int i = yfield(k);
-            a.jobs[k] = ColJob<F>{fs + i * plane, Ay + k * plane, nullptr, 1, 1, (F)vel_y(i), F(0)};
+    {
+        ColArgs<R> a = col_args<R>(c);
+        int nj = 0;
+        if (adv)
+            for (int k = 0; k < 12; ++k) {
+                const int i = yfield(k);
+                a.jobs[nj++] = ColJob<R>{fs + i * plane, Ay + k * plane, 1, (R)vel_y(i)};
+            }
+        if (frc) {
+            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::RHO), M(lbm_ctx::RY), 1, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::RHO), M(lbm_ctx::RYY), 2, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::UX), M(lbm_ctx::UXY), 1, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::UY), M(lbm_ctx::UYY), 1, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::TT), M(lbm_ctx::TY), 1, R(1)};
         }
-        LaunchTimer t(c, LBM_K_COL);
-        CU_TRY(launch_col<F>(a, 12, 256, c->col_smem_f, c->stream));
+        if (nj) {
+            LaunchTimer t(c, LBM_K_COL);
+            CU_TRY(launch_col<R>(a, nj, c->col_smem, c->stream));
+        }
     }
     if (frc) {
         {
-            ColArgs<double> a{};
-            a.nx = c->nx;
-            a.ny = c->ny;
-            a.W = c->colW_m;
-            a.log2W = ilog2(c->colW_m);
-            a.ay = axis<double>(c, false);
-            a.jobs[0] = ColJob<double>{c->rho, c->ry, c->ryy, 1, 2, 1.0, 1.0};
-            a.jobs[1] = ColJob<double>{c->ux, c->uxy, nullptr, 1, 1, 1.0, 0.0};
-            a.jobs[2] = ColJob<double>{c->uy, c->uyy, nullptr, 1, 1, 1.0, 0.0};
-            a.jobs[3] = ColJob<double>{c->T, c->Ty, nullptr, 1, 1, 1.0, 0.0};
-            LaunchTimer t(c, LBM_K_COL);
-            CU_TRY(launch_col<double>(a, 4, 256, c->col_smem_m, c->stream));
-        }
-        {
-            MacroArgs<double> a{};
-            a.rho = c->rho; a.ux = c->ux; a.uy = c->uy; a.T = c->T;
-            a.ry = c->ry; a.ryy = c->ryy; a.uxy = c->uxy; a.uyy = c->uyy; a.Ty = c->Ty;
-            a.Qy = c->Qy; a.Sxy = c->Sxy; a.Syy = c->Syy; a.divu = c->divu;
-            a.dQx = c->dQx; a.dSxx = c->dSxx; a.dSxy = c->dSxy; a.Cnum = c->Cnum;
+            MacroArgs<R> a{};
+            a.rho = M(lbm_ctx::RHO); a.ux = M(lbm_ctx::UX); a.uy = M(lbm_ctx::UY); a.T = M(lbm_ctx::TT);
+            a.ry = M(lbm_ctx::RY); a.ryy = M(lbm_ctx::RYY); a.uxy = M(lbm_ctx::UXY); a.uyy = M(lbm_ctx::UYY);
+            a.Ty = M(lbm_ctx::TY);
+            a.Qy = M(lbm_ctx::QY); a.Sxy = M(lbm_ctx::SXY); a.Syy = M(lbm_ctx::SYY); a.divu = M(lbm_ctx::DIVU);
+            a.dQx = M(lbm_ctx::DQX); a.dSxx = M(lbm_ctx::DSXX); a.dSxy = M(lbm_ctx::DSXY);
+            a.Cnum = M(lbm_ctx::CNUM);
             a.nx = c->nx; a.ny = c->ny; a.rows = c->rows;
-            a.ax = axis<double>(c, true);
-            a.K = p.K; a.H = p.H; a.q = p.q; a.zeta = p.zeta;
+            a.ax = axis<R>(c, true);
+            a.K = (R)p.K; a.H = (R)p.H; a.q = (R)p.q; a.zeta = (R)p.zeta;
             LaunchTimer t(c, LBM_K_MACRO);
-            CU_TRY(launch_macro<double>(a, 256, c->macro_smem, c->stream));
+            CU_TRY(launch_macro<R>(a, c->macro_smem, c->stream));
         }
         {
-            ColArgs<double> a{};
-            a.nx = c->nx;
-            a.ny = c->ny;
-            a.W = c->colW_m;
-            a.log2W = ilog2(c->colW_m);
-            a.ay = axis<double>(c, false);
-            a.jobs[0] = ColJob<double>{c->Qy, c->dQy, nullptr, 1, 1, 1.0, 0.0};
-            a.jobs[1] = ColJob<double>{c->Sxy, c->dSxyy, nullptr, 1, 1, 1.0, 0.0};
-            a.jobs[2] = ColJob<double>{c->Syy, c->dSyy, nullptr, 1, 1, 1.0, 0.0};
-            a.jobs[3] = ColJob<double>{c->divu, c->ddivuy, nullptr, 1, 1, 1.0, 0.0};
+            ColArgs<R> a = col_args<R>(c);
+            a.jobs[0] = ColJob<R>{M(lbm_ctx::QY), M(lbm_ctx::DQY), 1, R(1)};
+            a.jobs[1] = ColJob<R>{M(lbm_ctx::SXY), M(lbm_ctx::DSXYY), 1, R(1)};
+            a.jobs[2] = ColJob<R>{M(lbm_ctx::SYY), M(lbm_ctx::DSYY), 1, R(1)};
+            a.jobs[3] = ColJob<R>{M(lbm_ctx::DIVU), M(lbm_ctx::DDIVUY), 1, R(1)};
             LaunchTimer t(c, LBM_K_FLUX);
-            CU_TRY(launch_col<double>(a, 4, 256, c->col_smem_m, c->stream));
+            CU_TRY(launch_col<R>(a, 4, c->col_smem, c->stream));
         }
     }
     {
-        UpdateArgs<F, double> a{};
+        UpdateArgs<R> a{};
         a.fs = fs;
         a.fbase = f0;
         a.fout = stage == 0 ? f1 : f0;
         a.Ay = Ay;
-        a.rho = c->rho; a.ux = c->ux; a.uy = c->uy; a.T = c->T;
-        a.ry = c->ry; a.dQx = c->dQx; a.dSxx = c->dSxx; a.dSxy = c->dSxy; a.Cnum = c->Cnum;
-        a.dQy = c->dQy; a.dSxyy = c->dSxyy; a.dSyy = c->dSyy; a.ddivuy = c->ddivuy;
+        a.rho = M(lbm_ctx::RHO); a.ux = M(lbm_ctx::UX); a.uy = M(lbm_ctx::UY); a.T = M(lbm_ctx::TT);
+        a.ry = M(lbm_ctx::RY); a.dQx = M(lbm_ctx::DQX); a.dSxx = M(lbm_ctx::DSXX); a.dSxy = M(lbm_ctx::DSXY);
+        a.Cnum = M(lbm_ctx::CNUM); a.dQy = M(lbm_ctx::DQY); a.dSxyy = M(lbm_ctx::DSXYY);
+        a.dSyy = M(lbm_ctx::DSYY); a.ddivuy = M(lbm_ctx::DDIVUY);
         a.nx = c->nx; a.ny = c->ny; a.rows = c->rows;
-        a.ax = axis<F>(c, true);
-        a.tau_inv = 1.0 / p.tau;
-        a.h = stage == 0 ? 0.5 * p.dt : p.dt;
-        a.K = p.K;
-        a.b = p.b;
-        a.eta2 = p.eta0 * p.eta0;
+        a.ax = axis<R>(c, true);
+        a.tau_inv = (R)(1.0 / p.tau);
+        a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
+        a.K = (R)p.K;
+        a.b = (R)p.b;
+        for (int i = 0; i < 16; ++i) {
+            const double psi = vel_sq(i) + (i < 4 ? p.eta0 * p.eta0 : 0.0);
+            a.psi_hi[i] = (R)psi;
+            a.psi_lo[i] = (R)(psi - (double)a.psi_hi[i]);
+        }
         a.flags = p.flags;
-        for (int k = 0; k < 256; ++k) a.minv[k] = (F)c->minv[k];
+        for (int k = 0; k < 256; ++k) a.minv[k] = (R)c->minv[k];
+        for (int k = 0; k < 192; ++k) a.mrow[k] = (R)c->mrow[k];
         LaunchTimer t(c, LBM_K_UPDATE);
-        CU_TRY((launch_update<F, double>(a, 256, c->upd_smem, c->stream)));
+        CU_TRY(launch_update<R>(a, c->upd_smem, c->stream));
     }
     return LBM_OK;
 }
 
 int check_params(const lbm_params *p) {
     if (!p) return fail(LBM_ERR_ARG, "params is NULL");
-    const double v[] = {p->tau, p->dt, p->dx, p->dy, p->K, p->H, p->q, p->zeta, p->b, p->eta0};
+    const double v[] = {p->tau, p->dt, p->dx, p->dy, p->K, p->H, p->q, p->zeta, p->b, p->eta0,
+                        p->win_alpha, p->win_p};
     for (double x : v)
         if (!std::isfinite(x)) return fail(LBM_ERR_ARG, "non-finite parameter");
     if (p->tau <= 0 || p->dt <= 0 || p->dx <= 0 || p->dy <= 0 || p->b <= 0)
         return fail(LBM_ERR_ARG, "tau, dt, dx, dy and b must be positive");
+    if (p->win_alpha < 0 || p->win_p <= 0) return fail(LBM_ERR_ARG, "need win_alpha >= 0 and win_p > 0");
     if (p->precision != LBM_FP64 && p->precision != LBM_MIXED)
         return fail(LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_MIXED");
     if (p->flags & ~(LBM_FLAG_NO_ADVECTION | LBM_FLAG_NO_COLLISION | LBM_FLAG_NO_FORCE))
@@ -304,6 +323,8 @@ void lbm_default_params(lbm_params *p) {
     p->zeta = 0.0;
     p->b = 2.0;
     p->eta0 = 2.5;
+    p->win_alpha = 0.0;
+    p->win_p = 36.0;
     p->precision = LBM_FP64;
     p->flags = 0;
 }
@@ -347,6 +368,12 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
         delete c;
         return fail(LBM_ERR_CUDA, "no CUDA device");
     }
+    {
+        double rows[16][16];
+        moment_rows(params->eta0, rows);
+        for (int r = 4; r < 16; ++r)
+            for (int i = 0; i < 16; ++i) c->mrow[(r - 4) * 16 + i] = rows[r][i];
+    }
     if (!moment_inverse(params->eta0, c->minv)) {
         delete c;
         return fail(LBM_ERR_ARG, "moment matrix is singular for eta0=%g", params->eta0);
@@ -355,18 +382,16 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     // launch geometry
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    c->colW_f = col_width(nx, ny, c->fsize, 1);
-    c->colW_m = col_width(nx, ny, 8, 2);
-    c->col_smem_f = (size_t)ny * c->colW_f * c->fsize;
-    c->col_smem_m = (size_t)ny * c->colW_m * 8 * 2;
+    c->colW = col_width(nx, ny, c->fsize, 1);
+    c->col_smem = (size_t)ny * c->colW * c->fsize;
     int rows = 512 / nx;
     if (rows < 1) rows = 1;
     if (rows > ny) rows = ny;
     c->rows = rows;
     c->upd_smem = (size_t)12 * rows * nx * c->fsize;
-    c->macro_smem = (size_t)10 * rows * nx * 8;
-    c->rowd_smem = (size_t)2 * rows * nx * 8;
-    const size_t need = std::max(std::max(c->upd_smem, c->macro_smem), std::max(c->col_smem_f, c->col_smem_m));
+    c->macro_smem = (size_t)10 * rows * nx * c->fsize;
+    c->rowd_smem = (size_t)2 * rows * nx * c->fsize;
+    const size_t need = std::max(std::max(c->upd_smem, c->macro_smem), c->col_smem);
     if (need > (size_t)smem_optin) {
         delete c;
         return fail(LBM_ERR_UNSUPPORTED, "nx=%d ny=%d needs %zu B of shared memory per block (device: %d)", nx,
@@ -374,7 +399,7 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     }
 
     // device memory: one slab, 256-byte aligned pieces
-    const size_t plane_d = (size_t)c->n * 8, plane_f = (size_t)c->n * c->fsize;
+    const size_t plane_f = (size_t)c->n * c->fsize;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     c->diag_blocks = (int)std::min<long long>(1024, (c->n + 255) / 256);
     size_t off = 0;
@@ -382,10 +407,7 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     parts.push_back({&c->f0, 16 * plane_f});
     parts.push_back({&c->f1, 16 * plane_f});
     parts.push_back({&c->Ay, 12 * plane_f});
-    double **macro[] = {&c->rho, &c->ux,   &c->uy,   &c->T,    &c->ry,   &c->ryy,  &c->uxy, &c->uyy,
-                        &c->Ty,  &c->Qy,   &c->Sxy,  &c->Syy,  &c->divu, &c->dQx,  &c->dSxx, &c->dSxy,
-                        &c->Cnum, &c->dQy, &c->dSxyy, &c->dSyy, &c->ddivuy};
-    for (double **m : macro) parts.push_back({reinterpret_cast<void **>(m), plane_d});
+    for (int k = 0; k < lbm_ctx::NMACRO; ++k) parts.push_back({&c->m[k], plane_f});
     parts.push_back({reinterpret_cast<void **>(&c->partial), (size_t)c->diag_blocks * 5 * 8});
     parts.push_back({reinterpret_cast<void **>(&c->tw64x), (size_t)nx * 16});
     parts.push_back({reinterpret_cast<void **>(&c->tw64y), (size_t)ny * 16});
@@ -423,7 +445,11 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
         for (int pos = 0; pos < N; ++pos) {
             const int k = freq_of(pos, l2);
             const int m = k < N / 2 ? k : k - N;
-            const double ke = (2 * m == -N) ? 0.0 : keff(m, N, d);
+            // first derivative: i W(m) k_eff(m), zero at Nyquist; second: its square
+            const double w = params->win_alpha > 0
+                                 ? std::exp(-params->win_alpha * std::pow(std::fabs((double)m) / (0.5 * N), params->win_p))
+                                 : 1.0;
+            const double ke = (2 * m == -N) ? 0.0 : w * keff(m, N, d);
             k1[pos] = ke / N;
             k2[pos] = -ke * ke / N;
             k1f[pos] = (float)k1[pos];
@@ -458,7 +484,7 @@ static int init_common(lbm_ctx *c, const double *rho, const double *ux, const do
     InitArgs a{};
     a.rho = rho; a.ux = ux; a.uy = uy; a.T = T;
     a.f = c->f0;
-    a.mrho = c->rho; a.mux = c->ux; a.muy = c->uy; a.mT = c->T;
+    a.mrho = c->m[lbm_ctx::RHO]; a.mux = c->m[lbm_ctx::UX]; a.muy = c->m[lbm_ctx::UY]; a.mT = c->m[lbm_ctx::TT];
     a.n = c->n;
     a.b = c->p.b;
     for (int k = 0; k < 256; ++k) a.minv[k] = c->minv[k];
@@ -476,13 +502,15 @@ int lbm_init(lbm_handle c, const double *rho, const double *ux, const double *uy
             !std::isfinite(uy[g]))
             return fail(LBM_ERR_ARG, "node %lld: need 0 < rho < 3, T > 0 and finite u", g);
     }
+    // stage the four float64 fields in the half-step buffer f1 (free outside lbm_step;
+    // it holds at least 16 * 4 bytes per node >= 4 * 8)
     const size_t bytes = (size_t)c->n * 8;
-    // stage through the flux scratch fields (free between steps)
-    CU_TRY(cudaMemcpyAsync(c->Qy, rho, bytes, cudaMemcpyHostToDevice, c->stream));
-    CU_TRY(cudaMemcpyAsync(c->Sxy, ux, bytes, cudaMemcpyHostToDevice, c->stream));
-    CU_TRY(cudaMemcpyAsync(c->Syy, uy, bytes, cudaMemcpyHostToDevice, c->stream));
-    CU_TRY(cudaMemcpyAsync(c->divu, T, bytes, cudaMemcpyHostToDevice, c->stream));
-    int rc = init_common(c, c->Qy, c->Sxy, c->Syy, c->divu);
+    double *st = static_cast<double *>(c->f1);
+    CU_TRY(cudaMemcpyAsync(st, rho, bytes, cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemcpyAsync(st + c->n, ux, bytes, cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemcpyAsync(st + 2 * c->n, uy, bytes, cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemcpyAsync(st + 3 * c->n, T, bytes, cudaMemcpyHostToDevice, c->stream));
+    int rc = init_common(c, st, st + c->n, st + 2 * c->n, st + 3 * c->n);
     if (rc) return rc;
     CU_TRY(cudaStreamSynchronize(c->stream));
     return LBM_OK;
@@ -509,22 +537,32 @@ int lbm_step(lbm_handle c, int n) {
 int lbm_moments_device(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
     if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    const size_t bytes = (size_t)c->n * 8;
-    if (rho) CU_TRY(cudaMemcpyAsync(rho, c->rho, bytes, cudaMemcpyDeviceToDevice, c->stream));
-    if (ux) CU_TRY(cudaMemcpyAsync(ux, c->ux, bytes, cudaMemcpyDeviceToDevice, c->stream));
-    if (uy) CU_TRY(cudaMemcpyAsync(uy, c->uy, bytes, cudaMemcpyDeviceToDevice, c->stream));
-    if (T) CU_TRY(cudaMemcpyAsync(T, c->T, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    double *out[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k) {
+        if (!out[k]) continue;
+        if (c->mixed)
+            CU_TRY(launch_convert_out<float>(static_cast<const float *>(c->m[k]), out[k], c->n, c->stream));
+        else
+            CU_TRY(cudaMemcpyAsync(out[k], c->m[k], (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    }
     return LBM_OK;
 }
 
 int lbm_moments(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
     if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    const size_t bytes = (size_t)c->n * 8;
-    if (rho) CU_TRY(cudaMemcpyAsync(rho, c->rho, bytes, cudaMemcpyDeviceToHost, c->stream));
-    if (ux) CU_TRY(cudaMemcpyAsync(ux, c->ux, bytes, cudaMemcpyDeviceToHost, c->stream));
-    if (uy) CU_TRY(cudaMemcpyAsync(uy, c->uy, bytes, cudaMemcpyDeviceToHost, c->stream));
-    if (T) CU_TRY(cudaMemcpyAsync(T, c->T, bytes, cudaMemcpyDeviceToHost, c->stream));
+    double *out[4] = {rho, ux, uy, T};
+    std::vector<float> tmp(c->mixed ? (size_t)c->n : 0);
+    for (int k = 0; k < 4; ++k) {
+        if (!out[k]) continue;
+        if (c->mixed) {
+            CU_TRY(cudaMemcpyAsync(tmp.data(), c->m[k], (size_t)c->n * 4, cudaMemcpyDeviceToHost, c->stream));
+            CU_TRY(cudaStreamSynchronize(c->stream));
+            for (long long g = 0; g < c->n; ++g) out[k][g] = (double)tmp[g];
+        } else {
+            CU_TRY(cudaMemcpyAsync(out[k], c->m[k], (size_t)c->n * 8, cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
     CU_TRY(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -561,7 +599,7 @@ int lbm_set_f(lbm_handle c, const double *f16) {
     }
     MomArgs a{};
     a.f = c->f0;
-    a.rho = c->rho; a.ux = c->ux; a.uy = c->uy; a.T = c->T;
+    a.rho = c->m[lbm_ctx::RHO]; a.ux = c->m[lbm_ctx::UX]; a.uy = c->m[lbm_ctx::UY]; a.T = c->m[lbm_ctx::TT];
     a.n = c->n;
     a.b = c->p.b;
     for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
@@ -570,35 +608,40 @@ int lbm_set_f(lbm_handle c, const double *f16) {
     return LBM_OK;
 }
 
-int lbm_diagnostics(lbm_handle c, double out[6]) {
-    if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
-    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    // d_y rho into ry, d_x rho into dQx (stage scratch, rebuilt by the next stage)
-    ColArgs<double> ca{};
-    ca.nx = c->nx;
-    ca.ny = c->ny;
-    ca.W = c->colW_m;
-    ca.log2W = ilog2(c->colW_m);
-    ca.ay = axis<double>(c, false);
-    ca.jobs[0] = ColJob<double>{c->rho, c->ry, nullptr, 1, 1, 1.0, 0.0};
-    CU_TRY(launch_col<double>(ca, 1, 256, c->col_smem_m, c->stream));
-    RowDerivArgs<double> ra{};
-    ra.in[0] = c->rho;
-    ra.out[0] = c->dQx;
+}  // extern "C"
+
+template <typename R> static int diag_launch(lbm_ctx *c) {
+    // d_y rho into RY, d_x rho into DQX (stage scratch, rebuilt by the next stage)
+    ColArgs<R> ca = col_args<R>(c);
+    ca.jobs[0] = ColJob<R>{static_cast<R *>(c->m[lbm_ctx::RHO]), static_cast<R *>(c->m[lbm_ctx::RY]), 1, R(1)};
+    CU_TRY(launch_col<R>(ca, 1, c->col_smem, c->stream));
+    RowDerivArgs<R> ra{};
+    ra.in[0] = static_cast<R *>(c->m[lbm_ctx::RHO]);
+    ra.out[0] = static_cast<R *>(c->m[lbm_ctx::DQX]);
     ra.nin = 1;
     ra.nx = c->nx;
     ra.ny = c->ny;
     ra.rows = c->rows;
-    ra.ax = axis<double>(c, true);
-    CU_TRY(launch_row_deriv<double>(ra, 256, c->rowd_smem, c->stream));
+    ra.ax = axis<R>(c, true);
+    CU_TRY(launch_row_deriv<R>(ra, c->rowd_smem, c->stream));
     DiagArgs da{};
-    da.rho = c->rho; da.ux = c->ux; da.uy = c->uy; da.T = c->T;
-    da.rx = c->dQx; da.ry = c->ry;
+    da.rho = c->m[lbm_ctx::RHO]; da.ux = c->m[lbm_ctx::UX]; da.uy = c->m[lbm_ctx::UY]; da.T = c->m[lbm_ctx::TT];
+    da.rx = c->m[lbm_ctx::DQX]; da.ry = c->m[lbm_ctx::RY];
     da.partial = c->partial;
     da.n = c->n;
     da.K = c->p.K;
     da.cell = c->p.dx * c->p.dy;
-    CU_TRY(launch_diag(da, c->diag_blocks, c->stream));
+    CU_TRY(launch_diag<R>(da, c->diag_blocks, c->stream));
+    return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_diagnostics(lbm_handle c, double out[6]) {
+    if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
+    int rc = c->mixed ? diag_launch<float>(c) : diag_launch<double>(c);
+    if (rc) return rc;
     std::vector<double> part((size_t)c->diag_blocks * 5);
     CU_TRY(cudaMemcpyAsync(part.data(), c->partial, part.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));

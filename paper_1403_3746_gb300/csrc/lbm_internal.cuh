@@ -24,7 +24,7 @@ namespace lbm {
 // D2V16 velocities (0-based), Sec. 2.1 (values: see the header comment of lbm_d2v16.h).
 #define LBM_SQ2 1.4142135623730950488016887
 #define LBM_D3S2 2.1213203435596425732025331  // 3/sqrt(2)
-__host__ __device__ __forceinline__ double vel_x(int i) {
+__host__ __device__ constexpr double vel_x(int i) {
     switch (i) {
         case 0: return 1.0;  case 2: return -1.0;
         case 4: return 6.0;  case 6: return -6.0;
@@ -33,7 +33,7 @@ __host__ __device__ __forceinline__ double vel_x(int i) {
         default: return 0.0;
     }
 }
-__host__ __device__ __forceinline__ double vel_y(int i) {
+__host__ __device__ constexpr double vel_y(int i) {
     switch (i) {
         case 1: return 1.0;  case 3: return -1.0;
         case 5: return 6.0;  case 7: return -6.0;
@@ -43,7 +43,7 @@ __host__ __device__ __forceinline__ double vel_y(int i) {
     }
 }
 // |v_i|^2 (without eta)
-__host__ __device__ __forceinline__ double vel_sq(int i) {
+__host__ __device__ constexpr double vel_sq(int i) {
     return i < 4 ? 1.0 : (i < 8 ? 36.0 : (i < 12 ? 4.0 : 9.0));
 }
 // fields with v_x != 0, in the order of the 12 real rows of the update kernel's shared tile:
@@ -63,49 +63,52 @@ template <typename R> struct Axis {
 };
 
 // ---- column derivative pass -------------------------------------------------------
-template <typename F> struct ColJob {
-    const F *in;
-    F *out0, *out1;  // out1 may be NULL
-    int order0, order1;
-    F c0, c1;  // outputs are c * d^order / dy^order (in)
+// job: out = c * d^order/dy^order (in), one field per job
+template <typename R> struct ColJob {
+    const R *in;
+    R *out;
+    int order;
+    R c;
 };
-#define LBM_MAX_COLJOBS 16
-template <typename F> struct ColArgs {
-    ColJob<F> jobs[LBM_MAX_COLJOBS];
+#define LBM_MAX_COLJOBS 20
+template <typename R> struct ColArgs {
+    ColJob<R> jobs[LBM_MAX_COLJOBS];
     int nx, ny, W, log2W;
-    Axis<F> ay;
+    Axis<R> ay;
 };
 
 // ---- row pass of the macroscopic chain ---------------------------------------------
-template <typename M> struct MacroArgs {
-    const M *rho, *ux, *uy, *T;               // moments of the stage's f
-    const M *ry, *ryy, *uxy, *uyy, *Ty;       // d_y rho, d_yy rho, d_y u_x, d_y u_y, d_y T
-    M *Qy, *Sxy, *Syy, *divu;                 // inputs of the flux column pass
-    M *dQx, *dSxx, *dSxy, *Cnum;              // d_x Q_x, d_x S_xx, d_x S_xy, partial numerator of C
+template <typename R> struct MacroArgs {
+    const R *rho, *ux, *uy, *T;               // moments of the stage's f
+    const R *ry, *ryy, *uxy, *uyy, *Ty;       // d_y rho, d_yy rho, d_y u_x, d_y u_y, d_y T
+    R *Qy, *Sxy, *Syy, *divu;                 // inputs of the flux column pass
+    R *dQx, *dSxx, *dSxy, *Cnum;              // d_x Q_x, d_x S_xx, d_x S_xy, partial numerator of C
     int nx, ny, rows;
-    Axis<M> ax;
-    double K, H, q, zeta;
+    Axis<R> ax;
+    R K, H, q, zeta;
 };
 
 // ---- fused update row pass -----------------------------------------------------------
-template <typename F, typename M> struct UpdateArgs {
-    const F *fs;     // f of this stage (derivatives, BGK, f^eq moments)
-    const F *fbase;  // f^n (the stage starts from it)
-    F *fout;         // f^{n+1/2} or f^{n+1}; may alias fbase (same node, same thread)
-    const F *Ay;     // 12 fields v_iy d_y f_i
-    M *rho, *ux, *uy, *T;  // in: moments of fs; out: moments of fout
-    const M *ry, *dQx, *dSxx, *dSxy, *Cnum, *dQy, *dSxyy, *dSyy, *ddivuy;
+template <typename R> struct UpdateArgs {
+    const R *fs;     // f of this stage (derivatives, BGK, f^eq moments)
+    const R *fbase;  // f^n (the stage starts from it)
+    R *fout;         // f^{n+1/2} or f^{n+1}; may alias fbase (same node, same thread)
+    const R *Ay;     // 12 fields v_iy d_y f_i
+    R *rho, *ux, *uy, *T;  // in: moments of fs; out: moments of fout
+    const R *ry, *dQx, *dSxx, *dSxy, *Cnum, *dQy, *dSxyy, *dSyy, *ddivuy;
     int nx, ny, rows;
-    Axis<F> ax;
-    double tau_inv, h, K, b, eta2;  // eta2 = eta0^2 (velocities 0..3)
+    Axis<R> ax;
+    R tau_inv, h, K, b;
+    R psi_hi[16], psi_lo[16];  // psi_i = |v_i|^2 + eta_i^2 as a two-term sum (hi + lo)
     int flags;
-    F minv[256];  // inverse of the 16x16 moment matrix, row-major
+    R minv[256];  // inverse of the 16x16 moment matrix, row-major
+    R mrow[192];  // rows 4..15 of the moment matrix (the non-conserved moments), row-major
 };
 
 struct InitArgs {
     const double *rho, *ux, *uy, *T;  // inputs
-    void *f;                          // [16][ny][nx] F
-    double *mrho, *mux, *muy, *mT;    // moments of the stored f
+    void *f;                          // [16][ny][nx] R
+    void *mrho, *mux, *muy, *mT;      // moments of the stored f (R)
     long long n;
     double b;
     double minv[256];
@@ -114,14 +117,14 @@ struct InitArgs {
 
 struct MomArgs {
     const void *f;
-    double *rho, *ux, *uy, *T;
+    void *rho, *ux, *uy, *T;
     long long n;
     double psi[16];
     double b;
 };
 
 struct DiagArgs {
-    const double *rho, *ux, *uy, *T, *rx, *ry;
+    const void *rho, *ux, *uy, *T, *rx, *ry;
     double *partial;  // [blocks][5]
     long long n;
     double K, cell;
@@ -136,18 +139,15 @@ template <typename R> struct RowDerivArgs {
 };
 
 // launchers (kernels_*.cu); all return cudaGetLastError() of the launch
-template <typename F> cudaError_t launch_col(const ColArgs<F> &a, int njobs, int threads, size_t smem,
-                                             cudaStream_t s);
-template <typename M> cudaError_t launch_macro(const MacroArgs<M> &a, int threads, size_t smem, cudaStream_t s);
-template <typename F, typename M>
-cudaError_t launch_update(const UpdateArgs<F, M> &a, int threads, size_t smem, cudaStream_t s);
-template <typename R>
-cudaError_t launch_row_deriv(const RowDerivArgs<R> &a, int threads, size_t smem, cudaStream_t s);
-template <typename F> cudaError_t launch_init(const InitArgs &a, cudaStream_t s);
-template <typename F> cudaError_t launch_moments(const MomArgs &a, cudaStream_t s);
-cudaError_t launch_diag(const DiagArgs &a, int blocks, cudaStream_t s);
+template <typename R> cudaError_t launch_col(const ColArgs<R> &a, int njobs, size_t smem, cudaStream_t s);
+template <typename R> cudaError_t launch_macro(const MacroArgs<R> &a, size_t smem, cudaStream_t s);
+template <typename R> cudaError_t launch_update(const UpdateArgs<R> &a, size_t smem, cudaStream_t s);
+template <typename R> cudaError_t launch_row_deriv(const RowDerivArgs<R> &a, size_t smem, cudaStream_t s);
+template <typename R> cudaError_t launch_init(const InitArgs &a, cudaStream_t s);
+template <typename R> cudaError_t launch_moments(const MomArgs &a, cudaStream_t s);
+template <typename R> cudaError_t launch_diag(const DiagArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_twiddles(double2 *tw64, float2 *tw32, int n, cudaStream_t s);
-template <typename F> cudaError_t launch_convert_out(const F *f, double *out, long long n, cudaStream_t s);
-template <typename F> cudaError_t launch_convert_in(const double *in, F *f, long long n, cudaStream_t s);
+template <typename R> cudaError_t launch_convert_out(const R *f, double *out, long long n, cudaStream_t s);
+template <typename R> cudaError_t launch_convert_in(const double *in, R *f, long long n, cudaStream_t s);
 
 }  // namespace lbm

@@ -1,8 +1,11 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same
 seeded inputs, element by element.
 
-Error metric (per field, as the distributions f_1..f_4 vanish at rest when b = 2):
-    err = max |x_gpu - x_oracle| / max |x_oracle|
+Error metric, per field:
+    err_i = max |x_gpu - x_oracle| / max(max |x_oracle|, floor)
+The floor is 1% of the largest of the 16 distributions for f_i (f_1..f_4 vanish at rest
+when b = 2, and f^eq = M^-1 m^eq reaches them through cancellation, cond(M) ~ 2e3), and
+1e-3 for the velocity components; 0 otherwise.
 Bound for the FP64 path: 1e-10 after the run's steps (spectral derivatives, the moment
 inversion and the Runge-Kutta stages are evaluated in a different order than the
 oracle's, so results agree to rounding, amplified at most mildly over the steps).
@@ -56,13 +59,22 @@ def run_gpu(fields, steps, **kw):
         return s.get_f(), s.moments()
 
 
-def field_err(a, b):
-    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+def field_err(a, b, floor=0.0):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), floor, 1e-300))
+
+
+def f_errors(fg, fo):
+    floor = 1e-2 * np.max(np.abs(fo))
+    return [field_err(fg[i], fo[i], floor) for i in range(16)]
+
+
+def m_errors(mg, mo):
+    return [field_err(mg[k], mo[k], 1e-3 if k in (1, 2) else 0.0) for k in range(4)]
 
 
 def assert_parity(fg, mg, fo, mo, tol, what=""):
-    errs = [field_err(fg[i], fo[i]) for i in range(16)]
-    merrs = [field_err(mg[k], mo[k]) for k in range(4)]
+    errs, merrs = f_errors(fg, fo), m_errors(mg, mo)
+    print(f"{what}: max f err {max(errs):.3e}, moment errs {', '.join(f'{e:.2e}' for e in merrs)}")
     assert max(errs) <= tol, f"{what}: f errors {errs}"
     assert max(merrs) <= tol, f"{what}: moment errors {merrs}"
 
@@ -91,9 +103,9 @@ def test_init_is_equilibrium_of_the_given_moments():
         m = s.moments()
     d = D2V16(2.5)
     fo = init_feq(d, *fields, oracle.Params())
-    assert max(field_err(f[i], fo[i]) for i in range(16)) <= 1e-13
-    for a, b in zip(m, fields):
-        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b)) + 1e-15
+    # rounding of M^-1 itself (cond ~ 2e3) bounds the agreement at a few 1e-13
+    assert max(f_errors(f, fo)) <= 1e-12
+    assert max(m_errors(m, fields)) <= 1e-12
 
 
 @pytest.mark.parametrize("flags", [
@@ -158,8 +170,9 @@ def test_conservation_and_diagnostics():
         s.step(300)
         d1 = s.diagnostics()
     assert d1["steps"] == 300
-    assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
-    assert abs(d1["px"]) <= 1e-13 * d0["mass"] and abs(d1["py"]) <= 1e-13 * d0["mass"]
+    # sum_i f^eq_i = rho and sum_i I_i = 0 hold to rounding (cond(M) ~ 2e3) at every node
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-12 * d0["mass"]
+    assert abs(d1["px"]) <= 1e-12 * d0["mass"] and abs(d1["py"]) <= 1e-12 * d0["mass"]
 
 
 def test_set_get_roundtrip_and_errors():
@@ -184,3 +197,83 @@ def test_set_get_roundtrip_and_errors():
 def test_unsupported_row_length_in_fp64():
     with pytest.raises(lbm.LbmError, match="unsupported"):
         lbm.Simulation(4096, 8, lib_params())
+
+
+# ---- the FP32-spectral path (LBM_MIXED) against the FP64 oracle -------------------------
+# Bounds are normwise: f against max |f| over all 16 fields, rho and T relative, u as an
+# absolute error (the thermal speed sqrt(T) ~ 1 is the velocity scale). The float32
+# spectral derivative of a field of size |f| carries an error ~ eps32 k_max |f| log2 N,
+# i.e. ~1e-7 |f| per step after the dt v factor.
+MIX = dict(precision=lbm.LBM_MIXED)
+
+
+def mixed_errors(fg, mg, fo, mo):
+    ef = float(np.max(np.abs(fg - fo)) / np.max(np.abs(fo)))
+    er = field_err(mg[0], mo[0])
+    eT = field_err(mg[3], mo[3])
+    eu = float(max(np.max(np.abs(mg[1] - mo[1])), np.max(np.abs(mg[2] - mo[2]))))
+    return ef, er, eu, eT
+
+
+def test_mixed_slab_64_200_steps():
+    fields = slab_fields(64, 64)
+    fo, mo = run_oracle(fields, 200)
+    fg, mg = run_gpu(fields, 200, **MIX)
+    ef, er, eu, eT = mixed_errors(fg, mg, fo, mo)
+    print(f"mixed slab 64^2 x 200: f {ef:.2e}, rho {er:.2e}, |du| {eu:.2e}, T {eT:.2e}")
+    assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
+
+
+def test_mixed_droplet_1024_one_step():
+    # the benchmark workload: droplet R = 128, T = 0.9, phase-separation parameter set
+    T = 0.9
+    rl, rv = oracle.coexistence(T)
+    fields = synthetic.droplet(1024, 1024, 128, rl, rv, T, width=2.0)
+    fo, mo = run_oracle(fields, 1)
+    fg, mg = run_gpu(fields, 1, **MIX)
+    ef, er, eu, eT = mixed_errors(fg, mg, fo, mo)
+    print(f"mixed droplet 1024^2 x 1: f {ef:.2e}, rho {er:.2e}, |du| {eu:.2e}, T {eT:.2e}")
+    assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
+
+
+def test_mixed_conservation():
+    fields = synthetic.spinodal(128, 128, 1.0, 0.01, 0.9, seed=2)
+    with lbm.Simulation(128, 128, lib_params(**MIX)) as s:
+        s.init(*fields)
+        d0 = s.diagnostics()
+        s.step(300)
+        d1 = s.diagnostics()
+    dm = abs(d1["mass"] - d0["mass"]) / d0["mass"]
+    dp = max(abs(d1["px"]), abs(d1["py"])) / d0["mass"]
+    print(f"mixed 128^2 x 300: mass drift {dm:.2e}, momentum {dp:.2e}")
+    assert dm <= 1e-6 and dp <= 1e-6
+
+
+def test_windowed_derivatives_fp64():
+    # the exponential window of the windowed FFT (alpha = 36, p = 36) on both sides
+    fields = slab_fields(64, 32)
+    kw = dict(win_alpha=36.0, win_p=36.0)
+    fo, mo = run_oracle(fields, 20, **kw)
+    fg, mg = run_gpu(fields, 20, **kw)
+    assert_parity(fg, mg, fo, mo, TOL64, "window 64x32 x 20")
+    # the window changes the result (it is not silently ignored)
+    fn, _ = run_oracle(fields, 20)
+    assert max(f_errors(fn, fo)) > 1e-9
+
+
+def test_benchmark_workload_stays_bounded():
+    # 1024^2 droplet at T = 0.9 (phase-separation set), 2000 mixed / 300 FP64 steps:
+    # finite, mass conserved, spurious velocity bounded
+    T = 0.9
+    rl, rv = lbm.maxwell(T)
+    fields = synthetic.droplet(1024, 1024, 128, rl, rv, T, width=2.0)
+    for prec, steps in ((lbm.LBM_MIXED, 2000), (lbm.LBM_FP64, 300)):
+        with lbm.Simulation(1024, 1024, lib_params(precision=prec)) as s:
+            s.init(*fields)
+            d0 = s.diagnostics()
+            s.step(steps)
+            d1 = s.diagnostics()
+        print(f"precision {prec}: {steps} steps, mass drift {abs(d1['mass'] / d0['mass'] - 1):.2e}, "
+              f"umax {d1['umax']:.3e}, energy drift {abs(d1['energy'] / d0['energy'] - 1):.2e}")
+        assert abs(d1["mass"] / d0["mass"] - 1) < 1e-6
+        assert d1["umax"] < 0.1
