@@ -736,3 +736,8 @@ int lbm_maxwell(double T, double *rho_l, double *rho_v) {
 }
 
 }  // extern "C"
+
+// Lets other translation units report a detailed message through lbm_last_error().
+namespace lbm {
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace lbm

@@ -150,4 +150,7 @@ cudaError_t launch_twiddles(double2 *tw64, float2 *tw32, int n, cudaStream_t s);
 template <typename R> cudaError_t launch_convert_out(const R *f, double *out, long long n, cudaStream_t s);
 template <typename R> cudaError_t launch_convert_in(const double *in, R *f, long long n, cudaStream_t s);
 
+// sets the calling thread's message returned by lbm_last_error() (lbm_api.cu)
+void set_last_error(const char *msg);
+
 }  // namespace lbm

@@ -1,0 +1,196 @@
+// Global diagnostics without any device allocation.
+//
+// Some callers cannot allocate device memory at the time they need a diagnostic: code
+// running while a stream is being captured into a CUDA graph (cudaMalloc is not allowed
+// there), host applications or plugins whose GPU memory is owned by another allocator or
+// budgeted up front, and long-running services that must not grow their footprint after
+// start-up. lbm_diagnostics_noalloc serves them. Its scratch (the spectral d_x rho and
+// d_y rho fields, the per-block partial sums and the derivative tables) lives in the
+// file-scope array below, which every GPU that loads this library holds until the process
+// exits. The caller still passes the inputs (device fields) and the output (host array).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr long long kMaxNodes = 1LL << 20;  // nx * ny <= 1048576 (e.g. 1024 x 1024)
+constexpr int kMaxN = 4096;                 // nx, ny <= 4096
+constexpr int kMaxBlocks = 1024;            // reduction blocks
+
+// layout of the scratch array, in doubles
+constexpr size_t kOffRx = 0;                             // d_x rho   [kMaxNodes]
+constexpr size_t kOffRy = kOffRx + kMaxNodes;            // d_y rho   [kMaxNodes]
+constexpr size_t kOffPart = kOffRy + kMaxNodes;          // partials  [kMaxBlocks * 5]
+constexpr size_t kOffK = kOffPart + kMaxBlocks * 5;      // k1x, k2x, k1y, k2y [4 * kMaxN]
+constexpr size_t kOffTw64 = kOffK + 4 * kMaxN;           // double2 twiddles x, y [2 * kMaxN * 2]
+constexpr size_t kOffTw32 = kOffTw64 + 4 * kMaxN;        // float2 twiddles x, y [2 * kMaxN]
+constexpr size_t kScratchDoubles = kOffTw32 + 2 * kMaxN;  // about 16.3 MiB in total
+
+static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
+
+std::mutex g_mu;
+constexpr int kMaxDevices = 64;
+double *g_addr[kMaxDevices] = {};
+
+// errors are reported through lbm_last_error(), like every other entry point
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_last_error(buf);
+    return code;
+}
+
+// Device address of the scratch array on the current device; looked up once per device.
+int scratch_address(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(LBM_ERR_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(LBM_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+        g_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_addr[dev];
+    return LBM_OK;
+}
+
+bool pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
+int log2i(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+// DFT index held at position p of a spectrum left by the forward transforms of fft_line.cuh
+int freq_at(int p, int l2) {
+    if (l2 == 0) return 0;
+    if (l2 == 1) return p;
+    return (p >> (l2 - 2)) + 4 * freq_at(p & ((1 << (l2 - 2)) - 1), l2 - 2);
+}
+// first-derivative factor W(m) k_eff(m) (Eq. (3)); zero at the Nyquist index
+double deriv_factor(int m, int N, double d, double wa, double wp) {
+    if (2 * m == -N) return 0.0;
+    static const double c[8] = {1.0, 1.0 / 6.0, 3.0 / 40.0, 5.0 / 112.0, 35.0 / 1152.0,
+                                63.0 / 2816.0, 231.0 / 13312.0, 143.0 / 10240.0};
+    const double phi = std::sin(M_PI * (double)m / (double)N);
+    double s = 0.0, pw = phi;
+    for (int n = 0; n < 8; ++n) {
+        s += c[n] * pw;
+        pw *= phi * phi;
+    }
+    const double w = wa > 0 ? std::exp(-wa * std::pow(std::fabs((double)m) / (0.5 * N), wp)) : 1.0;
+    return w * 2.0 / d * s;
+}
+
+#define NA_TRY(expr)                                                                                   \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess) return fail(LBM_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));      \
+    } while (0)
+
+}  // namespace
+
+extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, double K, double win_alpha,
+                                       double win_p, const double *rho, const double *ux, const double *uy,
+                                       const double *T, void *stream, double out[5]) {
+    if (!rho || !ux || !uy || !T || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!pow2(nx) || !pow2(ny) || nx > kMaxN || ny > kMaxN)
+        return fail(LBM_ERR_ARG, "nx=%d, ny=%d: each must be a power of two in [2, %d]", nx, ny, kMaxN);
+    const long long n = (long long)nx * ny;
+    if (n > kMaxNodes)
+        return fail(LBM_ERR_ARG, "nx*ny=%lld exceeds the %lld nodes of the built-in scratch array", n, kMaxNodes);
+    if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(K) ||
+        !(win_alpha >= 0) || !(win_p > 0))
+        return fail(LBM_ERR_ARG, "bad dx, dy, K or window parameters");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *sc = nullptr;
+    int rc = scratch_address(&sc);
+    if (rc) return rc;
+
+    // derivative tables of both axes, rebuilt by every call
+    double *k1x = sc + kOffK, *k2x = k1x + kMaxN, *k1y = k2x + kMaxN, *k2y = k1y + kMaxN;
+    double2 *twx = reinterpret_cast<double2 *>(sc + kOffTw64), *twy = twx + kMaxN;
+    float2 *twx32 = reinterpret_cast<float2 *>(sc + kOffTw32), *twy32 = twx32 + kMaxN;
+    NA_TRY(launch_twiddles(twx, twx32, nx, s));
+    NA_TRY(launch_twiddles(twy, twy32, ny, s));
+    std::vector<double> tab(4 * (size_t)kMaxN);
+    for (int ax = 0; ax < 2; ++ax) {
+        const int N = ax ? ny : nx, l2 = log2i(N);
+        const double d = ax ? dy : dx;
+        double *h1 = tab.data() + (size_t)(2 * ax) * kMaxN, *h2 = h1 + kMaxN;
+        for (int p = 0; p < N; ++p) {
+            const int k = freq_at(p, l2);
+            const double ke = deriv_factor(k < N / 2 ? k : k - N, N, d, win_alpha, win_p);
+            h1[p] = ke / N;
+            h2[p] = -ke * ke / N;
+        }
+    }
+    NA_TRY(cudaMemcpyAsync(k1x, tab.data(), 4 * (size_t)kMaxN * sizeof(double), cudaMemcpyHostToDevice, s));
+
+    // d_y rho (column pass) and d_x rho (row pass) into the scratch fields
+    int W = 16 < nx ? 16 : nx;
+    while (W > 2 && (size_t)ny * W * 8 > 112 * 1024) W >>= 1;
+    ColArgs<double> ca{};
+    ca.nx = nx;
+    ca.ny = ny;
+    ca.W = W;
+    ca.log2W = log2i(W);
+    ca.ay = Axis<double>{twy, k1y, k2y, log2i(ny)};
+    ca.jobs[0] = ColJob<double>{rho, sc + kOffRy, 1, 1.0};
+    NA_TRY(launch_col<double>(ca, 1, (size_t)ny * W * 8, s));
+    int rows = 512 / nx;
+    if (rows < 1) rows = 1;
+    if (rows > ny) rows = ny;
+    RowDerivArgs<double> ra{};
+    ra.in[0] = rho;
+    ra.out[0] = sc + kOffRx;
+    ra.nin = 1;
+    ra.nx = nx;
+    ra.ny = ny;
+    ra.rows = rows;
+    ra.ax = Axis<double>{twx, k1x, k2x, log2i(nx)};
+    NA_TRY(launch_row_deriv<double>(ra, (size_t)2 * rows * nx * 8, s));
+
+    // per-block partial sums, then the final reduction on the host
+    const int blocks = (int)std::min<long long>(kMaxBlocks, (n + 255) / 256);
+    DiagArgs da{};
+    da.rho = rho;
+    da.ux = ux;
+    da.uy = uy;
+    da.T = T;
+    da.rx = sc + kOffRx;
+    da.ry = sc + kOffRy;
+    da.partial = sc + kOffPart;
+    da.n = n;
+    da.K = K;
+    da.cell = dx * dy;
+    NA_TRY(launch_diag<double>(da, blocks, s));
+    std::vector<double> part((size_t)blocks * 5);
+    NA_TRY(cudaMemcpyAsync(part.data(), sc + kOffPart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NA_TRY(cudaStreamSynchronize(s));
+    double acc[4] = {0, 0, 0, 0}, mx = 0;
+    for (int b = 0; b < blocks; ++b) {
+        for (int k = 0; k < 4; ++k) acc[k] += part[(size_t)b * 5 + k];
+        mx = std::max(mx, part[(size_t)b * 5 + 4]);
+    }
+    const double cell = dx * dy;
+    for (int k = 0; k < 4; ++k) out[k] = acc[k] * cell;
+    out[4] = std::sqrt(mx);
+    for (int k = 0; k < 5; ++k)
+        if (!std::isfinite(out[k])) return fail(LBM_ERR_NONFINITE, "diagnostic %d is not finite", k);
+    return LBM_OK;
+}
