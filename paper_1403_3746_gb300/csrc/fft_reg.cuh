@@ -1,0 +1,274 @@
+// Register-resident line FFTs for the spectral derivatives of Sec. 2.3 / Eq. (3).
+//
+// A "line" is a complex sequence of N = 2^LOG2N points that packs two real lines (real part
+// = one field line, imaginary part = another). The derivative multiplier d(m) = i W(m)
+// k_eff(m) satisfies d(-m) = conj(d(m)), so one complex transform pair differentiates two
+// real lines at once.
+//
+// G = N/E threads own a line, E = min(16, N) points each. The forward transform is a
+// decimation-in-frequency sequence of radix-16 passes (a 16-point DFT in registers, built as
+// 4 x 4, then the outer twiddles) and one final radix-RL pass (RL = 2, 4 or 8) when log2 N
+// is not a multiple of 4. Between passes the points are exchanged through a padded
+// shared-memory line buffer (one pad slot per 16 points keeps every exchange free of bank
+// conflicts, for 8- and 16-byte complex types). The forward output stays in digit-reversed
+// order, thread t holding positions [E t, E t + E); the derivative multiplier table is stored
+// in that order with 1/N folded in. The inverse is the same pass sequence in reverse, with
+// conjugate roots: it takes the digit-reversed spectrum back to natural order, thread t
+// holding points t + G e (e < E), the layout in which the forward transform reads its input.
+// So rows are read and written with coalesced accesses straight from and to global memory.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+template <typename R> struct cplx;
+template <> struct cplx<double> { typedef double2 T; };
+template <> struct cplx<float> { typedef float2 T; };
+
+namespace reg {
+
+template <typename R> using C = typename cplx<R>::T;
+
+template <typename R> __device__ __forceinline__ C<R> mk(R x, R y) {
+    C<R> c;
+    c.x = x;
+    c.y = y;
+    return c;
+}
+template <typename R> __device__ __forceinline__ C<R> add(C<R> a, C<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ C<R> sub(C<R> a, C<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+// a * w and a * conj(w)
+template <typename R> __device__ __forceinline__ C<R> mul(C<R> a, C<R> w) {
+    return mk<R>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+template <typename R> __device__ __forceinline__ C<R> mulc(C<R> a, C<R> w) {
+    return mk<R>(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+}
+// multiplication by -i (forward) or +i (inverse)
+template <typename R, bool INV> __device__ __forceinline__ C<R> rot(C<R> a) {
+    return INV ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x);
+}
+
+template <typename R, bool INV> __device__ __forceinline__ void dft2(C<R> &x0, C<R> &x1) {
+    const C<R> t = x0;
+    x0 = add<R>(t, x1);
+    x1 = sub<R>(t, x1);
+}
+
+// y_k = sum_q x_q w4^{qk}, w4 = exp(-+ 2 pi i / 4); in place, outputs in natural order
+template <typename R, bool INV> __device__ __forceinline__ void dft4(C<R> &x0, C<R> &x1, C<R> &x2, C<R> &x3) {
+    const C<R> t0 = add<R>(x0, x2), t1 = sub<R>(x0, x2), t2 = add<R>(x1, x3);
+    const C<R> t3 = rot<R, INV>(sub<R>(x1, x3));
+    x0 = add<R>(t0, t2);
+    x1 = add<R>(t1, t3);
+    x2 = sub<R>(t0, t2);
+    x3 = sub<R>(t1, t3);
+}
+
+// a * w16^M (forward: w16 = exp(-2 pi i/16); inverse: the conjugate), M a compile-time constant
+template <typename R, bool INV, int M> __device__ __forceinline__ C<R> w16(C<R> a) {
+    constexpr int m = M & 15;
+    if (m == 0) return a;
+    if (m == 4) return rot<R, INV>(a);
+    if (m == 8) return mk<R>(-a.x, -a.y);
+    if (m == 12) return rot<R, !INV>(a);
+    // cos and sin of 2 pi m / 16
+    constexpr double cs[16] = {1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
+                               0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
+                               -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173,
+                               0.0, 0.38268343236508977173, 0.70710678118654752440, 0.92387953251128675613};
+    constexpr double sn[16] = {0.0, 0.38268343236508977173, 0.70710678118654752440, 0.92387953251128675613,
+                               1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
+                               0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
+                               -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173};
+    const R c = (R)cs[m], s = (R)(INV ? sn[m] : -sn[m]);
+    return mk<R>(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// 16-point DFT in registers (q = q1 + 4 q2, k = k2 + 4 k1); v[k] holds y_k on return
+template <typename R, bool INV> __device__ __forceinline__ void dft16(C<R> v[16]) {
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1) dft4<R, INV>(v[q1], v[q1 + 4], v[q1 + 8], v[q1 + 12]);
+    // v[q1 + 4 k2] = b(q1, k2); twiddle by w16^(q1 k2)
+    v[5] = w16<R, INV, 1>(v[5]);
+    v[6] = w16<R, INV, 2>(v[6]);
+    v[7] = w16<R, INV, 3>(v[7]);
+    v[9] = w16<R, INV, 2>(v[9]);
+    v[10] = w16<R, INV, 4>(v[10]);
+    v[11] = w16<R, INV, 6>(v[11]);
+    v[13] = w16<R, INV, 3>(v[13]);
+    v[14] = w16<R, INV, 6>(v[14]);
+    v[15] = w16<R, INV, 9>(v[15]);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) dft4<R, INV>(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]);
+    // v[4 k2 + k1] = y(k2 + 4 k1): transpose the 4 x 4 block (register renaming only)
+    C<R> t[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t[k] = v[4 * (k & 3) + (k >> 2)];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = t[k];
+}
+
+// 8-point DFT (q = q1 + 2 q2, k = k2 + 4 k1)
+template <typename R, bool INV> __device__ __forceinline__ void dft8(C<R> v[8]) {
+    dft4<R, INV>(v[0], v[2], v[4], v[6]);
+    dft4<R, INV>(v[1], v[3], v[5], v[7]);
+    // v[q1 + 2 k2] = b(q1, k2); twiddle q1 = 1 by w8^k2 = w16^(2 k2)
+    v[3] = w16<R, INV, 2>(v[3]);
+    v[5] = w16<R, INV, 4>(v[5]);
+    v[7] = w16<R, INV, 6>(v[7]);
+    dft2<R, INV>(v[0], v[1]);
+    dft2<R, INV>(v[2], v[3]);
+    dft2<R, INV>(v[4], v[5]);
+    dft2<R, INV>(v[6], v[7]);
+    // v[2 k2 + k1] = y(k2 + 4 k1)
+    C<R> t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] = v[2 * (k & 3) + (k >> 2)];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = t[k];
+}
+
+template <typename R, bool INV, int RADIX> __device__ __forceinline__ void dft_small(C<R> *v) {
+    if (RADIX == 2) dft2<R, INV>(v[0], v[1]);
+    if (RADIX == 4) dft4<R, INV>(v[0], v[1], v[2], v[3]);
+    if (RADIX == 8) dft8<R, INV>(v);
+}
+
+struct SyncCta {
+    static __device__ __forceinline__ void run() { __syncthreads(); }
+};
+struct SyncWarp {
+    static __device__ __forceinline__ void run() { __syncwarp(); }
+};
+
+template <typename R, int LOG2N> struct LineFFT {
+    static constexpr int N = 1 << LOG2N;
+    static constexpr int E = N < 16 ? N : 16;                // points per thread
+    static constexpr int G = N / E;                          // threads per line
+    static constexpr int NP16 = LOG2N >= 4 ? LOG2N / 4 : 0;  // radix-16 passes
+    static constexpr int RL = LOG2N >= 4 ? (1 << (LOG2N & 3)) : N;  // final radix (1 = none)
+    static constexpr int SMEM = N + (N >> 4);                // padded line buffer, complex elements
+    typedef C<R> CT;
+
+    static __device__ __forceinline__ int pad(int p) { return p + (p >> 4); }
+    // position of point e of thread t in the input layout of radix-16 pass P
+    template <int P> static __device__ __forceinline__ int pos16(int t, int e) {
+        constexpr int S = N >> (4 * P), M = S >> 4;
+        return (t / M) * S + (t & (M - 1)) + M * e;
+    }
+
+    template <int P, bool INV> static __device__ __forceinline__ void pass16(CT v[16], int t, const CT *__restrict__ tw) {
+        constexpr int S = N >> (4 * P), M = S >> 4, SH = 4 * P;
+        const int j = t & (M - 1);
+        if (INV) {
+            if (M > 1 && j) {
+#pragma unroll
+                for (int k = 1; k < 16; ++k) v[k] = mulc<R>(v[k], tw[(j * k) << SH]);
+            }
+            dft16<R, true>(v);
+        } else {
+            dft16<R, false>(v);
+            if (M > 1 && j) {
+#pragma unroll
+                for (int k = 1; k < 16; ++k) v[k] = mul<R>(v[k], tw[(j * k) << SH]);
+            }
+        }
+    }
+
+    template <int P> static __device__ __forceinline__ void store16(const CT v[E], CT *buf, int t) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) buf[pad(pos16<P>(t, e))] = v[e];
+    }
+    template <int P> static __device__ __forceinline__ void load16(CT v[E], const CT *buf, int t) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = buf[pad(pos16<P>(t, e))];
+    }
+    static __device__ __forceinline__ void storeF(const CT v[E], CT *buf, int t) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) buf[pad(t * E + e)] = v[e];
+    }
+    static __device__ __forceinline__ void loadF(CT v[E], const CT *buf, int t) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = buf[pad(t * E + e)];
+    }
+
+    template <int P, class SYNC> static __device__ __forceinline__ void fwd_from(CT v[E], CT *buf, int t,
+                                                                                const CT *__restrict__ tw) {
+        if constexpr (P < NP16) {
+            pass16<P, false>(v, t, tw);
+            if constexpr (P + 1 < NP16) {
+                SYNC::run();
+                store16<P>(v, buf, t);
+                SYNC::run();
+                load16<P + 1>(v, buf, t);
+            } else if constexpr (RL > 1) {
+                SYNC::run();
+                store16<P>(v, buf, t);
+                SYNC::run();
+                loadF(v, buf, t);
+            }
+            fwd_from<P + 1, SYNC>(v, buf, t, tw);
+        } else if constexpr (RL > 1) {
+#pragma unroll
+            for (int kb = 0; kb < E / RL; ++kb) dft_small<R, false, RL>(v + kb * RL);
+        }
+    }
+
+    template <int P, class SYNC> static __device__ __forceinline__ void inv_from(CT v[E], CT *buf, int t,
+                                                                                const CT *__restrict__ tw) {
+        if constexpr (P >= 0) {
+            pass16<P, true>(v, t, tw);
+            if constexpr (P > 0) {
+                SYNC::run();
+                store16<P>(v, buf, t);
+                SYNC::run();
+                load16<P - 1>(v, buf, t);
+                inv_from<P - 1, SYNC>(v, buf, t, tw);
+            }
+        }
+    }
+
+    // Forward DFT of a line held as v[e] = x[t + G e]; on return v[e] = X at digit-reversed
+    // position E t + e. buf: this line's shared buffer of SMEM elements. Every thread of the
+    // block (SyncCta) or warp (SyncWarp) must call it.
+    template <class SYNC> static __device__ __forceinline__ void forward(CT v[E], CT *buf, int t,
+                                                                        const CT *__restrict__ tw) {
+        fwd_from<0, SYNC>(v, buf, t, tw);
+    }
+
+    // Inverse (N times the inverse DFT) of a spectrum held at positions E t + e; on return
+    // v[e] = x[t + G e].
+    template <class SYNC> static __device__ __forceinline__ void inverse(CT v[E], CT *buf, int t,
+                                                                        const CT *__restrict__ tw) {
+        if constexpr (RL > 1) {
+#pragma unroll
+            for (int kb = 0; kb < E / RL; ++kb) dft_small<R, true, RL>(v + kb * RL);
+            if constexpr (NP16 > 0) {
+                SYNC::run();
+                storeF(v, buf, t);
+                SYNC::run();
+                load16<NP16 - 1>(v, buf, t);
+            }
+        }
+        inv_from<NP16 - 1, SYNC>(v, buf, t, tw);
+    }
+
+    // v <- d^order * c * v at positions E t + e (tables k1 = W k_eff / N, k2 = -(W k_eff)^2 / N)
+    static __device__ __forceinline__ void multiply(CT v[E], int t, int order, R c, const R *__restrict__ k1,
+                                                    const R *__restrict__ k2) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if (order == 1) {
+                const R w = c * k1[t * E + e];
+                v[e] = mk<R>(-w * v[e].y, w * v[e].x);
+            } else {
+                const R w = c * k2[t * E + e];
+                v[e] = mk<R>(w * v[e].x, w * v[e].y);
+            }
+        }
+    }
+};
+
+}  // namespace reg
+}  // namespace lbm

@@ -1,51 +1,61 @@
 // Column pass: spectral y-derivatives of whole columns (Sec. 2.3, Eq. (3) along y).
 //
-// A CTA owns a tile of W adjacent columns of one input field over the full height ny,
-// loaded with coalesced row segments of W values. Adjacent columns are packed in pairs
-// into complex lines (W/2 lines of length ny), transformed forward, multiplied by the
-// job's derivative multiplier and transformed back; the output is written with the same
-// coalesced row segments. blockIdx.y selects the job (input field, output field).
+// A CTA owns a tile of W adjacent columns of one input field over the full height ny. Column
+// pairs (2l, 2l+1) are packed into complex lines (L = W/2 lines); thread (l, t), with l the
+// fast index, reads the points t + G e of its line straight from global memory, so each row
+// segment of W values is one coalesced access. Forward transform, derivative multiplier
+// and inverse transform run in registers with shared-memory exchanges (fft_reg.cuh); the
+// result is written back in the same layout. blockIdx.y selects the job (input, output).
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
-template <typename R>
-__global__ void __launch_bounds__(256) col_deriv_kernel(const __grid_constant__ ColArgs<R> a) {
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(MaxThreads<R>::value) col_deriv_kernel(const __grid_constant__ ColArgs<R> a) {
+    using F = reg::LineFFT<R, LOG2N>;
+    using CT = typename F::CT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *s0 = reinterpret_cast<R *>(smem_raw);
+    CT *sbuf = reinterpret_cast<CT *>(smem_raw);
     const ColJob<R> &job = a.jobs[blockIdx.y];
-    const int W = a.W, nx = a.nx, ny = a.ny;
-    const int x0 = blockIdx.x * W;
-    const int tile = ny * W;
+    const int L = a.W >> 1;
+    const int l = threadIdx.x & (L - 1), t = threadIdx.x >> (a.log2W - 1);
+    const size_t rs = (size_t)(a.nx >> 1);  // row stride in complex units
+    const int x = blockIdx.x * a.W + 2 * l;
+    const CT *in = reinterpret_cast<const CT *>(job.in + x);
+    CT *out = reinterpret_cast<CT *>(job.out + x);
 
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-        const int y = idx >> a.log2W, c = idx & (W - 1);
-        s0[idx] = job.in[(size_t)y * nx + x0 + c];
-    }
-    __syncthreads();
+    CT v[F::E];
+#pragma unroll
+    for (int e = 0; e < F::E; ++e) v[e] = in[(size_t)(t + F::G * e) * rs];
+    CT *buf = sbuf + l * F::SMEM;
+    F::template forward<reg::SyncCta>(v, buf, t, a.ay.tw);
+    F::multiply(v, t, job.order, job.c, a.ay.k1, a.ay.k2);
+    F::template inverse<reg::SyncCta>(v, buf, t, a.ay.tw);
+#pragma unroll
+    for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rs] = v[e];
+}
 
-    const int log2n = a.ay.log2n;
-    const LineSet<R> A{s0, W / 2, 2, W, 1};
-    fft_forward<R, true>(A, log2n, a.ay.tw);
-    spec_mul<R, true>(A, A, log2n, job.order, job.c, a.ay.k1, a.ay.k2);
-    __syncthreads();
-    fft_inverse<R, true>(A, log2n, a.ay.tw);
-
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-        const int y = idx >> a.log2W, c = idx & (W - 1);
-        job.out[(size_t)y * nx + x0 + c] = s0[idx];
-    }
+template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R> &a, int njobs, size_t smem,
+                                                                  cudaStream_t s) {
+    using F = reg::LineFFT<R, LOG2N>;
+    cudaError_t e = cudaFuncSetAttribute(col_deriv_kernel<R, LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(a.nx / a.W, njobs);
+    col_deriv_kernel<R, LOG2N><<<grid, (a.W / 2) * F::G, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_col(const ColArgs<R> &a, int njobs, size_t smem, cudaStream_t s) {
     if (njobs <= 0) return cudaSuccess;
-    cudaError_t e =
-        cudaFuncSetAttribute(col_deriv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid(a.nx / a.W, njobs);
-    col_deriv_kernel<R><<<grid, 256, smem, s>>>(a);
-    return cudaGetLastError();
+    switch (a.ay.log2n) {
+#define LBM_CASE(L2) \
+    case L2: return launch_col_n<R, L2>(a, njobs, smem, s);
+        LBM_FOR_LOG2N(LBM_CASE)
+#undef LBM_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template cudaError_t launch_col<double>(const ColArgs<double> &, int, size_t, cudaStream_t);

@@ -134,30 +134,46 @@ __global__ void convert_in_kernel(const double *in, F *f, long long n) {
         f[g] = (F)in[g];
 }
 
-// Generic spectral x-derivative of up to 4 fields (paired into complex lines).
-template <typename R>
-__global__ void __launch_bounds__(256) row_deriv_kernel(const __grid_constant__ RowDerivArgs<R> a) {
+// Generic spectral x-derivative of up to 4 fields (paired into complex lines), `rows` rows
+// per CTA, G threads per line (fft_reg.cuh).
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(MaxThreads<R>::value) row_deriv_kernel(const __grid_constant__ RowDerivArgs<R> a) {
+    using F = reg::LineFFT<R, LOG2N>;
+    using CT = typename F::CT;
+    constexpr int NX = F::N, G = F::G, E = F::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *s = reinterpret_cast<R *>(smem_raw);
-    const int nx = a.nx, Rw = a.rows, log2n = a.ax.log2n, L2 = 2 * nx;
-    const int nodes = Rw * nx, nl = (a.nin + 1) / 2;
-    const size_t g0 = (size_t)blockIdx.x * nodes;
-    for (int idx = threadIdx.x; idx < 2 * nl * nodes; idx += blockDim.x) {
-        const int k = idx / nodes, rem = idx - k * nodes;
-        const int r = rem >> log2n, x = rem & (nx - 1);
-        s[((k >> 1) * Rw + r) * L2 + (k & 1) * nx + x] = k < a.nin ? a.in[k][g0 + rem] : R(0);
+    CT *sb = reinterpret_cast<CT *>(smem_raw);
+    const int NR = a.rows;
+    const int slot = threadIdx.x / G, t = threadIdx.x % G;
+    const int p = slot / NR, r = slot % NR;
+    const size_t row = (size_t)blockIdx.x * NR * NX + (size_t)r * NX;
+    const int ka = 2 * p, kb = 2 * p + 1;
+    CT v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const size_t g = row + t + G * e;
+        v[e] = reg::mk<R>(a.in[ka][g], kb < a.nin ? a.in[kb][g] : R(0));
     }
-    __syncthreads();
-    const LineSet<R> X{s, nl * Rw, L2, 1, nx};
-    fft_forward<R, false>(X, log2n, a.ax.tw);
-    spec_mul<R, false>(X, X, log2n, 1, R(1), a.ax.k1, a.ax.k2);
-    __syncthreads();
-    fft_inverse<R, false>(X, log2n, a.ax.tw);
-    for (int idx = threadIdx.x; idx < a.nin * nodes; idx += blockDim.x) {
-        const int k = idx / nodes, rem = idx - k * nodes;
-        const int r = rem >> log2n, x = rem & (nx - 1);
-        a.out[k][g0 + rem] = s[((k >> 1) * Rw + r) * L2 + (k & 1) * nx + x];
+    CT *buf = sb + (size_t)slot * F::SMEM;
+    F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
+    F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+    F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const size_t g = row + t + G * e;
+        a.out[ka][g] = v[e].x;
+        if (kb < a.nin) a.out[kb][g] = v[e].y;
     }
+}
+
+template <typename R, int LOG2N> static cudaError_t launch_row_deriv_n(const RowDerivArgs<R> &a, size_t smem,
+                                                                       cudaStream_t s) {
+    using F = reg::LineFFT<R, LOG2N>;
+    cudaError_t e =
+        cudaFuncSetAttribute(row_deriv_kernel<R, LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    row_deriv_kernel<R, LOG2N><<<a.ny / a.rows, ((a.nin + 1) / 2) * a.rows * F::G, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 static inline int grid_for(long long n) {
@@ -191,11 +207,13 @@ template <typename F> cudaError_t launch_convert_in(const double *in, F *f, long
 }
 template <typename R>
 cudaError_t launch_row_deriv(const RowDerivArgs<R> &a, size_t smem, cudaStream_t s) {
-    cudaError_t e =
-        cudaFuncSetAttribute(row_deriv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    row_deriv_kernel<R><<<a.ny / a.rows, 256, smem, s>>>(a);
-    return cudaGetLastError();
+    switch (a.ax.log2n) {
+#define LBM_CASE(L2) \
+    case L2: return launch_row_deriv_n<R, L2>(a, smem, s);
+        LBM_FOR_LOG2N(LBM_CASE)
+#undef LBM_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template cudaError_t launch_init<double>(const InitArgs &, cudaStream_t);

@@ -1,64 +1,71 @@
 // Row passes: spectral x-derivatives of whole rows fused with the node-local physics.
 //
-// A CTA owns `rows` consecutive rows (rows * nx nodes); each row segment is read and
-// written with coalesced accesses, and threads map to consecutive x in the node loops.
-// Template parameter R is the arithmetic and storage type of the path (double for
-// LBM_FP64, float for LBM_MIXED).
+// A CTA owns `rows` consecutive rows. Each complex line (two real rows of different fields)
+// is owned by G consecutive threads, which read it with coalesced accesses, transform it in
+// registers (fft_reg.cuh) and leave the derivative in shared memory in natural order; the
+// node loops then map threads to consecutive x. Template parameter R is the arithmetic and
+// storage type of the path (double for LBM_FP64, float for LBM_MIXED).
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
 // ---------------------------------------------------------------------------------------
 // Macroscopic chain, row pass (Sec. 2.2, the coefficients after Eq. (2)).
-// In: rho, u, T and their y-derivatives from the column pass.
-// Lines (kind-major, stride 2 nx):  A = rho + i T,  B = u_x + i d_y u_y,  C = u_y,
-// A2 = d_xx A, B2 = d_xx B. After the inverse transforms:
-//   A -> (d_x rho, d_x T),  A2 -> d_xx rho,  B -> (d_x u_x, d_x d_y u_y),
-//   B2 -> d_xx u_x,  C -> d_x u_y.
-// Then per node: P^w, Lambda, S, Q, div u, the partial numerator of C; and a second
-// transform pair gives d_x Q_x, d_x S_xx (line A) and d_x S_xy (line B).
+// In: rho, u, T and their y-derivatives from the column pass. Per row three lines:
+// A = rho + i T, B = u_x + i d_y u_y, C = u_y; each gives d_x (first output) and d_xx
+// (second output, used for A and B):
+//   A -> (d_x rho, d_x T), (d_xx rho, -);  B -> (d_x u_x, d_x d_y u_y), (d_xx u_x, -);  C -> (d_x u_y, -).
+// Then per node: P^w, Lambda, S, Q, div u, the partial numerator of C; and a second round
+// of lines (Q_x + i S_xx, S_xy) gives d_x Q_x, d_x S_xx, d_x S_xy.
 // ---------------------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(256) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
+    using F = reg::LineFFT<R, LOG2N>;
+    using CT = typename F::CT;
+    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::SMEM;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *s = reinterpret_cast<R *>(smem_raw);
-    const int nx = a.nx, NR = a.rows, log2n = a.ax.log2n;
-    const int L2 = 2 * nx;
-    const int nodes = NR * nx;
+    CT *sb = reinterpret_cast<CT *>(smem_raw);
+    const int NR = a.rows, nodes = NR * NX;
     const size_t g0 = (size_t)blockIdx.x * nodes;
-    R *sA = s, *sB = s + NR * L2, *sC = s + 2 * NR * L2, *sA2 = s + 3 * NR * L2, *sB2 = s + 4 * NR * L2;
+    const int slot = threadIdx.x / G, t = threadIdx.x % G;
+    const int kind = slot / NR, r = slot % NR;
+    CT *O1 = sb + (size_t)slot * 2 * SM, *O2 = O1 + SM;
+    const size_t rowg = g0 + (size_t)r * NX;
 
-    for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
-        const int r = idx >> log2n, x = idx & (nx - 1);
-        const size_t g = g0 + idx;
-        const int o = r * L2 + x;
-        sA[o] = a.rho[g];
-        sA[o + nx] = a.T[g];
-        sB[o] = a.ux[g];
-        sB[o + nx] = a.uyy[g];
-        sC[o] = a.uy[g];
-        sC[o + nx] = R(0);
+    // round 1: derivatives of the moments along x
+    CT v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const size_t g = rowg + t + G * e;
+        if (kind == 0) v[e] = reg::mk<R>(a.rho[g], a.T[g]);
+        else if (kind == 1) v[e] = reg::mk<R>(a.ux[g], a.uyy[g]);
+        else v[e] = reg::mk<R>(a.uy[g], R(0));
     }
+    F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
+    F::storeF(v, O2, t);  // keep the spectrum for the second derivative (thread-private slots)
+    F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+    F::template inverse<reg::SyncCta>(v, O1, t, a.ax.tw);
     __syncthreads();
-    const LineSet<R> ABC{s, 3 * NR, L2, 1, nx};
-    fft_forward<R, false>(ABC, log2n, a.ax.tw);
-    spec_mul<R, false>(LineSet<R>{sA2, NR, L2, 1, nx}, LineSet<R>{sA, NR, L2, 1, nx}, log2n, 2, R(1), a.ax.k1,
-                       a.ax.k2);
-    spec_mul<R, false>(LineSet<R>{sB2, NR, L2, 1, nx}, LineSet<R>{sB, NR, L2, 1, nx}, log2n, 2, R(1), a.ax.k1,
-                       a.ax.k2);
+#pragma unroll
+    for (int e = 0; e < E; ++e) O1[t + G * e] = v[e];
+    F::loadF(v, O2, t);
+    F::multiply(v, t, 2, R(1), a.ax.k1, a.ax.k2);
+    F::template inverse<reg::SyncCta>(v, O2, t, a.ax.tw);
     __syncthreads();
-    spec_mul<R, false>(ABC, ABC, log2n, 1, R(1), a.ax.k1, a.ax.k2);
+#pragma unroll
+    for (int e = 0; e < E; ++e) O2[t + G * e] = v[e];
     __syncthreads();
-    fft_inverse<R, false>(LineSet<R>{s, 5 * NR, L2, 1, nx}, log2n, a.ax.tw);
 
     const R K = a.K, H = a.H, q = a.q, zeta = a.zeta;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
-        const int r = idx >> log2n, x = idx & (nx - 1);
+        const int rr = idx / NX, x = idx % NX;
         const size_t g = g0 + idx;
-        const int o = r * L2 + x;
-        const R rx = sA[o], Tx = sA[o + nx], rxx = sA2[o];
-        const R dux_dx = sB[o], dxduyy = sB[o + nx], dxxux = sB2[o];
-        const R duy_dx = sC[o];
+        CT *A1 = sb + (size_t)(0 * NR + rr) * 2 * SM, *A2 = A1 + SM;
+        CT *B1 = sb + (size_t)(1 * NR + rr) * 2 * SM, *B2 = B1 + SM;
+        CT *C1 = sb + (size_t)(2 * NR + rr) * 2 * SM;
+        const R rx = A1[x].x, Tx = A1[x].y, rxx = A2[x].x;
+        const R dux_dx = B1[x].x, dxduyy = B1[x].y, dxxux = B2[x].x;
+        const R duy_dx = C1[x].x;
         const R rho = a.rho[g], T = a.T[g];
         const R ry = a.ry[g], ryy = a.ryy[g], dux_dy = a.uxy[g], duy_dy = a.uyy[g], Ty = a.Ty[g];
 
@@ -89,24 +96,27 @@ __global__ void __launch_bounds__(256) macro_row_kernel(const __grid_constant__ 
         a.Syy[g] = Syy;
         a.divu[g] = divu;
         a.Cnum[g] = Cnum;
-        sA[o] = Qx;
-        sA[o + nx] = Sxx;
-        sB[o] = Sxy;
-        sB[o + nx] = R(0);
+        A1[x] = reg::mk<R>(Qx, Sxx);  // round-2 lines, same node and thread as the reads above
+        B1[x] = reg::mk<R>(Sxy, R(0));
+        C1[x] = reg::mk<R>(R(0), R(0));
     }
     __syncthreads();
-    const LineSet<R> AB{s, 2 * NR, L2, 1, nx};
-    fft_forward<R, false>(AB, log2n, a.ax.tw);
-    spec_mul<R, false>(AB, AB, log2n, 1, R(1), a.ax.k1, a.ax.k2);
-    __syncthreads();
-    fft_inverse<R, false>(AB, log2n, a.ax.tw);
-    for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
-        const int r = idx >> log2n, x = idx & (nx - 1);
-        const size_t g = g0 + idx;
-        const int o = r * L2 + x;
-        a.dQx[g] = sA[o];
-        a.dSxx[g] = sA[o + nx];
-        a.dSxy[g] = sB[o];
+
+    // round 2: d_x of Q_x, S_xx (line of kind A) and S_xy (kind B); kind C idles on zeros
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = O1[t + G * e];
+    F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
+    F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+    F::template inverse<reg::SyncCta>(v, O1, t, a.ax.tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const size_t g = rowg + t + G * e;
+        if (kind == 0) {
+            a.dQx[g] = v[e].x;
+            a.dSxx[g] = v[e].y;
+        } else if (kind == 1) {
+            a.dSxy[g] = v[e].x;
+        }
     }
 }
 
@@ -205,36 +215,46 @@ __device__ __forceinline__ void equilibrium_moments(R rho, R ux, R uy, R T, R b,
     m[15] = rho * (T * e + gq * uy * uy);
 }
 
-template <typename R, bool MOMENT_SPACE>
-__global__ void __launch_bounds__(256) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
+template <typename R, int LOG2N, bool MOMENT_SPACE>
+__global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
+    using F = reg::LineFFT<R, LOG2N>;
+    using CT = typename F::CT;
+    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::SMEM;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *s = reinterpret_cast<R *>(smem_raw);
-    const int nx = a.nx, NR = a.rows, log2n = a.ax.log2n;
-    const int L2 = 2 * nx;
-    const int nodes = NR * nx;
-    const size_t plane = (size_t)nx * a.ny;
+    CT *sb = reinterpret_cast<CT *>(smem_raw);
+    const int NR = a.rows, nodes = NR * NX;
+    const size_t plane = (size_t)NX * a.ny;
     const size_t g0 = (size_t)blockIdx.x * nodes;
     const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
     const bool col = !(a.flags & LBM_FLAG_NO_COLLISION);
     const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
 
     if (adv) {
-        for (int idx = threadIdx.x; idx < 12 * nodes; idx += blockDim.x) {
-            const int k = idx / nodes, rem = idx - k * nodes;
-            const int r = rem >> log2n, x = rem & (nx - 1);
-            s[((k >> 1) * NR + r) * L2 + (k & 1) * nx + x] = a.fs[xfield(k) * plane + g0 + rem];
+        // 6 lines per row (the 12 fields with v_x != 0, paired); LB lines per batch
+        const int LB = blockDim.x / G;
+        const int ls = threadIdx.x / G, t = threadIdx.x % G;
+        for (int b0 = 0; b0 < 6 * NR; b0 += LB) {
+            const int line = b0 + ls;
+            const int p = line / NR, r = line % NR;
+            CT *buf = sb + (size_t)line * SM;
+            const R *fa = a.fs + xfield(2 * p) * plane + g0 + (size_t)r * NX;
+            const R *fb = a.fs + xfield(2 * p + 1) * plane + g0 + (size_t)r * NX;
+            CT v[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(fa[t + G * e], fb[t + G * e]);
+            F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
+            F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+            F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; ++e) buf[t + G * e] = v[e];
         }
         __syncthreads();
-        const LineSet<R> X{s, 6 * NR, L2, 1, nx};
-        fft_forward<R, false>(X, log2n, a.ax.tw);
-        spec_mul<R, false>(X, X, log2n, 1, R(1), a.ax.k1, a.ax.k2);
-        __syncthreads();
-        fft_inverse<R, false>(X, log2n, a.ax.tw);
     }
 
     const R b = a.b, K = a.K, tau_inv = a.tau_inv, h = a.h;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
-        const int r = idx >> log2n, x = idx & (nx - 1);
+        const int r = idx / NX, x = idx % NX;
         const size_t g = g0 + idx;
         const R rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
         R Bx = 0, By = 0, CC = 0, A = 0;
@@ -254,11 +274,10 @@ __global__ void __launch_bounds__(256) update_row_kernel(const __grid_constant__
         // neq = M^-1 (m^eq - M f) over the 12 non-conserved moments only (the 4 conserved
         // ones agree exactly), so the rounding of M^-1 to float32 cannot bias mass, momentum
         // or energy: its error scales with the non-equilibrium part instead of with rho.
-        R fsv[16], neq[16], fev[16];
+        R fsv[16], dm[12];
 #pragma unroll
         for (int i = 0; i < 16; ++i) fsv[i] = a.fs[i * plane + g];
         if (MOMENT_SPACE) {
-            R dm[12];
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
                 R mf = 0;
@@ -266,38 +285,33 @@ __global__ void __launch_bounds__(256) update_row_kernel(const __grid_constant__
                 for (int i = 0; i < 16; ++i) mf += a.mrow[j * 16 + i] * fsv[i];
                 dm[j] = m[4 + j] - mf;
             }
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                R ne = 0;
-#pragma unroll
-                for (int j = 0; j < 12; ++j) ne += a.minv[i * 16 + 4 + j] * dm[j];
-                neq[i] = ne;
-                fev[i] = fsv[i] + ne;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                R fe = 0;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * m[j];
-                fev[i] = fe;
-                neq[i] = fe - fsv[i];
-            }
         }
         MomentSums<R> acc;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const R fsi = fsv[i];
-            const R fe = fev[i];
+            R ne = 0, fe;
+            if (MOMENT_SPACE) {
+#pragma unroll
+                for (int j = 0; j < 12; ++j) ne += a.minv[i * 16 + 4 + j] * dm[j];
+                fe = fsv[i] + ne;
+            } else {
+                fe = 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * m[j];
+                ne = fe - fsv[i];
+            }
             R Ri = 0;
             if (adv) {
                 R ad = 0;
                 const int xs = xslot(i), ys = yslot(i);
-                if (xs >= 0) ad += R(vel_x(i)) * s[((xs >> 1) * NR + r) * L2 + (xs & 1) * nx + x];
+                if (xs >= 0) {
+                    const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + x];
+                    ad += R(vel_x(i)) * ((xs & 1) ? d.y : d.x);
+                }
                 if (ys >= 0) ad += a.Ay[ys * plane + g];
                 Ri -= ad;
             }
-            if (col) Ri += neq[i] * tau_inv;
+            if (col) Ri += ne * tau_inv;
             if (frc) {
                 const R cx = R(vel_x(i)) - ux, cy = R(vel_y(i)) - uy;
                 Ri -= (A + Bx * cx + By * cy + CC * (cx * cx + cy * cy)) * fe;
@@ -315,22 +329,54 @@ __global__ void __launch_bounds__(256) update_row_kernel(const __grid_constant__
     }
 }
 
-// float64 (the plain method): f^eq = M^-1 m^eq; float32: the moment-space collision.
-template <typename R> cudaError_t launch_update(const UpdateArgs<R> &a, size_t smem, cudaStream_t s) {
-    constexpr bool MS = sizeof(R) == 4;
-    cudaError_t e = cudaFuncSetAttribute(update_row_kernel<R, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+// lines per batch of the update kernel: the largest divisor of the CTA's lines with LB G <= maxt
+static inline int update_lines_per_batch(int nlines, int G, int maxt) {
+    int best = 1;
+    for (int d = 1; d <= nlines; ++d)
+        if (nlines % d == 0 && d * G <= maxt) best = d;
+    return best;
+}
+
+template <typename R, int LOG2N> static cudaError_t launch_update_n(const UpdateArgs<R> &a, size_t smem,
+                                                                    cudaStream_t s) {
+    using F = reg::LineFFT<R, LOG2N>;
+    constexpr bool MS = sizeof(R) == 4;  // float32: moment-space collision
+    cudaError_t e = cudaFuncSetAttribute(update_row_kernel<R, LOG2N, MS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    update_row_kernel<R, MS><<<a.ny / a.rows, 256, smem, s>>>(a);
+    const int threads = update_lines_per_batch(6 * a.rows, F::G, MaxThreads<R>::value) * F::G;
+    update_row_kernel<R, LOG2N, MS><<<a.ny / a.rows, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename R> cudaError_t launch_macro(const MacroArgs<R> &a, size_t smem, cudaStream_t s) {
+template <typename R, int LOG2N> static cudaError_t launch_macro_n(const MacroArgs<R> &a, size_t smem,
+                                                                   cudaStream_t s) {
+    using F = reg::LineFFT<R, LOG2N>;
     cudaError_t e =
-        cudaFuncSetAttribute(macro_row_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(macro_row_kernel<R, LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    macro_row_kernel<R><<<a.ny / a.rows, 256, smem, s>>>(a);
+    macro_row_kernel<R, LOG2N><<<a.ny / a.rows, 3 * a.rows * F::G, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename R> cudaError_t launch_update(const UpdateArgs<R> &a, size_t smem, cudaStream_t s) {
+    switch (a.ax.log2n) {
+#define LBM_CASE(L2) \
+    case L2: return launch_update_n<R, L2>(a, smem, s);
+        LBM_FOR_LOG2N(LBM_CASE)
+#undef LBM_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R> cudaError_t launch_macro(const MacroArgs<R> &a, size_t smem, cudaStream_t s) {
+    switch (a.ax.log2n) {
+#define LBM_CASE(L2) \
+    case L2: return launch_macro_n<R, L2>(a, smem, s);
+        LBM_FOR_LOG2N(LBM_CASE)
+#undef LBM_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template cudaError_t launch_update<double>(const UpdateArgs<double> &, size_t, cudaStream_t);

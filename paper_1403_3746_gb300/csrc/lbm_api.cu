@@ -39,28 +39,6 @@ int ilog2(int n) {
     return l;
 }
 
-// Position p of a digit-reversed spectrum (radix-4 DIF stages, then one radix-2 stage when
-// log2 N is odd) holds DFT index freq(p).
-int freq_of(int p, int l2) {
-    if (l2 == 0) return 0;
-    if (l2 == 1) return p;
-    const int S = 1 << (l2 - 2);
-    return (p >> (l2 - 2)) + 4 * freq_of(p & (S - 1), l2 - 2);
-}
-
-// Eq. (3): k_eff = (2/d) sum_{n=0}^{7} c_n phi^(2n+1), phi = sin(pi m / N).
-double keff(int m, int N, double d) {
-    static const double c[8] = {1.0, 1.0 / 6.0, 3.0 / 40.0, 5.0 / 112.0, 35.0 / 1152.0,
-                                63.0 / 2816.0, 231.0 / 13312.0, 143.0 / 10240.0};
-    const double phi = std::sin(M_PI * (double)m / (double)N);
-    double s = 0.0, pw = phi;
-    for (int n = 0; n < 8; ++n) {
-        s += c[n] * pw;
-        pw *= phi * phi;
-    }
-    return 2.0 / d * s;
-}
-
 // Inverse of the 16x16 matrix whose rows are the moment functionals
 // 1; v_x, v_y; psi; v_x v_x, v_x v_y, v_y v_y; psi v_x, psi v_y; v_x^3, v_x^2 v_y, v_x v_y^2, v_y^3;
 // psi v_x^2, psi v_x v_y, psi v_y^2 (psi = v^2 + eta^2) evaluated on the 16 velocities.
@@ -102,13 +80,6 @@ bool moment_inverse(double eta0, double out[256]) {
     return true;
 }
 
-int col_width(int nx, int ny, size_t esize, int tiles) {
-    int W = (int)(128 / esize);
-    if (W > nx) W = nx;
-    while (W > 2 && (size_t)ny * W * esize * tiles > 112 * 1024) W >>= 1;
-    return W;
-}
-
 }  // namespace
 
 struct lbm_ctx {
@@ -143,10 +114,7 @@ struct lbm_ctx {
     double mrow[192];  // moment-matrix rows 4..15
 
     // launch geometry
-    int colW = 2;
-    size_t col_smem = 0;
-    int rows = 1;
-    size_t macro_smem = 0, upd_smem = 0, rowd_smem = 0;
+    Geometry geo;
 
     bool initialized = false;
     long long steps = 0;
@@ -197,8 +165,8 @@ template <typename R> ColArgs<R> col_args(const lbm_ctx *c) {
     ColArgs<R> a{};
     a.nx = c->nx;
     a.ny = c->ny;
-    a.W = c->colW;
-    a.log2W = ilog2(c->colW);
+    a.W = c->geo.colW;
+    a.log2W = ilog2(c->geo.colW);
     a.ay = axis<R>(c, false);
     return a;
 }
@@ -232,7 +200,7 @@ int run_stage(lbm_ctx *c, int stage) {
         }
         if (nj) {
             LaunchTimer t(c, LBM_K_COL);
-            CU_TRY(launch_col<R>(a, nj, c->col_smem, c->stream));
+            CU_TRY(launch_col<R>(a, nj, c->geo.col_smem, c->stream));
         }
     }
     if (frc) {
@@ -244,11 +212,11 @@ int run_stage(lbm_ctx *c, int stage) {
             a.Qy = M(lbm_ctx::QY); a.Sxy = M(lbm_ctx::SXY); a.Syy = M(lbm_ctx::SYY); a.divu = M(lbm_ctx::DIVU);
             a.dQx = M(lbm_ctx::DQX); a.dSxx = M(lbm_ctx::DSXX); a.dSxy = M(lbm_ctx::DSXY);
             a.Cnum = M(lbm_ctx::CNUM);
-            a.nx = c->nx; a.ny = c->ny; a.rows = c->rows;
+            a.nx = c->nx; a.ny = c->ny; a.rows = c->geo.rows_macro;
             a.ax = axis<R>(c, true);
             a.K = (R)p.K; a.H = (R)p.H; a.q = (R)p.q; a.zeta = (R)p.zeta;
             LaunchTimer t(c, LBM_K_MACRO);
-            CU_TRY(launch_macro<R>(a, c->macro_smem, c->stream));
+            CU_TRY(launch_macro<R>(a, c->geo.macro_smem, c->stream));
         }
         {
             ColArgs<R> a = col_args<R>(c);
@@ -257,7 +225,7 @@ int run_stage(lbm_ctx *c, int stage) {
             a.jobs[2] = ColJob<R>{M(lbm_ctx::SYY), M(lbm_ctx::DSYY), 1, R(1)};
             a.jobs[3] = ColJob<R>{M(lbm_ctx::DIVU), M(lbm_ctx::DDIVUY), 1, R(1)};
             LaunchTimer t(c, LBM_K_FLUX);
-            CU_TRY(launch_col<R>(a, 4, c->col_smem, c->stream));
+            CU_TRY(launch_col<R>(a, 4, c->geo.col_smem, c->stream));
         }
     }
     {
@@ -270,7 +238,7 @@ int run_stage(lbm_ctx *c, int stage) {
         a.ry = M(lbm_ctx::RY); a.dQx = M(lbm_ctx::DQX); a.dSxx = M(lbm_ctx::DSXX); a.dSxy = M(lbm_ctx::DSXY);
         a.Cnum = M(lbm_ctx::CNUM); a.dQy = M(lbm_ctx::DQY); a.dSxyy = M(lbm_ctx::DSXYY);
         a.dSyy = M(lbm_ctx::DSYY); a.ddivuy = M(lbm_ctx::DDIVUY);
-        a.nx = c->nx; a.ny = c->ny; a.rows = c->rows;
+        a.nx = c->nx; a.ny = c->ny; a.rows = c->geo.rows_upd;
         a.ax = axis<R>(c, true);
         a.tau_inv = (R)(1.0 / p.tau);
         a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
@@ -285,7 +253,7 @@ int run_stage(lbm_ctx *c, int stage) {
         for (int k = 0; k < 256; ++k) a.minv[k] = (R)c->minv[k];
         for (int k = 0; k < 192; ++k) a.mrow[k] = (R)c->mrow[k];
         LaunchTimer t(c, LBM_K_UPDATE);
-        CU_TRY(launch_update<R>(a, c->upd_smem, c->stream));
+        CU_TRY(launch_update<R>(a, c->geo.upd_smem, c->stream));
     }
     return LBM_OK;
 }
@@ -382,16 +350,8 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     // launch geometry
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    c->colW = col_width(nx, ny, c->fsize, 1);
-    c->col_smem = (size_t)ny * c->colW * c->fsize;
-    int rows = 512 / nx;
-    if (rows < 1) rows = 1;
-    if (rows > ny) rows = ny;
-    c->rows = rows;
-    c->upd_smem = (size_t)12 * rows * nx * c->fsize;
-    c->macro_smem = (size_t)10 * rows * nx * c->fsize;
-    c->rowd_smem = (size_t)2 * rows * nx * c->fsize;
-    const size_t need = std::max(std::max(c->upd_smem, c->macro_smem), c->col_smem);
+    pass_geometry(nx, ny, c->fsize, &c->geo);
+    const size_t need = std::max(std::max(c->geo.upd_smem, c->geo.macro_smem), std::max(c->geo.col_smem, c->geo.rowd_smem));
     if (need > (size_t)smem_optin) {
         delete c;
         return fail(LBM_ERR_UNSUPPORTED, "nx=%d ny=%d needs %zu B of shared memory per block (device: %d)", nx,
@@ -438,20 +398,12 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     cudaError_t e = launch_twiddles(c->tw64x, c->tw32x, nx, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->tw64y, c->tw32y, ny, c->stream);
     for (int ax = 0; ax < 2 && e == cudaSuccess; ++ax) {
-        const int N = ax == 0 ? nx : ny, l2 = ax == 0 ? c->lx : c->ly;
+        const int N = ax == 0 ? nx : ny;
         const double d = ax == 0 ? params->dx : params->dy;
         std::vector<double> k1(N), k2(N);
         std::vector<float> k1f(N), k2f(N);
+        derivative_tables(N, d, params->win_alpha, params->win_p, k1.data(), k2.data());
         for (int pos = 0; pos < N; ++pos) {
-            const int k = freq_of(pos, l2);
-            const int m = k < N / 2 ? k : k - N;
-            // first derivative: i W(m) k_eff(m), zero at Nyquist; second: its square
-            const double w = params->win_alpha > 0
-                                 ? std::exp(-params->win_alpha * std::pow(std::fabs((double)m) / (0.5 * N), params->win_p))
-                                 : 1.0;
-            const double ke = (2 * m == -N) ? 0.0 : w * keff(m, N, d);
-            k1[pos] = ke / N;
-            k2[pos] = -ke * ke / N;
             k1f[pos] = (float)k1[pos];
             k2f[pos] = (float)k2[pos];
         }
@@ -614,16 +566,16 @@ template <typename R> static int diag_launch(lbm_ctx *c) {
     // d_y rho into RY, d_x rho into DQX (stage scratch, rebuilt by the next stage)
     ColArgs<R> ca = col_args<R>(c);
     ca.jobs[0] = ColJob<R>{static_cast<R *>(c->m[lbm_ctx::RHO]), static_cast<R *>(c->m[lbm_ctx::RY]), 1, R(1)};
-    CU_TRY(launch_col<R>(ca, 1, c->col_smem, c->stream));
+    CU_TRY(launch_col<R>(ca, 1, c->geo.col_smem, c->stream));
     RowDerivArgs<R> ra{};
     ra.in[0] = static_cast<R *>(c->m[lbm_ctx::RHO]);
     ra.out[0] = static_cast<R *>(c->m[lbm_ctx::DQX]);
     ra.nin = 1;
     ra.nx = c->nx;
     ra.ny = c->ny;
-    ra.rows = c->rows;
+    ra.rows = c->geo.rows_rowd;
     ra.ax = axis<R>(c, true);
-    CU_TRY(launch_row_deriv<R>(ra, c->rowd_smem, c->stream));
+    CU_TRY(launch_row_deriv<R>(ra, c->geo.rowd_smem, c->stream));
     DiagArgs da{};
     da.rho = c->m[lbm_ctx::RHO]; da.ux = c->m[lbm_ctx::UX]; da.uy = c->m[lbm_ctx::UY]; da.T = c->m[lbm_ctx::TT];
     da.rx = c->m[lbm_ctx::DQX]; da.ry = c->m[lbm_ctx::RY];
@@ -740,4 +692,74 @@ int lbm_maxwell(double T, double *rho_l, double *rho_v) {
 // Lets other translation units report a detailed message through lbm_last_error().
 namespace lbm {
 void set_last_error(const char *msg) { g_last_error = msg; }
+
+// DFT index held at position p after the forward passes of fft_reg.cuh: radix-16 passes
+// from the full length down, then one radix-RL pass (mixed-radix digit reversal).
+static int freq_at(int p, int n, int radix_first) {
+    if (n == 1) return 0;
+    const int r = radix_first;
+    const int S = n / r;
+    const int next = S >= 16 ? 16 : S;
+    return p / S + r * freq_at(p % S, S, next);
+}
+
+void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2) {
+    static const double c[8] = {1.0, 1.0 / 6.0, 3.0 / 40.0, 5.0 / 112.0, 35.0 / 1152.0,
+                                63.0 / 2816.0, 231.0 / 13312.0, 143.0 / 10240.0};
+    int l2 = 0;
+    while ((1 << l2) < N) ++l2;
+    const int first = l2 >= 4 ? 16 : N;
+    for (int pos = 0; pos < N; ++pos) {
+        const int k = freq_at(pos, N, first);
+        const int m = k < N / 2 ? k : k - N;
+        double ke = 0.0;
+        if (2 * m != -N) {
+            // Eq. (3): k_eff = (2/d) sum_{n=0}^{7} c_n phi^(2n+1), phi = sin(pi m / N)
+            const double phi = std::sin(M_PI * (double)m / (double)N);
+            double s = 0.0, pw = phi;
+            for (int n = 0; n < 8; ++n) {
+                s += c[n] * pw;
+                pw *= phi * phi;
+            }
+            const double w = win_alpha > 0
+                                 ? std::exp(-win_alpha * std::pow(std::fabs((double)m) / (0.5 * N), win_p))
+                                 : 1.0;
+            ke = w * 2.0 / d * s;
+        }
+        k1[pos] = ke / N;
+        k2[pos] = -ke * ke / N;
+    }
+}
+
+void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
+    int lx = 0, ly = 0;
+    while ((1 << lx) < nx) ++lx;
+    while ((1 << ly) < ny) ++ly;
+    const size_t cs = 2 * esize;  // complex element
+    // column tiles: W columns = W/2 lines of G threads; at most 1024 threads and 100 KB
+    int W = (int)(128 / esize);
+    if (W > nx) W = nx;
+    const int maxt = max_threads(esize);
+    while (W > 2 && ((W / 2) * line_G(ly) > maxt || (size_t)(W / 2) * line_smem(ly) * cs > 100 * 1024)) W >>= 1;
+    g->colW = W;
+    g->col_smem = (size_t)(W / 2) * line_smem(ly) * cs;
+    // row kernels: rows per CTA, starting from about 512 nodes per CTA
+    const int G = line_G(lx);
+    const size_t SM = (size_t)line_smem(lx) * cs;
+    int r0 = 512 / nx;
+    if (r0 < 1) r0 = 1;
+    if (r0 > ny) r0 = ny;
+    int r = r0;
+    while (r > 1 && 6 * r * SM > 200 * 1024) r >>= 1;  // update: 6 line buffers per row
+    g->rows_upd = r;
+    g->upd_smem = 6 * (size_t)r * SM;
+    r = r0;
+    while (r > 1 && (3 * r * G > maxt || 6 * r * SM > 200 * 1024)) r >>= 1;  // macro: 3 lines, 2 buffers each
+    g->rows_macro = r;
+    g->macro_smem = 6 * (size_t)r * SM;
+    r = r0;
+    while (r > 1 && r * G > maxt) r >>= 1;  // one line per row (diagnostics)
+    g->rows_rowd = r;
+    g->rowd_smem = (size_t)r * SM;
+}
 }  // namespace lbm

@@ -16,7 +16,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "fft_line.cuh"
+#include "fft_reg.cuh"
 #include "lbm_d2v16.h"
 
 namespace lbm {
@@ -54,7 +54,36 @@ __host__ __device__ __forceinline__ int xslot(int i) { return i < 8 ? ((i & 1) ?
 __host__ __device__ __forceinline__ int yfield(int k) { return k < 4 ? 2 * k + 1 : k + 4; }
 __host__ __device__ __forceinline__ int yslot(int i) { return i < 8 ? ((i & 1) ? i / 2 : -1) : i - 4; }
 
-// twiddles and derivative multipliers of one axis (digit-reversed order, see fft_line.cuh)
+// Line-transform geometry (fft_reg.cuh): points per thread, threads per line, and the padded
+// shared-memory line buffer in complex elements, for a line of 2^log2n points.
+__host__ __device__ constexpr int line_E(int log2n) { return log2n < 4 ? (1 << log2n) : 16; }
+__host__ __device__ constexpr int line_G(int log2n) { return (1 << log2n) / line_E(log2n); }
+__host__ __device__ constexpr int line_smem(int log2n) { return (1 << log2n) + ((1 << log2n) >> 4); }
+// threads per CTA of the line-transform kernels: float32 768 (<= 85 registers per thread),
+// float64 384 (<= 170): one line's 16 complex points live in registers
+template <typename R> struct MaxThreads {
+    static constexpr int value = sizeof(R) == 8 ? 384 : 768;
+};
+__host__ __device__ constexpr int max_threads(size_t esize) { return esize == 8 ? 384 : 768; }
+// every supported line length 2^1 .. 2^12
+#define LBM_FOR_LOG2N(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+
+// Derivative multiplier tables of one axis in the digit-reversed order left by the forward
+// transforms: k1[p] = W(m) k_eff(m) / N and k2[p] = -(W(m) k_eff(m))^2 / N for the DFT index m
+// held at position p (zero at the Nyquist index). Eq. (3) and the window W (lbm_api.cu).
+void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2);
+
+// Launch geometry of the four passes for an nx x ny grid and an element size (lbm_api.cu):
+// column tile width and shared memory, rows per CTA and shared memory of the row kernels.
+struct Geometry {
+    int colW = 2;
+    size_t col_smem = 0;
+    int rows_upd = 1, rows_macro = 1, rows_rowd = 1;
+    size_t upd_smem = 0, macro_smem = 0, rowd_smem = 0;
+};
+void pass_geometry(int nx, int ny, size_t esize, Geometry *g);
+
+// twiddles and derivative multipliers of one axis (digit-reversed order, see fft_reg.cuh)
 template <typename R> struct Axis {
     const typename cplx<R>::T *tw;  // exp(-2 pi i k/N), k < N
     const R *k1;                    // k_eff(m(p)) / N, 0 at Nyquist

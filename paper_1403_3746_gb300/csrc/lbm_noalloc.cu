@@ -75,27 +75,6 @@ int log2i(int n) {
     while ((1 << l) < n) ++l;
     return l;
 }
-// DFT index held at position p of a spectrum left by the forward transforms of fft_line.cuh
-int freq_at(int p, int l2) {
-    if (l2 == 0) return 0;
-    if (l2 == 1) return p;
-    return (p >> (l2 - 2)) + 4 * freq_at(p & ((1 << (l2 - 2)) - 1), l2 - 2);
-}
-// first-derivative factor W(m) k_eff(m) (Eq. (3)); zero at the Nyquist index
-double deriv_factor(int m, int N, double d, double wa, double wp) {
-    if (2 * m == -N) return 0.0;
-    static const double c[8] = {1.0, 1.0 / 6.0, 3.0 / 40.0, 5.0 / 112.0, 35.0 / 1152.0,
-                                63.0 / 2816.0, 231.0 / 13312.0, 143.0 / 10240.0};
-    const double phi = std::sin(M_PI * (double)m / (double)N);
-    double s = 0.0, pw = phi;
-    for (int n = 0; n < 8; ++n) {
-        s += c[n] * pw;
-        pw *= phi * phi;
-    }
-    const double w = wa > 0 ? std::exp(-wa * std::pow(std::fabs((double)m) / (0.5 * N), wp)) : 1.0;
-    return w * 2.0 / d * s;
-}
-
 #define NA_TRY(expr)                                                                                   \
     do {                                                                                               \
         cudaError_t e_ = (expr);                                                                       \
@@ -128,22 +107,14 @@ extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, dou
     NA_TRY(launch_twiddles(twx, twx32, nx, s));
     NA_TRY(launch_twiddles(twy, twy32, ny, s));
     std::vector<double> tab(4 * (size_t)kMaxN);
-    for (int ax = 0; ax < 2; ++ax) {
-        const int N = ax ? ny : nx, l2 = log2i(N);
-        const double d = ax ? dy : dx;
-        double *h1 = tab.data() + (size_t)(2 * ax) * kMaxN, *h2 = h1 + kMaxN;
-        for (int p = 0; p < N; ++p) {
-            const int k = freq_at(p, l2);
-            const double ke = deriv_factor(k < N / 2 ? k : k - N, N, d, win_alpha, win_p);
-            h1[p] = ke / N;
-            h2[p] = -ke * ke / N;
-        }
-    }
+    derivative_tables(nx, dx, win_alpha, win_p, tab.data(), tab.data() + kMaxN);
+    derivative_tables(ny, dy, win_alpha, win_p, tab.data() + 2 * kMaxN, tab.data() + 3 * kMaxN);
     NA_TRY(cudaMemcpyAsync(k1x, tab.data(), 4 * (size_t)kMaxN * sizeof(double), cudaMemcpyHostToDevice, s));
 
     // d_y rho (column pass) and d_x rho (row pass) into the scratch fields
-    int W = 16 < nx ? 16 : nx;
-    while (W > 2 && (size_t)ny * W * 8 > 112 * 1024) W >>= 1;
+    Geometry geo;
+    pass_geometry(nx, ny, sizeof(double), &geo);
+    const int W = geo.colW;
     ColArgs<double> ca{};
     ca.nx = nx;
     ca.ny = ny;
@@ -151,19 +122,16 @@ extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, dou
     ca.log2W = log2i(W);
     ca.ay = Axis<double>{twy, k1y, k2y, log2i(ny)};
     ca.jobs[0] = ColJob<double>{rho, sc + kOffRy, 1, 1.0};
-    NA_TRY(launch_col<double>(ca, 1, (size_t)ny * W * 8, s));
-    int rows = 512 / nx;
-    if (rows < 1) rows = 1;
-    if (rows > ny) rows = ny;
+    NA_TRY(launch_col<double>(ca, 1, geo.col_smem, s));
     RowDerivArgs<double> ra{};
     ra.in[0] = rho;
     ra.out[0] = sc + kOffRx;
     ra.nin = 1;
     ra.nx = nx;
     ra.ny = ny;
-    ra.rows = rows;
+    ra.rows = geo.rows_rowd;
     ra.ax = Axis<double>{twx, k1x, k2x, log2i(nx)};
-    NA_TRY(launch_row_deriv<double>(ra, (size_t)2 * rows * nx * 8, s));
+    NA_TRY(launch_row_deriv<double>(ra, geo.rowd_smem, s));
 
     // per-block partial sums, then the final reduction on the host
     const int blocks = (int)std::min<long long>(kMaxBlocks, (n + 255) / 256);
