@@ -149,6 +149,9 @@ template <typename R, int LOG2N> struct LineFFT {
     static constexpr int NP16 = LOG2N >= 4 ? LOG2N / 4 : 0;  // radix-16 passes
     static constexpr int RL = LOG2N >= 4 ? (1 << (LOG2N & 3)) : N;  // final radix (1 = none)
     static constexpr int SMEM = N + (N >> 4);                // padded line buffer, complex elements
+    // distance between consecutive line buffers: two extra elements shift each buffer by 16 or
+    // 32 bytes, so lines that share a warp (column tiles) do not collide on the same banks
+    static constexpr int STRIDE = SMEM + 2;
     typedef C<R> CT;
 
     static __device__ __forceinline__ int pad(int p) { return p + (p >> 4); }

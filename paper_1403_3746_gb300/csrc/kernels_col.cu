@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) col_deriv_kernel(const _
     CT v[F::E];
 #pragma unroll
     for (int e = 0; e < F::E; ++e) v[e] = in[(size_t)(t + F::G * e) * rs];
-    CT *buf = sbuf + l * F::SMEM;
+    CT *buf = sbuf + l * F::STRIDE;
     F::template forward<reg::SyncCta>(v, buf, t, a.ay.tw);
     F::multiply(v, t, job.order, job.c, a.ay.k1, a.ay.k2);
     F::template inverse<reg::SyncCta>(v, buf, t, a.ay.tw);

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) row_deriv_kernel(const _
         const size_t g = row + t + G * e;
         v[e] = reg::mk<R>(a.in[ka][g], kb < a.nin ? a.in[kb][g] : R(0));
     }
-    CT *buf = sb + (size_t)slot * F::SMEM;
+    CT *buf = sb + (size_t)slot * F::STRIDE;
     F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
     F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
     F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);

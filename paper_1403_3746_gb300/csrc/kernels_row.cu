@@ -5,6 +5,8 @@
 // registers (fft_reg.cuh) and leave the derivative in shared memory in natural order; the
 // node loops then map threads to consecutive x. Template parameter R is the arithmetic and
 // storage type of the path (double for LBM_FP64, float for LBM_MIXED).
+#include <type_traits>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -22,7 +24,7 @@ template <typename R, int LOG2N>
 __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N>;
     using CT = typename F::CT;
-    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::SMEM;
+    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sb = reinterpret_cast<CT *>(smem_raw);
     const int NR = a.rows, nodes = NR * NX;
@@ -215,11 +217,53 @@ __device__ __forceinline__ void equilibrium_moments(R rho, R ux, R uy, R T, R b,
     m[15] = rho * (T * e + gq * uy * uy);
 }
 
+// The 12 non-conserved moments 4..15 of the moment matrix as monomials v_x^px v_y^py, times
+// psi = |v|^2 + eta^2 for the psi rows: all known at compile time except the eta^2 part of
+// psi, which only velocities 0..3 carry.
+__host__ __device__ constexpr int mom_px(int j) {
+    constexpr int p[12] = {2, 1, 0, 1, 0, 3, 2, 1, 0, 2, 1, 0};
+    return p[j];
+}
+__host__ __device__ constexpr int mom_py(int j) {
+    constexpr int p[12] = {0, 1, 2, 0, 1, 0, 1, 2, 3, 0, 1, 2};
+    return p[j];
+}
+__host__ __device__ constexpr bool mom_psi(int j) { return j == 3 || j == 4 || j >= 9; }
+__host__ __device__ constexpr double ipow(double x, int n) { return n == 0 ? 1.0 : x * ipow(x, n - 1); }
+__host__ __device__ constexpr double mom_mono(int j, int i) {
+    return ipow(vel_x(i), mom_px(j)) * ipow(vel_y(i), mom_py(j));
+}
+// moment-matrix entry (4 + j, i) without the eta^2 part, and the coefficient of eta^2
+__host__ __device__ constexpr double mom_entry(int j, int i) {
+    return mom_mono(j, i) * (mom_psi(j) ? vel_sq(i) : 1.0);
+}
+__host__ __device__ constexpr double mom_entry_eta(int j, int i) {
+    return (mom_psi(j) && i < 4) ? mom_mono(j, i) : 0.0;
+}
+// Reflection symmetry: for an axis velocity the inverse-matrix entry of a moment that is odd
+// in the velocity's zero component vanishes identically (for every eta0).
+__host__ __device__ constexpr bool minv_zero(int i, int j) {
+    return i < 8 && ((vel_y(i) == 0.0 && (mom_py(j) & 1)) || (vel_x(i) == 0.0 && (mom_px(j) & 1)));
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
+template <int B, int E, class Fn> __device__ __forceinline__ void static_for(Fn &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// Prefetch a contiguous span into L2 (bulk, asynchronous; no data returned)
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename R, int LOG2N, bool MOMENT_SPACE>
 __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N>;
     using CT = typename F::CT;
-    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::SMEM;
+    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sb = reinterpret_cast<CT *>(smem_raw);
     const int NR = a.rows, nodes = NR * NX;
@@ -228,6 +272,37 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
     const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
     const bool col = !(a.flags & LBM_FLAG_NO_COLLISION);
     const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
+
+    // the node loop's other inputs start moving into L2 while the lines are transformed
+    {
+        const unsigned bytes = (unsigned)((size_t)nodes * sizeof(R));
+        if ((bytes & 15) == 0 && threadIdx.x < 45) {
+            const int k = threadIdx.x;
+            const R *p = nullptr;
+            if (k < 12) p = adv ? a.Ay + k * plane : nullptr;
+            else if (k < 28) p = a.fbase != a.fs ? a.fbase + (k - 12) * plane : nullptr;
+            else if (k < 32) p = a.fs + (2 * (k - 28) + 1) * plane;  // fields with v_x = 0
+            else {
+                switch (k - 32) {
+                    case 0: p = a.rho; break;
+                    case 1: p = a.ux; break;
+                    case 2: p = a.uy; break;
+                    case 3: p = a.T; break;
+                    case 4: p = a.ry; break;
+                    case 5: p = a.dQx; break;
+                    case 6: p = a.dSxx; break;
+                    case 7: p = a.dSxy; break;
+                    case 8: p = a.Cnum; break;
+                    case 9: p = a.dQy; break;
+                    case 10: p = a.dSxyy; break;
+                    case 11: p = a.dSyy; break;
+                    default: p = a.ddivuy; break;
+                }
+                if (!frc && k >= 36) p = nullptr;
+            }
+            if (p) prefetch_l2(p + g0, bytes);
+        }
+    }
 
     if (adv) {
         // 6 lines per row (the 12 fields with v_x != 0, paired); LB lines per batch
@@ -278,21 +353,27 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
 #pragma unroll
         for (int i = 0; i < 16; ++i) fsv[i] = a.fs[i * plane + g];
         if (MOMENT_SPACE) {
-#pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                R mf = 0;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) mf += a.mrow[j * 16 + i] * fsv[i];
-                dm[j] = m[4 + j] - mf;
-            }
+            const R eta2 = a.eta2;
+            static_for<0, 12>([&](auto J) {
+                constexpr int j = decltype(J)::value;
+                R mf = 0, me = 0;
+                static_for<0, 16>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    if constexpr (mom_entry(j, i) != 0.0) mf += R(mom_entry(j, i)) * fsv[i];
+                    if constexpr (mom_entry_eta(j, i) != 0.0) me += R(mom_entry_eta(j, i)) * fsv[i];
+                });
+                dm[j] = m[4 + j] - (mf + eta2 * me);
+            });
         }
         MomentSums<R> acc;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             R ne = 0, fe;
             if (MOMENT_SPACE) {
-#pragma unroll
-                for (int j = 0; j < 12; ++j) ne += a.minv[i * 16 + 4 + j] * dm[j];
+                static_for<0, 12>([&](auto J) {
+                    constexpr int j = decltype(J)::value;
+                    if (!minv_zero(i, j)) ne += a.minv[i * 16 + 4 + j] * dm[j];
+                });
                 fe = fsv[i] + ne;
             } else {
                 fe = 0;

@@ -111,7 +111,6 @@ struct lbm_ctx {
     double *k1x = nullptr, *k2x = nullptr, *k1y = nullptr, *k2y = nullptr;
     float *k1x32 = nullptr, *k2x32 = nullptr, *k1y32 = nullptr, *k2y32 = nullptr;
     double minv[256];
-    double mrow[192];  // moment-matrix rows 4..15
 
     // launch geometry
     Geometry geo;
@@ -251,7 +250,7 @@ int run_stage(lbm_ctx *c, int stage) {
         }
         a.flags = p.flags;
         for (int k = 0; k < 256; ++k) a.minv[k] = (R)c->minv[k];
-        for (int k = 0; k < 192; ++k) a.mrow[k] = (R)c->mrow[k];
+        a.eta2 = (R)(p.eta0 * p.eta0);
         LaunchTimer t(c, LBM_K_UPDATE);
         CU_TRY(launch_update<R>(a, c->geo.upd_smem, c->stream));
     }
@@ -335,12 +334,6 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
         return fail(LBM_ERR_CUDA, "no CUDA device");
-    }
-    {
-        double rows[16][16];
-        moment_rows(params->eta0, rows);
-        for (int r = 4; r < 16; ++r)
-            for (int i = 0; i < 16; ++i) c->mrow[(r - 4) * 16 + i] = rows[r][i];
     }
     if (!moment_inverse(params->eta0, c->minv)) {
         delete c;

@@ -54,11 +54,11 @@ __host__ __device__ __forceinline__ int xslot(int i) { return i < 8 ? ((i & 1) ?
 __host__ __device__ __forceinline__ int yfield(int k) { return k < 4 ? 2 * k + 1 : k + 4; }
 __host__ __device__ __forceinline__ int yslot(int i) { return i < 8 ? ((i & 1) ? i / 2 : -1) : i - 4; }
 
-// Line-transform geometry (fft_reg.cuh): points per thread, threads per line, and the padded
-// shared-memory line buffer in complex elements, for a line of 2^log2n points.
+// Line-transform geometry (fft_reg.cuh): points per thread, threads per line, and the stride
+// between padded shared-memory line buffers in complex elements, for a line of 2^log2n points.
 __host__ __device__ constexpr int line_E(int log2n) { return log2n < 4 ? (1 << log2n) : 16; }
 __host__ __device__ constexpr int line_G(int log2n) { return (1 << log2n) / line_E(log2n); }
-__host__ __device__ constexpr int line_smem(int log2n) { return (1 << log2n) + ((1 << log2n) >> 4); }
+__host__ __device__ constexpr int line_smem(int log2n) { return (1 << log2n) + ((1 << log2n) >> 4) + 2; }
 // threads per CTA of the line-transform kernels: float32 768 (<= 85 registers per thread),
 // float64 384 (<= 170): one line's 16 complex points live in registers
 template <typename R> struct MaxThreads {
@@ -127,11 +127,10 @@ template <typename R> struct UpdateArgs {
     const R *ry, *dQx, *dSxx, *dSxy, *Cnum, *dQy, *dSxyy, *dSyy, *ddivuy;
     int nx, ny, rows;
     Axis<R> ax;
-    R tau_inv, h, K, b;
+    R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
     R psi_hi[16], psi_lo[16];  // psi_i = |v_i|^2 + eta_i^2 as a two-term sum (hi + lo)
     int flags;
     R minv[256];  // inverse of the 16x16 moment matrix, row-major
-    R mrow[192];  // rows 4..15 of the moment matrix (the non-conserved moments), row-major
 };
 
 struct InitArgs {
