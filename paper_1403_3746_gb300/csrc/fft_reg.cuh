@@ -257,6 +257,14 @@ template <typename R, int LOG2N> struct LineFFT {
         inv_from<NP16 - 1, SYNC>(v, buf, t, tw);
     }
 
+    // Barriers only: a thread with no line in this transform calls it so that the block's
+    // barrier count matches the threads that run forward() or inverse() (same count each).
+    static constexpr int EXCHANGES = (NP16 > 1 ? NP16 - 1 : 0) + ((RL > 1 && NP16 > 0) ? 1 : 0);
+    template <class SYNC> static __device__ __forceinline__ void idle() {
+#pragma unroll
+        for (int k = 0; k < 2 * EXCHANGES; ++k) SYNC::run();
+    }
+
     // v <- d^order * c * v at positions E t + e (tables k1 = W k_eff / N, k2 = -(W k_eff)^2 / N)
     static __device__ __forceinline__ void multiply(CT v[E], int t, int order, R c, const R *__restrict__ k1,
                                                     const R *__restrict__ k2) {

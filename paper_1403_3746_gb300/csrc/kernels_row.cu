@@ -13,12 +13,12 @@ namespace lbm {
 
 // ---------------------------------------------------------------------------------------
 // Macroscopic chain, row pass (Sec. 2.2, the coefficients after Eq. (2)).
-// In: rho, u, T and their y-derivatives from the column pass. Per row three lines:
-// A = rho + i T, B = u_x + i d_y u_y, C = u_y; each gives d_x (first output) and d_xx
-// (second output, used for A and B):
-//   A -> (d_x rho, d_x T), (d_xx rho, -);  B -> (d_x u_x, d_x d_y u_y), (d_xx u_x, -);  C -> (d_x u_y, -).
-// Then per node: P^w, Lambda, S, Q, div u, the partial numerator of C; and a second round
-// of lines (Q_x + i S_xx, S_xy) gives d_x Q_x, d_x S_xx, d_x S_xy.
+// In: rho, u, T and their y-derivatives from the column pass. Per row two lines:
+// A = rho + i T -> (d_x rho, d_x T) and, from the same spectrum, d_xx rho;
+// B = u_x + i u_y -> (d_x u_x, d_x u_y).
+// Then per node: P^w, Lambda, S, Q, div u and the numerator of C without its
+// d_x(div u) term. A second round of lines, (Q_x + i S_xx) and (S_xy + i div u), gives
+// d_x Q_x, d_x S_xx, d_x S_xy and d_x(div u), which completes that numerator.
 // ---------------------------------------------------------------------------------------
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
@@ -28,10 +28,14 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sb = reinterpret_cast<CT *>(smem_raw);
     const int NR = a.rows, nodes = NR * NX;
+    // per row: line A owns buffers A1, A2; line B owns B1; then two per-node arrays
+    CT *lines = sb;                                  // [2 NR][2 SM]
+    R *cpart = reinterpret_cast<R *>(sb + (size_t)4 * NR * SM);  // [NR][NX] partial numerator of C
+    R *krx = cpart + nodes;                          // [NR][NX] K rho d_x rho
     const size_t g0 = (size_t)blockIdx.x * nodes;
     const int slot = threadIdx.x / G, t = threadIdx.x % G;
     const int kind = slot / NR, r = slot % NR;
-    CT *O1 = sb + (size_t)slot * 2 * SM, *O2 = O1 + SM;
+    CT *O1 = lines + (size_t)slot * 2 * SM, *O2 = O1 + SM;
     const size_t rowg = g0 + (size_t)r * NX;
 
     // round 1: derivatives of the moments along x
@@ -39,41 +43,42 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const size_t g = rowg + t + G * e;
-        if (kind == 0) v[e] = reg::mk<R>(a.rho[g], a.T[g]);
-        else if (kind == 1) v[e] = reg::mk<R>(a.ux[g], a.uyy[g]);
-        else v[e] = reg::mk<R>(a.uy[g], R(0));
+        v[e] = kind == 0 ? reg::mk<R>(a.rho[g], a.T[g]) : reg::mk<R>(a.ux[g], a.uy[g]);
     }
     F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
-    F::storeF(v, O2, t);  // keep the spectrum for the second derivative (thread-private slots)
+    if (kind == 0) F::storeF(v, O2, t);  // keep the spectrum of A for d_xx rho (thread-private slots)
     F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
     F::template inverse<reg::SyncCta>(v, O1, t, a.ax.tw);
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < E; ++e) O1[t + G * e] = v[e];
-    F::loadF(v, O2, t);
-    F::multiply(v, t, 2, R(1), a.ax.k1, a.ax.k2);
-    F::template inverse<reg::SyncCta>(v, O2, t, a.ax.tw);
+    if (kind == 0) {
+        F::loadF(v, O2, t);
+        F::multiply(v, t, 2, R(1), a.ax.k1, a.ax.k2);
+        F::template inverse<reg::SyncCta>(v, O2, t, a.ax.tw);
+    } else {
+        F::template idle<reg::SyncCta>();
+    }
     __syncthreads();
+    if (kind == 0) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) O2[t + G * e] = v[e];
+        for (int e = 0; e < E; ++e) O2[t + G * e] = v[e];
+    }
     __syncthreads();
 
     const R K = a.K, H = a.H, q = a.q, zeta = a.zeta;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int rr = idx / NX, x = idx % NX;
         const size_t g = g0 + idx;
-        CT *A1 = sb + (size_t)(0 * NR + rr) * 2 * SM, *A2 = A1 + SM;
-        CT *B1 = sb + (size_t)(1 * NR + rr) * 2 * SM, *B2 = B1 + SM;
-        CT *C1 = sb + (size_t)(2 * NR + rr) * 2 * SM;
+        CT *A1 = lines + (size_t)(0 * NR + rr) * 2 * SM, *A2 = A1 + SM;
+        CT *B1 = lines + (size_t)(1 * NR + rr) * 2 * SM;
         const R rx = A1[x].x, Tx = A1[x].y, rxx = A2[x].x;
-        const R dux_dx = B1[x].x, dxduyy = B1[x].y, dxxux = B2[x].x;
-        const R duy_dx = C1[x].x;
+        const R dux_dx = B1[x].x, duy_dx = B1[x].y;
         const R rho = a.rho[g], T = a.T[g];
         const R ry = a.ry[g], ryy = a.ryy[g], dux_dy = a.uxy[g], duy_dy = a.uyy[g], Ty = a.Ty[g];
 
         const R lap = rxx + ryy;
         const R divu = dux_dx + duy_dy;
-        const R ddivu_x = dxxux + dxduyy;  // d_x (div u)
         // van der Waals EOS (Sec. 2.2)
         const R rT = rho * T;
         const R Pw = R(3) * rT / (R(3) - rho) - R(1.125) * rho * rho;
@@ -88,23 +93,23 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
         const R Sxx = Pn + Lxx, Sxy = Lxy, Syy = Pn + Lyy;
         const R qrT = q * rT;
         const R Qx = qrT * Tx, Qy = qrT * Ty;
-        // numerator of C without the -K rho d_y rho d_y(div u) term (needs the flux pass)
+        // numerator of C without -K rho (d_x rho d_x(div u) + d_y rho d_y(div u)): the x term is
+        // added after round 2 below, the y term by the update pass (after the flux pass)
         const R L_gradu = Lxx * dux_dx + Lxy * (duy_dx + dux_dy) + Lyy * duy_dy;
         const R r_gradu_r = rx * (dux_dx * rx + duy_dx * ry) + ry * (dux_dy * rx + duy_dy * ry);
-        const R Cnum = (Pw - rT) * divu + L_gradu - zeta * divu * divu + R(1.125) * rho * rho * divu +
-                       K * (-R(0.5) * grr * divu - rho * rx * ddivu_x - r_gradu_r);
+        cpart[idx] = (Pw - rT) * divu + L_gradu - zeta * divu * divu + R(1.125) * rho * rho * divu +
+                     K * (-R(0.5) * grr * divu - r_gradu_r);
+        krx[idx] = K * rho * rx;
         a.Qy[g] = Qy;
         a.Sxy[g] = Sxy;
         a.Syy[g] = Syy;
         a.divu[g] = divu;
-        a.Cnum[g] = Cnum;
         A1[x] = reg::mk<R>(Qx, Sxx);  // round-2 lines, same node and thread as the reads above
-        B1[x] = reg::mk<R>(Sxy, R(0));
-        C1[x] = reg::mk<R>(R(0), R(0));
+        B1[x] = reg::mk<R>(Sxy, divu);
     }
     __syncthreads();
 
-    // round 2: d_x of Q_x, S_xx (line of kind A) and S_xy (kind B); kind C idles on zeros
+    // round 2: d_x of (Q_x, S_xx) on line A and of (S_xy, div u) on line B
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = O1[t + G * e];
     F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
@@ -112,12 +117,15 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
     F::template inverse<reg::SyncCta>(v, O1, t, a.ax.tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const size_t g = rowg + t + G * e;
+        const int x = t + G * e;
+        const size_t g = rowg + x;
         if (kind == 0) {
             a.dQx[g] = v[e].x;
             a.dSxx[g] = v[e].y;
-        } else if (kind == 1) {
+        } else {
             a.dSxy[g] = v[e].x;
+            const int n = r * NX + x;
+            a.Cnum[g] = cpart[n] - krx[n] * v[e].y;  // - K rho d_x rho d_x(div u)
         }
     }
 }
@@ -332,17 +340,24 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
         const int r = idx / NX, x = idx % NX;
         const size_t g = g0 + idx;
         const R rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
-        R Bx = 0, By = 0, CC = 0, A = 0;
+        // I_i = -[A + B.(v_i - u) + (C + C_q)|v_i - u|^2] f_i^eq expands, per node, into
+        // -(al + bx v_ix + by v_iy + cc |v_i|^2) f_i^eq; h (the stage's time step) is folded in.
+        R hal = 0, hbx = 0, hby = 0, hcc = 0;
         if (frc) {
             const R rT = rho * T;
             const R irT = R(1) / rT;
-            Bx = (a.dSxx[g] + a.dSxyy[g]) * irT;
-            By = (a.dSxy[g] + a.dSyy[g]) * irT;
+            const R Bx = (a.dSxx[g] + a.dSxyy[g]) * irT;
+            const R By = (a.dSxy[g] + a.dSyy[g]) * irT;
             const R C = (a.Cnum[g] - K * rho * a.ry[g] * a.ddivuy[g]) * (R(0.5) * irT / T);
             const R Cq = (a.dQx[g] + a.dQy[g]) * (irT / T);
-            CC = C + Cq;
-            A = R(-2) * CC * T;
+            const R CC = C + Cq;
+            const R A = R(-2) * CC * T;
+            hal = h * (A - Bx * ux - By * uy + CC * (ux * ux + uy * uy));
+            hbx = h * (Bx - R(2) * CC * ux);
+            hby = h * (By - R(2) * CC * uy);
+            hcc = h * CC;
         }
+        const R htau = h * tau_inv;
         R m[16];
         equilibrium_moments<R>(rho, ux, uy, T, b, m);
         // neq_i = f_i^eq - f_i. float64: f^eq = M^-1 m^eq directly. float32: in moment space,
@@ -381,7 +396,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
                 for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * m[j];
                 ne = fe - fsv[i];
             }
-            R Ri = 0;
+            R dfo = 0;  // h R_i
             if (adv) {
                 R ad = 0;
                 const int xs = xslot(i), ys = yslot(i);
@@ -390,14 +405,16 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
                     ad += R(vel_x(i)) * ((xs & 1) ? d.y : d.x);
                 }
                 if (ys >= 0) ad += a.Ay[ys * plane + g];
-                Ri -= ad;
+                dfo -= h * ad;
             }
-            if (col) Ri += ne * tau_inv;
+            if (col) dfo += htau * ne;
             if (frc) {
-                const R cx = R(vel_x(i)) - ux, cy = R(vel_y(i)) - uy;
-                Ri -= (A + Bx * cx + By * cy + CC * (cx * cx + cy * cy)) * fe;
+                R q = hal + hcc * R(vel_sq(i));
+                if (vel_x(i) != 0.0) q += hbx * R(vel_x(i));
+                if (vel_y(i) != 0.0) q += hby * R(vel_y(i));
+                dfo -= q * fe;
             }
-            const R fo = a.fbase[i * plane + g] + h * Ri;
+            const R fo = (a.fbase == a.fs ? fsv[i] : a.fbase[i * plane + g]) + dfo;
             a.fout[i * plane + g] = fo;
             acc.add(i, fo, a.psi_hi[i], a.psi_lo[i]);
         }
@@ -436,7 +453,7 @@ template <typename R, int LOG2N> static cudaError_t launch_macro_n(const MacroAr
     cudaError_t e =
         cudaFuncSetAttribute(macro_row_kernel<R, LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    macro_row_kernel<R, LOG2N><<<a.ny / a.rows, 3 * a.rows * F::G, smem, s>>>(a);
+    macro_row_kernel<R, LOG2N><<<a.ny / a.rows, 2 * a.rows * F::G, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -747,9 +747,11 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     g->rows_upd = r;
     g->upd_smem = 6 * (size_t)r * SM;
     r = r0;
-    while (r > 1 && (3 * r * G > maxt || 6 * r * SM > 200 * 1024)) r >>= 1;  // macro: 3 lines, 2 buffers each
+    // macro: 2 lines per row with 2 buffers each, plus 2 values per node
+    auto macro_bytes = [&](int rr) { return 4 * (size_t)rr * SM + 2 * (size_t)rr * nx * esize; };
+    while (r > 1 && (2 * r * G > maxt || macro_bytes(r) > 200 * 1024)) r >>= 1;
     g->rows_macro = r;
-    g->macro_smem = 6 * (size_t)r * SM;
+    g->macro_smem = macro_bytes(r);
     r = r0;
     while (r > 1 && r * G > maxt) r >>= 1;  // one line per row (diagnostics)
     g->rows_rowd = r;
