@@ -1,6 +1,7 @@
 // Column pass: spectral y-derivatives of whole columns (Sec. 2.3, Eq. (3) along y).
 //
-// A CTA owns a tile of W adjacent columns of one input field over the full height ny. Column
+// A CTA owns a tile of W adjacent columns of one input field over the full height ny (rows of
+// the field are `ld` elements apart, see the block layout in lbm_internal.cuh). Column
 // pairs (2l, 2l+1) are packed into complex lines (L = W/2 lines); thread (l, t), with l the
 // fast index, reads the points t + G e of its line straight from global memory, so each row
 // segment of W values is one coalesced access. Forward transform, derivative multiplier
@@ -19,20 +20,20 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) col_deriv_kernel(const _
     const ColJob<R> &job = a.jobs[blockIdx.y];
     const int L = a.W >> 1;
     const int l = threadIdx.x & (L - 1), t = threadIdx.x >> (a.log2W - 1);
-    const size_t rs = (size_t)(a.nx >> 1);  // row stride in complex units
+    const size_t rsi = (size_t)(job.ld_in >> 1), rso = (size_t)(job.ld_out >> 1);  // row strides, complex units
     const int x = blockIdx.x * a.W + 2 * l;
     const CT *in = reinterpret_cast<const CT *>(job.in + x);
     CT *out = reinterpret_cast<CT *>(job.out + x);
 
     CT v[F::E];
 #pragma unroll
-    for (int e = 0; e < F::E; ++e) v[e] = in[(size_t)(t + F::G * e) * rs];
+    for (int e = 0; e < F::E; ++e) v[e] = in[(size_t)(t + F::G * e) * rsi];
     CT *buf = sbuf + l * F::STRIDE;
     F::template forward<reg::SyncCta>(v, buf, t, a.ay.tw);
     F::multiply(v, t, job.order, job.c, a.ay.k1, a.ay.k2);
     F::template inverse<reg::SyncCta>(v, buf, t, a.ay.tw);
 #pragma unroll
-    for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rs] = v[e];
+    for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rso] = v[e];
 }
 
 template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R> &a, int njobs, size_t smem,

@@ -1,4 +1,5 @@
-// Setup, readout and diagnostic kernels (not on the per-step hot path).
+// Setup, readout and diagnostic kernels (not on the per-step hot path). Fields use the
+// row-interleaved block layout of lbm_internal.cuh.
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -8,35 +9,39 @@ namespace lbm {
 template <typename F>
 __global__ void init_feq_kernel(const __grid_constant__ InitArgs a) {
     F *f = reinterpret_cast<F *>(a.f);
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.n;
+    F *m = reinterpret_cast<F *>(a.m);
+    const long long n = (long long)a.nx * a.ny;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
          g += (long long)gridDim.x * blockDim.x) {
+        const long long y = g / a.nx, x = g - y * a.nx;
         const double rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
         const double u2 = ux * ux + uy * uy, b = a.b;
         const double e = (b + 2.0) * T + u2, gq = (b + 4.0) * T + u2;
-        const double m[16] = {rho,
-                              rho * ux,
-                              rho * uy,
-                              rho * (b * T + u2),
-                              rho * (T + ux * ux),
-                              rho * ux * uy,
-                              rho * (T + uy * uy),
-                              rho * ux * e,
-                              rho * uy * e,
-                              rho * ux * (3.0 * T + ux * ux),
-                              rho * uy * (T + ux * ux),
-                              rho * ux * (T + uy * uy),
-                              rho * uy * (3.0 * T + uy * uy),
-                              rho * (T * e + gq * ux * ux),
-                              rho * gq * ux * uy,
-                              rho * (T * e + gq * uy * uy)};
+        const double mq[16] = {rho,
+                               rho * ux,
+                               rho * uy,
+                               rho * (b * T + u2),
+                               rho * (T + ux * ux),
+                               rho * ux * uy,
+                               rho * (T + uy * uy),
+                               rho * ux * e,
+                               rho * uy * e,
+                               rho * ux * (3.0 * T + ux * ux),
+                               rho * uy * (T + ux * ux),
+                               rho * ux * (T + uy * uy),
+                               rho * uy * (3.0 * T + uy * uy),
+                               rho * (T * e + gq * ux * ux),
+                               rho * gq * ux * uy,
+                               rho * (T * e + gq * uy * uy)};
+        F *fn = f + y * NF_F * a.nx + x;
         double mr = 0, mjx = 0, mjy = 0, mE = 0;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             double fe = 0;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * m[j];
+            for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * mq[j];
             const F fs = (F)fe;
-            f[i * a.n + g] = fs;
+            fn[i * a.nx] = fs;
             const double fd = (double)fs;
             mr += fd;
             mjx += vel_x(i) * fd;
@@ -44,10 +49,11 @@ __global__ void init_feq_kernel(const __grid_constant__ InitArgs a) {
             mE += a.psi[i] * fd;
         }
         const double ir = 1.0 / mr, nux = mjx * ir, nuy = mjy * ir;
-        static_cast<F *>(a.mrho)[g] = (F)mr;
-        static_cast<F *>(a.mux)[g] = (F)nux;
-        static_cast<F *>(a.muy)[g] = (F)nuy;
-        static_cast<F *>(a.mT)[g] = (F)((mE * ir - (nux * nux + nuy * nuy)) / b);
+        F *mn = m + y * NF_M * a.nx + x;
+        mn[M_RHO * a.nx] = (F)mr;
+        mn[M_UX * a.nx] = (F)nux;
+        mn[M_UY * a.nx] = (F)nuy;
+        mn[M_T * a.nx] = (F)((mE * ir - (nux * nux + nuy * nuy)) / b);
     }
 }
 
@@ -55,22 +61,27 @@ __global__ void init_feq_kernel(const __grid_constant__ InitArgs a) {
 template <typename F>
 __global__ void moments_kernel(const __grid_constant__ MomArgs a) {
     const F *f = reinterpret_cast<const F *>(a.f);
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.n;
+    F *m = reinterpret_cast<F *>(a.m);
+    const long long n = (long long)a.nx * a.ny;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
          g += (long long)gridDim.x * blockDim.x) {
+        const long long y = g / a.nx, x = g - y * a.nx;
+        const F *fn = f + y * NF_F * a.nx + x;
         double mr = 0, mjx = 0, mjy = 0, mE = 0;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const double fd = (double)f[i * a.n + g];
+            const double fd = (double)fn[i * a.nx];
             mr += fd;
             mjx += vel_x(i) * fd;
             mjy += vel_y(i) * fd;
             mE += a.psi[i] * fd;
         }
         const double ir = 1.0 / mr, nux = mjx * ir, nuy = mjy * ir;
-        static_cast<F *>(a.rho)[g] = (F)mr;
-        static_cast<F *>(a.ux)[g] = (F)nux;
-        static_cast<F *>(a.uy)[g] = (F)nuy;
-        static_cast<F *>(a.T)[g] = (F)((mE * ir - (nux * nux + nuy * nuy)) / a.b);
+        F *mn = m + y * NF_M * a.nx + x;
+        mn[M_RHO * a.nx] = (F)mr;
+        mn[M_UX * a.nx] = (F)nux;
+        mn[M_UY * a.nx] = (F)nuy;
+        mn[M_T * a.nx] = (F)((mE * ir - (nux * nux + nuy * nuy)) / a.b);
     }
 }
 
@@ -82,10 +93,13 @@ __global__ void __launch_bounds__(256) diag_kernel(const __grid_constant__ DiagA
     const R *prho = static_cast<const R *>(a.rho), *pux = static_cast<const R *>(a.ux);
     const R *puy = static_cast<const R *>(a.uy), *pT = static_cast<const R *>(a.T);
     const R *prx = static_cast<const R *>(a.rx), *pry = static_cast<const R *>(a.ry);
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.n;
+    const long long n = (long long)a.nx * a.ny;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
          g += (long long)gridDim.x * blockDim.x) {
-        const double rho = prho[g], ux = pux[g], uy = puy[g], T = pT[g];
-        const double rx = prx[g], ry = pry[g];
+        const long long y = g / a.nx, x = g - y * a.nx;
+        const long long o = y * a.ld + x;
+        const double rho = prho[o], ux = pux[o], uy = puy[o], T = pT[o];
+        const double rx = prx[o], ry = pry[o];
         const double u2 = ux * ux + uy * uy;
         s0 += rho;
         s1 += rho * ux;
@@ -121,32 +135,30 @@ __global__ void twiddle_kernel(double2 *tw64, float2 *tw32, int n) {
     }
 }
 
-template <typename F>
-__global__ void convert_out_kernel(const F *f, double *out, long long n) {
+// out[y][x] = src[y ld + x] as float64
+template <typename R>
+__global__ void field_out_kernel(const R *src, int ld, double *out, int nx, int ny) {
+    const long long n = (long long)nx * ny;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
-         g += (long long)gridDim.x * blockDim.x)
-        out[g] = (double)f[g];
-}
-template <typename F>
-__global__ void convert_in_kernel(const double *in, F *f, long long n) {
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
-         g += (long long)gridDim.x * blockDim.x)
-        f[g] = (F)in[g];
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long y = g / nx, x = g - y * nx;
+        out[g] = (double)src[y * ld + x];
+    }
 }
 
 // Generic spectral x-derivative of up to 4 fields (paired into complex lines), `rows` rows
-// per CTA, G threads per line (fft_reg.cuh).
+// per CTA, G threads per line (fft_reg.cuh); row y of every field at + y * ld.
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(MaxThreads<R>::value) row_deriv_kernel(const __grid_constant__ RowDerivArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N>;
     using CT = typename F::CT;
-    constexpr int NX = F::N, G = F::G, E = F::E;
+    constexpr int G = F::G, E = F::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sb = reinterpret_cast<CT *>(smem_raw);
     const int NR = a.rows;
     const int slot = threadIdx.x / G, t = threadIdx.x % G;
     const int p = slot / NR, r = slot % NR;
-    const size_t row = (size_t)blockIdx.x * NR * NX + (size_t)r * NX;
+    const size_t row = (size_t)(blockIdx.x * NR + r) * a.ld;
     const int ka = 2 * p, kb = 2 * p + 1;
     CT v[E];
 #pragma unroll
@@ -182,11 +194,11 @@ static inline int grid_for(long long n) {
 }
 
 template <typename F> cudaError_t launch_init(const InitArgs &a, cudaStream_t s) {
-    init_feq_kernel<F><<<grid_for(a.n), 256, 0, s>>>(a);
+    init_feq_kernel<F><<<grid_for((long long)a.nx * a.ny), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <typename F> cudaError_t launch_moments(const MomArgs &a, cudaStream_t s) {
-    moments_kernel<F><<<grid_for(a.n), 256, 0, s>>>(a);
+    moments_kernel<F><<<grid_for((long long)a.nx * a.ny), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <typename R> cudaError_t launch_diag(const DiagArgs &a, int blocks, cudaStream_t s) {
@@ -197,12 +209,9 @@ cudaError_t launch_twiddles(double2 *tw64, float2 *tw32, int n, cudaStream_t s) 
     twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw64, tw32, n);
     return cudaGetLastError();
 }
-template <typename F> cudaError_t launch_convert_out(const F *f, double *out, long long n, cudaStream_t s) {
-    convert_out_kernel<F><<<grid_for(n), 256, 0, s>>>(f, out, n);
-    return cudaGetLastError();
-}
-template <typename F> cudaError_t launch_convert_in(const double *in, F *f, long long n, cudaStream_t s) {
-    convert_in_kernel<F><<<grid_for(n), 256, 0, s>>>(in, f, n);
+template <typename R>
+cudaError_t launch_field_out(const R *src, int ld, double *out, int nx, int ny, cudaStream_t s) {
+    field_out_kernel<R><<<grid_for((long long)nx * ny), 256, 0, s>>>(src, ld, out, nx, ny);
     return cudaGetLastError();
 }
 template <typename R>
@@ -220,10 +229,8 @@ template cudaError_t launch_init<double>(const InitArgs &, cudaStream_t);
 template cudaError_t launch_init<float>(const InitArgs &, cudaStream_t);
 template cudaError_t launch_moments<double>(const MomArgs &, cudaStream_t);
 template cudaError_t launch_moments<float>(const MomArgs &, cudaStream_t);
-template cudaError_t launch_convert_out<double>(const double *, double *, long long, cudaStream_t);
-template cudaError_t launch_convert_out<float>(const float *, double *, long long, cudaStream_t);
-template cudaError_t launch_convert_in<double>(const double *, double *, long long, cudaStream_t);
-template cudaError_t launch_convert_in<float>(const double *, float *, long long, cudaStream_t);
+template cudaError_t launch_field_out<double>(const double *, int, double *, int, int, cudaStream_t);
+template cudaError_t launch_field_out<float>(const float *, int, double *, int, int, cudaStream_t);
 template cudaError_t launch_row_deriv<double>(const RowDerivArgs<double> &, size_t, cudaStream_t);
 template cudaError_t launch_row_deriv<float>(const RowDerivArgs<float> &, size_t, cudaStream_t);
 template cudaError_t launch_diag<double>(const DiagArgs &, int, cudaStream_t);

@@ -3,13 +3,29 @@
 // A CTA owns `rows` consecutive rows. Each complex line (two real rows of different fields)
 // is owned by G consecutive threads, which read it with coalesced accesses, transform it in
 // registers (fft_reg.cuh) and leave the derivative in shared memory in natural order; the
-// node loops then map threads to consecutive x. Template parameter R is the arithmetic and
-// storage type of the path (double for LBM_FP64, float for LBM_MIXED).
+// node loops then map threads to consecutive x. Fields live in row-interleaved blocks
+// [ny][NF][nx] (lbm_internal.cuh): a node's fields are nx apart. Template parameter R is
+// the arithmetic and storage type of the path (double for LBM_FP64, float for LBM_MIXED).
 #include <type_traits>
 
 #include "lbm_internal.cuh"
 
 namespace lbm {
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
+template <int B, int E, class Fn> __device__ __forceinline__ void static_for(Fn &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// Prefetch a contiguous span into L2 (bulk, asynchronous; no data returned). The bulk form
+// needs a 16-byte aligned address and size; other spans (tiny grids) are skipped.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    if (((reinterpret_cast<uintptr_t>(p) | bytes) & 15) != 0 || bytes == 0) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // ---------------------------------------------------------------------------------------
 // Macroscopic chain, row pass (Sec. 2.2, the coefficients after Eq. (2)).
@@ -29,21 +45,25 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
     CT *sb = reinterpret_cast<CT *>(smem_raw);
     const int NR = a.rows, nodes = NR * NX;
     // per row: line A owns buffers A1, A2; line B owns B1; then two per-node arrays
-    CT *lines = sb;                                  // [2 NR][2 SM]
+    CT *lines = sb;                                              // [2 NR][2 SM]
     R *cpart = reinterpret_cast<R *>(sb + (size_t)4 * NR * SM);  // [NR][NX] partial numerator of C
-    R *krx = cpart + nodes;                          // [NR][NX] K rho d_x rho
-    const size_t g0 = (size_t)blockIdx.x * nodes;
+    R *krx = cpart + nodes;                                      // [NR][NX] K rho d_x rho
+    const int y0 = blockIdx.x * NR;
     const int slot = threadIdx.x / G, t = threadIdx.x % G;
     const int kind = slot / NR, r = slot % NR;
     CT *O1 = lines + (size_t)slot * 2 * SM, *O2 = O1 + SM;
-    const size_t rowg = g0 + (size_t)r * NX;
+    R *mrow = a.m + (size_t)(y0 + r) * NF_M * NX;  // this line's row of the macroscopic block
+
+    if (threadIdx.x < NR)  // the node loop's inputs from the column pass start moving into L2
+        prefetch_l2(a.m + ((size_t)(y0 + threadIdx.x) * NF_M + M_RY) * NX, 5 * NX * sizeof(R));
 
     // round 1: derivatives of the moments along x
     CT v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const size_t g = rowg + t + G * e;
-        v[e] = kind == 0 ? reg::mk<R>(a.rho[g], a.T[g]) : reg::mk<R>(a.ux[g], a.uy[g]);
+        const int x = t + G * e;
+        v[e] = kind == 0 ? reg::mk<R>(mrow[M_RHO * NX + x], mrow[M_T * NX + x])
+                         : reg::mk<R>(mrow[M_UX * NX + x], mrow[M_UY * NX + x]);
     }
     F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
     if (kind == 0) F::storeF(v, O2, t);  // keep the spectrum of A for d_xx rho (thread-private slots)
@@ -69,13 +89,14 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
     const R K = a.K, H = a.H, q = a.q, zeta = a.zeta;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int rr = idx / NX, x = idx % NX;
-        const size_t g = g0 + idx;
+        R *mn = a.m + (size_t)(y0 + rr) * NF_M * NX + x;  // this node: field k at mn[k * NX]
         CT *A1 = lines + (size_t)(0 * NR + rr) * 2 * SM, *A2 = A1 + SM;
         CT *B1 = lines + (size_t)(1 * NR + rr) * 2 * SM;
         const R rx = A1[x].x, Tx = A1[x].y, rxx = A2[x].x;
         const R dux_dx = B1[x].x, duy_dx = B1[x].y;
-        const R rho = a.rho[g], T = a.T[g];
-        const R ry = a.ry[g], ryy = a.ryy[g], dux_dy = a.uxy[g], duy_dy = a.uyy[g], Ty = a.Ty[g];
+        const R rho = mn[M_RHO * NX], T = mn[M_T * NX];
+        const R ry = mn[M_RY * NX], ryy = mn[M_RYY * NX], dux_dy = mn[M_UXY * NX], duy_dy = mn[M_UYY * NX];
+        const R Ty = mn[M_TY * NX];
 
         const R lap = rxx + ryy;
         const R divu = dux_dx + duy_dy;
@@ -100,10 +121,10 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
         cpart[idx] = (Pw - rT) * divu + L_gradu - zeta * divu * divu + R(1.125) * rho * rho * divu +
                      K * (-R(0.5) * grr * divu - r_gradu_r);
         krx[idx] = K * rho * rx;
-        a.Qy[g] = Qy;
-        a.Sxy[g] = Sxy;
-        a.Syy[g] = Syy;
-        a.divu[g] = divu;
+        mn[M_QY * NX] = Qy;
+        mn[M_SXY * NX] = Sxy;
+        mn[M_SYY * NX] = Syy;
+        mn[M_DIVU * NX] = divu;
         A1[x] = reg::mk<R>(Qx, Sxx);  // round-2 lines, same node and thread as the reads above
         B1[x] = reg::mk<R>(Sxy, divu);
     }
@@ -118,14 +139,13 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int x = t + G * e;
-        const size_t g = rowg + x;
         if (kind == 0) {
-            a.dQx[g] = v[e].x;
-            a.dSxx[g] = v[e].y;
+            mrow[M_DQX * NX + x] = v[e].x;
+            mrow[M_DSXX * NX + x] = v[e].y;
         } else {
-            a.dSxy[g] = v[e].x;
+            mrow[M_DSXY * NX + x] = v[e].x;
             const int n = r * NX + x;
-            a.Cnum[g] = cpart[n] - krx[n] * v[e].y;  // - K rho d_x rho d_x(div u)
+            mrow[M_CNUM * NX + x] = cpart[n] - krx[n] * v[e].y;  // - K rho d_x rho d_x(div u)
         }
     }
 }
@@ -254,19 +274,6 @@ __host__ __device__ constexpr bool minv_zero(int i, int j) {
     return i < 8 && ((vel_y(i) == 0.0 && (mom_py(j) & 1)) || (vel_x(i) == 0.0 && (mom_px(j) & 1)));
 }
 
-// compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
-template <int B, int E, class Fn> __device__ __forceinline__ void static_for(Fn &&f) {
-    if constexpr (B < E) {
-        f(std::integral_constant<int, B>{});
-        static_for<B + 1, E>(f);
-    }
-}
-
-// Prefetch a contiguous span into L2 (bulk, asynchronous; no data returned)
-__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 template <typename R, int LOG2N, bool MOMENT_SPACE>
 __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N>;
@@ -275,41 +282,20 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sb = reinterpret_cast<CT *>(smem_raw);
     const int NR = a.rows, nodes = NR * NX;
-    const size_t plane = (size_t)NX * a.ny;
-    const size_t g0 = (size_t)blockIdx.x * nodes;
+    const int y0 = blockIdx.x * NR;
     const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
     const bool col = !(a.flags & LBM_FLAG_NO_COLLISION);
     const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
+    const bool same_base = a.fbase == a.fs;
 
     // the node loop's other inputs start moving into L2 while the lines are transformed
-    {
-        const unsigned bytes = (unsigned)((size_t)nodes * sizeof(R));
-        if ((bytes & 15) == 0 && threadIdx.x < 45) {
-            const int k = threadIdx.x;
-            const R *p = nullptr;
-            if (k < 12) p = adv ? a.Ay + k * plane : nullptr;
-            else if (k < 28) p = a.fbase != a.fs ? a.fbase + (k - 12) * plane : nullptr;
-            else if (k < 32) p = a.fs + (2 * (k - 28) + 1) * plane;  // fields with v_x = 0
-            else {
-                switch (k - 32) {
-                    case 0: p = a.rho; break;
-                    case 1: p = a.ux; break;
-                    case 2: p = a.uy; break;
-                    case 3: p = a.T; break;
-                    case 4: p = a.ry; break;
-                    case 5: p = a.dQx; break;
-                    case 6: p = a.dSxx; break;
-                    case 7: p = a.dSxy; break;
-                    case 8: p = a.Cnum; break;
-                    case 9: p = a.dQy; break;
-                    case 10: p = a.dSxyy; break;
-                    case 11: p = a.dSyy; break;
-                    default: p = a.ddivuy; break;
-                }
-                if (!frc && k >= 36) p = nullptr;
-            }
-            if (p) prefetch_l2(p + g0, bytes);
-        }
+    if (threadIdx.x < NR) {
+        const size_t y = y0 + threadIdx.x;
+        prefetch_l2(a.fs + y * NF_F * NX, NF_F * NX * sizeof(R));
+        if (adv) prefetch_l2(a.Ay + y * NF_A * NX, NF_A * NX * sizeof(R));
+        if (!same_base) prefetch_l2(a.fbase + y * NF_F * NX, NF_F * NX * sizeof(R));
+        prefetch_l2(a.m + y * NF_M * NX, (M_RY + 1) * NX * sizeof(R));
+        if (frc) prefetch_l2(a.m + (y * NF_M + M_DQX) * NX, (NF_M - M_DQX) * NX * sizeof(R));
     }
 
     if (adv) {
@@ -320,8 +306,8 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
             const int line = b0 + ls;
             const int p = line / NR, r = line % NR;
             CT *buf = sb + (size_t)line * SM;
-            const R *fa = a.fs + xfield(2 * p) * plane + g0 + (size_t)r * NX;
-            const R *fb = a.fs + xfield(2 * p + 1) * plane + g0 + (size_t)r * NX;
+            const R *frow = a.fs + (size_t)(y0 + r) * NF_F * NX;
+            const R *fa = frow + xfield(2 * p) * NX, *fb = frow + xfield(2 * p + 1) * NX;
             CT v[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(fa[t + G * e], fb[t + G * e]);
@@ -338,18 +324,21 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
     const R b = a.b, K = a.K, tau_inv = a.tau_inv, h = a.h;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int r = idx / NX, x = idx % NX;
-        const size_t g = g0 + idx;
-        const R rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
+        const size_t y = y0 + r;
+        const R *fn = a.fs + y * NF_F * NX + x;       // field i at fn[i * NX]
+        const R *an = a.Ay + y * NF_A * NX + x;       // slot k at an[k * NX]
+        R *mn = a.m + y * NF_M * NX + x;              // macro field k at mn[k * NX]
+        const R rho = mn[M_RHO * NX], ux = mn[M_UX * NX], uy = mn[M_UY * NX], T = mn[M_T * NX];
         // I_i = -[A + B.(v_i - u) + (C + C_q)|v_i - u|^2] f_i^eq expands, per node, into
         // -(al + bx v_ix + by v_iy + cc |v_i|^2) f_i^eq; h (the stage's time step) is folded in.
         R hal = 0, hbx = 0, hby = 0, hcc = 0;
         if (frc) {
             const R rT = rho * T;
             const R irT = R(1) / rT;
-            const R Bx = (a.dSxx[g] + a.dSxyy[g]) * irT;
-            const R By = (a.dSxy[g] + a.dSyy[g]) * irT;
-            const R C = (a.Cnum[g] - K * rho * a.ry[g] * a.ddivuy[g]) * (R(0.5) * irT / T);
-            const R Cq = (a.dQx[g] + a.dQy[g]) * (irT / T);
+            const R Bx = (mn[M_DSXX * NX] + mn[M_DSXYY * NX]) * irT;
+            const R By = (mn[M_DSXY * NX] + mn[M_DSYY * NX]) * irT;
+            const R C = (mn[M_CNUM * NX] - K * rho * mn[M_RY * NX] * mn[M_DDIVUY * NX]) * (R(0.5) * irT / T);
+            const R Cq = (mn[M_DQX * NX] + mn[M_DQY * NX]) * (irT / T);
             const R CC = C + Cq;
             const R A = R(-2) * CC * T;
             hal = h * (A - Bx * ux - By * uy + CC * (ux * ux + uy * uy));
@@ -366,7 +355,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
         // or energy: its error scales with the non-equilibrium part instead of with rho.
         R fsv[16], dm[12];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) fsv[i] = a.fs[i * plane + g];
+        for (int i = 0; i < 16; ++i) fsv[i] = fn[i * NX];
         if (MOMENT_SPACE) {
             const R eta2 = a.eta2;
             static_for<0, 12>([&](auto J) {
@@ -380,6 +369,8 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
                 dm[j] = m[4 + j] - (mf + eta2 * me);
             });
         }
+        const R *bn = a.fbase + y * NF_F * NX + x;
+        R *on = a.fout + y * NF_F * NX + x;
         MomentSums<R> acc;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -404,7 +395,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
                     const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + x];
                     ad += R(vel_x(i)) * ((xs & 1) ? d.y : d.x);
                 }
-                if (ys >= 0) ad += a.Ay[ys * plane + g];
+                if (ys >= 0) ad += an[ys * NX];
                 dfo -= h * ad;
             }
             if (col) dfo += htau * ne;
@@ -414,16 +405,16 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
                 if (vel_y(i) != 0.0) q += hby * R(vel_y(i));
                 dfo -= q * fe;
             }
-            const R fo = (a.fbase == a.fs ? fsv[i] : a.fbase[i * plane + g]) + dfo;
-            a.fout[i * plane + g] = fo;
+            const R fo = (same_base ? fsv[i] : bn[i * NX]) + dfo;
+            on[i * NX] = fo;
             acc.add(i, fo, a.psi_hi[i], a.psi_lo[i]);
         }
         R nr, nux, nuy, nT;
         acc.finish(b, nr, nux, nuy, nT);
-        a.rho[g] = nr;
-        a.ux[g] = nux;
-        a.uy[g] = nuy;
-        a.T[g] = nT;
+        mn[M_RHO * NX] = nr;
+        mn[M_UX * NX] = nux;
+        mn[M_UY * NX] = nuy;
+        mn[M_T * NX] = nT;
     }
 }
 

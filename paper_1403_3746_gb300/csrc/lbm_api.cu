@@ -93,16 +93,11 @@ struct lbm_ctx {
 
     char *slab = nullptr;
     size_t slab_bytes = 0;
-    // state and stage scratch; element type is double (LBM_FP64) or float (LBM_MIXED)
-    void *f0 = nullptr, *f1 = nullptr, *Ay = nullptr;
-    enum {
-        RHO, UX, UY, TT,                      // moments of the current f
-        RY, RYY, UXY, UYY, TY,                // column pass: y-derivatives of the moments
-        QY, SXY, SYY, DIVU, DQX, DSXX, DSXY, CNUM,  // macro row pass outputs
-        DQY, DSXYY, DSYY, DDIVUY,             // flux column pass outputs
-        NMACRO
-    };
-    void *m[NMACRO] = {};
+    // state and stage scratch in row-interleaved blocks (lbm_internal.cuh); element type is
+    // double (LBM_FP64) or float (LBM_MIXED)
+    void *f0 = nullptr, *f1 = nullptr;  // [ny][16][nx]: f^n (then f^{n+1}) and f^{n+1/2}
+    void *Ay = nullptr;                 // [ny][12][nx]
+    void *m = nullptr;                  // [ny][NF_M][nx]
     double *partial = nullptr;
     int diag_blocks = 0;
     // per-axis tables
@@ -176,11 +171,12 @@ int run_stage(lbm_ctx *c, int stage) {
     const lbm_params &p = c->p;
     const bool adv = !(p.flags & LBM_FLAG_NO_ADVECTION);
     const bool frc = !(p.flags & LBM_FLAG_NO_FORCE);
-    const size_t plane = (size_t)c->n;
+    const int nx = c->nx;
     R *f0 = static_cast<R *>(c->f0), *f1 = static_cast<R *>(c->f1);
-    R *Ay = static_cast<R *>(c->Ay);
+    R *Ay = static_cast<R *>(c->Ay), *m = static_cast<R *>(c->m);
     const R *fs = stage == 0 ? f0 : f1;
-    auto M = [c](int k) { return static_cast<R *>(c->m[k]); };
+    const int ldf = NF_F * nx, lda = NF_A * nx, ldm = NF_M * nx;
+    auto M = [m, nx](int k) { return m + (size_t)k * nx; };  // first row of macro field k
 
     {
         ColArgs<R> a = col_args<R>(c);
@@ -188,14 +184,14 @@ int run_stage(lbm_ctx *c, int stage) {
         if (adv)
             for (int k = 0; k < 12; ++k) {
                 const int i = yfield(k);
-                a.jobs[nj++] = ColJob<R>{fs + i * plane, Ay + k * plane, 1, (R)vel_y(i)};
+                a.jobs[nj++] = ColJob<R>{fs + (size_t)i * nx, Ay + (size_t)k * nx, ldf, lda, 1, (R)vel_y(i)};
             }
         if (frc) {
-            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::RHO), M(lbm_ctx::RY), 1, R(1)};
-            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::RHO), M(lbm_ctx::RYY), 2, R(1)};
-            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::UX), M(lbm_ctx::UXY), 1, R(1)};
-            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::UY), M(lbm_ctx::UYY), 1, R(1)};
-            a.jobs[nj++] = ColJob<R>{M(lbm_ctx::TT), M(lbm_ctx::TY), 1, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RY), ldm, ldm, 1, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RYY), ldm, ldm, 2, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(M_UX), M(M_UXY), ldm, ldm, 1, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(M_UY), M(M_UYY), ldm, ldm, 1, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(M_T), M(M_TY), ldm, ldm, 1, R(1)};
         }
         if (nj) {
             LaunchTimer t(c, LBM_K_COL);
@@ -205,12 +201,7 @@ int run_stage(lbm_ctx *c, int stage) {
     if (frc) {
         {
             MacroArgs<R> a{};
-            a.rho = M(lbm_ctx::RHO); a.ux = M(lbm_ctx::UX); a.uy = M(lbm_ctx::UY); a.T = M(lbm_ctx::TT);
-            a.ry = M(lbm_ctx::RY); a.ryy = M(lbm_ctx::RYY); a.uxy = M(lbm_ctx::UXY); a.uyy = M(lbm_ctx::UYY);
-            a.Ty = M(lbm_ctx::TY);
-            a.Qy = M(lbm_ctx::QY); a.Sxy = M(lbm_ctx::SXY); a.Syy = M(lbm_ctx::SYY); a.divu = M(lbm_ctx::DIVU);
-            a.dQx = M(lbm_ctx::DQX); a.dSxx = M(lbm_ctx::DSXX); a.dSxy = M(lbm_ctx::DSXY);
-            a.Cnum = M(lbm_ctx::CNUM);
+            a.m = m;
             a.nx = c->nx; a.ny = c->ny; a.rows = c->geo.rows_macro;
             a.ax = axis<R>(c, true);
             a.K = (R)p.K; a.H = (R)p.H; a.q = (R)p.q; a.zeta = (R)p.zeta;
@@ -219,10 +210,10 @@ int run_stage(lbm_ctx *c, int stage) {
         }
         {
             ColArgs<R> a = col_args<R>(c);
-            a.jobs[0] = ColJob<R>{M(lbm_ctx::QY), M(lbm_ctx::DQY), 1, R(1)};
-            a.jobs[1] = ColJob<R>{M(lbm_ctx::SXY), M(lbm_ctx::DSXYY), 1, R(1)};
-            a.jobs[2] = ColJob<R>{M(lbm_ctx::SYY), M(lbm_ctx::DSYY), 1, R(1)};
-            a.jobs[3] = ColJob<R>{M(lbm_ctx::DIVU), M(lbm_ctx::DDIVUY), 1, R(1)};
+            a.jobs[0] = ColJob<R>{M(M_QY), M(M_DQY), ldm, ldm, 1, R(1)};
+            a.jobs[1] = ColJob<R>{M(M_SXY), M(M_DSXYY), ldm, ldm, 1, R(1)};
+            a.jobs[2] = ColJob<R>{M(M_SYY), M(M_DSYY), ldm, ldm, 1, R(1)};
+            a.jobs[3] = ColJob<R>{M(M_DIVU), M(M_DDIVUY), ldm, ldm, 1, R(1)};
             LaunchTimer t(c, LBM_K_FLUX);
             CU_TRY(launch_col<R>(a, 4, c->geo.col_smem, c->stream));
         }
@@ -233,10 +224,7 @@ int run_stage(lbm_ctx *c, int stage) {
         a.fbase = f0;
         a.fout = stage == 0 ? f1 : f0;
         a.Ay = Ay;
-        a.rho = M(lbm_ctx::RHO); a.ux = M(lbm_ctx::UX); a.uy = M(lbm_ctx::UY); a.T = M(lbm_ctx::TT);
-        a.ry = M(lbm_ctx::RY); a.dQx = M(lbm_ctx::DQX); a.dSxx = M(lbm_ctx::DSXX); a.dSxy = M(lbm_ctx::DSXY);
-        a.Cnum = M(lbm_ctx::CNUM); a.dQy = M(lbm_ctx::DQY); a.dSxyy = M(lbm_ctx::DSXYY);
-        a.dSyy = M(lbm_ctx::DSYY); a.ddivuy = M(lbm_ctx::DDIVUY);
+        a.m = m;
         a.nx = c->nx; a.ny = c->ny; a.rows = c->geo.rows_upd;
         a.ax = axis<R>(c, true);
         a.tau_inv = (R)(1.0 / p.tau);
@@ -360,7 +348,7 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     parts.push_back({&c->f0, 16 * plane_f});
     parts.push_back({&c->f1, 16 * plane_f});
     parts.push_back({&c->Ay, 12 * plane_f});
-    for (int k = 0; k < lbm_ctx::NMACRO; ++k) parts.push_back({&c->m[k], plane_f});
+    parts.push_back({&c->m, (size_t)NF_M * plane_f});
     parts.push_back({reinterpret_cast<void **>(&c->partial), (size_t)c->diag_blocks * 5 * 8});
     parts.push_back({reinterpret_cast<void **>(&c->tw64x), (size_t)nx * 16});
     parts.push_back({reinterpret_cast<void **>(&c->tw64y), (size_t)ny * 16});
@@ -429,8 +417,9 @@ static int init_common(lbm_ctx *c, const double *rho, const double *ux, const do
     InitArgs a{};
     a.rho = rho; a.ux = ux; a.uy = uy; a.T = T;
     a.f = c->f0;
-    a.mrho = c->m[lbm_ctx::RHO]; a.mux = c->m[lbm_ctx::UX]; a.muy = c->m[lbm_ctx::UY]; a.mT = c->m[lbm_ctx::TT];
-    a.n = c->n;
+    a.m = c->m;
+    a.nx = c->nx;
+    a.ny = c->ny;
     a.b = c->p.b;
     for (int k = 0; k < 256; ++k) a.minv[k] = c->minv[k];
     for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
@@ -479,73 +468,89 @@ int lbm_step(lbm_handle c, int n) {
     return LBM_OK;
 }
 
+// rho, u_x, u_y, T (macro fields 0..3) as dense float64 [ny][nx] device arrays
+static int moments_to_device(lbm_ctx *c, double *const out[4]) {
+    for (int k = 0; k < 4; ++k) {
+        if (!out[k]) continue;
+        const int ld = NF_M * c->nx;
+        if (c->mixed)
+            CU_TRY(launch_field_out<float>(static_cast<const float *>(c->m) + (size_t)k * c->nx, ld, out[k], c->nx,
+                                           c->ny, c->stream));
+        else
+            CU_TRY(launch_field_out<double>(static_cast<const double *>(c->m) + (size_t)k * c->nx, ld, out[k],
+                                            c->nx, c->ny, c->stream));
+    }
+    return LBM_OK;
+}
+
 int lbm_moments_device(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
     if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    double *out[4] = {rho, ux, uy, T};
-    for (int k = 0; k < 4; ++k) {
-        if (!out[k]) continue;
-        if (c->mixed)
-            CU_TRY(launch_convert_out<float>(static_cast<const float *>(c->m[k]), out[k], c->n, c->stream));
-        else
-            CU_TRY(cudaMemcpyAsync(out[k], c->m[k], (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
-    }
-    return LBM_OK;
+    double *const out[4] = {rho, ux, uy, T};
+    return moments_to_device(c, out);
 }
 
 int lbm_moments(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
     if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    double *out[4] = {rho, ux, uy, T};
-    std::vector<float> tmp(c->mixed ? (size_t)c->n : 0);
-    for (int k = 0; k < 4; ++k) {
-        if (!out[k]) continue;
-        if (c->mixed) {
-            CU_TRY(cudaMemcpyAsync(tmp.data(), c->m[k], (size_t)c->n * 4, cudaMemcpyDeviceToHost, c->stream));
-            CU_TRY(cudaStreamSynchronize(c->stream));
-            for (long long g = 0; g < c->n; ++g) out[k][g] = (double)tmp[g];
-        } else {
-            CU_TRY(cudaMemcpyAsync(out[k], c->m[k], (size_t)c->n * 8, cudaMemcpyDeviceToHost, c->stream));
-        }
-    }
+    // gather through the half-step buffer (free outside lbm_step), 4 x n doubles <= its size
+    double *st = static_cast<double *>(c->f1);
+    double *const dev[4] = {rho ? st : nullptr, ux ? st + c->n : nullptr, uy ? st + 2 * c->n : nullptr,
+                            T ? st + 3 * c->n : nullptr};
+    int rc = moments_to_device(c, dev);
+    if (rc) return rc;
+    double *const host[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k)
+        if (host[k])
+            CU_TRY(cudaMemcpyAsync(host[k], dev[k], (size_t)c->n * 8, cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 
+// the API's [16][ny][nx] float64 layout <-> the device block [ny][16][nx]
 int lbm_get_f(lbm_handle c, double *f16) {
     if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
     if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    const size_t cnt = (size_t)16 * c->n;
-    if (!c->mixed) {
-        CU_TRY(cudaMemcpyAsync(f16, c->f0, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
-        CU_TRY(cudaStreamSynchronize(c->stream));
-        return LBM_OK;
-    }
-    std::vector<float> tmp(cnt);
-    CU_TRY(cudaMemcpyAsync(tmp.data(), c->f0, cnt * 4, cudaMemcpyDeviceToHost, c->stream));
+    const size_t cnt = (size_t)16 * c->n, nx = c->nx, ny = c->ny;
+    std::vector<unsigned char> tmp(cnt * c->fsize);
+    CU_TRY(cudaMemcpyAsync(tmp.data(), c->f0, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
-    for (size_t k = 0; k < cnt; ++k) f16[k] = (double)tmp[k];
+    for (size_t y = 0; y < ny; ++y)
+        for (size_t i = 0; i < 16; ++i) {
+            const size_t src = (y * 16 + i) * nx, dst = (i * ny + y) * nx;
+            if (c->mixed) {
+                const float *sp = reinterpret_cast<const float *>(tmp.data()) + src;
+                for (size_t x = 0; x < nx; ++x) f16[dst + x] = (double)sp[x];
+            } else {
+                std::memcpy(f16 + dst, reinterpret_cast<const double *>(tmp.data()) + src, nx * 8);
+            }
+        }
     return LBM_OK;
 }
 
 int lbm_set_f(lbm_handle c, const double *f16) {
     if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
-    const size_t cnt = (size_t)16 * c->n;
+    const size_t cnt = (size_t)16 * c->n, nx = c->nx, ny = c->ny;
     for (size_t k = 0; k < cnt; ++k)
         if (!std::isfinite(f16[k])) return fail(LBM_ERR_NONFINITE, "f16[%zu] is not finite", k);
-    if (!c->mixed) {
-        CU_TRY(cudaMemcpyAsync(c->f0, f16, cnt * 8, cudaMemcpyHostToDevice, c->stream));
-        CU_TRY(cudaStreamSynchronize(c->stream));
-    } else {
-        std::vector<float> tmp(cnt);
-        for (size_t k = 0; k < cnt; ++k) tmp[k] = (float)f16[k];
-        CU_TRY(cudaMemcpyAsync(c->f0, tmp.data(), cnt * 4, cudaMemcpyHostToDevice, c->stream));
-        CU_TRY(cudaStreamSynchronize(c->stream));
-    }
+    std::vector<unsigned char> tmp(cnt * c->fsize);
+    for (size_t y = 0; y < ny; ++y)
+        for (size_t i = 0; i < 16; ++i) {
+            const size_t src = (i * ny + y) * nx, dst = (y * 16 + i) * nx;
+            if (c->mixed) {
+                float *dp = reinterpret_cast<float *>(tmp.data()) + dst;
+                for (size_t x = 0; x < nx; ++x) dp[x] = (float)f16[src + x];
+            } else {
+                std::memcpy(reinterpret_cast<double *>(tmp.data()) + dst, f16 + src, nx * 8);
+            }
+        }
+    CU_TRY(cudaMemcpyAsync(c->f0, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
     MomArgs a{};
     a.f = c->f0;
-    a.rho = c->m[lbm_ctx::RHO]; a.ux = c->m[lbm_ctx::UX]; a.uy = c->m[lbm_ctx::UY]; a.T = c->m[lbm_ctx::TT];
-    a.n = c->n;
+    a.m = c->m;
+    a.nx = c->nx;
+    a.ny = c->ny;
     a.b = c->p.b;
     for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
     CU_TRY(c->mixed ? launch_moments<float>(a, c->stream) : launch_moments<double>(a, c->stream));
@@ -556,13 +561,16 @@ int lbm_set_f(lbm_handle c, const double *f16) {
 }  // extern "C"
 
 template <typename R> static int diag_launch(lbm_ctx *c) {
-    // d_y rho into RY, d_x rho into DQX (stage scratch, rebuilt by the next stage)
+    // d_y rho into M_RY, d_x rho into M_DQX (stage scratch, rebuilt by the next stage)
+    R *m = static_cast<R *>(c->m);
+    const int nx = c->nx, ldm = NF_M * nx;
     ColArgs<R> ca = col_args<R>(c);
-    ca.jobs[0] = ColJob<R>{static_cast<R *>(c->m[lbm_ctx::RHO]), static_cast<R *>(c->m[lbm_ctx::RY]), 1, R(1)};
+    ca.jobs[0] = ColJob<R>{m + (size_t)M_RHO * nx, m + (size_t)M_RY * nx, ldm, ldm, 1, R(1)};
     CU_TRY(launch_col<R>(ca, 1, c->geo.col_smem, c->stream));
     RowDerivArgs<R> ra{};
-    ra.in[0] = static_cast<R *>(c->m[lbm_ctx::RHO]);
-    ra.out[0] = static_cast<R *>(c->m[lbm_ctx::DQX]);
+    ra.in[0] = m + (size_t)M_RHO * nx;
+    ra.out[0] = m + (size_t)M_DQX * nx;
+    ra.ld = ldm;
     ra.nin = 1;
     ra.nx = c->nx;
     ra.ny = c->ny;
@@ -570,10 +578,16 @@ template <typename R> static int diag_launch(lbm_ctx *c) {
     ra.ax = axis<R>(c, true);
     CU_TRY(launch_row_deriv<R>(ra, c->geo.rowd_smem, c->stream));
     DiagArgs da{};
-    da.rho = c->m[lbm_ctx::RHO]; da.ux = c->m[lbm_ctx::UX]; da.uy = c->m[lbm_ctx::UY]; da.T = c->m[lbm_ctx::TT];
-    da.rx = c->m[lbm_ctx::DQX]; da.ry = c->m[lbm_ctx::RY];
+    da.rho = m + (size_t)M_RHO * nx;
+    da.ux = m + (size_t)M_UX * nx;
+    da.uy = m + (size_t)M_UY * nx;
+    da.T = m + (size_t)M_T * nx;
+    da.rx = m + (size_t)M_DQX * nx;
+    da.ry = m + (size_t)M_RY * nx;
+    da.ld = ldm;
     da.partial = c->partial;
-    da.n = c->n;
+    da.nx = c->nx;
+    da.ny = c->ny;
     da.K = c->p.K;
     da.cell = c->p.dx * c->p.dy;
     CU_TRY(launch_diag<R>(da, c->diag_blocks, c->stream));
@@ -581,7 +595,6 @@ template <typename R> static int diag_launch(lbm_ctx *c) {
 }
 
 extern "C" {
-
 int lbm_diagnostics(lbm_handle c, double out[6]) {
     if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
     if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");

@@ -91,11 +91,30 @@ template <typename R> struct Axis {
     int log2n;
 };
 
+// ---- HBM layout ------------------------------------------------------------------------
+// Row-interleaved field blocks: a group of NF fields over an nx x ny grid is stored as
+// [ny][NF][nx], so that field k of row y starts at (y NF + k) nx. One row of one field is
+// contiguous (row passes and column tiles stay coalesced), and the NF values of a node are
+// nx apart: one base address per node, the fields at immediate offsets.
+constexpr int NF_F = 16;  // distributions f_i
+constexpr int NF_A = 12;  // y-advection partials v_iy d_y f_i of the fields with v_iy != 0
+// macroscopic block: moments, then the stage intermediates
+enum MacroField {
+    M_RHO, M_UX, M_UY, M_T,                    // moments of the current f
+    M_RY, M_RYY, M_UXY, M_UYY, M_TY,           // column pass: d_y rho, d_yy rho, d_y u_x, d_y u_y, d_y T
+    M_QY, M_SXY, M_SYY, M_DIVU,                // macro row pass -> flux column pass
+    M_DQX, M_DSXX, M_DSXY, M_CNUM,             // macro row pass -> update pass
+    M_DQY, M_DSXYY, M_DSYY, M_DDIVUY,          // flux column pass -> update pass
+    NF_M
+};
+
 // ---- column derivative pass -------------------------------------------------------
-// job: out = c * d^order/dy^order (in), one field per job
+// job: out = c * d^order/dy^order (in), one field per job; in/out point at the field's first
+// row, row y at + y * ld (elements)
 template <typename R> struct ColJob {
     const R *in;
     R *out;
+    int ld_in, ld_out;
     int order;
     R c;
 };
@@ -108,10 +127,7 @@ template <typename R> struct ColArgs {
 
 // ---- row pass of the macroscopic chain ---------------------------------------------
 template <typename R> struct MacroArgs {
-    const R *rho, *ux, *uy, *T;               // moments of the stage's f
-    const R *ry, *ryy, *uxy, *uyy, *Ty;       // d_y rho, d_yy rho, d_y u_x, d_y u_y, d_y T
-    R *Qy, *Sxy, *Syy, *divu;                 // inputs of the flux column pass
-    R *dQx, *dSxx, *dSxy, *Cnum;              // d_x Q_x, d_x S_xx, d_x S_xy, partial numerator of C
+    R *m;  // macroscopic block [ny][NF_M][nx]
     int nx, ny, rows;
     Axis<R> ax;
     R K, H, q, zeta;
@@ -119,12 +135,11 @@ template <typename R> struct MacroArgs {
 
 // ---- fused update row pass -----------------------------------------------------------
 template <typename R> struct UpdateArgs {
-    const R *fs;     // f of this stage (derivatives, BGK, f^eq moments)
+    const R *fs;     // f of this stage (derivatives, BGK, f^eq moments), [ny][16][nx]
     const R *fbase;  // f^n (the stage starts from it)
     R *fout;         // f^{n+1/2} or f^{n+1}; may alias fbase (same node, same thread)
-    const R *Ay;     // 12 fields v_iy d_y f_i
-    R *rho, *ux, *uy, *T;  // in: moments of fs; out: moments of fout
-    const R *ry, *dQx, *dSxx, *dSxy, *Cnum, *dQy, *dSxyy, *dSyy, *ddivuy;
+    const R *Ay;     // [ny][12][nx]: v_iy d_y f_i
+    R *m;            // macroscopic block; moments of fs in, moments of fout out
     int nx, ny, rows;
     Axis<R> ax;
     R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
@@ -134,33 +149,36 @@ template <typename R> struct UpdateArgs {
 };
 
 struct InitArgs {
-    const double *rho, *ux, *uy, *T;  // inputs
-    void *f;                          // [16][ny][nx] R
-    void *mrho, *mux, *muy, *mT;      // moments of the stored f (R)
-    long long n;
+    const double *rho, *ux, *uy, *T;  // inputs, [ny][nx]
+    void *f;                          // [ny][16][nx] R
+    void *m;                          // macroscopic block: the moments of the stored f (R)
+    int nx, ny;
     double b;
     double minv[256];
     double psi[16];
 };
 
 struct MomArgs {
-    const void *f;
-    void *rho, *ux, *uy, *T;
-    long long n;
+    const void *f;  // [ny][16][nx]
+    void *m;        // macroscopic block
+    int nx, ny;
     double psi[16];
     double b;
 };
 
+// rho, u, T, d_x rho, d_y rho: row y of each at p + y * ld
 struct DiagArgs {
     const void *rho, *ux, *uy, *T, *rx, *ry;
+    int ld;
     double *partial;  // [blocks][5]
-    long long n;
+    int nx, ny;
     double K, cell;
 };
 
 template <typename R> struct RowDerivArgs {
     const R *in[4];
     R *out[4];
+    int ld;  // row stride of every in / out field (elements)
     int nin;  // 1..4 inputs (paired two per complex line)
     int nx, ny, rows;
     Axis<R> ax;
@@ -175,8 +193,9 @@ template <typename R> cudaError_t launch_init(const InitArgs &a, cudaStream_t s)
 template <typename R> cudaError_t launch_moments(const MomArgs &a, cudaStream_t s);
 template <typename R> cudaError_t launch_diag(const DiagArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_twiddles(double2 *tw64, float2 *tw32, int n, cudaStream_t s);
-template <typename R> cudaError_t launch_convert_out(const R *f, double *out, long long n, cudaStream_t s);
-template <typename R> cudaError_t launch_convert_in(const double *in, R *f, long long n, cudaStream_t s);
+// strided copies between a field of a block (row y at src + y ld) and a dense float64 array [ny][nx]
+template <typename R>
+cudaError_t launch_field_out(const R *src, int ld, double *out, int nx, int ny, cudaStream_t s);
 
 // sets the calling thread's message returned by lbm_last_error() (lbm_api.cu)
 void set_last_error(const char *msg);

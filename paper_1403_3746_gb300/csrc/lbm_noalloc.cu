@@ -121,11 +121,12 @@ extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, dou
     ca.W = W;
     ca.log2W = log2i(W);
     ca.ay = Axis<double>{twy, k1y, k2y, log2i(ny)};
-    ca.jobs[0] = ColJob<double>{rho, sc + kOffRy, 1, 1.0};
+    ca.jobs[0] = ColJob<double>{rho, sc + kOffRy, nx, nx, 1, 1.0};
     NA_TRY(launch_col<double>(ca, 1, geo.col_smem, s));
     RowDerivArgs<double> ra{};
     ra.in[0] = rho;
     ra.out[0] = sc + kOffRx;
+    ra.ld = nx;
     ra.nin = 1;
     ra.nx = nx;
     ra.ny = ny;
@@ -142,8 +143,10 @@ extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, dou
     da.T = T;
     da.rx = sc + kOffRx;
     da.ry = sc + kOffRy;
+    da.ld = nx;
     da.partial = sc + kOffPart;
-    da.n = n;
+    da.nx = nx;
+    da.ny = ny;
     da.K = K;
     da.cell = dx * dy;
     NA_TRY(launch_diag<double>(da, blocks, s));
