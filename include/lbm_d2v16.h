@@ -161,6 +161,43 @@ int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, double K, doub
                             const double *rho, const double *ux, const double *uy, const double *T,
                             void *stream, double out[5]);
 
+/* ---- batches of independent simulations ------------------------------------------------
+ * Many independent runs of Eq. (1) (parameter scans, ensembles over initial states, the
+ * coexistence curve of Sec. 3.1 at several temperatures need one run per temperature) are
+ * advanced together. Instances of equal grid size are stacked along y in one set of device
+ * buffers and advanced by the same launches (the row passes see one nx x (count ny) grid,
+ * the column passes take the instance from the grid's z index); groups of different sizes
+ * run as parallel branches of one CUDA graph per step. All instances share one lbm_params;
+ * every instance is its own doubly periodic domain, bit for bit the run a separate handle
+ * of the same size and params would make. */
+typedef struct lbm_batch_ctx *lbm_batch;
+
+/* Creates count >= 1 instances, instance k of size nx[k] x ny[k] (powers of two in
+ * [2, 4096]; at most 65535 instances of one size and count * ny <= 2^24 per size: else
+ * LBM_ERR_ARG). params is copied; stream as in lbm_create. *out owns all device memory. */
+int lbm_batch_create(int count, const int *nx, const int *ny, const lbm_params *params, void *stream,
+                     lbm_batch *out);
+
+/* Number of instances (0 for NULL). */
+int lbm_batch_count(lbm_batch b);
+
+/* lbm_init of instance k (host buffers [ny[k]][nx[k]]); resets that instance's step count. */
+int lbm_batch_init(lbm_batch b, int k, const double *rho, const double *ux, const double *uy, const double *T);
+
+/* Advances every instance by n >= 0 Runge-Kutta steps, asynchronously on the stream (one
+ * graph launch per step). LBM_ERR_STATE until every instance has been initialised. */
+int lbm_batch_step(lbm_batch b, int n);
+
+/* lbm_moments, lbm_get_f and lbm_diagnostics of instance k (host buffers of its size;
+ * out[5] of the diagnostics counts the steps since lbm_batch_init(b, k, ...)). Each
+ * synchronises the stream. */
+int lbm_batch_moments(lbm_batch b, int k, double *rho, double *ux, double *uy, double *T);
+int lbm_batch_get_f(lbm_batch b, int k, double *f16);
+int lbm_batch_diagnostics(lbm_batch b, int k, double out[6]);
+
+/* Frees all device memory of the batch (synchronises first). NULL is ignored. */
+void lbm_batch_destroy(lbm_batch b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,15 @@ _SIGS = {
     "lbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                _P, _P, _P, _P, _P, _D]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.POINTER(lbm_params), _P,
+                                        ctypes.POINTER(_P)]),
+    "lbm_batch_count": (ctypes.c_int, [_P]),
+    "lbm_batch_init": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
+    "lbm_batch_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lbm_batch_moments": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
+    "lbm_batch_get_f": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "lbm_batch_diagnostics": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "lbm_batch_destroy": (None, [_P]),
 }
 
 
@@ -220,3 +229,66 @@ class Simulation:
 
     def device_bytes(self):
         return int(lib().lbm_device_bytes(self._h))
+
+
+class Batch:
+    """Independent simulations advanced together (lbm_batch_create .. lbm_batch_destroy).
+    sizes: list of (nx, ny), one per instance; all share `params`."""
+
+    def __init__(self, sizes, params=None, stream=None):
+        self.sizes = [(int(nx), int(ny)) for nx, ny in sizes]
+        self.params = params if params is not None else default_params()
+        cnt = len(self.sizes)
+        nxs = (ctypes.c_int * max(cnt, 1))(*[s[0] for s in self.sizes])
+        nys = (ctypes.c_int * max(cnt, 1))(*[s[1] for s in self.sizes])
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream) if isinstance(stream, int) else (stream or ctypes.c_void_p())
+        _check(lib().lbm_batch_create(cnt, ctypes.cast(nxs, _P), ctypes.cast(nys, _P),
+                                      ctypes.byref(self.params), s, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return int(lib().lbm_batch_count(self._h))
+
+    def _shape(self, k):
+        nx, ny = self.sizes[k]
+        return (ny, nx)
+
+    def init(self, k, rho, ux, uy, T):
+        arrs = [_host(a, self._shape(k)) for a in (rho, ux, uy, T)]
+        _check(lib().lbm_batch_init(self._h, int(k), *[_ptr(a) for a in arrs]))
+
+    def step(self, n=1):
+        _check(lib().lbm_batch_step(self._h, int(n)))
+
+    def moments(self, k):
+        out = [np.empty(self._shape(k)) for _ in range(4)]
+        _check(lib().lbm_batch_moments(self._h, int(k), *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def get_f(self, k):
+        f = np.empty((16,) + self._shape(k))
+        _check(lib().lbm_batch_get_f(self._h, int(k), _ptr(f)))
+        return f
+
+    def diagnostics(self, k):
+        out = (ctypes.c_double * 6)()
+        _check(lib().lbm_batch_diagnostics(self._h, int(k), out))
+        return dict(zip(("mass", "px", "py", "energy", "umax", "steps"), list(out)))

@@ -22,8 +22,10 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) col_deriv_kernel(const _
     const int l = threadIdx.x & (L - 1), t = threadIdx.x >> (a.log2W - 1);
     const size_t rsi = (size_t)(job.ld_in >> 1), rso = (size_t)(job.ld_out >> 1);  // row strides, complex units
     const int x = blockIdx.x * a.W + 2 * l;
-    const CT *in = reinterpret_cast<const CT *>(job.in + x);
-    CT *out = reinterpret_cast<CT *>(job.out + x);
+    // blockIdx.z: instance of a batch stacked along y (ny rows each)
+    const size_t z = blockIdx.z;
+    const CT *in = reinterpret_cast<const CT *>(job.in + z * a.ny * job.ld_in + x);
+    CT *out = reinterpret_cast<CT *>(job.out + z * a.ny * job.ld_out + x);
 
     CT v[F::E];
 #pragma unroll
@@ -42,7 +44,7 @@ template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R
     cudaError_t e = cudaFuncSetAttribute(col_deriv_kernel<R, LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(a.nx / a.W, njobs);
+    dim3 grid(a.nx / a.W, njobs, a.nb > 0 ? a.nb : 1);
     col_deriv_kernel<R, LOG2N><<<grid, (a.W / 2) * F::G, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -1,11 +1,18 @@
 // C ABI of the D2V16-FFT-TLB library: simulation contexts, host-side tables and the
 // orchestration of the four kernel passes of each Runge-Kutta stage (Sec. 2.3).
+//
+// A context holds nb >= 1 independent simulations of one grid size stacked along y: the row
+// passes are row-local and treat them as one nx x (nb ny) grid, the column passes take the
+// instance from grid.z. A batch (lbm_batch_*) groups instances of different sizes into
+// contexts, one per size, whose steps run as parallel branches of one CUDA graph.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "lbm_internal.cuh"
@@ -39,7 +46,7 @@ int ilog2(int n) {
     return l;
 }
 
-// Inverse of the 16x16 matrix whose rows are the moment functionals
+// Rows of the 16x16 matrix of moment functionals
 // 1; v_x, v_y; psi; v_x v_x, v_x v_y, v_y v_y; psi v_x, psi v_y; v_x^3, v_x^2 v_y, v_x v_y^2, v_y^3;
 // psi v_x^2, psi v_x v_y, psi v_y^2 (psi = v^2 + eta^2) evaluated on the 16 velocities.
 void moment_rows(double eta0, double rows[16][16]) {
@@ -53,6 +60,7 @@ void moment_rows(double eta0, double rows[16][16]) {
     }
 }
 
+// its inverse, by Gauss-Jordan elimination with partial pivoting
 bool moment_inverse(double eta0, double out[256]) {
     double a[16][32], rows[16][16];
     moment_rows(eta0, rows);
@@ -83,8 +91,9 @@ bool moment_inverse(double eta0, double out[256]) {
 }  // namespace
 
 struct lbm_ctx {
-    int nx = 0, ny = 0, lx = 0, ly = 0;
-    long long n = 0;  // nodes
+    int nx = 0, ny = 0, lx = 0, ly = 0;  // ny: rows of one instance
+    int nb = 1;                          // instances stacked along y
+    long long n = 0;                     // nodes of one instance
     lbm_params p{};
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -93,11 +102,11 @@ struct lbm_ctx {
 
     char *slab = nullptr;
     size_t slab_bytes = 0;
-    // state and stage scratch in row-interleaved blocks (lbm_internal.cuh); element type is
-    // double (LBM_FP64) or float (LBM_MIXED)
-    void *f0 = nullptr, *f1 = nullptr;  // [ny][16][nx]: f^n (then f^{n+1}) and f^{n+1/2}
-    void *Ay = nullptr;                 // [ny][12][nx]
-    void *m = nullptr;                  // [ny][NF_M][nx]
+    // state and stage scratch in row-interleaved blocks (lbm_internal.cuh) over nb * ny rows;
+    // element type double (LBM_FP64) or float (LBM_MIXED)
+    void *f0 = nullptr, *f1 = nullptr;  // [nb ny][16][nx]: f^n (then f^{n+1}) and f^{n+1/2}
+    void *Ay = nullptr;                 // [nb ny][12][nx]
+    void *m = nullptr;                  // [nb ny][NF_M][nx]
     double *partial = nullptr;
     int diag_blocks = 0;
     // per-axis tables
@@ -107,17 +116,39 @@ struct lbm_ctx {
     float *k1x32 = nullptr, *k2x32 = nullptr, *k1y32 = nullptr, *k2y32 = nullptr;
     double minv[256];
 
-    // launch geometry
-    Geometry geo;
+    Geometry geo;  // launch geometry
 
-    bool initialized = false;
+    std::vector<char> initialized;  // per instance
     long long steps = 0;
+
+    // one captured step (both stages) for lbm_step when timing is off
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
 
     // per-launch timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_cls;
     size_t ev_used = 0;
+
+    bool all_initialized() const {
+        for (char v : initialized)
+            if (!v) return false;
+        return true;
+    }
+    size_t row0(int k) const { return (size_t)k * ny; }  // first row of instance k
+};
+
+struct lbm_batch_ctx {
+    std::vector<lbm_ctx *> groups;              // one context per grid size
+    std::vector<std::pair<int, int>> where;      // instance -> (group, index in group)
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> branch;            // one capture stream per group
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<long long> steps;                // per instance, since its lbm_batch_init
 };
 
 namespace {
@@ -155,23 +186,24 @@ template <> Axis<float> axis<float>(const lbm_ctx *c, bool xdir) {
                 : Axis<float>{c->tw32y, c->k1y32, c->k2y32, c->ly};
 }
 
-template <typename R> ColArgs<R> col_args(const lbm_ctx *c) {
+template <typename R> ColArgs<R> col_args(const lbm_ctx *c, int nb) {
     ColArgs<R> a{};
     a.nx = c->nx;
     a.ny = c->ny;
     a.W = c->geo.colW;
     a.log2W = ilog2(c->geo.colW);
+    a.nb = nb;
     a.ay = axis<R>(c, false);
     return a;
 }
 
-// one Runge-Kutta stage: K_COL, K_MACRO, K_FLUX, K_UPDATE
+// one Runge-Kutta stage of all instances: K_COL, K_MACRO, K_FLUX, K_UPDATE
 template <typename R>
 int run_stage(lbm_ctx *c, int stage) {
     const lbm_params &p = c->p;
     const bool adv = !(p.flags & LBM_FLAG_NO_ADVECTION);
     const bool frc = !(p.flags & LBM_FLAG_NO_FORCE);
-    const int nx = c->nx;
+    const int nx = c->nx, rows = c->nb * c->ny;
     R *f0 = static_cast<R *>(c->f0), *f1 = static_cast<R *>(c->f1);
     R *Ay = static_cast<R *>(c->Ay), *m = static_cast<R *>(c->m);
     const R *fs = stage == 0 ? f0 : f1;
@@ -179,7 +211,7 @@ int run_stage(lbm_ctx *c, int stage) {
     auto M = [m, nx](int k) { return m + (size_t)k * nx; };  // first row of macro field k
 
     {
-        ColArgs<R> a = col_args<R>(c);
+        ColArgs<R> a = col_args<R>(c, c->nb);
         int nj = 0;
         if (adv)
             for (int k = 0; k < 12; ++k) {
@@ -202,14 +234,14 @@ int run_stage(lbm_ctx *c, int stage) {
         {
             MacroArgs<R> a{};
             a.m = m;
-            a.nx = c->nx; a.ny = c->ny; a.rows = c->geo.rows_macro;
+            a.nx = nx; a.ny = rows; a.rows = c->geo.rows_macro;
             a.ax = axis<R>(c, true);
             a.K = (R)p.K; a.H = (R)p.H; a.q = (R)p.q; a.zeta = (R)p.zeta;
             LaunchTimer t(c, LBM_K_MACRO);
             CU_TRY(launch_macro<R>(a, c->geo.macro_smem, c->stream));
         }
         {
-            ColArgs<R> a = col_args<R>(c);
+            ColArgs<R> a = col_args<R>(c, c->nb);
             a.jobs[0] = ColJob<R>{M(M_QY), M(M_DQY), ldm, ldm, 1, R(1)};
             a.jobs[1] = ColJob<R>{M(M_SXY), M(M_DSXYY), ldm, ldm, 1, R(1)};
             a.jobs[2] = ColJob<R>{M(M_SYY), M(M_DSYY), ldm, ldm, 1, R(1)};
@@ -225,12 +257,13 @@ int run_stage(lbm_ctx *c, int stage) {
         a.fout = stage == 0 ? f1 : f0;
         a.Ay = Ay;
         a.m = m;
-        a.nx = c->nx; a.ny = c->ny; a.rows = c->geo.rows_upd;
+        a.nx = nx; a.ny = rows; a.rows = c->geo.rows_upd;
         a.ax = axis<R>(c, true);
         a.tau_inv = (R)(1.0 / p.tau);
         a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
         a.K = (R)p.K;
         a.b = (R)p.b;
+        a.eta2 = (R)(p.eta0 * p.eta0);
         for (int i = 0; i < 16; ++i) {
             const double psi = vel_sq(i) + (i < 4 ? p.eta0 * p.eta0 : 0.0);
             a.psi_hi[i] = (R)psi;
@@ -238,10 +271,43 @@ int run_stage(lbm_ctx *c, int stage) {
         }
         a.flags = p.flags;
         for (int k = 0; k < 256; ++k) a.minv[k] = (R)c->minv[k];
-        a.eta2 = (R)(p.eta0 * p.eta0);
         LaunchTimer t(c, LBM_K_UPDATE);
         CU_TRY(launch_update<R>(a, c->geo.upd_smem, c->stream));
     }
+    return LBM_OK;
+}
+
+int run_step_launches(lbm_ctx *c) {
+    for (int st = 0; st < 2; ++st) {
+        int rc = c->mixed ? run_stage<float>(c, st) : run_stage<double>(c, st);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+// Captures one step of the context (launches on `s`, then restores its stream) into a graph.
+int capture_into(lbm_ctx *c, cudaStream_t s) {
+    cudaStream_t saved = c->stream;
+    c->stream = s;
+    const int rc = run_step_launches(c);
+    c->stream = saved;
+    return rc;
+}
+
+int build_step_graph(lbm_ctx *c) {
+    if (!c->cap) CU_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    CU_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+    const int rc = capture_into(c, c->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    CU_TRY(e);
+    const cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    CU_TRY(ei);
     return LBM_OK;
 }
 
@@ -261,50 +327,26 @@ int check_params(const lbm_params *p) {
     return LBM_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-void lbm_default_params(lbm_params *p) {
-    if (!p) return;
-    std::memset(p, 0, sizeof *p);
-    p->tau = 1e-4;
-    p->dt = 1e-4;
-    p->dx = 1.0 / 256.0;
-    p->dy = 1.0 / 256.0;
-    p->K = 5e-6;
-    p->H = 0.0;
-    p->q = -0.004;
-    p->zeta = 0.0;
-    p->b = 2.0;
-    p->eta0 = 2.5;
-    p->win_alpha = 0.0;
-    p->win_p = 36.0;
-    p->precision = LBM_FP64;
-    p->flags = 0;
+void free_ctx(lbm_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaFree(c->slab);
+    delete c;
 }
 
-const char *lbm_strerror(int code) {
-    switch (code) {
-        case LBM_OK: return "ok";
-        case LBM_ERR_ARG: return "invalid argument";
-        case LBM_ERR_NOMEM: return "device allocation failed";
-        case LBM_ERR_CUDA: return "CUDA error";
-        case LBM_ERR_NONFINITE: return "non-finite value in the state";
-        case LBM_ERR_TIMEOUT: return "device wait timed out";
-        case LBM_ERR_STATE: return "call out of order";
-        case LBM_ERR_UNSUPPORTED: return "unsupported size or precision";
-        default: return "unknown error";
-    }
-}
-
-const char *lbm_last_error(void) { return g_last_error.c_str(); }
-
-int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handle *out) {
-    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+// nb instances of nx x ny, all device memory in one slab
+int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t stream, lbm_ctx **out) {
     *out = nullptr;
     if (!is_pow2(nx) || !is_pow2(ny) || nx > 4096 || ny > 4096)
         return fail(LBM_ERR_ARG, "nx=%d, ny=%d: each must be a power of two in [2, 4096]", nx, ny);
+    // instances: grid.z of the column passes (<= 65535), rows of the row passes (< 2^31 CTAs)
+    if (nb < 1 || nb > 65535 || (long long)nb * ny > (1LL << 24))
+        return fail(LBM_ERR_ARG, "%d instances of %d x %d: need 1 <= count <= 65535 and count * ny <= 2^24", nb, nx,
+                    ny);
     int rc = check_params(params);
     if (rc) return rc;
 
@@ -312,13 +354,15 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     if (!c) return fail(LBM_ERR_NOMEM, "host allocation failed");
     c->nx = nx;
     c->ny = ny;
+    c->nb = nb;
     c->lx = ilog2(nx);
     c->ly = ilog2(ny);
     c->n = (long long)nx * ny;
     c->p = *params;
-    c->stream = static_cast<cudaStream_t>(stream);
+    c->stream = stream;
     c->mixed = params->precision == LBM_MIXED;
     c->fsize = c->mixed ? 4 : 8;
+    c->initialized.assign(nb, 0);
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
         return fail(LBM_ERR_CUDA, "no CUDA device");
@@ -332,7 +376,8 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     pass_geometry(nx, ny, c->fsize, &c->geo);
-    const size_t need = std::max(std::max(c->geo.upd_smem, c->geo.macro_smem), std::max(c->geo.col_smem, c->geo.rowd_smem));
+    const size_t need =
+        std::max(std::max(c->geo.upd_smem, c->geo.macro_smem), std::max(c->geo.col_smem, c->geo.rowd_smem));
     if (need > (size_t)smem_optin) {
         delete c;
         return fail(LBM_ERR_UNSUPPORTED, "nx=%d ny=%d needs %zu B of shared memory per block (device: %d)", nx,
@@ -340,7 +385,7 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     }
 
     // device memory: one slab, 256-byte aligned pieces
-    const size_t plane_f = (size_t)c->n * c->fsize;
+    const size_t plane_f = (size_t)c->n * nb * c->fsize;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     c->diag_blocks = (int)std::min<long long>(1024, (c->n + 255) / 256);
     size_t off = 0;
@@ -405,38 +450,31 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
     return LBM_OK;
 }
 
-void lbm_destroy(lbm_handle c) {
-    if (!c) return;
-    cudaStreamSynchronize(c->stream);
-    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-    cudaFree(c->slab);
-    delete c;
-}
-
-static int init_common(lbm_ctx *c, const double *rho, const double *ux, const double *uy, const double *T) {
+// f_i := f_i^eq(rho, u, T) for instance k from device arrays [ny][nx]
+int init_instance(lbm_ctx *c, int k, const double *rho, const double *ux, const double *uy, const double *T) {
     InitArgs a{};
     a.rho = rho; a.ux = ux; a.uy = uy; a.T = T;
-    a.f = c->f0;
-    a.m = c->m;
+    a.f = static_cast<char *>(c->f0) + c->row0(k) * NF_F * c->nx * c->fsize;
+    a.m = static_cast<char *>(c->m) + c->row0(k) * NF_M * c->nx * c->fsize;
     a.nx = c->nx;
     a.ny = c->ny;
     a.b = c->p.b;
-    for (int k = 0; k < 256; ++k) a.minv[k] = c->minv[k];
+    for (int j = 0; j < 256; ++j) a.minv[j] = c->minv[j];
     for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
     CU_TRY(c->mixed ? launch_init<float>(a, c->stream) : launch_init<double>(a, c->stream));
-    c->initialized = true;
+    c->initialized[k] = 1;
     c->steps = 0;
     return LBM_OK;
 }
 
-int lbm_init(lbm_handle c, const double *rho, const double *ux, const double *uy, const double *T) {
-    if (!c || !rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "NULL argument");
+int init_instance_host(lbm_ctx *c, int k, const double *rho, const double *ux, const double *uy, const double *T) {
+    if (!rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "NULL argument");
     for (long long g = 0; g < c->n; ++g) {
         if (!(rho[g] > 0.0 && rho[g] < 3.0) || !(T[g] > 0.0) || !std::isfinite(T[g]) || !std::isfinite(ux[g]) ||
             !std::isfinite(uy[g]))
             return fail(LBM_ERR_ARG, "node %lld: need 0 < rho < 3, T > 0 and finite u", g);
     }
-    // stage the four float64 fields in the half-step buffer f1 (free outside lbm_step;
+    // stage the four float64 fields in the half-step buffer f1 (free outside a step;
     // it holds at least 16 * 4 bytes per node >= 4 * 8)
     const size_t bytes = (size_t)c->n * 8;
     double *st = static_cast<double *>(c->f1);
@@ -444,76 +482,48 @@ int lbm_init(lbm_handle c, const double *rho, const double *ux, const double *uy
     CU_TRY(cudaMemcpyAsync(st + c->n, ux, bytes, cudaMemcpyHostToDevice, c->stream));
     CU_TRY(cudaMemcpyAsync(st + 2 * c->n, uy, bytes, cudaMemcpyHostToDevice, c->stream));
     CU_TRY(cudaMemcpyAsync(st + 3 * c->n, T, bytes, cudaMemcpyHostToDevice, c->stream));
-    int rc = init_common(c, st, st + c->n, st + 2 * c->n, st + 3 * c->n);
+    int rc = init_instance(c, k, st, st + c->n, st + 2 * c->n, st + 3 * c->n);
     if (rc) return rc;
     CU_TRY(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 
-int lbm_init_device(lbm_handle c, const double *rho, const double *ux, const double *uy, const double *T) {
-    if (!c || !rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "NULL argument");
-    return init_common(c, rho, ux, uy, T);
-}
-
-int lbm_step(lbm_handle c, int n) {
-    if (!c || n < 0) return fail(LBM_ERR_ARG, "bad handle or n < 0");
-    if (!c->initialized) return fail(LBM_ERR_STATE, "lbm_step before lbm_init / lbm_set_f");
-    for (int s = 0; s < n; ++s) {
-        for (int st = 0; st < 2; ++st) {
-            int rc = c->mixed ? run_stage<float>(c, st) : run_stage<double>(c, st);
-            if (rc) return rc;
-        }
-        ++c->steps;
-    }
-    return LBM_OK;
-}
-
-// rho, u_x, u_y, T (macro fields 0..3) as dense float64 [ny][nx] device arrays
-static int moments_to_device(lbm_ctx *c, double *const out[4]) {
-    for (int k = 0; k < 4; ++k) {
-        if (!out[k]) continue;
-        const int ld = NF_M * c->nx;
+// rho, u_x, u_y, T (macro fields 0..3) of instance k as dense float64 [ny][nx] device arrays
+int moments_to_device(lbm_ctx *c, int k, double *const out[4]) {
+    const int ld = NF_M * c->nx;
+    for (int j = 0; j < 4; ++j) {
+        if (!out[j]) continue;
+        const size_t off = c->row0(k) * ld + (size_t)j * c->nx;
         if (c->mixed)
-            CU_TRY(launch_field_out<float>(static_cast<const float *>(c->m) + (size_t)k * c->nx, ld, out[k], c->nx,
-                                           c->ny, c->stream));
+            CU_TRY(launch_field_out<float>(static_cast<const float *>(c->m) + off, ld, out[j], c->nx, c->ny,
+                                           c->stream));
         else
-            CU_TRY(launch_field_out<double>(static_cast<const double *>(c->m) + (size_t)k * c->nx, ld, out[k],
-                                            c->nx, c->ny, c->stream));
+            CU_TRY(launch_field_out<double>(static_cast<const double *>(c->m) + off, ld, out[j], c->nx, c->ny,
+                                            c->stream));
     }
     return LBM_OK;
 }
 
-int lbm_moments_device(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
-    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
-    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    double *const out[4] = {rho, ux, uy, T};
-    return moments_to_device(c, out);
-}
-
-int lbm_moments(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
-    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
-    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    // gather through the half-step buffer (free outside lbm_step), 4 x n doubles <= its size
+int moments_host(lbm_ctx *c, int k, double *rho, double *ux, double *uy, double *T) {
+    // gather through the half-step buffer (free outside a step), 4 x n doubles <= its size
     double *st = static_cast<double *>(c->f1);
     double *const dev[4] = {rho ? st : nullptr, ux ? st + c->n : nullptr, uy ? st + 2 * c->n : nullptr,
                             T ? st + 3 * c->n : nullptr};
-    int rc = moments_to_device(c, dev);
+    int rc = moments_to_device(c, k, dev);
     if (rc) return rc;
     double *const host[4] = {rho, ux, uy, T};
-    for (int k = 0; k < 4; ++k)
-        if (host[k])
-            CU_TRY(cudaMemcpyAsync(host[k], dev[k], (size_t)c->n * 8, cudaMemcpyDeviceToHost, c->stream));
+    for (int j = 0; j < 4; ++j)
+        if (host[j]) CU_TRY(cudaMemcpyAsync(host[j], dev[j], (size_t)c->n * 8, cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 
-// the API's [16][ny][nx] float64 layout <-> the device block [ny][16][nx]
-int lbm_get_f(lbm_handle c, double *f16) {
-    if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
-    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
+// the API's [16][ny][nx] float64 layout <-> the device block [ny][16][nx] of instance k
+int get_f_host(lbm_ctx *c, int k, double *f16) {
     const size_t cnt = (size_t)16 * c->n, nx = c->nx, ny = c->ny;
     std::vector<unsigned char> tmp(cnt * c->fsize);
-    CU_TRY(cudaMemcpyAsync(tmp.data(), c->f0, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
+    const char *src0 = static_cast<const char *>(c->f0) + c->row0(k) * NF_F * nx * c->fsize;
+    CU_TRY(cudaMemcpyAsync(tmp.data(), src0, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
     for (size_t y = 0; y < ny; ++y)
         for (size_t i = 0; i < 16; ++i) {
@@ -528,11 +538,10 @@ int lbm_get_f(lbm_handle c, double *f16) {
     return LBM_OK;
 }
 
-int lbm_set_f(lbm_handle c, const double *f16) {
-    if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
+int set_f_host(lbm_ctx *c, int k, const double *f16) {
     const size_t cnt = (size_t)16 * c->n, nx = c->nx, ny = c->ny;
-    for (size_t k = 0; k < cnt; ++k)
-        if (!std::isfinite(f16[k])) return fail(LBM_ERR_NONFINITE, "f16[%zu] is not finite", k);
+    for (size_t j = 0; j < cnt; ++j)
+        if (!std::isfinite(f16[j])) return fail(LBM_ERR_NONFINITE, "f16[%zu] is not finite", j);
     std::vector<unsigned char> tmp(cnt * c->fsize);
     for (size_t y = 0; y < ny; ++y)
         for (size_t i = 0; i < 16; ++i) {
@@ -544,27 +553,26 @@ int lbm_set_f(lbm_handle c, const double *f16) {
                 std::memcpy(reinterpret_cast<double *>(tmp.data()) + dst, f16 + src, nx * 8);
             }
         }
-    CU_TRY(cudaMemcpyAsync(c->f0, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, c->stream));
+    char *f = static_cast<char *>(c->f0) + c->row0(k) * NF_F * nx * c->fsize;
+    CU_TRY(cudaMemcpyAsync(f, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
     MomArgs a{};
-    a.f = c->f0;
-    a.m = c->m;
+    a.f = f;
+    a.m = static_cast<char *>(c->m) + c->row0(k) * NF_M * nx * c->fsize;
     a.nx = c->nx;
     a.ny = c->ny;
     a.b = c->p.b;
     for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
     CU_TRY(c->mixed ? launch_moments<float>(a, c->stream) : launch_moments<double>(a, c->stream));
-    c->initialized = true;
+    c->initialized[k] = 1;
     return LBM_OK;
 }
 
-}  // extern "C"
-
-template <typename R> static int diag_launch(lbm_ctx *c) {
-    // d_y rho into M_RY, d_x rho into M_DQX (stage scratch, rebuilt by the next stage)
-    R *m = static_cast<R *>(c->m);
+template <typename R> int diag_launch(lbm_ctx *c, int k) {
+    // d_y rho into M_RY, d_x rho into M_DQX of instance k (stage scratch, rebuilt by the next stage)
     const int nx = c->nx, ldm = NF_M * nx;
-    ColArgs<R> ca = col_args<R>(c);
+    R *m = static_cast<R *>(c->m) + c->row0(k) * ldm;
+    ColArgs<R> ca = col_args<R>(c, 1);
     ca.jobs[0] = ColJob<R>{m + (size_t)M_RHO * nx, m + (size_t)M_RY * nx, ldm, ldm, 1, R(1)};
     CU_TRY(launch_col<R>(ca, 1, c->geo.col_smem, c->stream));
     RowDerivArgs<R> ra{};
@@ -594,30 +602,133 @@ template <typename R> static int diag_launch(lbm_ctx *c) {
     return LBM_OK;
 }
 
-extern "C" {
-int lbm_diagnostics(lbm_handle c, double out[6]) {
-    if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
-    if (!c->initialized) return fail(LBM_ERR_STATE, "no state yet");
-    int rc = c->mixed ? diag_launch<float>(c) : diag_launch<double>(c);
+int diagnostics_instance(lbm_ctx *c, int k, long long steps, double out[6]) {
+    int rc = c->mixed ? diag_launch<float>(c, k) : diag_launch<double>(c, k);
     if (rc) return rc;
     std::vector<double> part((size_t)c->diag_blocks * 5);
     CU_TRY(cudaMemcpyAsync(part.data(), c->partial, part.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
     double s[4] = {0, 0, 0, 0}, mx = 0;
     for (int b = 0; b < c->diag_blocks; ++b) {
-        for (int k = 0; k < 4; ++k) s[k] += part[b * 5 + k];
+        for (int j = 0; j < 4; ++j) s[j] += part[b * 5 + j];
         mx = std::max(mx, part[b * 5 + 4]);
     }
     const double cell = c->p.dx * c->p.dy;
-    out[0] = s[0] * cell;
-    out[1] = s[1] * cell;
-    out[2] = s[2] * cell;
-    out[3] = s[3] * cell;
+    for (int j = 0; j < 4; ++j) out[j] = s[j] * cell;
     out[4] = std::sqrt(mx);
-    out[5] = (double)c->steps;
-    for (int k = 0; k < 5; ++k)
-        if (!std::isfinite(out[k])) return fail(LBM_ERR_NONFINITE, "diagnostic %d is not finite", k);
+    out[5] = (double)steps;
+    for (int j = 0; j < 5; ++j)
+        if (!std::isfinite(out[j])) return fail(LBM_ERR_NONFINITE, "diagnostic %d is not finite", j);
     return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->tau = 1e-4;
+    p->dt = 1e-4;
+    p->dx = 1.0 / 256.0;
+    p->dy = 1.0 / 256.0;
+    p->K = 5e-6;
+    p->H = 0.0;
+    p->q = -0.004;
+    p->zeta = 0.0;
+    p->b = 2.0;
+    p->eta0 = 2.5;
+    p->win_alpha = 0.0;
+    p->win_p = 36.0;
+    p->precision = LBM_FP64;
+    p->flags = 0;
+}
+
+const char *lbm_strerror(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_NOMEM: return "device allocation failed";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_NONFINITE: return "non-finite value in the state";
+        case LBM_ERR_TIMEOUT: return "device wait timed out";
+        case LBM_ERR_STATE: return "call out of order";
+        case LBM_ERR_UNSUPPORTED: return "unsupported size or precision";
+        default: return "unknown error";
+    }
+}
+
+const char *lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handle *out) {
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    return create_ctx(nx, ny, 1, params, static_cast<cudaStream_t>(stream), out);
+}
+
+void lbm_destroy(lbm_handle c) { free_ctx(c); }
+
+int lbm_init(lbm_handle c, const double *rho, const double *ux, const double *uy, const double *T) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    return init_instance_host(c, 0, rho, ux, uy, T);
+}
+
+int lbm_init_device(lbm_handle c, const double *rho, const double *ux, const double *uy, const double *T) {
+    if (!c || !rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "NULL argument");
+    return init_instance(c, 0, rho, ux, uy, T);
+}
+
+int lbm_step(lbm_handle c, int n) {
+    if (!c || n < 0) return fail(LBM_ERR_ARG, "bad handle or n < 0");
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "lbm_step before lbm_init / lbm_set_f");
+    if (n == 0) return LBM_OK;
+    if (c->timing) {  // direct launches, each between the timing events
+        for (int s = 0; s < n; ++s) {
+            int rc = run_step_launches(c);
+            if (rc) return rc;
+            ++c->steps;
+        }
+        return LBM_OK;
+    }
+    if (!c->graph) {
+        int rc = build_step_graph(c);
+        if (rc) return rc;
+    }
+    for (int s = 0; s < n; ++s) {
+        CU_TRY(cudaGraphLaunch(c->graph, c->stream));
+        ++c->steps;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments_device(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
+    double *const out[4] = {rho, ux, uy, T};
+    return moments_to_device(c, 0, out);
+}
+
+int lbm_moments(lbm_handle c, double *rho, double *ux, double *uy, double *T) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
+    return moments_host(c, 0, rho, ux, uy, T);
+}
+
+int lbm_get_f(lbm_handle c, double *f16) {
+    if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
+    return get_f_host(c, 0, f16);
+}
+
+int lbm_set_f(lbm_handle c, const double *f16) {
+    if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
+    return set_f_host(c, 0, f16);
+}
+
+int lbm_diagnostics(lbm_handle c, double out[6]) {
+    if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
+    return diagnostics_instance(c, 0, c->steps, out);
 }
 
 int lbm_synchronize(lbm_handle c) {
@@ -693,6 +804,150 @@ int lbm_maxwell(double T, double *rho_l, double *rho_v) {
     return LBM_OK;
 }
 
+// ---- batches of independent simulations ---------------------------------------------------
+
+int lbm_batch_create(int count, const int *nx, const int *ny, const lbm_params *params, void *stream,
+                     lbm_batch *out) {
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !nx || !ny) return fail(LBM_ERR_ARG, "need count >= 1 and size arrays");
+    int rc = check_params(params);
+    if (rc) return rc;
+    // group the instances by grid size, keeping the order of first appearance
+    std::vector<std::pair<int, int>> sizes;
+    std::vector<int> group_of(count), index_in(count);
+    std::vector<int> counts;
+    for (int k = 0; k < count; ++k) {
+        if (!is_pow2(nx[k]) || !is_pow2(ny[k]) || nx[k] > 4096 || ny[k] > 4096)
+            return fail(LBM_ERR_ARG, "instance %d: nx=%d, ny=%d must be powers of two in [2, 4096]", k, nx[k], ny[k]);
+        int g = -1;
+        for (size_t j = 0; j < sizes.size(); ++j)
+            if (sizes[j] == std::make_pair(nx[k], ny[k])) g = (int)j;
+        if (g < 0) {
+            g = (int)sizes.size();
+            sizes.push_back({nx[k], ny[k]});
+            counts.push_back(0);
+        }
+        group_of[k] = g;
+        index_in[k] = counts[g]++;
+    }
+    lbm_batch_ctx *b = new (std::nothrow) lbm_batch_ctx();
+    if (!b) return fail(LBM_ERR_NOMEM, "host allocation failed");
+    b->stream = static_cast<cudaStream_t>(stream);
+    for (size_t g = 0; g < sizes.size(); ++g) {
+        lbm_ctx *c = nullptr;
+        rc = create_ctx(sizes[g].first, sizes[g].second, counts[g], params, b->stream, &c);
+        if (rc) {
+            lbm_batch_destroy(b);
+            return rc;
+        }
+        b->groups.push_back(c);
+    }
+    for (int k = 0; k < count; ++k) b->where.push_back({group_of[k], index_in[k]});
+    b->steps.assign(count, 0);
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaStream_t s : b->branch) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (lbm_ctx *c : b->groups) free_ctx(c);
+    delete b;
+}
+
+int lbm_batch_count(lbm_batch b) { return b ? (int)b->where.size() : 0; }
+
+int lbm_batch_init(lbm_batch b, int k, const double *rho, const double *ux, const double *uy, const double *T) {
+    if (!b || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
+    lbm_ctx *c = b->groups[b->where[k].first];
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    const int rc = init_instance_host(c, b->where[k].second, rho, ux, uy, T);
+    if (rc == LBM_OK) b->steps[k] = 0;
+    return rc;
+}
+
+// One graph per step: the groups' launches are parallel branches forked from and joined back
+// into the capture stream.
+static int build_batch_graph(lbm_batch b) {
+    const size_t G = b->groups.size();
+    if (!b->cap) CU_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    if (!b->fork) CU_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    while (b->branch.size() < G) {
+        cudaStream_t s;
+        CU_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        b->branch.push_back(s);
+        cudaEvent_t e;
+        CU_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->join.push_back(e);
+    }
+    CU_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+    int rc = LBM_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->cap);
+    for (size_t g = 0; g < G && rc == LBM_OK && e == cudaSuccess; ++g) {
+        e = cudaStreamWaitEvent(b->branch[g], b->fork, 0);
+        if (e == cudaSuccess) rc = capture_into(b->groups[g], b->branch[g]);
+        if (rc == LBM_OK && e == cudaSuccess) e = cudaEventRecord(b->join[g], b->branch[g]);
+        if (rc == LBM_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[g], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
+    if (rc || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc) return rc;
+        return fail(LBM_ERR_CUDA, "batch graph capture: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    CU_TRY(ei);
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, int n) {
+    if (!b || n < 0) return fail(LBM_ERR_ARG, "bad batch or n < 0");
+    for (lbm_ctx *c : b->groups)
+        if (!c->all_initialized()) return fail(LBM_ERR_STATE, "lbm_batch_step before every instance is initialised");
+    if (n == 0) return LBM_OK;
+    if (!b->graph) {
+        int rc = build_batch_graph(b);
+        if (rc) return rc;
+    }
+    for (int s = 0; s < n; ++s) CU_TRY(cudaGraphLaunch(b->graph, b->stream));
+    for (long long &s : b->steps) s += n;
+    return LBM_OK;
+}
+
+int lbm_batch_moments(lbm_batch b, int k, double *rho, double *ux, double *uy, double *T) {
+    if (!b || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
+    lbm_ctx *c = b->groups[b->where[k].first];
+    if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    return moments_host(c, b->where[k].second, rho, ux, uy, T);
+}
+
+int lbm_batch_get_f(lbm_batch b, int k, double *f16) {
+    if (!b || !f16 || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
+    lbm_ctx *c = b->groups[b->where[k].first];
+    if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    return get_f_host(c, b->where[k].second, f16);
+}
+
+int lbm_batch_diagnostics(lbm_batch b, int k, double out[6]) {
+    if (!b || !out || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
+    lbm_ctx *c = b->groups[b->where[k].first];
+    if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    return diagnostics_instance(c, b->where[k].second, b->steps[k], out);
+}
+
 }  // extern "C"
 
 // Lets other translation units report a detailed message through lbm_last_error().
@@ -742,7 +997,7 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     while ((1 << lx) < nx) ++lx;
     while ((1 << ly) < ny) ++ly;
     const size_t cs = 2 * esize;  // complex element
-    // column tiles: W columns = W/2 lines of G threads; at most 1024 threads and 100 KB
+    // column tiles: W columns = W/2 lines of G threads; at most max_threads and 100 KB
     int W = (int)(128 / esize);
     if (W > nx) W = nx;
     const int maxt = max_threads(esize);

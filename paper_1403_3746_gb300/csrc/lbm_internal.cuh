@@ -121,7 +121,8 @@ template <typename R> struct ColJob {
 #define LBM_MAX_COLJOBS 20
 template <typename R> struct ColArgs {
     ColJob<R> jobs[LBM_MAX_COLJOBS];
-    int nx, ny, W, log2W;
+    int nx, ny, W, log2W;  // ny: rows of one instance
+    int nb;                // instances stacked along y (grid.z); row k ny + y of a field = instance k, row y
     Axis<R> ay;
 };
 

@@ -73,3 +73,15 @@ def test_error_strings(L):
     assert L.lbm_strerror(0) == b"ok"
     assert L.lbm_strerror(-7).startswith(b"unsupported")
     assert L.lbm_strerror(-99) == b"unknown error"
+
+
+@pytest.mark.parametrize("sizes", [[], [(16, 16), (24, 16)], [(16, 16), (16, 8192)], [(2, 1)]])
+def test_batch_create_rejects_bad_sizes_before_touching_the_device(L, sizes):
+    p = lbm.default_params()
+    n = max(len(sizes), 1)
+    nx = (ctypes.c_int * n)(*[s[0] for s in sizes])
+    ny = (ctypes.c_int * n)(*[s[1] for s in sizes])
+    h = ctypes.c_void_p()
+    assert L.lbm_batch_create(len(sizes), nx, ny, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert not h.value
+    assert L.lbm_batch_count(None) == 0
