@@ -181,6 +181,34 @@ def e2e_path(lbm, torch, precision, steps, fields):
             "note": "init from pinned host + per step lbm_step and lbm_diagnostics + final moments"}
 
 
+BATCH_SIZES = [128] * 32 + [256] * 32 + [512] * 32
+BATCH_WORKLOAD = ("96 independent spinodal quenches (32 each at 128^2, 256^2, 512^2), rho = 1 +/- 1% noise, "
+                  "T_k uniform in [0.80, 0.95]")
+
+
+def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream):
+    """The batched form: all instances advanced by one graph launch per step. The state
+    (about 2.9 GB in LBM_MIXED) is far larger than L2, so no flush is needed between steps."""
+    p = lbm.default_params(precision=precision, **PARAMS)
+    temps = synthetic.quench_temperatures(4, len(BATCH_SIZES))
+    nodes = sum(n * n for n in BATCH_SIZES)
+    with lbm.Batch([(n, n) for n in BATCH_SIZES], p, stream=stream.cuda_stream) as b:
+        for k, n in enumerate(BATCH_SIZES):
+            b.init(k, *synthetic.spinodal(n, n, 1.0, 0.01, float(temps[k]), seed=4000 + k))
+        with torch.cuda.stream(stream):
+            b.step(warmup)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(steps)
+            e1.record(stream)
+            stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        ok = all(abs(b.diagnostics(k)["mass"]) > 0 for k in (0, len(BATCH_SIZES) - 1))
+    return {"value": nodes * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "steps": steps,
+            "ms_per_step": ms / steps, "nodes": nodes, "finite": ok}
+
+
 ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
@@ -249,6 +277,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched form and the error table")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
@@ -304,6 +333,26 @@ def main():
     launches = sum(c for _, c in kern.values())
     e2e = e2e_path(lbm, torch, lbm.LBM_MIXED, max(10, args.steps // 4), fields) if rank == 0 else None
 
+    extras = {}
+    if not args.no_extras:
+        kb = max(5, args.steps // 10)
+        extras["batched_form"] = {
+            "workload": BATCH_WORKLOAD, "launch": "one CUDA graph per step, size groups as parallel branches",
+            "mixed": batch_path(lbm, torch, synthetic, lbm.LBM_MIXED, kb, 3, stream),
+            "fp64": batch_path(lbm, torch, synthetic, lbm.LBM_FP64, max(3, kb // 4), 3, stream)}
+        if rank == 0:
+            from paper_1403_3746_gb300 import accuracy
+            tab = accuracy.error_table()
+            sl, dr = tab["slab"]["rows"], tab["droplet"]["rows"]
+            extras["accuracy_mixed_vs_fp64"] = {
+                "coexistence_rel_err_max": max(max(r["rel_err_rho_l"], r["rel_err_rho_v"]) for r in sl),
+                "mass_drift_mixed_max": max(abs(r["mass_drift_mixed"]) for r in sl + dr),
+                "mass_drift_fp64_max": max(abs(r["mass_drift_fp64"]) for r in sl + dr),
+                "spurious_velocity_rel_err_max": max(r["rel_err_umax"] for r in dr),
+                "pressure_jump_rel_err_max": max(r["rel_err_dp"] for r in dr),
+                "runs": f"slabs 256x2 at T={[r['T'] for r in sl]}, {tab['slab']['steps']} steps; droplets "
+                        f"R={[r['R'] for r in dr]} on 128^2 at T=0.9, {tab['droplet']['steps']} steps"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ts = run_oracle(N_GRID, 2, 0, RADIUS)
@@ -328,6 +377,7 @@ def main():
             "clocks": clocks, "wall_s_timed_loop": wall,
             "check": {"mass": diag["mass"], "umax": diag["umax"]},
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -1,0 +1,95 @@
+"""Error of the mixed-precision path (LBM_MIXED) against the plain float64 path (LBM_FP64),
+stated per physical result of Sec. 3 on the same seeded inputs:
+
+* coexistence densities of a flat liquid slab (Sec. 3.1), measured in the bulk of each phase;
+* relative mass drift over the run;
+* spurious (parasitic) velocity max |u| around a static droplet (Sec. 3.3);
+* droplet pressure jump P_in - P_out of the van der Waals pressure (Laplace test, Sec. 3.3).
+
+Both paths run through the library (each instance set advanced as one batch); the float64
+path agrees with the oracle to round-off on short runs, so it stands in for it on runs of
+thousands of steps, which the oracle cannot finish quickly. Host-side numpy only reduces the
+moments the library returns.
+"""
+import numpy as np
+
+import synthetic
+
+from . import Batch, LBM_FP64, LBM_MIXED, default_params, maxwell
+
+PHASE = dict(tau=1e-4, dt=1e-4, dx=1 / 256, dy=1 / 256, K=5e-6, q=-0.004, b=2.0)
+
+
+def vdw_pressure(rho, T):
+    """Van der Waals pressure with a = 9/8, b = 1/3 (Sec. 2.2): P = 3 rho T/(3 - rho) - 9 rho^2/8."""
+    return 3.0 * rho * T / (3.0 - rho) - 1.125 * rho * rho
+
+
+def slab_runs(temps, precision, nx=256, ny=2, steps=20000, params=None):
+    """Flat slabs (liquid in the middle half of x) at each temperature, advanced `steps` steps.
+    Returns per temperature (rho_l, rho_v, mass drift): bulk means over the central nx/8 of the
+    liquid and the outer nx/8 of the vapour."""
+    p = default_params(precision=precision, **(params or PHASE))
+    out = []
+    with Batch([(nx, ny)] * len(temps), p) as b:
+        mass0 = []
+        for k, T in enumerate(temps):
+            rl, rv = maxwell(T)
+            fields = synthetic.slab(nx, ny, rl, rv, T, center=nx / 2, half_width=nx / 4, width=2.0)
+            b.init(k, *fields)
+            mass0.append(b.diagnostics(k)["mass"])
+        b.step(steps)
+        w = nx // 16
+        for k in range(len(temps)):
+            rho = b.moments(k)[0].mean(axis=0)
+            rho_l = float(rho[nx // 2 - w: nx // 2 + w].mean())
+            rho_v = float(np.concatenate([rho[:w], rho[nx - w:]]).mean())
+            drift = (b.diagnostics(k)["mass"] - mass0[k]) / mass0[k]
+            out.append((rho_l, rho_v, drift))
+    return out
+
+
+def droplet_runs(radii, precision, n=128, T=0.9, steps=10000, params=None):
+    """Static droplets of radius R (cells) centred in an n x n box at temperature T.
+    Returns per radius (P_in - P_out, max |u|, mass drift); P_in at the centre node,
+    P_out averaged over the four corner nodes."""
+    p = default_params(precision=precision, **(params or PHASE))
+    rl, rv = maxwell(T)
+    out = []
+    with Batch([(n, n)] * len(radii), p) as b:
+        mass0 = []
+        for k, R in enumerate(radii):
+            b.init(k, *synthetic.droplet(n, n, R, rl, rv, T, width=2.0))
+            mass0.append(b.diagnostics(k)["mass"])
+        b.step(steps)
+        for k in range(len(radii)):
+            rho, ux, uy, Tf = b.moments(k)
+            P = vdw_pressure(rho, Tf)
+            p_in = float(P[n // 2, n // 2])
+            p_out = float(np.mean([P[0, 0], P[0, n - 1], P[n - 1, 0], P[n - 1, n - 1]]))
+            umax = float(np.sqrt(ux * ux + uy * uy).max())
+            drift = (b.diagnostics(k)["mass"] - mass0[k]) / mass0[k]
+            out.append((p_in - p_out, umax, drift))
+    return out
+
+
+def error_table(temps=(0.85, 0.9, 0.95), radii=(8, 12, 16, 24, 32), slab_steps=20000, drop_steps=10000):
+    """Runs both precisions and returns the per-result comparison (plain dicts, JSON-ready)."""
+    s64 = slab_runs(temps, LBM_FP64, steps=slab_steps)
+    s32 = slab_runs(temps, LBM_MIXED, steps=slab_steps)
+    d64 = droplet_runs(radii, LBM_FP64, steps=drop_steps)
+    d32 = droplet_runs(radii, LBM_MIXED, steps=drop_steps)
+    coex = []
+    for T, a, m in zip(temps, s64, s32):
+        rl, rv = maxwell(T)
+        coex.append({"T": T, "rho_l_fp64": a[0], "rho_l_mixed": m[0], "rho_v_fp64": a[1], "rho_v_mixed": m[1],
+                     "rel_err_rho_l": abs(m[0] - a[0]) / abs(a[0]), "rel_err_rho_v": abs(m[1] - a[1]) / abs(a[1]),
+                     "maxwell_rho_l": rl, "maxwell_rho_v": rv,
+                     "mass_drift_fp64": a[2], "mass_drift_mixed": m[2]})
+    drops = []
+    for R, a, m in zip(radii, d64, d32):
+        drops.append({"R": R, "dp_fp64": a[0], "dp_mixed": m[0], "rel_err_dp": abs(m[0] - a[0]) / abs(a[0]),
+                      "umax_fp64": a[1], "umax_mixed": m[1], "rel_err_umax": abs(m[1] - a[1]) / abs(a[1]),
+                      "mass_drift_fp64": a[2], "mass_drift_mixed": m[2]})
+    return {"slab": {"nx": 256, "ny": 2, "steps": slab_steps, "rows": coex},
+            "droplet": {"n": 128, "T": 0.9, "steps": drop_steps, "rows": drops}}
