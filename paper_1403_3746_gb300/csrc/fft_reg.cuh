@@ -11,8 +11,9 @@
 // is not a multiple of 4. Between passes the points are exchanged through a padded
 // shared-memory line buffer (one pad slot per 16 points keeps every exchange free of bank
 // conflicts, for 8- and 16-byte complex types). The forward output stays in digit-reversed
-// order, thread t holding positions [E t, E t + E); the derivative multiplier table is stored
-// in that order with 1/N folded in. The inverse is the same pass sequence in reverse, with
+// order, thread t holding positions [E t, E t + E); the derivative multiplier table holds
+// position E t + e at index G e + t (1/N folded in), so the G threads of a line read
+// consecutive entries. The inverse is the same pass sequence in reverse, with
 // conjugate roots: it takes the digit-reversed spectrum back to natural order, thread t
 // holding points t + G e (e < E), the layout in which the forward transform reads its input.
 // So rows are read and written with coalesced accesses straight from and to global memory.
@@ -142,6 +143,26 @@ struct SyncWarp {
     static __device__ __forceinline__ void run() { __syncwarp(); }
 };
 
+// Twiddle table of a line length n = 2^log2n: for each radix-16 pass P (span S = n / 16^P,
+// M = S / 16 sub-sequences, M > 1) the roots w_n^(16^P j k) for k = 1..15, j = 0..M-1 at
+// index twiddle_offset(n, P) + (k - 1) M + j, so the threads of a pass (consecutive j)
+// read consecutive entries. The table has fewer than n entries.
+__host__ __device__ constexpr int twiddle_offset(int n, int P) {
+    return P == 0 ? 0 : twiddle_offset(n, P - 1) + 15 * (n >> (4 * P));
+}
+// exponent a (root w_n^a) stored at table index idx; -1 for an unused slot
+__host__ __device__ inline int twiddle_exponent(int n, int idx) {
+    for (int P = 0, off = 0; (n >> (4 * (P + 1))) >= 1; ++P) {
+        const int M = n >> (4 * (P + 1));
+        if (idx < off + 15 * M) {
+            const int k = (idx - off) / M + 1, j = (idx - off) % M;
+            return (int)(((long long)j * k << (4 * P)) & (n - 1));
+        }
+        off += 15 * M;
+    }
+    return -1;
+}
+
 template <typename R, int LOG2N> struct LineFFT {
     static constexpr int N = 1 << LOG2N;
     static constexpr int E = N < 16 ? N : 16;                // points per thread
@@ -162,19 +183,20 @@ template <typename R, int LOG2N> struct LineFFT {
     }
 
     template <int P, bool INV> static __device__ __forceinline__ void pass16(CT v[16], int t, const CT *__restrict__ tw) {
-        constexpr int S = N >> (4 * P), M = S >> 4, SH = 4 * P;
+        constexpr int S = N >> (4 * P), M = S >> 4;
         const int j = t & (M - 1);
+        const CT *twp = tw + twiddle_offset(N, P) + j;  // root of (j, k) at twp[(k - 1) M]
         if (INV) {
             if (M > 1 && j) {
 #pragma unroll
-                for (int k = 1; k < 16; ++k) v[k] = mulc<R>(v[k], tw[(j * k) << SH]);
+                for (int k = 1; k < 16; ++k) v[k] = mulc<R>(v[k], twp[(k - 1) * M]);
             }
             dft16<R, true>(v);
         } else {
             dft16<R, false>(v);
             if (M > 1 && j) {
 #pragma unroll
-                for (int k = 1; k < 16; ++k) v[k] = mul<R>(v[k], tw[(j * k) << SH]);
+                for (int k = 1; k < 16; ++k) v[k] = mul<R>(v[k], twp[(k - 1) * M]);
             }
         }
     }
@@ -265,16 +287,17 @@ template <typename R, int LOG2N> struct LineFFT {
         for (int k = 0; k < 2 * EXCHANGES; ++k) SYNC::run();
     }
 
-    // v <- d^order * c * v at positions E t + e (tables k1 = W k_eff / N, k2 = -(W k_eff)^2 / N)
+    // v <- d^order * c * v at positions E t + e (tables k1 = W k_eff / N, k2 = -(W k_eff)^2 / N,
+    // position E t + e at index G e + t)
     static __device__ __forceinline__ void multiply(CT v[E], int t, int order, R c, const R *__restrict__ k1,
                                                     const R *__restrict__ k2) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             if (order == 1) {
-                const R w = c * k1[t * E + e];
+                const R w = c * k1[G * e + t];
                 v[e] = mk<R>(-w * v[e].y, w * v[e].x);
             } else {
-                const R w = c * k2[t * E + e];
+                const R w = c * k2[G * e + t];
                 v[e] = mk<R>(w * v[e].x, w * v[e].y);
             }
         }

@@ -124,14 +124,16 @@ __global__ void __launch_bounds__(256) diag_kernel(const __grid_constant__ DiagA
         for (int k = 0; k < 5; ++k) a.partial[blockIdx.x * 5 + k] = red[k][0];
 }
 
-// tw[k] = exp(-2 pi i k / n), evaluated in float64 with sincospi (exact argument scaling),
+// Twiddle table in the per-pass layout of fft_reg.cuh: entry idx = exp(-2 pi i a / n) with
+// a = twiddle_exponent(n, idx), evaluated in float64 with sincospi (exact argument scaling),
 // rounded once for the float32 table.
 __global__ void twiddle_kernel(double2 *tw64, float2 *tw32, int n) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        double s, c;
-        sincospi(-2.0 * (double)k / (double)n, &s, &c);
-        tw64[k] = make_double2(c, s);
-        tw32[k] = make_float2((float)c, (float)s);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int a = reg::twiddle_exponent(n, idx);
+        double s = 0.0, c = 1.0;
+        if (a > 0) sincospi(-2.0 * (double)a / (double)n, &s, &c);
+        tw64[idx] = make_double2(c, s);
+        tw32[idx] = make_float2((float)c, (float)s);
     }
 }
 

@@ -275,7 +275,7 @@ __host__ __device__ constexpr bool minv_zero(int i, int j) {
 }
 
 template <typename R, int LOG2N, bool MOMENT_SPACE>
-__global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
+__global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N>;
     using CT = typename F::CT;
     constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE;
@@ -299,24 +299,31 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) update_row_kernel(const 
     }
 
     if (adv) {
-        // 6 lines per row (the 12 fields with v_x != 0, paired); LB lines per batch
-        const int LB = blockDim.x / G;
+        // 6 lines per row (the 12 fields with v_x != 0, paired); LB lines per batch (LB divides
+        // 6 NR); threads past LB G only take part in the barriers
+        const int LB = a.lines_per_batch;
         const int ls = threadIdx.x / G, t = threadIdx.x % G;
         for (int b0 = 0; b0 < 6 * NR; b0 += LB) {
-            const int line = b0 + ls;
-            const int p = line / NR, r = line % NR;
-            CT *buf = sb + (size_t)line * SM;
-            const R *frow = a.fs + (size_t)(y0 + r) * NF_F * NX;
-            const R *fa = frow + xfield(2 * p) * NX, *fb = frow + xfield(2 * p + 1) * NX;
-            CT v[E];
+            if (ls < LB) {
+                const int line = b0 + ls;
+                const int p = line / NR, r = line % NR;
+                CT *buf = sb + (size_t)line * SM;
+                const R *frow = a.fs + (size_t)(y0 + r) * NF_F * NX;
+                const R *fa = frow + xfield(2 * p) * NX, *fb = frow + xfield(2 * p + 1) * NX;
+                CT v[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(fa[t + G * e], fb[t + G * e]);
-            F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
-            F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
-            F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
-            __syncthreads();
+                for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(fa[t + G * e], fb[t + G * e]);
+                F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
+                F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+                F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
+                __syncthreads();
 #pragma unroll
-            for (int e = 0; e < E; ++e) buf[t + G * e] = v[e];
+                for (int e = 0; e < E; ++e) buf[t + G * e] = v[e];
+            } else {
+                F::template idle<reg::SyncCta>();
+                F::template idle<reg::SyncCta>();
+                __syncthreads();
+            }
         }
         __syncthreads();
     }
@@ -433,8 +440,14 @@ template <typename R, int LOG2N> static cudaError_t launch_update_n(const Update
     cudaError_t e = cudaFuncSetAttribute(update_row_kernel<R, LOG2N, MS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int threads = update_lines_per_batch(6 * a.rows, F::G, MaxThreads<R>::value) * F::G;
-    update_row_kernel<R, LOG2N, MS><<<a.ny / a.rows, threads, smem, s>>>(a);
+    // LB line transforms at a time; at least one thread per node of the CTA's rows (up to the cap)
+    constexpr int cap = PassThreads<R>::value;
+    UpdateArgs<R> b = a;
+    b.lines_per_batch = update_lines_per_batch(6 * a.rows, F::G, cap);
+    const int nodes = a.rows * F::N;
+    int threads = b.lines_per_batch * F::G;
+    if (threads < nodes) threads = nodes < cap ? ((nodes + 31) & ~31) : cap;
+    update_row_kernel<R, LOG2N, MS><<<a.ny / a.rows, threads, smem, s>>>(b);
     return cudaGetLastError();
 }
 

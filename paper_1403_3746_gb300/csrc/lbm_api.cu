@@ -970,6 +970,7 @@ void derivative_tables(int N, double d, double win_alpha, double win_p, double *
     int l2 = 0;
     while ((1 << l2) < N) ++l2;
     const int first = l2 >= 4 ? 16 : N;
+    const int E = N < 16 ? N : 16, G = N / E;  // stored at G e + t for position E t + e
     for (int pos = 0; pos < N; ++pos) {
         const int k = freq_at(pos, N, first);
         const int m = k < N / 2 ? k : k - N;
@@ -987,8 +988,9 @@ void derivative_tables(int N, double d, double win_alpha, double win_p, double *
                                  : 1.0;
             ke = w * 2.0 / d * s;
         }
-        k1[pos] = ke / N;
-        k2[pos] = -ke * ke / N;
+        const int at = G * (pos % E) + pos / E;
+        k1[at] = ke / N;
+        k2[at] = -ke * ke / N;
     }
 }
 
@@ -997,11 +999,11 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     while ((1 << lx) < nx) ++lx;
     while ((1 << ly) < ny) ++ly;
     const size_t cs = 2 * esize;  // complex element
-    // column tiles: W columns = W/2 lines of G threads; at most max_threads and 100 KB
+    // column tiles: W columns = W/2 lines of G threads; at most pass_threads and 100 KB
     int W = (int)(128 / esize);
     if (W > nx) W = nx;
-    const int maxt = max_threads(esize);
-    while (W > 2 && ((W / 2) * line_G(ly) > maxt || (size_t)(W / 2) * line_smem(ly) * cs > 100 * 1024)) W >>= 1;
+    const int maxt = max_threads(esize), colt = pass_threads(esize);
+    while (W > 2 && ((W / 2) * line_G(ly) > colt || (size_t)(W / 2) * line_smem(ly) * cs > 100 * 1024)) W >>= 1;
     g->colW = W;
     g->col_smem = (size_t)(W / 2) * line_smem(ly) * cs;
     // row kernels: rows per CTA, starting from about 512 nodes per CTA

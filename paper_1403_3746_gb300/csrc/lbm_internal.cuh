@@ -65,6 +65,13 @@ template <typename R> struct MaxThreads {
     static constexpr int value = sizeof(R) == 8 ? 384 : 768;
 };
 __host__ __device__ constexpr int max_threads(size_t esize) { return esize == 8 ? 384 : 768; }
+// column and update kernels: float32 CTAs of at most 512 threads, two resident per SM
+// (<= 64 registers per thread); float64 as above
+template <typename R> struct PassThreads {
+    static constexpr int value = sizeof(R) == 8 ? 384 : 512;
+    static constexpr int min_blocks = sizeof(R) == 8 ? 1 : 2;
+};
+__host__ __device__ constexpr int pass_threads(size_t esize) { return esize == 8 ? 384 : 512; }
 // every supported line length 2^1 .. 2^12
 #define LBM_FOR_LOG2N(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 
@@ -142,6 +149,7 @@ template <typename R> struct UpdateArgs {
     const R *Ay;     // [ny][12][nx]: v_iy d_y f_i
     R *m;            // macroscopic block; moments of fs in, moments of fout out
     int nx, ny, rows;
+    int lines_per_batch;  // line transforms in flight per batch (the other threads wait)
     Axis<R> ax;
     R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
     R psi_hi[16], psi_lo[16];  // psi_i = |v_i|^2 + eta_i^2 as a two-term sum (hi + lo)
