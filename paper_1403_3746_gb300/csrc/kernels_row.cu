@@ -37,21 +37,21 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
 // d_x Q_x, d_x S_xx, d_x S_xy and d_x(div u), which completes that numerator.
 // ---------------------------------------------------------------------------------------
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
+__global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R, LOG2N>::min_blocks) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N>;
     using CT = typename F::CT;
     constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sb = reinterpret_cast<CT *>(smem_raw);
     const int NR = a.rows, nodes = NR * NX;
-    // per row: line A owns buffers A1, A2; line B owns B1; then two per-node arrays
-    CT *lines = sb;                                              // [2 NR][2 SM]
-    R *cpart = reinterpret_cast<R *>(sb + (size_t)4 * NR * SM);  // [NR][NX] partial numerator of C
-    R *krx = cpart + nodes;                                      // [NR][NX] K rho d_x rho
+    // per row three line buffers: A1, A2 (line A) and B1 (line B); then K rho d_x rho per node.
+    // The partial numerator of C waits in its own global slot (M_CNUM) between the rounds.
+    CT *lines = sb;                                            // [NR][3 SM]
+    R *krx = reinterpret_cast<R *>(sb + (size_t)3 * NR * SM);  // [NR][NX]
     const int y0 = blockIdx.x * NR;
     const int slot = threadIdx.x / G, t = threadIdx.x % G;
     const int kind = slot / NR, r = slot % NR;
-    CT *O1 = lines + (size_t)slot * 2 * SM, *O2 = O1 + SM;
+    CT *O1 = lines + (size_t)r * 3 * SM + (kind == 0 ? 0 : 2 * SM), *O2 = O1 + SM;  // O2: line A only
     R *mrow = a.m + (size_t)(y0 + r) * NF_M * NX;  // this line's row of the macroscopic block
 
     if (threadIdx.x < NR)  // the node loop's inputs from the column pass start moving into L2
@@ -90,8 +90,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int rr = idx / NX, x = idx % NX;
         R *mn = a.m + (size_t)(y0 + rr) * NF_M * NX + x;  // this node: field k at mn[k * NX]
-        CT *A1 = lines + (size_t)(0 * NR + rr) * 2 * SM, *A2 = A1 + SM;
-        CT *B1 = lines + (size_t)(1 * NR + rr) * 2 * SM;
+        CT *A1 = lines + (size_t)rr * 3 * SM, *A2 = A1 + SM, *B1 = A1 + 2 * SM;
         const R rx = A1[x].x, Tx = A1[x].y, rxx = A2[x].x;
         const R dux_dx = B1[x].x, duy_dx = B1[x].y;
         const R rho = mn[M_RHO * NX], T = mn[M_T * NX];
@@ -118,8 +117,8 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
         // added after round 2 below, the y term by the update pass (after the flux pass)
         const R L_gradu = Lxx * dux_dx + Lxy * (duy_dx + dux_dy) + Lyy * duy_dy;
         const R r_gradu_r = rx * (dux_dx * rx + duy_dx * ry) + ry * (dux_dy * rx + duy_dy * ry);
-        cpart[idx] = (Pw - rT) * divu + L_gradu - zeta * divu * divu + R(1.125) * rho * rho * divu +
-                     K * (-R(0.5) * grr * divu - r_gradu_r);
+        mn[M_CNUM * NX] = (Pw - rT) * divu + L_gradu - zeta * divu * divu + R(1.125) * rho * rho * divu +
+                          K * (-R(0.5) * grr * divu - r_gradu_r);
         krx[idx] = K * rho * rx;
         mn[M_QY * NX] = Qy;
         mn[M_SXY * NX] = Sxy;
@@ -144,8 +143,8 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) macro_row_kernel(const _
             mrow[M_DSXX * NX + x] = v[e].y;
         } else {
             mrow[M_DSXY * NX + x] = v[e].x;
-            const int n = r * NX + x;
-            mrow[M_CNUM * NX + x] = cpart[n] - krx[n] * v[e].y;  // - K rho d_x rho d_x(div u)
+            // - K rho d_x rho d_x(div u); the partial value was written by this CTA's node loop
+            mrow[M_CNUM * NX + x] -= krx[r * NX + x] * v[e].y;
         }
     }
 }

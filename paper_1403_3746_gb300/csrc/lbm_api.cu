@@ -1017,9 +1017,10 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     g->rows_upd = r;
     g->upd_smem = 6 * (size_t)r * SM;
     r = r0;
-    // macro: 2 lines per row with 2 buffers each, plus 2 values per node
-    auto macro_bytes = [&](int rr) { return 4 * (size_t)rr * SM + 2 * (size_t)rr * nx * esize; };
-    while (r > 1 && (2 * r * G > maxt || macro_bytes(r) > 200 * 1024)) r >>= 1;
+    // macro: 2 lines per row with 3 buffers, plus 1 value per node
+    auto macro_bytes = [&](int rr) { return 3 * (size_t)rr * SM + (size_t)rr * nx * esize; };
+    const int mact = macro_threads(esize, lx);
+    while (r > 1 && (2 * r * G > mact || macro_bytes(r) > 200 * 1024)) r >>= 1;
     g->rows_macro = r;
     g->macro_smem = macro_bytes(r);
     r = r0;

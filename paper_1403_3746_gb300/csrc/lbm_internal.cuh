@@ -72,6 +72,16 @@ template <typename R> struct PassThreads {
     static constexpr int min_blocks = sizeof(R) == 8 ? 1 : 2;
 };
 __host__ __device__ constexpr int pass_threads(size_t esize) { return esize == 8 ? 384 : 512; }
+// macroscopic row pass (two lines of G threads per row): float32 CTAs of max(128, 2 G)
+// threads; at 128 (nx <= 1024) seven are resident per SM (<= 72 registers per thread), so
+// that 1024 rows fit in one wave of 152 SMs
+__host__ __device__ constexpr int macro_threads(size_t esize, int log2n) {
+    return esize == 8 ? 384 : (2 * line_G(log2n) > 128 ? 2 * line_G(log2n) : 128);
+}
+template <typename R, int LOG2N> struct MacroThreads {
+    static constexpr int value = macro_threads(sizeof(R), LOG2N);
+    static constexpr int min_blocks = sizeof(R) == 8 ? 1 : (value == 128 ? 7 : 1);
+};
 // every supported line length 2^1 .. 2^12
 #define LBM_FOR_LOG2N(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 
