@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
 
     CT v[F::E];
 #pragma unroll
-    for (int e = 0; e < F::E; ++e) v[e] = in[(size_t)(t + F::G * e) * rsi];
+    for (int e = 0; e < F::E; ++e) v[e] = __ldcg(in + (size_t)(t + F::G * e) * rsi);  // L2 only: single use
     CT *buf = sbuf + l * F::STRIDE;
     F::template forward<reg::SyncCta>(v, buf, t, a.ay.tw);
     F::multiply(v, t, job.order, job.c, a.ay.k1, a.ay.k2);

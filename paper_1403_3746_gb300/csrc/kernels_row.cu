@@ -12,6 +12,10 @@
 
 namespace lbm {
 
+// Streaming global load: cached in L2 only, so single-use data does not evict the line
+// transforms' tables (and register spills) from L1.
+template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
 // compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
 template <int B, int E, class Fn> __device__ __forceinline__ void static_for(Fn &&f) {
     if constexpr (B < E) {
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
                 const R *fa = frow + xfield(2 * p) * NX, *fb = frow + xfield(2 * p + 1) * NX;
                 CT v[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(fa[t + G * e], fb[t + G * e]);
+                for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(ldcg(fa + t + G * e), ldcg(fb + t + G * e));
                 F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
                 F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
                 F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
@@ -334,17 +338,19 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         const R *fn = a.fs + y * NF_F * NX + x;       // field i at fn[i * NX]
         const R *an = a.Ay + y * NF_A * NX + x;       // slot k at an[k * NX]
         R *mn = a.m + y * NF_M * NX + x;              // macro field k at mn[k * NX]
-        const R rho = mn[M_RHO * NX], ux = mn[M_UX * NX], uy = mn[M_UY * NX], T = mn[M_T * NX];
+        const R rho = ldcg(mn + M_RHO * NX), ux = ldcg(mn + M_UX * NX), uy = ldcg(mn + M_UY * NX);
+        const R T = ldcg(mn + M_T * NX);
         // I_i = -[A + B.(v_i - u) + (C + C_q)|v_i - u|^2] f_i^eq expands, per node, into
         // -(al + bx v_ix + by v_iy + cc |v_i|^2) f_i^eq; h (the stage's time step) is folded in.
         R hal = 0, hbx = 0, hby = 0, hcc = 0;
         if (frc) {
             const R rT = rho * T;
             const R irT = R(1) / rT;
-            const R Bx = (mn[M_DSXX * NX] + mn[M_DSXYY * NX]) * irT;
-            const R By = (mn[M_DSXY * NX] + mn[M_DSYY * NX]) * irT;
-            const R C = (mn[M_CNUM * NX] - K * rho * mn[M_RY * NX] * mn[M_DDIVUY * NX]) * (R(0.5) * irT / T);
-            const R Cq = (mn[M_DQX * NX] + mn[M_DQY * NX]) * (irT / T);
+            const R Bx = (ldcg(mn + M_DSXX * NX) + ldcg(mn + M_DSXYY * NX)) * irT;
+            const R By = (ldcg(mn + M_DSXY * NX) + ldcg(mn + M_DSYY * NX)) * irT;
+            const R C = (ldcg(mn + M_CNUM * NX) - K * rho * ldcg(mn + M_RY * NX) * ldcg(mn + M_DDIVUY * NX)) *
+                        (R(0.5) * irT / T);
+            const R Cq = (ldcg(mn + M_DQX * NX) + ldcg(mn + M_DQY * NX)) * (irT / T);
             const R CC = C + Cq;
             const R A = R(-2) * CC * T;
             hal = h * (A - Bx * ux - By * uy + CC * (ux * ux + uy * uy));
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         // or energy: its error scales with the non-equilibrium part instead of with rho.
         R fsv[16], dm[12];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) fsv[i] = fn[i * NX];
+        for (int i = 0; i < 16; ++i) fsv[i] = ldcg(fn + i * NX);
         if (MOMENT_SPACE) {
             const R eta2 = a.eta2;
             static_for<0, 12>([&](auto J) {
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
                     const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + x];
                     ad += R(vel_x(i)) * ((xs & 1) ? d.y : d.x);
                 }
-                if (ys >= 0) ad += an[ys * NX];
+                if (ys >= 0) ad += ldcg(an + ys * NX);
                 dfo -= h * ad;
             }
             if (col) dfo += htau * ne;
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
                 if (vel_y(i) != 0.0) q += hby * R(vel_y(i));
                 dfo -= q * fe;
             }
-            const R fo = (same_base ? fsv[i] : bn[i * NX]) + dfo;
+            const R fo = (same_base ? fsv[i] : ldcg(bn + i * NX)) + dfo;
             on[i * NX] = fo;
             acc.add(i, fo, a.psi_hi[i], a.psi_lo[i]);
         }
