@@ -258,6 +258,7 @@ int run_stage(lbm_ctx *c, int stage) {
         a.Ay = Ay;
         a.m = m;
         a.nx = nx; a.ny = rows; a.rows = c->geo.rows_upd;
+        a.raw = c->geo.upd_raw ? 1 : 0;
         a.ax = axis<R>(c, true);
         a.tau_inv = (R)(1.0 / p.tau);
         a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
@@ -1015,7 +1016,11 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     int r = r0;
     while (r > 1 && 6 * r * SM > 200 * 1024) r >>= 1;  // update: 6 line buffers per row
     g->rows_upd = r;
-    g->upd_smem = 6 * (size_t)r * SM;
+    // the raw rows of the 12 transformed fields are kept when the CTA still fits twice per SM
+    // (float32) or once (float64, register-limited to one CTA anyway)
+    const size_t raw_bytes = 12 * (size_t)r * nx * esize;
+    g->upd_raw = 6 * (size_t)r * SM + raw_bytes <= (esize == 4 ? 110u : 200u) * 1024;
+    g->upd_smem = 6 * (size_t)r * SM + (g->upd_raw ? raw_bytes : 0);
     r = r0;
     // macro: 2 lines per row with 3 buffers, plus 1 value per node
     auto macro_bytes = [&](int rr) { return 3 * (size_t)rr * SM + (size_t)rr * nx * esize; };
