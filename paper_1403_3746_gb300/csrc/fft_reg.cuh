@@ -36,8 +36,17 @@ template <typename R> __device__ __forceinline__ C<R> mk(R x, R y) {
     c.y = y;
     return c;
 }
-template <typename R> __device__ __forceinline__ C<R> add(C<R> a, C<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
-template <typename R> __device__ __forceinline__ C<R> sub(C<R> a, C<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+// Complex addition and subtraction of the butterflies. PK = true: float32 pairs as one packed
+// two-lane instruction (add.rn.f32x2, sm_100 and later), the same IEEE results with half
+// the instructions; used by the kernels whose registers allow the pairing.
+template <typename R, bool PK> struct Arith {
+    static __device__ __forceinline__ C<R> add(C<R> a, C<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ C<R> sub(C<R> a, C<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+};
+template <> struct Arith<float, true> {
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+};
 // a * w and a * conj(w)
 template <typename R> __device__ __forceinline__ C<R> mul(C<R> a, C<R> w) {
     return mk<R>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
@@ -50,20 +59,20 @@ template <typename R, bool INV> __device__ __forceinline__ C<R> rot(C<R> a) {
     return INV ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x);
 }
 
-template <typename R, bool INV> __device__ __forceinline__ void dft2(C<R> &x0, C<R> &x1) {
+template <typename R, bool INV, bool PK> __device__ __forceinline__ void dft2(C<R> &x0, C<R> &x1) {
     const C<R> t = x0;
-    x0 = add<R>(t, x1);
-    x1 = sub<R>(t, x1);
+    x0 = Arith<R, PK>::add(t, x1);
+    x1 = Arith<R, PK>::sub(t, x1);
 }
 
 // y_k = sum_q x_q w4^{qk}, w4 = exp(-+ 2 pi i / 4); in place, outputs in natural order
-template <typename R, bool INV> __device__ __forceinline__ void dft4(C<R> &x0, C<R> &x1, C<R> &x2, C<R> &x3) {
-    const C<R> t0 = add<R>(x0, x2), t1 = sub<R>(x0, x2), t2 = add<R>(x1, x3);
-    const C<R> t3 = rot<R, INV>(sub<R>(x1, x3));
-    x0 = add<R>(t0, t2);
-    x1 = add<R>(t1, t3);
-    x2 = sub<R>(t0, t2);
-    x3 = sub<R>(t1, t3);
+template <typename R, bool INV, bool PK> __device__ __forceinline__ void dft4(C<R> &x0, C<R> &x1, C<R> &x2, C<R> &x3) {
+    const C<R> t0 = Arith<R, PK>::add(x0, x2), t1 = Arith<R, PK>::sub(x0, x2), t2 = Arith<R, PK>::add(x1, x3);
+    const C<R> t3 = rot<R, INV>(Arith<R, PK>::sub(x1, x3));
+    x0 = Arith<R, PK>::add(t0, t2);
+    x1 = Arith<R, PK>::add(t1, t3);
+    x2 = Arith<R, PK>::sub(t0, t2);
+    x3 = Arith<R, PK>::sub(t1, t3);
 }
 
 // a * w16^M (forward: w16 = exp(-2 pi i/16); inverse: the conjugate), M a compile-time constant
@@ -87,9 +96,9 @@ template <typename R, bool INV, int M> __device__ __forceinline__ C<R> w16(C<R> 
 }
 
 // 16-point DFT in registers (q = q1 + 4 q2, k = k2 + 4 k1); v[k] holds y_k on return
-template <typename R, bool INV> __device__ __forceinline__ void dft16(C<R> v[16]) {
+template <typename R, bool INV, bool PK> __device__ __forceinline__ void dft16(C<R> v[16]) {
 #pragma unroll
-    for (int q1 = 0; q1 < 4; ++q1) dft4<R, INV>(v[q1], v[q1 + 4], v[q1 + 8], v[q1 + 12]);
+    for (int q1 = 0; q1 < 4; ++q1) dft4<R, INV, PK>(v[q1], v[q1 + 4], v[q1 + 8], v[q1 + 12]);
     // v[q1 + 4 k2] = b(q1, k2); twiddle by w16^(q1 k2)
     v[5] = w16<R, INV, 1>(v[5]);
     v[6] = w16<R, INV, 2>(v[6]);
@@ -101,7 +110,7 @@ template <typename R, bool INV> __device__ __forceinline__ void dft16(C<R> v[16]
     v[14] = w16<R, INV, 6>(v[14]);
     v[15] = w16<R, INV, 9>(v[15]);
 #pragma unroll
-    for (int k2 = 0; k2 < 4; ++k2) dft4<R, INV>(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]);
+    for (int k2 = 0; k2 < 4; ++k2) dft4<R, INV, PK>(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]);
     // v[4 k2 + k1] = y(k2 + 4 k1): transpose the 4 x 4 block (register renaming only)
     C<R> t[16];
 #pragma unroll
@@ -111,17 +120,17 @@ template <typename R, bool INV> __device__ __forceinline__ void dft16(C<R> v[16]
 }
 
 // 8-point DFT (q = q1 + 2 q2, k = k2 + 4 k1)
-template <typename R, bool INV> __device__ __forceinline__ void dft8(C<R> v[8]) {
-    dft4<R, INV>(v[0], v[2], v[4], v[6]);
-    dft4<R, INV>(v[1], v[3], v[5], v[7]);
+template <typename R, bool INV, bool PK> __device__ __forceinline__ void dft8(C<R> v[8]) {
+    dft4<R, INV, PK>(v[0], v[2], v[4], v[6]);
+    dft4<R, INV, PK>(v[1], v[3], v[5], v[7]);
     // v[q1 + 2 k2] = b(q1, k2); twiddle q1 = 1 by w8^k2 = w16^(2 k2)
     v[3] = w16<R, INV, 2>(v[3]);
     v[5] = w16<R, INV, 4>(v[5]);
     v[7] = w16<R, INV, 6>(v[7]);
-    dft2<R, INV>(v[0], v[1]);
-    dft2<R, INV>(v[2], v[3]);
-    dft2<R, INV>(v[4], v[5]);
-    dft2<R, INV>(v[6], v[7]);
+    dft2<R, INV, PK>(v[0], v[1]);
+    dft2<R, INV, PK>(v[2], v[3]);
+    dft2<R, INV, PK>(v[4], v[5]);
+    dft2<R, INV, PK>(v[6], v[7]);
     // v[2 k2 + k1] = y(k2 + 4 k1)
     C<R> t[8];
 #pragma unroll
@@ -130,10 +139,10 @@ template <typename R, bool INV> __device__ __forceinline__ void dft8(C<R> v[8]) 
     for (int k = 0; k < 8; ++k) v[k] = t[k];
 }
 
-template <typename R, bool INV, int RADIX> __device__ __forceinline__ void dft_small(C<R> *v) {
-    if (RADIX == 2) dft2<R, INV>(v[0], v[1]);
-    if (RADIX == 4) dft4<R, INV>(v[0], v[1], v[2], v[3]);
-    if (RADIX == 8) dft8<R, INV>(v);
+template <typename R, bool INV, int RADIX, bool PK> __device__ __forceinline__ void dft_small(C<R> *v) {
+    if (RADIX == 2) dft2<R, INV, PK>(v[0], v[1]);
+    if (RADIX == 4) dft4<R, INV, PK>(v[0], v[1], v[2], v[3]);
+    if (RADIX == 8) dft8<R, INV, PK>(v);
 }
 
 struct SyncCta {
@@ -163,7 +172,7 @@ __host__ __device__ inline int twiddle_exponent(int n, int idx) {
     return -1;
 }
 
-template <typename R, int LOG2N> struct LineFFT {
+template <typename R, int LOG2N, bool PK = false> struct LineFFT {
     static constexpr int N = 1 << LOG2N;
     static constexpr int E = N < 16 ? N : 16;                // points per thread
     static constexpr int G = N / E;                          // threads per line
@@ -191,9 +200,9 @@ template <typename R, int LOG2N> struct LineFFT {
 #pragma unroll
                 for (int k = 1; k < 16; ++k) v[k] = mulc<R>(v[k], twp[(k - 1) * M]);
             }
-            dft16<R, true>(v);
+            dft16<R, true, PK>(v);
         } else {
-            dft16<R, false>(v);
+            dft16<R, false, PK>(v);
             if (M > 1 && j) {
 #pragma unroll
                 for (int k = 1; k < 16; ++k) v[k] = mul<R>(v[k], twp[(k - 1) * M]);
@@ -236,7 +245,7 @@ template <typename R, int LOG2N> struct LineFFT {
             fwd_from<P + 1, SYNC>(v, buf, t, tw);
         } else if constexpr (RL > 1) {
 #pragma unroll
-            for (int kb = 0; kb < E / RL; ++kb) dft_small<R, false, RL>(v + kb * RL);
+            for (int kb = 0; kb < E / RL; ++kb) dft_small<R, false, RL, PK>(v + kb * RL);
         }
     }
 
@@ -268,7 +277,7 @@ template <typename R, int LOG2N> struct LineFFT {
                                                                         const CT *__restrict__ tw) {
         if constexpr (RL > 1) {
 #pragma unroll
-            for (int kb = 0; kb < E / RL; ++kb) dft_small<R, true, RL>(v + kb * RL);
+            for (int kb = 0; kb < E / RL; ++kb) dft_small<R, true, RL, PK>(v + kb * RL);
             if constexpr (NP16 > 0) {
                 SYNC::run();
                 storeF(v, buf, t);

@@ -13,7 +13,7 @@ namespace lbm {
 
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) col_deriv_kernel(const __grid_constant__ ColArgs<R> a) {
-    using F = reg::LineFFT<R, LOG2N>;
+    using F = reg::LineFFT<R, LOG2N, true>;
     using CT = typename F::CT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sbuf = reinterpret_cast<CT *>(smem_raw);

@@ -42,7 +42,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
 // ---------------------------------------------------------------------------------------
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R, LOG2N>::min_blocks) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
-    using F = reg::LineFFT<R, LOG2N>;
+    using F = reg::LineFFT<R, LOG2N, true>;
     using CT = typename F::CT;
     constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
