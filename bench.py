@@ -10,10 +10,11 @@ the plain FP64 path measured beside it.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Timing: W untimed steps, then K steps each between CUDA events on the library's stream,
-with a 256 MiB buffer written between steps (outside the events) to flush the 126 MB L2.
-Under torchrun every rank runs its own replica (no data-path collective: a single grid
-does not shard without an all-to-all, see the design notes); value = all ranks' node
-updates / the slowest rank's time. One JSON line is printed by rank 0.
+with a 256 MiB buffer written between steps (outside the events) to flush the 126 MB L2;
+then K more steps with per-launch events around every kernel, which give the per-kernel
+durations of the roofline object. Under torchrun every rank runs its own replica (no
+data-path collective: a single grid does not shard without an all-to-all); value = all
+ranks' node updates / the slowest rank's time. One JSON line is printed by rank 0.
 """
 import argparse
 import hashlib
@@ -126,8 +127,25 @@ def make_fields(lbm, synthetic, n=N_GRID, radius=RADIUS):
 
 
 def time_path(lbm, torch, precision, steps, warmup, fields, stream):
+    """Two timed loops of `steps` steps each on the same state, an L2 flush between steps.
+    Loop A (the headline): lbm_step as the library runs it (one CUDA graph per step), one event
+    pair around each step. Loop B: per-launch timing on (direct launches, an event pair around
+    every kernel), which gives each kernel's mean duration for the roofline."""
     p = lbm.default_params(precision=precision, **PARAMS)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def loop(sim):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b in ev:
+            a.record(stream)
+            sim.step(1)
+            b.record(stream)
+            flush.fill_(float(len(ev)))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], time.perf_counter() - t0
+
     with lbm.Simulation(N_GRID, N_GRID, p, stream=stream.cuda_stream) as sim:
         sim.init(*fields)
         with torch.cuda.stream(stream):
@@ -135,23 +153,13 @@ def time_path(lbm, torch, precision, steps, warmup, fields, stream):
                 sim.step(1)
                 flush.fill_(1.0)
             stream.synchronize()
+            step_ms, wall = loop(sim)
             sim.timing(True)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(steps)]
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for a, b in ev:
-                a.record(stream)
-                sim.step(1)
-                b.record(stream)
-                flush.fill_(float(len(ev)))
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
-        step_ms = [a.elapsed_time(b) for a, b in ev]
+            step_ms_b, _ = loop(sim)
         kern = {k: sim.timing_read(k) for k in ELEMS_PER_NODE}
         sim.timing(False)
         diag = sim.diagnostics()
-    return step_ms, kern, wall, diag
+    return step_ms, kern, wall, diag, step_ms_b
 
 
 def e2e_path(lbm, torch, precision, steps, fields):
@@ -306,7 +314,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
-        step_ms, kern, wall, diag = time_path(lbm, torch, lbm.LBM_MIXED, args.steps, args.warmup, fields, stream)
+        step_ms, kern, wall, diag, step_ms_b = time_path(lbm, torch, lbm.LBM_MIXED, args.steps, args.warmup, fields,
+                                                          stream)
     clocks = clk.summary()
     total_ms = sum(step_ms)
     if world > 1:
@@ -318,7 +327,7 @@ def main():
 
     # FP64 path on the same workload (plain method)
     k64 = args.fp64_steps or max(3, args.steps // 10)
-    step64, kern64, _, _ = time_path(lbm, torch, lbm.LBM_FP64, k64, min(args.warmup, 3), fields, stream)
+    step64, kern64, _, _, _ = time_path(lbm, torch, lbm.LBM_FP64, k64, min(args.warmup, 3), fields, stream)
     fp64_mlups = n * k64 / (sum(step64) * 1e-3) / 1e6
 
     dom = max(kern, key=lambda k: kern[k][0])
@@ -329,8 +338,10 @@ def main():
     roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom] + "<float>", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": ncu_traffic(dom, "mixed"),
                 "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                "duration_source": "mean CUDA-event time per launch in a second timed loop of the same steps "
+                                   "with an event pair around every kernel",
                 "step_frac": ELEMS_PER_NODE_STEP * 4 * n / (total_ms * 1e-3 / args.steps) / 1e9 / hbm}
-    launches = sum(c for _, c in kern.values())
+    launches = sum(c for _, c in kern.values())  # loop B; loop A's graphs hold the same kernels per step
     e2e = e2e_path(lbm, torch, lbm.LBM_MIXED, max(10, args.steps // 4), fields) if rank == 0 else None
 
     extras = {}
@@ -367,6 +378,7 @@ def main():
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (moment sums compensated)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "LBM_MIXED", "l2": "flushed between steps (256 MiB write)",
+                       "launch": "lbm_step: one CUDA graph per step (8 kernels)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_mlups, "unit": "MLUPS", "steps": k64,
                           "ms_per_step": sum(step64) / k64,
@@ -374,6 +386,7 @@ def main():
                           "bound": "alu (fp64)", "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS},
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
             "roofline": roofline, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
+            "ms_per_step_kernel_timed_loop": sum(step_ms_b) / args.steps,
             "clocks": clocks, "wall_s_timed_loop": wall,
             "check": {"mass": diag["mass"], "umax": diag["umax"]},
         }

@@ -13,7 +13,8 @@ Readings:
 * The window W of the "windowed" FFT scheme is not specified in the paper. It is read
   as a per-axis exponential filter W(m) = exp(-alpha (|m|/(N/2))^p) (Hou and Li, J.
   Comput. Phys. 226 (2007): alpha = 36, p = 36) applied with each first derivative
-  along that derivative's own axis; alpha = 0 (W = 1) is Eq. (3) exactly.
+  along that derivative's own axis; alpha = 0 (W = 1) is Eq. (3) exactly. Against the paper
+  the window is "parity unpinned" (its form is a reading); tests pin it to this definition.
 """
 import numpy as np
 

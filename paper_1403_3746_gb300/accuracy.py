@@ -3,8 +3,9 @@ stated per physical result of Sec. 3 on the same seeded inputs:
 
 * coexistence densities of a flat liquid slab (Sec. 3.1), measured in the bulk of each phase;
 * relative mass drift over the run;
-* spurious (parasitic) velocity max |u| around a static droplet (Sec. 3.3);
-* droplet pressure jump P_in - P_out of the van der Waals pressure (Laplace test, Sec. 3.3).
+* pressure jump P_in - P_out of the van der Waals pressure across a static circular droplet
+  (the relaxed state of the droplet runs of Sec. 3.3; Laplace law);
+* spurious (parasitic) velocity max |u| around that droplet.
 
 Both paths run through the library (each instance set advanced as one batch); the float64
 path agrees with the oracle to round-off on short runs, so it stands in for it on runs of

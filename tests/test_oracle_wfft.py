@@ -91,3 +91,28 @@ def test_fft_derivative_matches_brute_force_dft(nx, ny):
             ref = dft_deriv_matrix(ny, dy, oy) @ ref
         got = spectral_deriv(h, ox, oy, dx, dy)
         assert np.allclose(got, ref, rtol=0, atol=1e-11 * max(1.0, np.abs(ref).max()))
+
+
+def test_windowed_derivative_of_single_modes():
+    # The window is a reading (the paper does not give W): pinned here to its stated form.
+    # For a pure x-mode of index m and a pure y-mode of index n, the windowed first
+    # derivative is the unwindowed one times exp(-alpha (|m|/(N/2))^p), computed here from the
+    # closed form, and a derivative along x leaves a y-mode's window out entirely.
+    nx, ny, dx, dy, alpha, p = 32, 16, 0.1, 0.2, 36.0, 8.0
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    for m in (3, 9, 14):
+        h = np.sin(2 * np.pi * m * x / nx) * np.ones((ny, 1))
+        plain = spectral_deriv(h, 1, 0, dx, dy)
+        wind = spectral_deriv(h, 1, 0, dx, dy, alpha, p)
+        w = np.exp(-alpha * (m / (nx / 2)) ** p)
+        assert np.allclose(wind, w * plain, rtol=0, atol=1e-13 * np.max(np.abs(plain)))
+        # second derivative carries the window twice (composition of first derivatives)
+        wind2 = spectral_deriv(h, 2, 0, dx, dy, alpha, p)
+        plain2 = spectral_deriv(h, 2, 0, dx, dy)
+        assert np.allclose(wind2, w * w * plain2, rtol=0, atol=1e-13 * np.max(np.abs(plain2)))
+    for n in (2, 5, 7):
+        g = np.cos(2 * np.pi * n * y / ny) * np.sin(2 * np.pi * 3 * x / nx)
+        plain = spectral_deriv(g, 1, 0, dx, dy)
+        wind = spectral_deriv(g, 1, 0, dx, dy, alpha, p)
+        assert np.allclose(wind, np.exp(-alpha * (3 / (nx / 2)) ** p) * plain, rtol=0, atol=1e-13)
