@@ -20,6 +20,14 @@ Readings:
   stages follow Eq. (1): with R(f) = -v . grad f - (f - f^eq)/tau + I,
   f^{n+1/2} = f^n + (dt/2) R(f^n) and f^{n+1} = f^n + dt R(f^{n+1/2}), where f^eq and I
   of each stage are built from the moments of that stage's f.
+
+Numerical variants (Sec. 3.2 runs the D2V33 comparison model with the 8th-order modified
+wavenumber and the forward Euler scheme): `keff_terms` keeps the first terms of the series
+of Eq. (3) (8 = 16th order, 4 = 8th order) and `scheme = "euler"` advances
+f^{n+1} = f^n + dt R(f^n). Isothermal mode (the fixed temperature of the droplet runs of
+Sec. 3.3): with T_iso > 0, f^eq and I_i of every stage use T = T_iso at every node instead of
+the temperature moment of f (the energy equation is replaced by a thermostat; mass and
+momentum stay conserved).
 """
 from dataclasses import dataclass
 
@@ -59,6 +67,9 @@ class Params:
     force: bool = True
     collide: bool = True
     advect: bool = True
+    keff_terms: int = 8
+    scheme: str = "rk2"
+    T_iso: float = 0.0
 
     @staticmethod
     def phase_separation():
@@ -85,7 +96,7 @@ def forcing_terms(dvm, rho, ux, uy, T, fe, p):
     """Eq. (2) and the coefficient definitions after it. Returns I (16, ny, nx) and a dict
     of the intermediate fields (A, B_x, B_y, C, C_q, ...)."""
     def D(h, ox, oy):
-        return spectral_deriv(h, ox, oy, p.dx, p.dy, p.win_alpha, p.win_p)
+        return spectral_deriv(h, ox, oy, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms)
 
     # spatial derivatives of the macroscopic fields
     rx, ry = D(rho, 1, 0), D(rho, 0, 1)
@@ -136,14 +147,16 @@ def advection(dvm, f, p):
     """v_i . grad f_i for all 16 fields (Eq. (1) left side), by the FFT scheme of Eq. (3)."""
     out = np.empty_like(f)
     for i in range(16):
-        out[i] = dvm.vx[i] * spectral_deriv(f[i], 1, 0, p.dx, p.dy, p.win_alpha, p.win_p) \
-            + dvm.vy[i] * spectral_deriv(f[i], 0, 1, p.dx, p.dy, p.win_alpha, p.win_p)
+        out[i] = dvm.vx[i] * spectral_deriv(f[i], 1, 0, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms) \
+            + dvm.vy[i] * spectral_deriv(f[i], 0, 1, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms)
     return out
 
 
 def rhs(dvm, f, p):
     """R(f) = -v . grad f - (f - f^eq)/tau + I, with f^eq and I from the moments of f."""
     rho, ux, uy, T = moments(dvm, f, p.b)
+    if p.T_iso > 0.0:
+        T = np.full_like(rho, p.T_iso)
     fe = feq(dvm, rho, ux, uy, T, p.b, _minv(dvm))
     R = np.zeros_like(f)
     if p.advect:
@@ -157,13 +170,18 @@ def rhs(dvm, f, p):
 
 
 def rk2_step(dvm, f, p):
-    """Sec. 2.3: two-stage (midpoint) Runge-Kutta step of Eq. (1)."""
+    """Sec. 2.3: two-stage (midpoint) Runge-Kutta step of Eq. (1); the forward Euler step
+    f + dt R(f) when p.scheme == "euler"."""
+    if p.scheme == "euler":
+        return f + p.dt * rhs(dvm, f, p)
     fh = f + 0.5 * p.dt * rhs(dvm, f, p)
     return f + p.dt * rhs(dvm, fh, p)
 
 
 def init_feq(dvm, rho, ux, uy, T, p):
-    """f_i := f_i^eq(rho, u, T) (the initial state of every run)."""
+    """f_i := f_i^eq(rho, u, T) (the initial state of every run; T = T_iso in isothermal mode)."""
+    if p.T_iso > 0.0:
+        T = np.full_like(rho, p.T_iso)
     return feq(dvm, rho, ux, uy, T, p.b, _minv(dvm))
 
 

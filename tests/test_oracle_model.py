@@ -234,3 +234,56 @@ def test_density_and_temperature_gradients_together(dvm):
     assert np.max(np.abs(ex["C"])) < 1e-12 * np.max(np.abs(Cq))
     # the grad(M/T) part alone is >= 100x the tolerance above (dropping or flipping it fails)
     assert np.min(np.abs(K * g1 / (rho * T))[np.abs(g1) > 0.5 * np.abs(g1).max()]) > 100 * 1e-8 * np.max(np.abs(Bx))
+
+
+def test_euler_bgk_decay_rate(dvm):
+    # forward Euler (the D2V33 runs' scheme, Sec. 3.2): the non-equilibrium part of a uniform
+    # state is multiplied by 1 - z per step, z = dt/tau.
+    p = Params(tau=4e-4, dt=1e-4, scheme="euler")
+    shape = (4, 8)
+    rho, ux, uy, T = (np.full(shape, v) for v in (0.9, -0.02, 0.04, 0.95))
+    fe = init_feq(dvm, rho, ux, uy, T, p)
+    Cns = np.array([np.ones(16), dvm.vx, dvm.vy, dvm.psi])
+    d = np.random.default_rng(7).standard_normal(16)
+    d -= Cns.T @ np.linalg.solve(Cns @ Cns.T, Cns @ d)
+    d *= 1e-3
+    g = rk2_step(dvm, fe + d[:, None, None], p)
+    z = p.dt / p.tau
+    assert np.max(np.abs((g - fe) - (1 - z) * d[:, None, None])) < 1e-13
+
+
+def test_euler_advection_amplification(dvm):
+    # collision and forcing off: forward Euler multiplies each Fourier mode of f_i by
+    # 1 - i dt k . v_i (|.| > 1: the scheme amplifies pure advection, as expected of Euler).
+    p = Params(collide=False, force=False, dt=2e-4, scheme="euler")
+    N = 32
+    X, Y = np.meshgrid(np.arange(N) * p.dx, np.arange(N) * p.dy)
+    kv = 2 * np.pi / (N * p.dx) * np.array([2.0, -1.0])
+    xi = kv[0] * X + kv[1] * Y
+    a = np.linspace(0.4, 1.1, 16)
+    c = np.linspace(0.02, 0.01, 16)
+    f = a[:, None, None] + c[:, None, None] * np.sin(xi)[None]
+    g = rk2_step(dvm, f, p)
+    th = p.dt * (kv[0] * dvm.vx + kv[1] * dvm.vy)
+    ref = a[:, None, None] + c[:, None, None] * ((1 - 1j * th)[:, None, None] * (-1j) * np.exp(1j * xi)[None]).real
+    assert np.max(np.abs(g - ref)) < 1e-13
+
+
+def test_isothermal_relaxation_to_the_thermostat(dvm):
+    # isothermal mode: uniform state whose temperature moment T0 differs from T_iso. Gradients
+    # vanish (I = 0, no advection), mass and momentum are conserved, so the target
+    # f^eq(rho, u, T_iso) is fixed and f - f^eq(T_iso) is multiplied by 1 - z + z^2/2 per step.
+    p = Params(tau=3e-4, dt=1e-4, T_iso=0.9)
+    shape = (4, 4)
+    rho, ux, uy = (np.full(shape, v) for v in (1.2, 0.03, 0.01))
+    T0 = np.full(shape, 0.97)
+    f0 = feq(dvm, rho, ux, uy, T0, p.b)
+    target = feq(dvm, rho, ux, uy, np.full(shape, 0.9), p.b)
+    f = f0.copy()
+    z = p.dt / p.tau
+    for n in range(1, 4):
+        f = rk2_step(dvm, f, p)
+        assert np.max(np.abs((f - target) - (1 - z + z * z / 2) ** n * (f0 - target))) < 1e-13
+    r, vx, vy, T = moments(dvm, f, p.b)
+    assert np.allclose(r, 1.2, rtol=0, atol=1e-14) and np.allclose(vx, 0.03, rtol=0, atol=1e-14)
+    assert np.all(np.abs(T - 0.9) < np.abs(0.97 - 0.9))

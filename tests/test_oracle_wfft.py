@@ -116,3 +116,19 @@ def test_windowed_derivative_of_single_modes():
         plain = spectral_deriv(g, 1, 0, dx, dy)
         wind = spectral_deriv(g, 1, 0, dx, dy, alpha, p)
         assert np.allclose(wind, np.exp(-alpha * (3 / (nx / 2)) ** p) * plain, rtol=0, atol=1e-13)
+
+
+def test_keff_with_four_terms_is_eighth_order():
+    # the 8th-order scheme of the D2V33 runs (Sec. 3.2) keeps the first four terms:
+    # k - k_eff ~ c_4 phi^9, log-log slope ~9; and it is the arcsin series truncated there.
+    N, dx = 4096, 1.0
+    m = np.array([N * np.arcsin(0.5) / np.pi, N * np.arcsin(0.4) / np.pi])
+    k = 2.0 * np.pi * m / (N * dx)
+    err = k - keff(m, N, dx, terms=4)
+    slope = np.log(err[0] / err[1]) / np.log(0.5 / 0.4)
+    assert np.all(err > 0) and 9.0 <= slope <= 10.5
+    phi = 0.3
+    x = sympy.symbols("x")
+    ser = sympy.series(sympy.asin(x), x, 0, 9).removeO()
+    mm = N * np.arcsin(phi) / np.pi
+    assert keff(mm, N, 2.0, terms=4) == pytest.approx(float(ser.subs(x, phi)), rel=1e-14)
