@@ -44,12 +44,18 @@ extern "C" {
 
 /* precision of the hot path */
 #define LBM_FP64 0   /* every step in float64 (the plain method) */
-#define LBM_MIXED 1  /* f-field storage, its FFTs and the update in float32; see DESIGN notes */
+#define LBM_MIXED 1  /* f storage, all transforms and the update in float32; float64 tables; moment
+                        sums compensated (float64-class); collision in moment space */
 
 /* test hooks: switch terms of Eq. (1) off */
 #define LBM_FLAG_NO_ADVECTION 1 /* drop v_i . grad f_i */
 #define LBM_FLAG_NO_COLLISION 2 /* drop -(f_i - f_i^eq)/tau */
 #define LBM_FLAG_NO_FORCE 4     /* drop I_i (and skip the macroscopic derivative chain) */
+/* variants */
+#define LBM_FLAG_EULER 8        /* forward Euler f^{n+1} = f^n + dt R(f^n) instead of the two-stage
+                                   Runge-Kutta scheme (the D2V33 runs' scheme of Sec. 3.2) */
+#define LBM_FLAG_ISOTHERMAL 16  /* T = T_iso in f^eq and I_i at every node instead of the temperature
+                                   moment (thermostat; mass and momentum stay conserved) */
 
 typedef struct lbm_params {
     double tau;   /* relaxation time (Eq. (1)) */
@@ -66,13 +72,16 @@ typedef struct lbm_params {
     double win_p;     /* along each derivative's axis; win_alpha = 0 (default): W = 1, Eq. (3) */
     int precision; /* LBM_FP64 or LBM_MIXED */
     int flags;     /* LBM_FLAG_* bits, 0 for the full model */
+    double T_iso;  /* temperature of LBM_FLAG_ISOTHERMAL (> 0 when the flag is set) */
+    int keff_terms; /* terms of the series of Eq. (3), 1..8: 8 = 16th order (default), 4 = 8th order */
+    int reserved;   /* 0 */
 } lbm_params;
 
 typedef struct lbm_ctx *lbm_handle;
 
 /* Fills *p with the phase-separation set of Sec. 3.2 (tau = dt = 1e-4, dx = dy = 1/256,
  * K = 5e-6, H = 0, zeta = 0) with q = -0.004 and b = 2 (Sec. 3.1), eta0 = 2.5, no window
- * (win_alpha = 0, win_p = 36), FP64, no flags. */
+ * (win_alpha = 0, win_p = 36), FP64, no flags, T_iso = 0, keff_terms = 8. */
 void lbm_default_params(lbm_params *p);
 
 /* Creates a simulation on the current CUDA device. nx, ny: powers of two, 2 <= n <= 4096
@@ -82,14 +91,16 @@ void lbm_default_params(lbm_params *p);
 int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handle *out);
 
 /* Sets f_i := f_i^eq(rho, u, T) at every node (the initial state of Sec. 3's runs) and
- * resets the step counter. Host buffers, [ny][nx] float64 each; T > 0 and 0 < rho < 3. */
+ * resets the step counter. Host buffers, [ny][nx] float64 each; T > 0 and 0 < rho < 3.
+ * With LBM_FLAG_ISOTHERMAL the T buffer is checked but T_iso is used. */
 int lbm_init(lbm_handle h, const double *rho, const double *ux, const double *uy, const double *T);
 
 /* Same as lbm_init with device buffers (asynchronous on the handle's stream). */
 int lbm_init_device(lbm_handle h, const double *rho, const double *ux, const double *uy,
                     const double *T);
 
-/* Advances n >= 0 full Runge-Kutta steps (Sec. 2.3), asynchronously on the stream. */
+/* Advances n >= 0 full Runge-Kutta steps (Sec. 2.3; forward Euler steps with
+ * LBM_FLAG_EULER), asynchronously on the stream. */
 int lbm_step(lbm_handle h, int n);
 
 /* Moments rho, u_x, u_y, T of the current f (Sec. 2.1) into host buffers [ny][nx].

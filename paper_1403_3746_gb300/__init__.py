@@ -20,6 +20,8 @@ LBM_MIXED = 1
 LBM_FLAG_NO_ADVECTION = 1
 LBM_FLAG_NO_COLLISION = 2
 LBM_FLAG_NO_FORCE = 4
+LBM_FLAG_EULER = 8
+LBM_FLAG_ISOTHERMAL = 16
 KERNELS = {"col": 0, "macro": 1, "flux": 2, "update": 3}
 
 _lib = None
@@ -34,7 +36,8 @@ class lbm_params(ctypes.Structure):
                 ("dy", ctypes.c_double), ("K", ctypes.c_double), ("H", ctypes.c_double),
                 ("q", ctypes.c_double), ("zeta", ctypes.c_double), ("b", ctypes.c_double),
                 ("eta0", ctypes.c_double), ("win_alpha", ctypes.c_double), ("win_p", ctypes.c_double),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("T_iso", ctypes.c_double),
+                ("keff_terms", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -14,7 +14,7 @@ __global__ void init_feq_kernel(const __grid_constant__ InitArgs a) {
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
          g += (long long)gridDim.x * blockDim.x) {
         const long long y = g / a.nx, x = g - y * a.nx;
-        const double rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T[g];
+        const double rho = a.rho[g], ux = a.ux[g], uy = a.uy[g], T = a.T_iso > 0.0 ? a.T_iso : a.T[g];
         const double u2 = ux * ux + uy * uy, b = a.b;
         const double e = (b + 2.0) * T + u2, gq = (b + 4.0) * T + u2;
         const double mq[16] = {rho,
@@ -53,7 +53,7 @@ __global__ void init_feq_kernel(const __grid_constant__ InitArgs a) {
         mn[M_RHO * a.nx] = (F)mr;
         mn[M_UX * a.nx] = (F)nux;
         mn[M_UY * a.nx] = (F)nuy;
-        mn[M_T * a.nx] = (F)((mE * ir - (nux * nux + nuy * nuy)) / b);
+        mn[M_T * a.nx] = a.T_iso > 0.0 ? (F)a.T_iso : (F)((mE * ir - (nux * nux + nuy * nuy)) / b);
     }
 }
 
@@ -81,7 +81,7 @@ __global__ void moments_kernel(const __grid_constant__ MomArgs a) {
         mn[M_RHO * a.nx] = (F)mr;
         mn[M_UX * a.nx] = (F)nux;
         mn[M_UY * a.nx] = (F)nuy;
-        mn[M_T * a.nx] = (F)((mE * ir - (nux * nux + nuy * nuy)) / a.b);
+        mn[M_T * a.nx] = a.T_iso > 0.0 ? (F)a.T_iso : (F)((mE * ir - (nux * nux + nuy * nuy)) / a.b);
     }
 }
 

@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
     const bool col = !(a.flags & LBM_FLAG_NO_COLLISION);
     const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
     const bool same_base = a.fbase == a.fs;
+    const bool iso = a.flags & LBM_FLAG_ISOTHERMAL;
     // raw rows of the 12 transformed fields (slot k = xslot(i)), [12][NR NX], when a.raw
     R *sraw = reinterpret_cast<R *>(sb + (size_t)6 * NR * SM);
     const bool raw = a.raw && adv;
@@ -376,11 +377,18 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         // neq = M^-1 (m^eq - M f) over the 12 non-conserved moments only (the 4 conserved
         // ones agree exactly), so the rounding of M^-1 to float32 cannot bias mass, momentum
         // or energy: its error scales with the non-equilibrium part instead of with rho.
-        R fsv[16], dm[12];
+        R fsv[16], dm[12], dE = 0;
 #pragma unroll
         for (int i = 0; i < 16; ++i)
             fsv[i] = (raw && xslot(i) >= 0) ? sraw[(size_t)xslot(i) * nodes + idx] : ldcg(fn + i * NX);
         if (MOMENT_SPACE) {
+            // isothermal: the energy moment (row 3) is not conserved by the thermostat either
+            if (iso) {
+                R me = 0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) me += a.psi_hi[i] * fsv[i];
+                dE = m[3] - me;
+            }
             const R eta2 = a.eta2;
             static_for<0, 12>([&](auto J) {
                 constexpr int j = decltype(J)::value;
@@ -404,6 +412,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
                     constexpr int j = decltype(J)::value;
                     if (!minv_zero(i, j)) ne += a.minv[i * 16 + 4 + j] * dm[j];
                 });
+                if (iso) ne += a.minv[i * 16 + 3] * dE;
                 fe = fsv[i] + ne;
             } else {
                 fe = 0;
@@ -435,6 +444,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         }
         R nr, nux, nuy, nT;
         acc.finish(b, nr, nux, nuy, nT);
+        if (iso) nT = a.T_iso;
         mn[M_RHO * NX] = nr;
         mn[M_UX * NX] = nux;
         mn[M_UY * NX] = nuy;

@@ -197,7 +197,9 @@ template <typename R> ColArgs<R> col_args(const lbm_ctx *c, int nb) {
     return a;
 }
 
-// one Runge-Kutta stage of all instances: K_COL, K_MACRO, K_FLUX, K_UPDATE
+// One stage of all instances: K_COL, K_MACRO, K_FLUX, K_UPDATE. stage 0 / 1: the two
+// Runge-Kutta stages (f^{n+1/2} = f^n + dt/2 R(f^n) into f1; f^{n+1} = f^n + dt R(f^{n+1/2})
+// into f0); stage 2: a forward Euler step f^{n+1} = f^n + dt R(f^n) in place in f0.
 template <typename R>
 int run_stage(lbm_ctx *c, int stage) {
     const lbm_params &p = c->p;
@@ -206,7 +208,7 @@ int run_stage(lbm_ctx *c, int stage) {
     const int nx = c->nx, rows = c->nb * c->ny;
     R *f0 = static_cast<R *>(c->f0), *f1 = static_cast<R *>(c->f1);
     R *Ay = static_cast<R *>(c->Ay), *m = static_cast<R *>(c->m);
-    const R *fs = stage == 0 ? f0 : f1;
+    const R *fs = stage == 1 ? f1 : f0;
     const int ldf = NF_F * nx, lda = NF_A * nx, ldm = NF_M * nx;
     auto M = [m, nx](int k) { return m + (size_t)k * nx; };  // first row of macro field k
 
@@ -254,7 +256,7 @@ int run_stage(lbm_ctx *c, int stage) {
         UpdateArgs<R> a{};
         a.fs = fs;
         a.fbase = f0;
-        a.fout = stage == 0 ? f1 : f0;
+        a.fout = stage == 0 ? f1 : f0;  // stage 2 (Euler): in place, same node, same thread
         a.Ay = Ay;
         a.m = m;
         a.nx = nx; a.ny = rows; a.rows = c->geo.rows_upd;
@@ -262,6 +264,7 @@ int run_stage(lbm_ctx *c, int stage) {
         a.ax = axis<R>(c, true);
         a.tau_inv = (R)(1.0 / p.tau);
         a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
+        a.T_iso = (R)p.T_iso;
         a.K = (R)p.K;
         a.b = (R)p.b;
         a.eta2 = (R)(p.eta0 * p.eta0);
@@ -279,6 +282,7 @@ int run_stage(lbm_ctx *c, int stage) {
 }
 
 int run_step_launches(lbm_ctx *c) {
+    if (c->p.flags & LBM_FLAG_EULER) return c->mixed ? run_stage<float>(c, 2) : run_stage<double>(c, 2);
     for (int st = 0; st < 2; ++st) {
         int rc = c->mixed ? run_stage<float>(c, st) : run_stage<double>(c, st);
         if (rc) return rc;
@@ -323,8 +327,12 @@ int check_params(const lbm_params *p) {
     if (p->win_alpha < 0 || p->win_p <= 0) return fail(LBM_ERR_ARG, "need win_alpha >= 0 and win_p > 0");
     if (p->precision != LBM_FP64 && p->precision != LBM_MIXED)
         return fail(LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_MIXED");
-    if (p->flags & ~(LBM_FLAG_NO_ADVECTION | LBM_FLAG_NO_COLLISION | LBM_FLAG_NO_FORCE))
+    if (p->flags & ~(LBM_FLAG_NO_ADVECTION | LBM_FLAG_NO_COLLISION | LBM_FLAG_NO_FORCE | LBM_FLAG_EULER |
+                     LBM_FLAG_ISOTHERMAL))
         return fail(LBM_ERR_ARG, "unknown flag bits");
+    if (p->keff_terms < 1 || p->keff_terms > 8) return fail(LBM_ERR_ARG, "keff_terms must be in [1, 8]");
+    if ((p->flags & LBM_FLAG_ISOTHERMAL) && !(std::isfinite(p->T_iso) && p->T_iso > 0))
+        return fail(LBM_ERR_ARG, "LBM_FLAG_ISOTHERMAL needs a finite T_iso > 0");
     return LBM_OK;
 }
 
@@ -429,7 +437,7 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
         const double d = ax == 0 ? params->dx : params->dy;
         std::vector<double> k1(N), k2(N);
         std::vector<float> k1f(N), k2f(N);
-        derivative_tables(N, d, params->win_alpha, params->win_p, k1.data(), k2.data());
+        derivative_tables(N, d, params->win_alpha, params->win_p, k1.data(), k2.data(), params->keff_terms);
         for (int pos = 0; pos < N; ++pos) {
             k1f[pos] = (float)k1[pos];
             k2f[pos] = (float)k2[pos];
@@ -460,6 +468,7 @@ int init_instance(lbm_ctx *c, int k, const double *rho, const double *ux, const 
     a.nx = c->nx;
     a.ny = c->ny;
     a.b = c->p.b;
+    a.T_iso = (c->p.flags & LBM_FLAG_ISOTHERMAL) ? c->p.T_iso : 0.0;
     for (int j = 0; j < 256; ++j) a.minv[j] = c->minv[j];
     for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
     CU_TRY(c->mixed ? launch_init<float>(a, c->stream) : launch_init<double>(a, c->stream));
@@ -563,6 +572,7 @@ int set_f_host(lbm_ctx *c, int k, const double *f16) {
     a.nx = c->nx;
     a.ny = c->ny;
     a.b = c->p.b;
+    a.T_iso = (c->p.flags & LBM_FLAG_ISOTHERMAL) ? c->p.T_iso : 0.0;
     for (int i = 0; i < 16; ++i) a.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
     CU_TRY(c->mixed ? launch_moments<float>(a, c->stream) : launch_moments<double>(a, c->stream));
     c->initialized[k] = 1;
@@ -644,6 +654,9 @@ void lbm_default_params(lbm_params *p) {
     p->win_p = 36.0;
     p->precision = LBM_FP64;
     p->flags = 0;
+    p->T_iso = 0.0;
+    p->keff_terms = 8;
+    p->reserved = 0;
 }
 
 const char *lbm_strerror(int code) {
@@ -965,7 +978,7 @@ static int freq_at(int p, int n, int radix_first) {
     return p / S + r * freq_at(p % S, S, next);
 }
 
-void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2) {
+void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2, int terms) {
     static const double c[8] = {1.0, 1.0 / 6.0, 3.0 / 40.0, 5.0 / 112.0, 35.0 / 1152.0,
                                 63.0 / 2816.0, 231.0 / 13312.0, 143.0 / 10240.0};
     int l2 = 0;
@@ -977,10 +990,10 @@ void derivative_tables(int N, double d, double win_alpha, double win_p, double *
         const int m = k < N / 2 ? k : k - N;
         double ke = 0.0;
         if (2 * m != -N) {
-            // Eq. (3): k_eff = (2/d) sum_{n=0}^{7} c_n phi^(2n+1), phi = sin(pi m / N)
+            // Eq. (3): k_eff = (2/d) sum_{n=0}^{terms-1} c_n phi^(2n+1), phi = sin(pi m / N)
             const double phi = std::sin(M_PI * (double)m / (double)N);
             double s = 0.0, pw = phi;
-            for (int n = 0; n < 8; ++n) {
+            for (int n = 0; n < terms; ++n) {
                 s += c[n] * pw;
                 pw *= phi * phi;
             }

@@ -88,7 +88,7 @@ template <typename R, int LOG2N> struct MacroThreads {
 // Derivative multiplier tables of one axis in the digit-reversed order left by the forward
 // transforms: k1[p] = W(m) k_eff(m) / N and k2[p] = -(W(m) k_eff(m))^2 / N for the DFT index m
 // held at position p (zero at the Nyquist index). Eq. (3) and the window W (lbm_api.cu).
-void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2);
+void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2, int terms = 8);
 
 // Launch geometry of the four passes for an nx x ny grid and an element size (lbm_api.cu):
 // column tile width and shared memory, rows per CTA and shared memory of the row kernels.
@@ -164,6 +164,7 @@ template <typename R> struct UpdateArgs {
     int raw;              // keep the transformed rows of f in shared memory for the node loop
     Axis<R> ax;
     R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
+    R T_iso;                   // LBM_FLAG_ISOTHERMAL: T at every node
     R psi_hi[16], psi_lo[16];  // psi_i = |v_i|^2 + eta_i^2 as a two-term sum (hi + lo)
     int flags;
     R minv[256];  // inverse of the 16x16 moment matrix, row-major
@@ -175,6 +176,7 @@ struct InitArgs {
     void *m;                          // macroscopic block: the moments of the stored f (R)
     int nx, ny;
     double b;
+    double T_iso;  // > 0: isothermal (T_iso replaces the input T)
     double minv[256];
     double psi[16];
 };
@@ -185,6 +187,7 @@ struct MomArgs {
     int nx, ny;
     double psi[16];
     double b;
+    double T_iso;  // > 0: isothermal (stored as the temperature field)
 };
 
 // rho, u, T, d_x rho, d_y rho: row y of each at p + y * ld

@@ -1,0 +1,40 @@
+"""Liquid-vapour coexistence with the parameters of Sec. 3.1 (512 x 2 box, dx = 0.02,
+dt = 5e-5, K = 1e-5, q = -0.004): the bulk densities of flat vapour | liquid | vapour states
+stay at the Maxwell construction of the van der Waals fluid (lbm_maxwell, itself checked
+against the oracle's equal-area construction) across the temperature range the paper
+reports (down to T = 0.8), and the stepwise protocol (lower T, continue from the current
+profile) runs and stays finite."""
+import numpy as np
+import pytest
+
+import paper_1403_3746_gb300 as lbm
+from paper_1403_3746_gb300 import build as lbm_build
+from paper_1403_3746_gb300 import coexistence as cx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lbm_build.build()
+
+
+def test_coexistence_densities_match_maxwell():
+    rows = cx.coexistence_parallel([0.95, 0.9, 0.85, 0.8], steps=100000)
+    for r in rows:
+        print(r)
+        assert r["rel_l"] < 2e-3 and r["rel_v"] < 5e-3, r
+
+
+def test_stepwise_protocol_runs():
+    ml, mv = lbm.maxwell(0.95)
+    start = cx.initial_profile(rho_v=mv, rho_l=ml, T=0.95)
+    rows = cx.coexistence_curve([0.95, 0.93], start=start, check_every=5000, tol=1e-5, min_steps=20000,
+                                max_steps=60000)
+    for r in rows:
+        print(r)
+        assert r["finite"]
+    r0 = rows[0]
+    assert abs(r0["rho_l"] / r0["maxwell_rho_l"] - 1) < 2e-3 and abs(r0["rho_v"] / r0["maxwell_rho_v"] - 1) < 5e-3
+    # after lowering T the phases move apart, towards the new Maxwell pair
+    assert rows[1]["rho_l"] > r0["rho_l"] and rows[1]["rho_v"] < r0["rho_v"]

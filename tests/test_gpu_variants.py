@@ -1,0 +1,97 @@
+"""GPU parity of the numerical variants and the isothermal mode against the FP64 oracle:
+forward Euler (LBM_FLAG_EULER), the 8th-order modified wavenumber (keff_terms = 4) - the
+numerics of the D2V33 runs of Sec. 3.2 - and the thermostat T = T_iso (LBM_FLAG_ISOTHERMAL).
+Same per-field metric and 1e-10 bound as tests/test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from oracle.dvm import D2V16
+from oracle.model import init_feq, rk2_step
+
+import paper_1403_3746_gb300 as lbm
+from paper_1403_3746_gb300 import build as lbm_build
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-10
+PHASE = dict(tau=1e-4, dt=1e-4, dx=1 / 256, dy=1 / 256, K=5e-6, q=-0.004, b=2.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lbm_build.build()
+
+
+def oracle_params(flags=0, T_iso=0.0, keff_terms=8, **kw):
+    return oracle.Params(scheme="euler" if flags & lbm.LBM_FLAG_EULER else "rk2",
+                         T_iso=T_iso if flags & lbm.LBM_FLAG_ISOTHERMAL else 0.0,
+                         keff_terms=keff_terms, **kw)
+
+
+def run_both(fields, steps, precision=lbm.LBM_FP64, **kw):
+    p = oracle_params(**kw)
+    d = D2V16(p.eta0)
+    f = init_feq(d, *fields, p)
+    for _ in range(steps):
+        f = rk2_step(d, f, p)
+    ny, nx = fields[0].shape
+    with lbm.Simulation(nx, ny, lbm.default_params(precision=precision, **kw)) as s:
+        s.init(*fields)
+        s.step(steps)
+        fg, mg = s.get_f(), s.moments()
+    return fg, mg, f, oracle.moments(d, f, p.b)
+
+
+def errors(fg, mg, fo, mo):
+    floor = 1e-2 * np.max(np.abs(fo))
+    ef = max(float(np.max(np.abs(fg[i] - fo[i])) / max(np.max(np.abs(fo[i])), floor)) for i in range(16))
+    em = [float(np.max(np.abs(mg[k] - mo[k])) / max(np.max(np.abs(mo[k])), 1e-3 if k in (1, 2) else 0.0))
+          for k in range(4)]
+    return ef, em
+
+
+def slab(nx=64, ny=64, T=0.9, seed=1):
+    rl, rv = oracle.coexistence(T)
+    return synthetic.slab(nx, ny, rl, rv, T, center=nx / 2, half_width=nx / 4, width=2.0, noise=1e-4, seed=seed)
+
+
+@pytest.mark.parametrize("flags,terms,steps", [(lbm.LBM_FLAG_EULER, 8, 40), (0, 4, 40),
+                                               (lbm.LBM_FLAG_EULER, 4, 40)])
+def test_numerical_variants_fp64(flags, terms, steps):
+    kw = dict(PHASE, flags=flags, keff_terms=terms)
+    if flags & lbm.LBM_FLAG_EULER:
+        kw["dt"] = 1e-5  # the Euler runs of Sec. 3.2 take dt = 1e-5
+    fg, mg, fo, mo = run_both(slab(), steps, **kw)
+    ef, em = errors(fg, mg, fo, mo)
+    print(f"flags={flags} terms={terms}: f {ef:.2e}, moments {em}")
+    assert ef <= TOL64 and max(em) <= TOL64
+
+
+def test_isothermal_fp64_slab_and_relaxation():
+    # a slab at T = 0.9 held by the thermostat, and a spinodal state at T = 0.95 relaxing to 0.9
+    for fields in (slab(), synthetic.spinodal(64, 32, 1.0, 0.02, 0.95, seed=11)):
+        fg, mg, fo, mo = run_both(fields, 30, flags=lbm.LBM_FLAG_ISOTHERMAL, T_iso=0.9, **PHASE)
+        ef, em = errors(fg, mg, fo, mo)
+        print(f"isothermal: f {ef:.2e}, moments {em}")
+        assert ef <= TOL64 and max(em[:3]) <= TOL64
+        assert np.all(mg[3] == 0.9)  # the stored temperature field is the thermostat's
+
+
+def test_isothermal_mixed_tracks_fp64():
+    fields = synthetic.spinodal(128, 64, 1.0, 0.02, 0.95, seed=12)
+    out = {}
+    for prec in (lbm.LBM_FP64, lbm.LBM_MIXED):
+        with lbm.Simulation(128, 64, lbm.default_params(precision=prec, flags=lbm.LBM_FLAG_ISOTHERMAL,
+                                                        T_iso=0.9, **PHASE)) as s:
+            s.init(*fields)
+            d0 = s.diagnostics()
+            s.step(200)
+            out[prec] = (s.get_f(), s.moments(), d0, s.diagnostics())
+    f64, m64, _, _ = out[lbm.LBM_FP64]
+    f32, m32, d0, d1 = out[lbm.LBM_MIXED]
+    rel = float(np.linalg.norm(f32 - f64) / np.linalg.norm(f64))
+    drho = float(np.max(np.abs(m32[0] - m64[0])) / np.max(np.abs(m64[0])))
+    print(f"isothermal mixed vs FP64: f {rel:.2e}, rho {drho:.2e}, mass drift {(d1['mass'] - d0['mass']) / d0['mass']:.2e}")
+    assert rel <= 2e-6 and drho <= 2e-6
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-6 * d0["mass"]

@@ -85,3 +85,19 @@ def test_batch_create_rejects_bad_sizes_before_touching_the_device(L, sizes):
     assert L.lbm_batch_create(len(sizes), nx, ny, ctypes.byref(p), None, ctypes.byref(h)) == -1
     assert not h.value
     assert L.lbm_batch_count(None) == 0
+
+
+@pytest.mark.parametrize("kw", [dict(keff_terms=0), dict(keff_terms=9), dict(flags=16),
+                                dict(flags=16, T_iso=-1.0), dict(flags=16, T_iso=float("inf")),
+                                dict(flags=32)])
+def test_create_rejects_bad_variant_params(L, kw):
+    p = lbm.default_params(**kw)
+    h = ctypes.c_void_p()
+    assert L.lbm_create(16, 16, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert not h.value
+
+
+def test_variant_defaults(L):
+    p = lbm.default_params()
+    assert p.keff_terms == 8 and p.T_iso == 0.0 and p.reserved == 0
+    assert ctypes.sizeof(lbm.lbm_params) == 12 * 8 + 2 * 4 + 8 + 2 * 4
