@@ -148,6 +148,18 @@ int lbm_timing_read(lbm_handle h, int kernel, double *ms, long long *launches);
 /* Device bytes held by the handle. */
 size_t lbm_device_bytes(lbm_handle h);
 
+/* Launch shapes (no counterpart in the paper: a performance service). geometry[0]: width in
+ * columns of the column-pass tiles; geometry[1], geometry[2]: rows per CTA of the macro and
+ * update row passes. lbm_autotune times every legal candidate of each (column tiles with at
+ * most 100 KB of line buffers; row CTAs of at most 4096 nodes and 200 KB) on the handle's own
+ * buffers with the passes of a Runge-Kutta stage, keeps the fastest, and reports the chosen
+ * shapes and their measured times (ms per pass; either pointer may be NULL). The state is
+ * unchanged (the moment fields the update pass rewrites are saved and restored) and results
+ * do not depend on the shapes. Needs an initialised state; allocates a temporary device
+ * buffer of 4 fields; synchronises the stream. */
+int lbm_geometry(lbm_handle h, int geometry[3]);
+int lbm_autotune(lbm_handle h, int geometry[3], double ms[3]);
+
 /* lbm_diagnostics for callers that cannot allocate device memory. The paper has no
  * counterpart: this is a library service. Examples: code running while a stream is being
  * captured into a CUDA graph (cudaMalloc is not permitted during capture), host applications
@@ -205,6 +217,11 @@ int lbm_batch_step(lbm_batch b, int n);
 int lbm_batch_moments(lbm_batch b, int k, double *rho, double *ux, double *uy, double *T);
 int lbm_batch_get_f(lbm_batch b, int k, double *f16);
 int lbm_batch_diagnostics(lbm_batch b, int k, double out[6]);
+
+/* lbm_autotune for every size group of the batch (all instances initialised); the launch
+ * shapes of instance k's group via lbm_batch_geometry. */
+int lbm_batch_autotune(lbm_batch b);
+int lbm_batch_geometry(lbm_batch b, int k, int geometry[3]);
 
 /* Frees all device memory of the batch (synchronises first). NULL is ignored. */
 void lbm_batch_destroy(lbm_batch b);

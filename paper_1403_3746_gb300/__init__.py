@@ -74,6 +74,10 @@ _SIGS = {
     "lbm_batch_get_f": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lbm_batch_diagnostics": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "lbm_batch_destroy": (None, [_P]),
+    "lbm_geometry": (ctypes.c_int, [_P, _P]),
+    "lbm_autotune": (ctypes.c_int, [_P, _P, _P]),
+    "lbm_batch_autotune": (ctypes.c_int, [_P]),
+    "lbm_batch_geometry": (ctypes.c_int, [_P, ctypes.c_int, _P]),
 }
 
 
@@ -233,6 +237,20 @@ class Simulation:
     def device_bytes(self):
         return int(lib().lbm_device_bytes(self._h))
 
+    def geometry(self):
+        """(column tile width, rows per CTA of the macro pass, rows per CTA of the update pass)."""
+        g = (ctypes.c_int * 3)()
+        _check(lib().lbm_geometry(self._h, ctypes.cast(g, _P)))
+        return tuple(g)
+
+    def autotune(self):
+        """Times the launch-shape candidates on this simulation and keeps the fastest;
+        returns (geometry, ms per pass)."""
+        g = (ctypes.c_int * 3)()
+        ms = (ctypes.c_double * 3)()
+        _check(lib().lbm_autotune(self._h, ctypes.cast(g, _P), ctypes.cast(ms, _P)))
+        return tuple(g), tuple(ms)
+
 
 class Batch:
     """Independent simulations advanced together (lbm_batch_create .. lbm_batch_destroy).
@@ -295,3 +313,11 @@ class Batch:
         out = (ctypes.c_double * 6)()
         _check(lib().lbm_batch_diagnostics(self._h, int(k), out))
         return dict(zip(("mass", "px", "py", "energy", "umax", "steps"), list(out)))
+
+    def autotune(self):
+        _check(lib().lbm_batch_autotune(self._h))
+
+    def geometry(self, k):
+        g = (ctypes.c_int * 3)()
+        _check(lib().lbm_batch_geometry(self._h, int(k), ctypes.cast(g, _P)))
+        return tuple(g)

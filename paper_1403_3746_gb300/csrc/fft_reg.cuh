@@ -145,8 +145,14 @@ template <typename R, bool INV, int RADIX, bool PK> __device__ __forceinline__ v
     if (RADIX == 8) dft8<R, INV, PK>(v);
 }
 
+// CTA-wide barrier in its non-aligned form (PTX barrier.sync without .aligned): threads of one
+// warp may reach it from different branches. Kernels give their threads different roles (a
+// thread transforms a line, or only keeps the barrier count while others do), and the split
+// between roles need not fall on a warp boundary; the aligned form (__syncthreads) would be
+// undefined there. Same memory ordering among the CTA's threads as __syncthreads.
+__device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;" ::: "memory"); }
 struct SyncCta {
-    static __device__ __forceinline__ void run() { __syncthreads(); }
+    static __device__ __forceinline__ void run() { cta_barrier(); }
 };
 struct SyncWarp {
     static __device__ __forceinline__ void run() { __syncwarp(); }

@@ -291,9 +291,6 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
     const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
     const bool same_base = a.fbase == a.fs;
     const bool iso = a.flags & LBM_FLAG_ISOTHERMAL;
-    // raw rows of the 12 transformed fields (slot k = xslot(i)), [12][NR NX], when a.raw
-    R *sraw = reinterpret_cast<R *>(sb + (size_t)6 * NR * SM);
-    const bool raw = a.raw && adv;
 
     // the node loop's other inputs start moving into L2 while the lines are transformed
     if (threadIdx.x < NR) {
@@ -320,24 +317,16 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
                 CT v[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(ldcg(fa + t + G * e), ldcg(fb + t + G * e));
-                if (raw) {
-                    R *ra = sraw + (size_t)(2 * p) * nodes + r * NX, *rb = ra + nodes;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        ra[t + G * e] = v[e].x;
-                        rb[t + G * e] = v[e].y;
-                    }
-                }
                 F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
                 F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
                 F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
-                __syncthreads();
+                reg::cta_barrier();
 #pragma unroll
                 for (int e = 0; e < E; ++e) buf[t + G * e] = v[e];
             } else {
                 F::template idle<reg::SyncCta>();
                 F::template idle<reg::SyncCta>();
-                __syncthreads();
+                reg::cta_barrier();
             }
         }
         __syncthreads();
@@ -380,7 +369,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         R fsv[16], dm[12], dE = 0;
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-            fsv[i] = (raw && xslot(i) >= 0) ? sraw[(size_t)xslot(i) * nodes + idx] : ldcg(fn + i * NX);
+            fsv[i] = ldcg(fn + i * NX);
         if (MOMENT_SPACE) {
             // isothermal: the energy moment (row 3) is not conserved by the thermostat either
             if (iso) {

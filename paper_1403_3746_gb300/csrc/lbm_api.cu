@@ -200,8 +200,11 @@ template <typename R> ColArgs<R> col_args(const lbm_ctx *c, int nb) {
 // One stage of all instances: K_COL, K_MACRO, K_FLUX, K_UPDATE. stage 0 / 1: the two
 // Runge-Kutta stages (f^{n+1/2} = f^n + dt/2 R(f^n) into f1; f^{n+1} = f^n + dt R(f^{n+1/2})
 // into f0); stage 2: a forward Euler step f^{n+1} = f^n + dt R(f^n) in place in f0.
+// pass selection for run_stage (all by default; the autotuner times them one at a time)
+enum { PASS_COL = 1, PASS_MACRO = 2, PASS_FLUX = 4, PASS_UPDATE = 8, PASS_ALL = 15 };
+
 template <typename R>
-int run_stage(lbm_ctx *c, int stage) {
+int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
     const lbm_params &p = c->p;
     const bool adv = !(p.flags & LBM_FLAG_NO_ADVECTION);
     const bool frc = !(p.flags & LBM_FLAG_NO_FORCE);
@@ -227,12 +230,12 @@ int run_stage(lbm_ctx *c, int stage) {
             a.jobs[nj++] = ColJob<R>{M(M_UY), M(M_UYY), ldm, ldm, 1, R(1)};
             a.jobs[nj++] = ColJob<R>{M(M_T), M(M_TY), ldm, ldm, 1, R(1)};
         }
-        if (nj) {
+        if (nj && (passes & PASS_COL)) {
             LaunchTimer t(c, LBM_K_COL);
             CU_TRY(launch_col<R>(a, nj, c->geo.col_smem, c->stream));
         }
     }
-    if (frc) {
+    if (frc && (passes & PASS_MACRO)) {
         {
             MacroArgs<R> a{};
             a.m = m;
@@ -242,6 +245,8 @@ int run_stage(lbm_ctx *c, int stage) {
             LaunchTimer t(c, LBM_K_MACRO);
             CU_TRY(launch_macro<R>(a, c->geo.macro_smem, c->stream));
         }
+    }
+    if (frc && (passes & PASS_FLUX)) {
         {
             ColArgs<R> a = col_args<R>(c, c->nb);
             a.jobs[0] = ColJob<R>{M(M_QY), M(M_DQY), ldm, ldm, 1, R(1)};
@@ -252,7 +257,7 @@ int run_stage(lbm_ctx *c, int stage) {
             CU_TRY(launch_col<R>(a, 4, c->geo.col_smem, c->stream));
         }
     }
-    {
+    if (passes & PASS_UPDATE) {
         UpdateArgs<R> a{};
         a.fs = fs;
         a.fbase = f0;
@@ -260,7 +265,6 @@ int run_stage(lbm_ctx *c, int stage) {
         a.Ay = Ay;
         a.m = m;
         a.nx = nx; a.ny = rows; a.rows = c->geo.rows_upd;
-        a.raw = c->geo.upd_raw ? 1 : 0;
         a.ax = axis<R>(c, true);
         a.tau_inv = (R)(1.0 / p.tau);
         a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
@@ -314,6 +318,147 @@ int build_step_graph(lbm_ctx *c) {
     cudaGraphDestroy(g);
     CU_TRY(ei);
     return LBM_OK;
+}
+
+// ---- autotuner: tile and CTA shapes by measurement ------------------------------------
+
+// Candidate column tile widths: W columns (W/2 complex lines of G threads) with at most
+// pass_threads threads and 100 KB of line buffers.
+std::vector<int> col_candidates(const lbm_ctx *c) {
+    std::vector<int> out;
+    const size_t cs = 2 * c->fsize;
+    for (int W = 2; W <= c->nx && W * (int)c->fsize <= 256; W *= 2)
+        if ((W / 2) * line_G(c->ly) <= pass_threads(c->fsize) && (size_t)(W / 2) * line_smem(c->ly) * cs <= 100 * 1024)
+            out.push_back(W);
+    return out;
+}
+// Candidate rows per CTA of the update pass (6 line buffers per row, at most 200 KB).
+std::vector<int> upd_candidates(const lbm_ctx *c) {
+    std::vector<int> out;
+    const size_t SM = (size_t)line_smem(c->lx) * 2 * c->fsize;
+    for (int r = 1; r <= c->ny && r * c->nx <= 4096; r *= 2)
+        if (6 * r * SM <= 200 * 1024) out.push_back(r);
+    return out;
+}
+// Candidate rows per CTA of the macro pass (two lines per row within its thread bound).
+std::vector<int> macro_candidates(const lbm_ctx *c) {
+    std::vector<int> out;
+    const size_t SM = (size_t)line_smem(c->lx) * 2 * c->fsize;
+    for (int r = 1; r <= c->ny && r * c->nx <= 4096; r *= 2)
+        if (2 * r * line_G(c->lx) <= macro_threads(c->fsize, c->lx) &&
+            3 * r * SM + (size_t)r * c->nx * c->fsize <= 200 * 1024)
+            out.push_back(r);
+    return out;
+}
+
+template <typename R> int run_stage(lbm_ctx *c, int stage, int passes);
+
+// Times `passes` of Runge-Kutta stage 1 on the current buffers: one untimed launch, then the
+// mean of three.
+template <typename R> int time_passes(lbm_ctx *c, int passes, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+    int rc = run_stage<R>(c, 0, passes);
+    if (rc) return rc;
+    CU_TRY(cudaEventRecord(e0, c->stream));
+    for (int k = 0; k < 3 && rc == LBM_OK; ++k) rc = run_stage<R>(c, 0, passes);
+    if (rc) return rc;
+    CU_TRY(cudaEventRecord(e1, c->stream));
+    CU_TRY(cudaEventSynchronize(e1));
+    CU_TRY(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= 3.0f;
+    return LBM_OK;
+}
+
+// Chooses the column tile width and the rows per CTA of the macro and update passes by timing
+// every candidate on the context's own buffers. The passes of stage 1 read f^n and the
+// moments and write scratch (f^{n+1/2}, Ay, the derivative fields), except that the update
+// pass overwrites the moment fields: those are saved first and restored at the end, so the
+// state is unchanged. Per-row and per-column work does not depend on these shapes, so results
+// stay bit for bit the same.
+template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[3]) {
+    const bool timing = c->timing;
+    c->timing = false;
+    const size_t es = c->fsize, rows = (size_t)c->nb * c->ny;
+    void *save = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LBM_OK;
+    auto done = [&](int code) {
+        if (save) cudaFree(save);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        c->timing = timing;
+        return code;
+    };
+    if (cudaMalloc(&save, 4 * c->nx * es * rows) != cudaSuccess) {
+        cudaGetLastError();
+        return done(fail(LBM_ERR_NOMEM, "autotune: no scratch for the moment fields"));
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return done(fail(LBM_ERR_CUDA, "autotune: cudaEventCreate failed"));
+    // moment fields M_RHO..M_T: 4 nx contiguous elements per row of the macroscopic block
+    if (cudaMemcpy2DAsync(save, 4 * c->nx * es, c->m, NF_M * c->nx * es, 4 * c->nx * es, rows,
+                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return done(fail(LBM_ERR_CUDA, "autotune: saving the moments failed"));
+    if ((rc = run_stage<R>(c, 0, PASS_ALL))) return done(rc);
+
+    const bool frc = !(c->p.flags & LBM_FLAG_NO_FORCE);
+    float t = 0;
+    // column tile width (column and flux passes)
+    {
+        int bestW = c->geo.colW;
+        float bt = 1e30f;
+        for (int W : col_candidates(c)) {
+            c->geo.colW = W;
+            c->geo.col_smem = (size_t)(W / 2) * line_smem(c->ly) * 2 * es;
+            if ((rc = time_passes<R>(c, PASS_COL | PASS_FLUX, e0, e1, &t))) return done(rc);
+            if (t < bt) bt = t, bestW = W;
+        }
+        c->geo.colW = bestW;
+        c->geo.col_smem = (size_t)(bestW / 2) * line_smem(c->ly) * 2 * es;
+        best_ms[0] = bt;
+    }
+    const size_t SM = (size_t)line_smem(c->lx) * 2 * es;
+    best_ms[1] = 0;
+    if (frc) {
+        int bestr = c->geo.rows_macro;
+        float bt = 1e30f;
+        for (int r : macro_candidates(c)) {
+            c->geo.rows_macro = r;
+            c->geo.macro_smem = 3 * r * SM + (size_t)r * c->nx * es;
+            if ((rc = time_passes<R>(c, PASS_MACRO, e0, e1, &t))) return done(rc);
+            if (t < bt) bt = t, bestr = r;
+        }
+        c->geo.rows_macro = bestr;
+        c->geo.macro_smem = 3 * bestr * SM + (size_t)bestr * c->nx * es;
+        best_ms[1] = bt;
+    }
+    {
+        int bestr = c->geo.rows_upd;
+        float bt = 1e30f;
+        for (int r : upd_candidates(c)) {
+            c->geo.rows_upd = r;
+            c->geo.upd_smem = 6 * r * SM;
+            if ((rc = time_passes<R>(c, PASS_UPDATE, e0, e1, &t))) return done(rc);
+            if (t < bt) bt = t, bestr = r;
+        }
+        c->geo.rows_upd = bestr;
+        c->geo.upd_smem = 6 * bestr * SM;
+        best_ms[2] = bt;
+    }
+    if (cudaMemcpy2DAsync(c->m, NF_M * c->nx * es, save, 4 * c->nx * es, 4 * c->nx * es, rows,
+                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return done(fail(LBM_ERR_CUDA, "autotune: restoring the moments failed"));
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return done(fail(LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError())));
+    if (c->graph) {  // recaptured with the new shapes at the next step
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return done(LBM_OK);
+}
+
+int autotune_ctx(lbm_ctx *c, float best_ms[3]) {
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "autotune needs an initialised state");
+    return c->mixed ? autotune_impl<float>(c, best_ms) : autotune_impl<double>(c, best_ms);
 }
 
 int check_params(const lbm_params *p) {
@@ -778,6 +923,24 @@ int lbm_timing_read(lbm_handle c, int kernel, double *ms, long long *launches) {
 
 size_t lbm_device_bytes(lbm_handle c) { return c ? c->slab_bytes : 0; }
 
+int lbm_geometry(lbm_handle c, int geometry[3]) {
+    if (!c || !geometry) return fail(LBM_ERR_ARG, "NULL argument");
+    geometry[0] = c->geo.colW;
+    geometry[1] = c->geo.rows_macro;
+    geometry[2] = c->geo.rows_upd;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle c, int geometry[3], double ms[3]) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    float t[3] = {0, 0, 0};
+    const int rc = autotune_ctx(c, t);
+    if (rc) return rc;
+    if (ms)
+        for (int k = 0; k < 3; ++k) ms[k] = t[k];
+    return geometry ? lbm_geometry(c, geometry) : LBM_OK;
+}
+
 // Maxwell construction (Sec. 3.1) in chemical-potential form: equal pressure and equal
 // mu(rho) = T ln(rho/(3 - rho)) + 3T/(3 - rho) - 9 rho/4 on the two outer branches of the
 // van der Waals isotherm, by nested bisection on the saturation pressure.
@@ -877,6 +1040,26 @@ void lbm_batch_destroy(lbm_batch b) {
 }
 
 int lbm_batch_count(lbm_batch b) { return b ? (int)b->where.size() : 0; }
+
+int lbm_batch_autotune(lbm_batch b) {
+    if (!b) return fail(LBM_ERR_ARG, "NULL batch");
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    for (lbm_ctx *c : b->groups) {
+        float t[3];
+        const int rc = autotune_ctx(c, t);
+        if (rc) return rc;
+    }
+    if (b->graph) {  // recaptured with the new shapes at the next step
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_geometry(lbm_batch b, int k, int geometry[3]) {
+    if (!b || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
+    return lbm_geometry(b->groups[b->where[k].first], geometry);
+}
 
 int lbm_batch_init(lbm_batch b, int k, const double *rho, const double *ux, const double *uy, const double *T) {
     if (!b || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
@@ -1029,11 +1212,7 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     int r = r0;
     while (r > 1 && 6 * r * SM > 200 * 1024) r >>= 1;  // update: 6 line buffers per row
     g->rows_upd = r;
-    // the raw rows of the 12 transformed fields are kept when the CTA still fits twice per SM
-    // (float32) or once (float64, register-limited to one CTA anyway)
-    const size_t raw_bytes = 12 * (size_t)r * nx * esize;
-    g->upd_raw = 6 * (size_t)r * SM + raw_bytes <= (esize == 4 ? 110u : 200u) * 1024;
-    g->upd_smem = 6 * (size_t)r * SM + (g->upd_raw ? raw_bytes : 0);
+    g->upd_smem = 6 * (size_t)r * SM;
     r = r0;
     // macro: 2 lines per row with 3 buffers, plus 1 value per node
     auto macro_bytes = [&](int rr) { return 3 * (size_t)rr * SM + (size_t)rr * nx * esize; };

@@ -97,7 +97,6 @@ struct Geometry {
     size_t col_smem = 0;
     int rows_upd = 1, rows_macro = 1, rows_rowd = 1;
     size_t upd_smem = 0, macro_smem = 0, rowd_smem = 0;
-    bool upd_raw = false;  // update pass keeps the 12 transformed rows of f in shared memory
 };
 void pass_geometry(int nx, int ny, size_t esize, Geometry *g);
 
@@ -161,7 +160,6 @@ template <typename R> struct UpdateArgs {
     R *m;            // macroscopic block; moments of fs in, moments of fout out
     int nx, ny, rows;
     int lines_per_batch;  // line transforms in flight per batch (the other threads wait)
-    int raw;              // keep the transformed rows of f in shared memory for the node loop
     Axis<R> ax;
     R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
     R T_iso;                   // LBM_FLAG_ISOTHERMAL: T at every node
