@@ -148,6 +148,7 @@ def time_path(lbm, torch, precision, steps, warmup, fields, stream):
 
     with lbm.Simulation(N_GRID, N_GRID, p, stream=stream.cuda_stream) as sim:
         sim.init(*fields)
+        geometry, _ = sim.autotune()  # launch shapes by measurement, before any timed step
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 sim.step(1)
@@ -159,7 +160,7 @@ def time_path(lbm, torch, precision, steps, warmup, fields, stream):
         kern = {k: sim.timing_read(k) for k in ELEMS_PER_NODE}
         sim.timing(False)
         diag = sim.diagnostics()
-    return step_ms, kern, wall, diag, step_ms_b
+    return step_ms, kern, wall, diag, step_ms_b, geometry
 
 
 def e2e_path(lbm, torch, precision, steps, fields):
@@ -203,6 +204,8 @@ def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream):
     with lbm.Batch([(n, n) for n in BATCH_SIZES], p, stream=stream.cuda_stream) as b:
         for k, n in enumerate(BATCH_SIZES):
             b.init(k, *synthetic.spinodal(n, n, 1.0, 0.01, float(temps[k]), seed=4000 + k))
+        b.autotune()  # launch shapes per size group, by measurement
+        shapes = {f"{n}x{n}": list(b.geometry(BATCH_SIZES.index(n))) for n in sorted(set(BATCH_SIZES))}
         with torch.cuda.stream(stream):
             b.step(warmup)
             stream.synchronize()
@@ -214,7 +217,7 @@ def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream):
         ms = e0.elapsed_time(e1)
         ok = all(abs(b.diagnostics(k)["mass"]) > 0 for k in (0, len(BATCH_SIZES) - 1))
     return {"value": nodes * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "steps": steps,
-            "ms_per_step": ms / steps, "nodes": nodes, "finite": ok}
+            "ms_per_step": ms / steps, "nodes": nodes, "finite": ok, "launch_shapes": shapes}
 
 
 ORACLE_SNIPPET = r"""
@@ -314,8 +317,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
-        step_ms, kern, wall, diag, step_ms_b = time_path(lbm, torch, lbm.LBM_MIXED, args.steps, args.warmup, fields,
-                                                          stream)
+        step_ms, kern, wall, diag, step_ms_b, geom = time_path(lbm, torch, lbm.LBM_MIXED, args.steps, args.warmup,
+                                                                fields, stream)
     clocks = clk.summary()
     total_ms = sum(step_ms)
     if world > 1:
@@ -327,7 +330,7 @@ def main():
 
     # FP64 path on the same workload (plain method)
     k64 = args.fp64_steps or max(3, args.steps // 10)
-    step64, kern64, _, _, _ = time_path(lbm, torch, lbm.LBM_FP64, k64, min(args.warmup, 3), fields, stream)
+    step64, kern64, _, _, _, geom64 = time_path(lbm, torch, lbm.LBM_FP64, k64, min(args.warmup, 3), fields, stream)
     fp64_mlups = n * k64 / (sum(step64) * 1e-3) / 1e6
 
     dom = max(kern, key=lambda k: kern[k][0])
@@ -379,8 +382,10 @@ def main():
             "vs_baseline": None, "dtype": "f32 (moment sums compensated)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "LBM_MIXED", "l2": "flushed between steps (256 MiB write)",
                        "launch": "lbm_step: one CUDA graph per step (8 kernels)",
+                       "launch_shapes": {"col_tile_width": geom[0], "macro_rows_per_cta": geom[1],
+                                         "update_rows_per_cta": geom[2], "chosen_by": "lbm_autotune"},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "fp64_path": {"value": fp64_mlups, "unit": "MLUPS", "steps": k64,
+            "fp64_path": {"value": fp64_mlups, "unit": "MLUPS", "steps": k64, "launch_shapes": list(geom64),
                           "ms_per_step": sum(step64) / k64,
                           "kernels_ms_per_step": {k: v[0] / k64 for k, v in kern64.items()},
                           "bound": "alu (fp64)", "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS},
