@@ -1,4 +1,5 @@
-"""Global diagnostics of a state: total mass, momentum, total energy and maximum speed.
+"""Global diagnostics of a state: total mass, momentum, total energy and maximum speed, and
+the circularly averaged structure factor of the density.
 
 Total energy density (Sec. 2.2, after the recovered equations):
     e_T = rho T - 9 rho^2 / 8 + K |grad rho|^2 / 2 + rho u^2 / 2,
@@ -9,6 +10,29 @@ import numpy as np
 
 from .dvm import moments
 from .wfft import spectral_deriv
+
+
+def shell_index(nx, ny):
+    """Shell b of each 2D DFT index (my, mx): b = round(|q|), q = (mx N/nx, my N/ny), N = max(nx, ny),
+    with mx, my the signed DFT indices in [-n/2, n/2) (|q| in units of 2 pi / L of the longer axis)."""
+    N = max(nx, ny)
+    mx = np.fft.fftfreq(nx) * nx * (N / nx)
+    my = np.fft.fftfreq(ny) * ny * (N / ny)
+    return np.rint(np.sqrt(mx[None, :] ** 2 + my[:, None] ** 2)).astype(np.int64)
+
+
+def structure_factor(rho, nbins):
+    """Circularly averaged structure factor of the density (the domain-growth measure of the
+    phase-separation runs, Sec. 3.2): S(b) = mean over shell b of |rho_hat(m)|^2 / (nx ny),
+    rho_hat the unnormalised 2D DFT of rho - mean(rho). Returns (S, count) for b < nbins."""
+    ny, nx = rho.shape
+    P = np.abs(np.fft.fft2(rho - rho.mean())) ** 2 / (nx * ny)
+    b = shell_index(nx, ny).ravel()
+    keep = b < nbins
+    tot = np.bincount(b[keep], weights=P.ravel()[keep], minlength=nbins)[:nbins]
+    cnt = np.bincount(b[keep], minlength=nbins)[:nbins].astype(np.float64)
+    S = np.divide(tot, cnt, out=np.zeros(nbins), where=cnt > 0)
+    return S, cnt
 
 
 def diagnostics(dvm, f, p):

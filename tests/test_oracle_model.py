@@ -287,3 +287,23 @@ def test_isothermal_relaxation_to_the_thermostat(dvm):
     r, vx, vy, T = moments(dvm, f, p.b)
     assert np.allclose(r, 1.2, rtol=0, atol=1e-14) and np.allclose(vx, 0.03, rtol=0, atol=1e-14)
     assert np.all(np.abs(T - 0.9) < np.abs(0.97 - 0.9))
+
+
+def test_structure_factor_of_single_modes_and_parseval():
+    # rho = 1 + a cos(2 pi (3 x + 4 y)/N): the DFT of rho - mean has two entries of modulus
+    # a N^2 / 2 at (3, 4) and (-3, -4), both on shell 5, so S(5) = 2 (a N^2/2)^2 / N^2 / count(5)
+    # and every other shell is 0. Parseval: sum_b S(b) count(b) = sum (rho - mean)^2 (all shells).
+    from oracle.diag import structure_factor
+    N, a = 32, 0.03
+    x = np.arange(N)[None, :]
+    y = np.arange(N)[:, None]
+    rho = 1.0 + a * np.cos(2 * np.pi * (3 * x + 4 * y) / N)
+    S, cnt = structure_factor(rho, 40)
+    ref = 2 * (a * N * N / 2) ** 2 / (N * N) / cnt[5]
+    assert S[5] == pytest.approx(ref, rel=1e-12)
+    assert np.max(np.abs(np.delete(S, 5))) < 1e-20
+    rng = np.random.default_rng(3)
+    r = 1.0 + 0.01 * rng.standard_normal((16, 32))
+    S, cnt = structure_factor(r, 64)
+    assert np.sum(S * cnt) == pytest.approx(np.sum((r - r.mean()) ** 2), rel=1e-12)
+    assert cnt.sum() == 16 * 32
