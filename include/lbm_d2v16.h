@@ -120,6 +120,16 @@ int lbm_set_f(lbm_handle h, const double *f16);
  * max |u|, and the number of steps taken. Synchronises the stream. */
 int lbm_diagnostics(lbm_handle h, double out[6]);
 
+/* Circularly averaged structure factor of the density (the domain-growth measure of the
+ * phase-separation runs, Sec. 3.2), computed on the device in float64 from the current
+ * density: S[b] = mean over shell b of |rho_hat(m)|^2 / (nx ny) for b < nbins (1..8192),
+ * rho_hat the unnormalised 2D DFT of rho, shell b = round(|q|) with q = (m_x N/nx, m_y N/ny),
+ * N = max(nx, ny), m the signed DFT indices; S[0] (the mean) is reported as 0. count[b]
+ * (optional, may be NULL) receives the number of indices in shell b. Host arrays of nbins
+ * doubles. Uses the half-step buffer as scratch and a temporary device buffer of
+ * (nx + ny) ints + nbins doubles; synchronises the stream. */
+int lbm_structure_factor(lbm_handle h, int nbins, double *S, double *count);
+
 /* Waits for all work of the handle; returns LBM_ERR_CUDA if a kernel failed. */
 int lbm_synchronize(lbm_handle h);
 
@@ -221,6 +231,8 @@ int lbm_batch_diagnostics(lbm_batch b, int k, double out[6]);
 /* lbm_autotune for every size group of the batch (all instances initialised); the launch
  * shapes of instance k's group via lbm_batch_geometry. */
 int lbm_batch_autotune(lbm_batch b);
+/* lbm_structure_factor of instance k. */
+int lbm_batch_structure_factor(lbm_batch b, int k, int nbins, double *S, double *count);
 int lbm_batch_geometry(lbm_batch b, int k, int geometry[3]);
 
 /* Frees all device memory of the batch (synchronises first). NULL is ignored. */

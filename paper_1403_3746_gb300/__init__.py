@@ -75,6 +75,8 @@ _SIGS = {
     "lbm_batch_diagnostics": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "lbm_batch_destroy": (None, [_P]),
     "lbm_geometry": (ctypes.c_int, [_P, _P]),
+    "lbm_structure_factor": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "lbm_batch_structure_factor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "lbm_autotune": (ctypes.c_int, [_P, _P, _P]),
     "lbm_batch_autotune": (ctypes.c_int, [_P]),
     "lbm_batch_geometry": (ctypes.c_int, [_P, ctypes.c_int, _P]),
@@ -237,6 +239,12 @@ class Simulation:
     def device_bytes(self):
         return int(lib().lbm_device_bytes(self._h))
 
+    def structure_factor(self, nbins):
+        """(S, count): circularly averaged structure factor of the density, nbins shells."""
+        S, cnt = np.empty(nbins), np.empty(nbins)
+        _check(lib().lbm_structure_factor(self._h, int(nbins), _ptr(S), _ptr(cnt)))
+        return S, cnt
+
     def geometry(self):
         """(column tile width, rows per CTA of the macro pass, rows per CTA of the update pass)."""
         g = (ctypes.c_int * 3)()
@@ -316,6 +324,11 @@ class Batch:
 
     def autotune(self):
         _check(lib().lbm_batch_autotune(self._h))
+
+    def structure_factor(self, k, nbins):
+        S, cnt = np.empty(nbins), np.empty(nbins)
+        _check(lib().lbm_batch_structure_factor(self._h, int(k), int(nbins), _ptr(S), _ptr(cnt)))
+        return S, cnt
 
     def geometry(self, k):
         g = (ctypes.c_int * 3)()

@@ -778,9 +778,80 @@ int diagnostics_instance(lbm_ctx *c, int k, long long steps, double out[6]) {
     return LBM_OK;
 }
 
+// Circularly averaged structure factor of instance k's density (kernels_sf.cu): the spectra
+// go to the half-step buffer f1 (16 bytes per node, free outside a step); the frequency
+// tables and shell sums to a temporary device buffer.
+int structure_factor_instance(lbm_ctx *c, int k, int nbins, double *S, double *count) {
+    if (nbins < 1 || nbins > 8192) return fail(LBM_ERR_ARG, "nbins must be in [1, 8192]");
+    const int nx = c->nx, ny = c->ny, N = std::max(nx, ny);
+    const size_t ldm = (size_t)NF_M * nx;
+    SfArgs a{};
+    a.rho = static_cast<const char *>(c->m) + c->row0(k) * ldm * c->fsize;  // M_RHO is field 0
+    a.ld = (int)ldm;
+    a.nx = nx; a.ny = ny; a.lx = c->lx; a.ly = c->ly;
+    a.rows = std::max(1, std::min(ny, 256 / line_G(c->lx)));
+    a.cols = std::max(1, std::min(nx, 256 / line_G(c->ly)));
+    a.Z = static_cast<double2 *>(c->f1);
+    a.twx = c->tw64x; a.twy = c->tw64y;
+    const size_t tab_bytes = ((size_t)(nx + ny) * sizeof(int) + 255) & ~(size_t)255;
+    char *tmp = nullptr;
+    if (cudaMalloc(&tmp, tab_bytes + (size_t)nbins * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ERR_NOMEM, "structure factor: no device scratch");
+    }
+    struct Free {
+        char *p;
+        ~Free() { cudaFree(p); }
+    } free_tmp{tmp};
+    int *fx = reinterpret_cast<int *>(tmp), *fy = fx + nx;
+    double *dS = reinterpret_cast<double *>(tmp + tab_bytes);
+    a.fx = fx; a.fy = fy;
+    a.sx = (double)N / nx; a.sy = (double)N / ny;
+    a.nbins = nbins;
+    a.S = dS;
+    std::vector<int> hx(nx), hy(ny);
+    position_frequencies(nx, hx.data());
+    position_frequencies(ny, hy.data());
+    CU_TRY(cudaMemcpyAsync(fx, hx.data(), nx * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemcpyAsync(fy, hy.data(), ny * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemsetAsync(dS, 0, nbins * sizeof(double), c->stream));
+    CU_TRY(c->mixed ? launch_structure_factor<float>(a, c->stream) : launch_structure_factor<double>(a, c->stream));
+    std::vector<double> tot(nbins);
+    CU_TRY(cudaMemcpyAsync(tot.data(), dS, nbins * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    // shell populations from the same index geometry; shell 0 (the mean) reported as 0
+    std::vector<double> cnt(nbins, 0.0);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const double qx = hx[x] * a.sx, qy = hy[y] * a.sy;
+            const int b = (int)std::rint(std::sqrt(qx * qx + qy * qy));
+            if (b < nbins) cnt[b] += 1.0;
+        }
+    for (int b = 0; b < nbins; ++b) {
+        S[b] = (b == 0 || cnt[b] == 0) ? 0.0 : tot[b] / cnt[b];
+        if (count) count[b] = cnt[b];
+        if (!std::isfinite(S[b])) return fail(LBM_ERR_NONFINITE, "structure factor bin %d is not finite", b);
+    }
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int lbm_structure_factor(lbm_handle c, int nbins, double *S, double *count) {
+    if (!c || !S) return fail(LBM_ERR_ARG, "NULL argument");
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
+    return structure_factor_instance(c, 0, nbins, S, count);
+}
+
+int lbm_batch_structure_factor(lbm_batch b, int k, int nbins, double *S, double *count) {
+    if (!b || !S || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
+    lbm_ctx *c = b->groups[b->where[k].first];
+    if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    return structure_factor_instance(c, b->where[k].second, nbins, S, count);
+}
 
 void lbm_default_params(lbm_params *p) {
     if (!p) return;
@@ -1159,6 +1230,16 @@ static int freq_at(int p, int n, int radix_first) {
     const int S = n / r;
     const int next = S >= 16 ? 16 : S;
     return p / S + r * freq_at(p % S, S, next);
+}
+
+void position_frequencies(int N, int *out) {
+    int l2 = 0;
+    while ((1 << l2) < N) ++l2;
+    const int first = l2 >= 4 ? 16 : N;
+    for (int p = 0; p < N; ++p) {
+        const int k = freq_at(p, N, first);
+        out[p] = k < N / 2 ? k : k - N;
+    }
 }
 
 void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2, int terms) {

@@ -206,6 +206,20 @@ template <typename R> struct RowDerivArgs {
     Axis<R> ax;
 };
 
+// ---- structure factor (kernels_sf.cu) -------------------------------------------------
+struct SfArgs {
+    const void *rho;         // density field, row y at rho + y * ld (element type of the path)
+    int ld;                  // row stride in elements
+    int nx, ny, lx, ly;      // grid and log2 sizes
+    int rows, cols;          // rows per CTA of the row pass, columns per CTA of the column pass
+    double2 *Z;              // scratch [ny][nx]: row spectra (digit-reversed positions)
+    const double2 *twx, *twy;  // float64 twiddle tables of the two axes
+    const int *fx, *fy;      // signed DFT index at each position of the two axes
+    double sx, sy;           // shell scaling N/nx, N/ny (N = max(nx, ny))
+    int nbins;
+    double *S;               // [nbins] sums of |rho_hat|^2 / (nx ny) per shell (zeroed by the caller)
+};
+
 // launchers (kernels_*.cu); all return cudaGetLastError() of the launch
 template <typename R> cudaError_t launch_col(const ColArgs<R> &a, int njobs, size_t smem, cudaStream_t s);
 template <typename R> cudaError_t launch_macro(const MacroArgs<R> &a, size_t smem, cudaStream_t s);
@@ -218,6 +232,10 @@ cudaError_t launch_twiddles(double2 *tw64, float2 *tw32, int n, cudaStream_t s);
 // strided copies between a field of a block (row y at src + y ld) and a dense float64 array [ny][nx]
 template <typename R>
 cudaError_t launch_field_out(const R *src, int ld, double *out, int nx, int ny, cudaStream_t s);
+
+template <typename R> cudaError_t launch_structure_factor(const SfArgs &a, cudaStream_t s);
+// signed DFT index held at each position of a forward line transform of length N (lbm_api.cu)
+void position_frequencies(int N, int *out);
 
 // sets the calling thread's message returned by lbm_last_error() (lbm_api.cu)
 void set_last_error(const char *msg);
