@@ -16,6 +16,13 @@ namespace lbm {
 // transforms' tables (and register spills) from L1.
 template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
+// a / b in the path's precision: float64 divides exactly; float32 uses the reciprocal unit and
+// one multiply (__fdividef, within 2 ulp for the O(1) physical operands here) instead of the
+// IEEE division sequence.
+template <typename R> __device__ __forceinline__ R quot(R a, R b);
+template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float quot<float>(float a, float b) { return __fdividef(a, b); }
+
 // compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
 template <int B, int E, class Fn> __device__ __forceinline__ void static_for(Fn &&f) {
     if constexpr (B < E) {
@@ -105,10 +112,10 @@ __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R,
         const R divu = dux_dx + duy_dy;
         // van der Waals EOS (Sec. 2.2)
         const R rT = rho * T;
-        const R Pw = R(3) * rT / (R(3) - rho) - R(1.125) * rho * rho;
+        const R Pw = quot(R(3) * rT, R(3) - rho) - R(1.125) * rho * rho;
         // Lambda with M = K + H T and grad(M/T) = -K grad T / T^2
         const R Mc = K + H * T;
-        const R iT2 = R(1) / (T * T);
+        const R iT2 = quot(R(1), T * T);
         const R gx = -K * Tx * iT2, gy = -K * Ty * iT2;
         const R grr = rx * rx + ry * ry;
         const R iso = Mc * (rho * lap + R(0.5) * grr) + rT * (rx * gx + ry * gy);
@@ -210,9 +217,10 @@ template <> struct MomentSums<float> {
     __device__ __forceinline__ void finish(float b, float &rho, float &ux, float &uy, float &T) const {
         rho = rs + rc;
         const float jx = xs + xc, jy = ys + yc, E = es + ec;
-        ux = jx / rho;
-        uy = jy / rho;
-        T = (E / rho - (ux * ux + uy * uy)) / b;
+        const float ir = __fdividef(1.0f, rho);
+        ux = jx * ir;
+        uy = jy * ir;
+        T = __fdividef(E * ir - (ux * ux + uy * uy), b);
     }
 };
 
@@ -346,12 +354,12 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         R hal = 0, hbx = 0, hby = 0, hcc = 0;
         if (frc) {
             const R rT = rho * T;
-            const R irT = R(1) / rT;
+            const R irT = quot(R(1), rT), irTT = quot(irT, T);
             const R Bx = (ldcg(mn + M_DSXX * NX) + ldcg(mn + M_DSXYY * NX)) * irT;
             const R By = (ldcg(mn + M_DSXY * NX) + ldcg(mn + M_DSYY * NX)) * irT;
             const R C = (ldcg(mn + M_CNUM * NX) - K * rho * ldcg(mn + M_RY * NX) * ldcg(mn + M_DDIVUY * NX)) *
-                        (R(0.5) * irT / T);
-            const R Cq = (ldcg(mn + M_DQX * NX) + ldcg(mn + M_DQY * NX)) * (irT / T);
+                        (R(0.5) * irTT);
+            const R Cq = (ldcg(mn + M_DQX * NX) + ldcg(mn + M_DQY * NX)) * irTT;
             const R CC = C + Cq;
             const R A = R(-2) * CC * T;
             hal = h * (A - Bx * ux - By * uy + CC * (ux * ux + uy * uy));
