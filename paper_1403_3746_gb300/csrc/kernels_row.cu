@@ -188,20 +188,50 @@ template <> struct MomentSums<double> {
 };
 
 __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
-    const float t = s + x;
-    const float bp = t - s;
-    c += (s - (t - bp)) + (x - bp);
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    c += __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
     s = t;
 }
 __device__ __forceinline__ void dot2_acc(float &s, float &c, float f, float wh, float wl) {
-    const float p = f * wh;
+    const float p = __fmul_rn(f, wh);
     const float e = fmaf(f, wh, -p);  // exact: f*wh = p + e
     two_sum_acc(s, c, p);
     c += fmaf(f, wl, e);
 }
 
+// Knuth's TwoSum and TwoDiff: a + b = s + e and a - b = d + e exactly (no fused operations).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+__device__ __forceinline__ void two_diff(float a, float b, float &d, float &e) { two_sum(a, -b, d, e); }
+
 template <> struct MomentSums<float> {
     float rs = 0, rc = 0, xs = 0, xc = 0, ys = 0, yc = 0, es = 0, ec = 0;
+    // Velocities i and i + 2 are opposite: their contributions enter through the exact pair
+    // sum fi + fk = S + eS (to rho and E, weight psi_i) and difference fi - fk = D + eD (to j,
+    // weight v_i); the rounding terms eS, eD are added to the compensations.
+    template <int I> __device__ __forceinline__ void add_pair(float fi, float fk, float psi_hi, float psi_lo) {
+        float S, eS, D, eD;
+        two_sum(fi, fk, S, eS);
+        two_diff(fi, fk, D, eD);
+        two_sum_acc(rs, rc, S);
+        rc += eS;
+        dot2_acc(es, ec, S, psi_hi, psi_lo);
+        ec = fmaf(psi_hi, eS, ec);
+        if constexpr (vel_x(I) != 0.0) {
+            constexpr float wh = (float)vel_x(I), wl = (float)(vel_x(I) - (double)(float)vel_x(I));
+            dot2_acc(xs, xc, D, wh, wl);
+            xc = fmaf(wh, eD, xc);
+        }
+        if constexpr (vel_y(I) != 0.0) {
+            constexpr float wh = (float)vel_y(I), wl = (float)(vel_y(I) - (double)(float)vel_y(I));
+            dot2_acc(ys, yc, D, wh, wl);
+            yc = fmaf(wh, eD, yc);
+        }
+    }
     __device__ __forceinline__ void add(int i, float f, float psi_hi, float psi_lo) {
         two_sum_acc(rs, rc, f);
         if (vel_x(i) != 0.0) {
@@ -284,6 +314,12 @@ __host__ __device__ constexpr double mom_entry_eta(int j, int i) {
 __host__ __device__ constexpr bool minv_zero(int i, int j) {
     return i < 8 && ((vel_y(i) == 0.0 && (mom_py(j) & 1)) || (vel_x(i) == 0.0 && (mom_px(j) & 1)));
 }
+// Opposite velocities: v_{i+2} = -v_i for i in {0, 1, 4, 5, 8, 9, 12, 13} (pair p, i = pair_rep(p)).
+// A moment of odd degree in v changes sign between the two, an even one does not; so does the
+// matching column of M^-1: M^-1[i+2][4+j] = +-M^-1[i][4+j] (M P = S M for the swap P of the
+// pairs and S = diag(+-1) of the moment parities).
+__host__ __device__ constexpr int pair_rep(int p) { return 4 * (p >> 1) + (p & 1); }
+__host__ __device__ constexpr bool mom_odd(int j) { return (mom_px(j) + mom_py(j)) & 1; }
 
 template <typename R, int LOG2N, bool MOMENT_SPACE>
 __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
@@ -370,74 +406,106 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         const R htau = h * tau_inv;
         R m[16];
         equilibrium_moments<R>(rho, ux, uy, T, b, m);
-        // neq_i = f_i^eq - f_i. float64: f^eq = M^-1 m^eq directly. float32: in moment space,
-        // neq = M^-1 (m^eq - M f) over the 12 non-conserved moments only (the 4 conserved
-        // ones agree exactly), so the rounding of M^-1 to float32 cannot bias mass, momentum
-        // or energy: its error scales with the non-equilibrium part instead of with rho.
-        R fsv[16], dm[12], dE = 0;
+        R fsv[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-            fsv[i] = ldcg(fn + i * NX);
-        if (MOMENT_SPACE) {
-            // isothermal: the energy moment (row 3) is not conserved by the thermostat either
-            if (iso) {
-                R me = 0;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) me += a.psi_hi[i] * fsv[i];
-                dE = m[3] - me;
-            }
-            const R eta2 = a.eta2;
-            static_for<0, 12>([&](auto J) {
-                constexpr int j = decltype(J)::value;
-                R mf = 0, me = 0;
-                static_for<0, 16>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    if constexpr (mom_entry(j, i) != 0.0) mf += R(mom_entry(j, i)) * fsv[i];
-                    if constexpr (mom_entry_eta(j, i) != 0.0) me += R(mom_entry_eta(j, i)) * fsv[i];
-                });
-                dm[j] = m[4 + j] - (mf + eta2 * me);
-            });
-        }
+        for (int i = 0; i < 16; ++i) fsv[i] = ldcg(fn + i * NX);
         const R *bn = a.fbase + y * NF_F * NX + x;
         R *on = a.fout + y * NF_F * NX + x;
-        MomentSums<R> acc;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            R ne = 0, fe;
-            if (MOMENT_SPACE) {
-                static_for<0, 12>([&](auto J) {
-                    constexpr int j = decltype(J)::value;
-                    if (!minv_zero(i, j)) ne += a.minv[i * 16 + 4 + j] * dm[j];
-                });
-                if (iso) ne += a.minv[i * 16 + 3] * dE;
-                fe = fsv[i] + ne;
-            } else {
-                fe = 0;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * m[j];
-                ne = fe - fsv[i];
-            }
+        // f_out_i = f_base_i + h R_i with the non-equilibrium part ne_i = f_i^eq - f_i and the
+        // forcing factor q_i = al + bx v_ix + by v_iy + cc |v_i|^2 (all with h folded in)
+        auto out_value = [&](auto I, R ne, R q) -> R {
+            constexpr int i = decltype(I)::value;
             R dfo = 0;  // h R_i
             if (adv) {
                 R ad = 0;
-                const int xs = xslot(i), ys = yslot(i);
-                if (xs >= 0) {
+                constexpr int xs = xslot(i), ys = yslot(i);
+                if constexpr (xs >= 0) {
                     const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + x];
                     ad += R(vel_x(i)) * ((xs & 1) ? d.y : d.x);
                 }
-                if (ys >= 0) ad += ldcg(an + ys * NX);
+                if constexpr (ys >= 0) ad += ldcg(an + ys * NX);
                 dfo -= h * ad;
             }
             if (col) dfo += htau * ne;
-            if (frc) {
-                R q = hal + hcc * R(vel_sq(i));
-                if (vel_x(i) != 0.0) q += hbx * R(vel_x(i));
-                if (vel_y(i) != 0.0) q += hby * R(vel_y(i));
-                dfo -= q * fe;
+            if (frc) dfo -= q * (fsv[i] + ne);
+            return (same_base ? fsv[i] : ldcg(bn + i * NX)) + dfo;
+        };
+        MomentSums<R> acc;
+        if constexpr (MOMENT_SPACE) {
+            // neq = M^-1 (m^eq - M f) over the 12 non-conserved moments only (the 4 conserved
+            // ones agree exactly), so the rounding of M^-1 to float32 cannot bias mass, momentum
+            // or energy: its error scales with the non-equilibrium part instead of with rho.
+            // Opposite-velocity pairs: even moments see fi + fk, odd ones fi - fk, and
+            // ne_i, ne_k = E +- O from the even and odd columns of M^-1.
+            R sp[8], dp[8];
+            static_for<0, 8>([&](auto P) {
+                constexpr int p = decltype(P)::value, i = pair_rep(p);
+                sp[p] = fsv[i] + fsv[i + 2];
+                dp[p] = fsv[i] - fsv[i + 2];
+            });
+            const R eta2 = a.eta2;
+            R dm[12];
+            static_for<0, 12>([&](auto J) {
+                constexpr int j = decltype(J)::value;
+                R mf = 0, me = 0;
+                static_for<0, 8>([&](auto P) {
+                    constexpr int p = decltype(P)::value, i = pair_rep(p);
+                    const R g = mom_odd(j) ? dp[p] : sp[p];
+                    if constexpr (mom_entry(j, i) != 0.0) mf += R(mom_entry(j, i)) * g;
+                    if constexpr (mom_entry_eta(j, i) != 0.0) me += R(mom_entry_eta(j, i)) * g;
+                });
+                dm[j] = m[4 + j] - (mf + eta2 * me);
+            });
+            // isothermal: the energy moment (row 3, even) is not conserved by the thermostat either
+            R dE = 0;
+            if (iso) {
+                R me = 0;
+                static_for<0, 8>([&](auto P) {
+                    constexpr int p = decltype(P)::value;
+                    me += a.psi_hi[pair_rep(p)] * sp[p];
+                });
+                dE = m[3] - me;
             }
-            const R fo = (same_base ? fsv[i] : ldcg(bn + i * NX)) + dfo;
-            on[i * NX] = fo;
-            acc.add(i, fo, a.psi_hi[i], a.psi_lo[i]);
+            static_for<0, 8>([&](auto P) {
+                constexpr int p = decltype(P)::value, i = pair_rep(p);
+                R ev = 0, od = 0;
+                static_for<0, 12>([&](auto J) {
+                    constexpr int j = decltype(J)::value;
+                    if constexpr (!minv_zero(i, j)) {
+                        if constexpr (mom_odd(j)) od += a.minv[i * 16 + 4 + j] * dm[j];
+                        else ev += a.minv[i * 16 + 4 + j] * dm[j];
+                    }
+                });
+                if (iso) ev += a.minv[i * 16 + 3] * dE;
+                R qe = 0, qo = 0;
+                if (frc) {
+                    qe = hal + hcc * R(vel_sq(i));
+                    if constexpr (vel_x(i) != 0.0) qo += hbx * R(vel_x(i));
+                    if constexpr (vel_y(i) != 0.0) qo += hby * R(vel_y(i));
+                }
+                const R fi = out_value(std::integral_constant<int, i>{}, ev + od, qe + qo);
+                const R fk = out_value(std::integral_constant<int, i + 2>{}, ev - od, qe - qo);
+                on[i * NX] = fi;
+                on[(i + 2) * NX] = fk;
+                acc.template add_pair<i>(fi, fk, a.psi_hi[i], a.psi_lo[i]);
+            });
+        } else {
+            // float64: f^eq = M^-1 m^eq directly
+            static_for<0, 16>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                R fe = 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) fe += a.minv[i * 16 + j] * m[j];
+                R q = 0;
+                if (frc) {
+                    q = hal + hcc * R(vel_sq(i));
+                    if constexpr (vel_x(i) != 0.0) q += hbx * R(vel_x(i));
+                    if constexpr (vel_y(i) != 0.0) q += hby * R(vel_y(i));
+                }
+                const R fo = out_value(I, fe - fsv[i], q);
+                on[i * NX] = fo;
+                acc.add(i, fo, a.psi_hi[i], a.psi_lo[i]);
+            });
         }
         R nr, nux, nuy, nT;
         acc.finish(b, nr, nux, nuy, nT);

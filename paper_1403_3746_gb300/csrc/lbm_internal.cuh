@@ -48,11 +48,11 @@ __host__ __device__ constexpr double vel_sq(int i) {
 }
 // fields with v_x != 0, in the order of the 12 real rows of the update kernel's shared tile:
 // row k holds field XF(k); complex line p packs rows 2p (real part) and 2p+1 (imag part)
-__host__ __device__ __forceinline__ int xfield(int k) { return k < 4 ? 2 * k : k + 4; }
-__host__ __device__ __forceinline__ int xslot(int i) { return i < 8 ? ((i & 1) ? -1 : i / 2) : i - 4; }
+__host__ __device__ constexpr int xfield(int k) { return k < 4 ? 2 * k : k + 4; }
+__host__ __device__ constexpr int xslot(int i) { return i < 8 ? ((i & 1) ? -1 : i / 2) : i - 4; }
 // fields with v_y != 0 and their slot in the 12-field column-pass output Ay
-__host__ __device__ __forceinline__ int yfield(int k) { return k < 4 ? 2 * k + 1 : k + 4; }
-__host__ __device__ __forceinline__ int yslot(int i) { return i < 8 ? ((i & 1) ? i / 2 : -1) : i - 4; }
+__host__ __device__ constexpr int yfield(int k) { return k < 4 ? 2 * k + 1 : k + 4; }
+__host__ __device__ constexpr int yslot(int i) { return i < 8 ? ((i & 1) ? i / 2 : -1) : i - 4; }
 
 // Line-transform geometry (fft_reg.cuh): points per thread, threads per line, and the stride
 // between padded shared-memory line buffers in complex elements, for a line of 2^log2n points.
