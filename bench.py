@@ -383,7 +383,8 @@ def main():
             "config": {"workload": WORKLOAD, "precision": "LBM_MIXED", "l2": "flushed between steps (256 MiB write)",
                        "launch": "lbm_step: one CUDA graph per step (8 kernels)",
                        "launch_shapes": {"col_tile_width": geom[0], "macro_rows_per_cta": geom[1],
-                                         "update_rows_per_cta": geom[2], "chosen_by": "lbm_autotune"},
+                                         "update_rows_per_cta": geom[2], "flux_tile_width": geom[3],
+                                         "chosen_by": "lbm_autotune"},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_mlups, "unit": "MLUPS", "steps": k64, "launch_shapes": list(geom64),
                           "ms_per_step": sum(step64) / k64,

@@ -160,15 +160,16 @@ size_t lbm_device_bytes(lbm_handle h);
 
 /* Launch shapes (no counterpart in the paper: a performance service). geometry[0]: width in
  * columns of the column-pass tiles; geometry[1], geometry[2]: rows per CTA of the macro and
- * update row passes. lbm_autotune times every legal candidate of each (column tiles with at
- * most 100 KB of line buffers; row CTAs of at most 4096 nodes and 200 KB) on the handle's own
- * buffers with the passes of a Runge-Kutta stage, keeps the fastest, and reports the chosen
- * shapes and their measured times (ms per pass; either pointer may be NULL). The state is
- * unchanged (the moment fields the update pass rewrites are saved and restored) and results
- * do not depend on the shapes. Needs an initialised state; allocates a temporary device
- * buffer of 4 fields; synchronises the stream. */
-int lbm_geometry(lbm_handle h, int geometry[3]);
-int lbm_autotune(lbm_handle h, int geometry[3], double ms[3]);
+ * update row passes; geometry[3]: width of the flux column-pass tiles. lbm_autotune times
+ * every legal candidate of each (column tiles with at most 100 KB of line buffers; row CTAs
+ * of at most 4096 nodes and 200 KB) on the handle's own buffers with the passes of a
+ * Runge-Kutta stage, keeps the fastest, and reports the chosen shapes and the measured time
+ * of each pass with them (ms: column, macro, update, flux; either pointer may be NULL). The
+ * state is unchanged (the moment fields the update pass rewrites are saved and restored) and
+ * results do not depend on the shapes. Needs an initialised state; allocates a temporary
+ * device buffer of 4 fields; synchronises the stream. */
+int lbm_geometry(lbm_handle h, int geometry[4]);
+int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
 
 /* lbm_diagnostics for callers that cannot allocate device memory. The paper has no
  * counterpart: this is a library service. Examples: code running while a stream is being
@@ -233,7 +234,7 @@ int lbm_batch_diagnostics(lbm_batch b, int k, double out[6]);
 int lbm_batch_autotune(lbm_batch b);
 /* lbm_structure_factor of instance k. */
 int lbm_batch_structure_factor(lbm_batch b, int k, int nbins, double *S, double *count);
-int lbm_batch_geometry(lbm_batch b, int k, int geometry[3]);
+int lbm_batch_geometry(lbm_batch b, int k, int geometry[4]);
 
 /* Frees all device memory of the batch (synchronises first). NULL is ignored. */
 void lbm_batch_destroy(lbm_batch b);

@@ -246,16 +246,17 @@ class Simulation:
         return S, cnt
 
     def geometry(self):
-        """(column tile width, rows per CTA of the macro pass, rows per CTA of the update pass)."""
-        g = (ctypes.c_int * 3)()
+        """(column tile width, rows per CTA of the macro pass, rows per CTA of the update pass,
+        flux column tile width)."""
+        g = (ctypes.c_int * 4)()
         _check(lib().lbm_geometry(self._h, ctypes.cast(g, _P)))
         return tuple(g)
 
     def autotune(self):
         """Times the launch-shape candidates on this simulation and keeps the fastest;
         returns (geometry, ms per pass)."""
-        g = (ctypes.c_int * 3)()
-        ms = (ctypes.c_double * 3)()
+        g = (ctypes.c_int * 4)()
+        ms = (ctypes.c_double * 4)()
         _check(lib().lbm_autotune(self._h, ctypes.cast(g, _P), ctypes.cast(ms, _P)))
         return tuple(g), tuple(ms)
 
@@ -331,6 +332,6 @@ class Batch:
         return S, cnt
 
     def geometry(self, k):
-        g = (ctypes.c_int * 3)()
+        g = (ctypes.c_int * 4)()
         _check(lib().lbm_batch_geometry(self._h, int(k), ctypes.cast(g, _P)))
         return tuple(g)

@@ -323,7 +323,7 @@ __host__ __device__ constexpr bool mom_odd(int j) { return (mom_px(j) + mom_py(j
 
 template <typename R, int LOG2N, bool MOMENT_SPACE>
 __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
-    using F = reg::LineFFT<R, LOG2N>;
+    using F = reg::LineFFT<R, LOG2N, true>;
     using CT = typename F::CT;
     constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -186,12 +186,12 @@ template <> Axis<float> axis<float>(const lbm_ctx *c, bool xdir) {
                 : Axis<float>{c->tw32y, c->k1y32, c->k2y32, c->ly};
 }
 
-template <typename R> ColArgs<R> col_args(const lbm_ctx *c, int nb) {
+template <typename R> ColArgs<R> col_args(const lbm_ctx *c, int nb, int W) {
     ColArgs<R> a{};
     a.nx = c->nx;
     a.ny = c->ny;
-    a.W = c->geo.colW;
-    a.log2W = ilog2(c->geo.colW);
+    a.W = W;
+    a.log2W = ilog2(W);
     a.nb = nb;
     a.ay = axis<R>(c, false);
     return a;
@@ -216,7 +216,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
     auto M = [m, nx](int k) { return m + (size_t)k * nx; };  // first row of macro field k
 
     {
-        ColArgs<R> a = col_args<R>(c, c->nb);
+        ColArgs<R> a = col_args<R>(c, c->nb, c->geo.colW);
         int nj = 0;
         if (adv)
             for (int k = 0; k < 12; ++k) {
@@ -248,13 +248,13 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
     }
     if (frc && (passes & PASS_FLUX)) {
         {
-            ColArgs<R> a = col_args<R>(c, c->nb);
+            ColArgs<R> a = col_args<R>(c, c->nb, c->geo.fluxW);
             a.jobs[0] = ColJob<R>{M(M_QY), M(M_DQY), ldm, ldm, 1, R(1)};
             a.jobs[1] = ColJob<R>{M(M_SXY), M(M_DSXYY), ldm, ldm, 1, R(1)};
             a.jobs[2] = ColJob<R>{M(M_SYY), M(M_DSYY), ldm, ldm, 1, R(1)};
             a.jobs[3] = ColJob<R>{M(M_DIVU), M(M_DDIVUY), ldm, ldm, 1, R(1)};
             LaunchTimer t(c, LBM_K_FLUX);
-            CU_TRY(launch_col<R>(a, 4, c->geo.col_smem, c->stream));
+            CU_TRY(launch_col<R>(a, 4, c->geo.flux_smem, c->stream));
         }
     }
     if (passes & PASS_UPDATE) {
@@ -374,7 +374,7 @@ template <typename R> int time_passes(lbm_ctx *c, int passes, cudaEvent_t e0, cu
 // pass overwrites the moment fields: those are saved first and restored at the end, so the
 // state is unchanged. Per-row and per-column work does not depend on these shapes, so results
 // stay bit for bit the same.
-template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[3]) {
+template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
     const bool timing = c->timing;
     c->timing = false;
     const size_t es = c->fsize, rows = (size_t)c->nb * c->ny;
@@ -399,22 +399,25 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[3]) {
                           cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
         return done(fail(LBM_ERR_CUDA, "autotune: saving the moments failed"));
     if ((rc = run_stage<R>(c, 0, PASS_ALL))) return done(rc);
-
     const bool frc = !(c->p.flags & LBM_FLAG_NO_FORCE);
+
     float t = 0;
-    // column tile width (column and flux passes)
-    {
-        int bestW = c->geo.colW;
+    // column tile widths of the column pass and of the flux column pass
+    for (int pass : {PASS_COL, PASS_FLUX}) {
+        if (pass == PASS_FLUX && !frc) continue;
+        int &Wg = pass == PASS_COL ? c->geo.colW : c->geo.fluxW;
+        size_t &Sg = pass == PASS_COL ? c->geo.col_smem : c->geo.flux_smem;
+        int bestW = Wg;
         float bt = 1e30f;
         for (int W : col_candidates(c)) {
-            c->geo.colW = W;
-            c->geo.col_smem = (size_t)(W / 2) * line_smem(c->ly) * 2 * es;
-            if ((rc = time_passes<R>(c, PASS_COL | PASS_FLUX, e0, e1, &t))) return done(rc);
+            Wg = W;
+            Sg = (size_t)(W / 2) * line_smem(c->ly) * 2 * es;
+            if ((rc = time_passes<R>(c, pass, e0, e1, &t))) return done(rc);
             if (t < bt) bt = t, bestW = W;
         }
-        c->geo.colW = bestW;
-        c->geo.col_smem = (size_t)(bestW / 2) * line_smem(c->ly) * 2 * es;
-        best_ms[0] = bt;
+        Wg = bestW;
+        Sg = (size_t)(bestW / 2) * line_smem(c->ly) * 2 * es;
+        best_ms[pass == PASS_COL ? 0 : 3] = bt;
     }
     const size_t SM = (size_t)line_smem(c->lx) * 2 * es;
     best_ms[1] = 0;
@@ -456,7 +459,7 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[3]) {
     return done(LBM_OK);
 }
 
-int autotune_ctx(lbm_ctx *c, float best_ms[3]) {
+int autotune_ctx(lbm_ctx *c, float best_ms[4]) {
     if (!c->all_initialized()) return fail(LBM_ERR_STATE, "autotune needs an initialised state");
     return c->mixed ? autotune_impl<float>(c, best_ms) : autotune_impl<double>(c, best_ms);
 }
@@ -531,7 +534,7 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     pass_geometry(nx, ny, c->fsize, &c->geo);
     const size_t need =
-        std::max(std::max(c->geo.upd_smem, c->geo.macro_smem), std::max(c->geo.col_smem, c->geo.rowd_smem));
+        std::max(std::max(c->geo.upd_smem, c->geo.macro_smem), std::max(c->geo.col_smem, c->geo.rowd_smem));  // flux = col
     if (need > (size_t)smem_optin) {
         delete c;
         return fail(LBM_ERR_UNSUPPORTED, "nx=%d ny=%d needs %zu B of shared memory per block (device: %d)", nx,
@@ -728,7 +731,7 @@ template <typename R> int diag_launch(lbm_ctx *c, int k) {
     // d_y rho into M_RY, d_x rho into M_DQX of instance k (stage scratch, rebuilt by the next stage)
     const int nx = c->nx, ldm = NF_M * nx;
     R *m = static_cast<R *>(c->m) + c->row0(k) * ldm;
-    ColArgs<R> ca = col_args<R>(c, 1);
+    ColArgs<R> ca = col_args<R>(c, 1, c->geo.colW);
     ca.jobs[0] = ColJob<R>{m + (size_t)M_RHO * nx, m + (size_t)M_RY * nx, ldm, ldm, 1, R(1)};
     CU_TRY(launch_col<R>(ca, 1, c->geo.col_smem, c->stream));
     RowDerivArgs<R> ra{};
@@ -994,21 +997,22 @@ int lbm_timing_read(lbm_handle c, int kernel, double *ms, long long *launches) {
 
 size_t lbm_device_bytes(lbm_handle c) { return c ? c->slab_bytes : 0; }
 
-int lbm_geometry(lbm_handle c, int geometry[3]) {
+int lbm_geometry(lbm_handle c, int geometry[4]) {
     if (!c || !geometry) return fail(LBM_ERR_ARG, "NULL argument");
     geometry[0] = c->geo.colW;
     geometry[1] = c->geo.rows_macro;
     geometry[2] = c->geo.rows_upd;
+    geometry[3] = c->geo.fluxW;
     return LBM_OK;
 }
 
-int lbm_autotune(lbm_handle c, int geometry[3], double ms[3]) {
+int lbm_autotune(lbm_handle c, int geometry[4], double ms[4]) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
-    float t[3] = {0, 0, 0};
+    float t[4] = {0, 0, 0, 0};
     const int rc = autotune_ctx(c, t);
     if (rc) return rc;
     if (ms)
-        for (int k = 0; k < 3; ++k) ms[k] = t[k];
+        for (int k = 0; k < 4; ++k) ms[k] = t[k];
     return geometry ? lbm_geometry(c, geometry) : LBM_OK;
 }
 
@@ -1116,7 +1120,7 @@ int lbm_batch_autotune(lbm_batch b) {
     if (!b) return fail(LBM_ERR_ARG, "NULL batch");
     CU_TRY(cudaStreamSynchronize(b->stream));
     for (lbm_ctx *c : b->groups) {
-        float t[3];
+        float t[4];
         const int rc = autotune_ctx(c, t);
         if (rc) return rc;
     }
@@ -1127,7 +1131,7 @@ int lbm_batch_autotune(lbm_batch b) {
     return LBM_OK;
 }
 
-int lbm_batch_geometry(lbm_batch b, int k, int geometry[3]) {
+int lbm_batch_geometry(lbm_batch b, int k, int geometry[4]) {
     if (!b || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
     return lbm_geometry(b->groups[b->where[k].first], geometry);
 }
@@ -1282,8 +1286,8 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     if (W > nx) W = nx;
     const int maxt = max_threads(esize), colt = pass_threads(esize);
     while (W > 2 && ((W / 2) * line_G(ly) > colt || (size_t)(W / 2) * line_smem(ly) * cs > 100 * 1024)) W >>= 1;
-    g->colW = W;
-    g->col_smem = (size_t)(W / 2) * line_smem(ly) * cs;
+    g->colW = g->fluxW = W;
+    g->col_smem = g->flux_smem = (size_t)(W / 2) * line_smem(ly) * cs;
     // row kernels: rows per CTA, starting from about 512 nodes per CTA
     const int G = line_G(lx);
     const size_t SM = (size_t)line_smem(lx) * cs;

@@ -93,8 +93,10 @@ void derivative_tables(int N, double d, double win_alpha, double win_p, double *
 // Launch geometry of the four passes for an nx x ny grid and an element size (lbm_api.cu):
 // column tile width and shared memory, rows per CTA and shared memory of the row kernels.
 struct Geometry {
-    int colW = 2;
+    int colW = 2;            // column pass of the f and macroscopic fields
     size_t col_smem = 0;
+    int fluxW = 2;           // flux column pass (tuned apart: 4 jobs instead of 17)
+    size_t flux_smem = 0;
     int rows_upd = 1, rows_macro = 1, rows_rowd = 1;
     size_t upd_smem = 0, macro_smem = 0, rowd_smem = 0;
 };
