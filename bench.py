@@ -126,7 +126,7 @@ def make_fields(lbm, synthetic, n=N_GRID, radius=RADIUS):
     return synthetic.droplet(n, n, radius, rl, rv, T0, width=2.0)
 
 
-def time_path(lbm, torch, precision, steps, warmup, fields, stream):
+def time_path(lbm, torch, precision, steps, warmup, fields, stream, autotune=True):
     """Two timed loops of `steps` steps each on the same state, an L2 flush between steps.
     Loop A (the headline): lbm_step as the library runs it (one CUDA graph per step), one event
     pair around each step. Loop B: per-launch timing on (direct launches, an event pair around
@@ -148,7 +148,7 @@ def time_path(lbm, torch, precision, steps, warmup, fields, stream):
 
     with lbm.Simulation(N_GRID, N_GRID, p, stream=stream.cuda_stream) as sim:
         sim.init(*fields)
-        geometry, _ = sim.autotune()  # launch shapes by measurement, before any timed step
+        geometry = sim.autotune()[0] if autotune else sim.geometry()  # launch shapes, before any timed step
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 sim.step(1)
@@ -289,6 +289,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched form and the error table")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (for profiler runs, whose timing would mislead the tuner)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
@@ -318,7 +320,7 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
         step_ms, kern, wall, diag, step_ms_b, geom = time_path(lbm, torch, lbm.LBM_MIXED, args.steps, args.warmup,
-                                                                fields, stream)
+                                                                fields, stream, not args.no_autotune)
     clocks = clk.summary()
     total_ms = sum(step_ms)
     if world > 1:
@@ -330,7 +332,8 @@ def main():
 
     # FP64 path on the same workload (plain method)
     k64 = args.fp64_steps or max(3, args.steps // 10)
-    step64, kern64, _, _, _, geom64 = time_path(lbm, torch, lbm.LBM_FP64, k64, min(args.warmup, 3), fields, stream)
+    step64, kern64, _, _, _, geom64 = time_path(lbm, torch, lbm.LBM_FP64, k64, min(args.warmup, 3), fields, stream,
+                                                not args.no_autotune)
     fp64_mlups = n * k64 / (sum(step64) * 1e-3) / 1e6
 
     dom = max(kern, key=lambda k: kern[k][0])
@@ -384,7 +387,7 @@ def main():
                        "launch": "lbm_step: one CUDA graph per step (8 kernels)",
                        "launch_shapes": {"col_tile_width": geom[0], "macro_rows_per_cta": geom[1],
                                          "update_rows_per_cta": geom[2], "flux_tile_width": geom[3],
-                                         "chosen_by": "lbm_autotune"},
+                                         "chosen_by": "defaults" if args.no_autotune else "lbm_autotune"},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_mlups, "unit": "MLUPS", "steps": k64, "launch_shapes": list(geom64),
                           "ms_per_step": sum(step64) / k64,

@@ -169,6 +169,9 @@ size_t lbm_device_bytes(lbm_handle h);
  * results do not depend on the shapes. Needs an initialised state; allocates a temporary
  * device buffer of 4 fields; synchronises the stream. */
 int lbm_geometry(lbm_handle h, int geometry[4]);
+/* Sets the launch shapes (same meaning as lbm_geometry) to any of the autotuner's legal
+ * candidates (LBM_ERR_ARG otherwise); results do not depend on them. Synchronises. */
+int lbm_set_geometry(lbm_handle h, const int geometry[4]);
 int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
 
 /* lbm_diagnostics for callers that cannot allocate device memory. The paper has no

@@ -75,6 +75,7 @@ _SIGS = {
     "lbm_batch_diagnostics": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "lbm_batch_destroy": (None, [_P]),
     "lbm_geometry": (ctypes.c_int, [_P, _P]),
+    "lbm_set_geometry": (ctypes.c_int, [_P, _P]),
     "lbm_structure_factor": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "lbm_batch_structure_factor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "lbm_autotune": (ctypes.c_int, [_P, _P, _P]),
@@ -251,6 +252,10 @@ class Simulation:
         g = (ctypes.c_int * 4)()
         _check(lib().lbm_geometry(self._h, ctypes.cast(g, _P)))
         return tuple(g)
+
+    def set_geometry(self, geometry):
+        g = (ctypes.c_int * 4)(*[int(v) for v in geometry])
+        _check(lib().lbm_set_geometry(self._h, ctypes.cast(g, _P)))
 
     def autotune(self):
         """Times the launch-shape candidates on this simulation and keeps the fastest;

@@ -529,8 +529,7 @@ template <typename R, int LOG2N> static cudaError_t launch_update_n(const Update
                                                                     cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N>;
     constexpr bool MS = sizeof(R) == 4;  // float32: moment-space collision
-    cudaError_t e = cudaFuncSetAttribute(update_row_kernel<R, LOG2N, MS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(update_row_kernel<R, LOG2N, MS>);
     if (e != cudaSuccess) return e;
     // LB line transforms at a time; at least one thread per node of the CTA's rows (up to the cap)
     constexpr int cap = PassThreads<R>::value;
@@ -546,8 +545,7 @@ template <typename R, int LOG2N> static cudaError_t launch_update_n(const Update
 template <typename R, int LOG2N> static cudaError_t launch_macro_n(const MacroArgs<R> &a, size_t smem,
                                                                    cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N>;
-    cudaError_t e =
-        cudaFuncSetAttribute(macro_row_kernel<R, LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N>);
     if (e != cudaSuccess) return e;
     macro_row_kernel<R, LOG2N><<<a.ny / a.rows, 2 * a.rows * F::G, smem, s>>>(a);
     return cudaGetLastError();

@@ -59,8 +59,7 @@ __global__ void __launch_bounds__(256) sf_col_kernel(const __grid_constant__ SfA
 template <typename R, int LOG2N> static cudaError_t sf_rows(const SfArgs &a, cudaStream_t s) {
     using F = reg::LineFFT<double, LOG2N>;
     const size_t smem = (size_t)a.rows * F::STRIDE * sizeof(double2);
-    cudaError_t e = cudaFuncSetAttribute(sf_row_kernel<R, LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_smem(sf_row_kernel<R, LOG2N>);
     if (e != cudaSuccess) return e;
     sf_row_kernel<R, LOG2N><<<a.ny / a.rows, a.rows * F::G, smem, s>>>(a);
     return cudaGetLastError();
@@ -69,7 +68,7 @@ template <typename R, int LOG2N> static cudaError_t sf_rows(const SfArgs &a, cud
 template <int LOG2N> static cudaError_t sf_cols(const SfArgs &a, cudaStream_t s) {
     using F = reg::LineFFT<double, LOG2N>;
     const size_t smem = (size_t)((a.nbins * 8 + 15) & ~15) + (size_t)a.cols * F::STRIDE * sizeof(double2);
-    cudaError_t e = cudaFuncSetAttribute(sf_col_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(sf_col_kernel<LOG2N>);
     if (e != cudaSuccess) return e;
     sf_col_kernel<LOG2N><<<a.nx / a.cols, a.cols * F::G, smem, s>>>(a);
     return cudaGetLastError();

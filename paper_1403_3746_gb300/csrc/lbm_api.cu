@@ -5,6 +5,7 @@
 // passes are row-local and treat them as one nx x (nb ny) grid, the column passes take the
 // instance from grid.z. A batch (lbm_batch_*) groups instances of different sizes into
 // contexts, one per size, whose steps run as parallel branches of one CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1003,6 +1004,32 @@ int lbm_geometry(lbm_handle c, int geometry[4]) {
     geometry[1] = c->geo.rows_macro;
     geometry[2] = c->geo.rows_upd;
     geometry[3] = c->geo.fluxW;
+    return LBM_OK;
+}
+
+int lbm_set_geometry(lbm_handle c, const int geometry[4]) {
+    if (!c || !geometry) return fail(LBM_ERR_ARG, "NULL argument");
+    auto has = [](const std::vector<int> &v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
+    const std::vector<int> cw = col_candidates(c);
+    if (!has(cw, geometry[0]) || !has(cw, geometry[3]))
+        return fail(LBM_ERR_ARG, "column tile widths %d, %d are not valid for %d x %d", geometry[0], geometry[3], c->nx,
+                    c->ny);
+    if (!has(macro_candidates(c), geometry[1])) return fail(LBM_ERR_ARG, "macro rows per CTA %d not valid", geometry[1]);
+    if (!has(upd_candidates(c), geometry[2])) return fail(LBM_ERR_ARG, "update rows per CTA %d not valid", geometry[2]);
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    const size_t es = c->fsize, SMc = (size_t)line_smem(c->ly) * 2 * es, SMr = (size_t)line_smem(c->lx) * 2 * es;
+    c->geo.colW = geometry[0];
+    c->geo.col_smem = (size_t)(geometry[0] / 2) * SMc;
+    c->geo.fluxW = geometry[3];
+    c->geo.flux_smem = (size_t)(geometry[3] / 2) * SMc;
+    c->geo.rows_macro = geometry[1];
+    c->geo.macro_smem = 3 * geometry[1] * SMr + (size_t)geometry[1] * c->nx * es;
+    c->geo.rows_upd = geometry[2];
+    c->geo.upd_smem = 6 * geometry[2] * SMr;
+    if (c->graph) {  // recaptured with the new shapes at the next step
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     return LBM_OK;
 }
 

@@ -222,6 +222,20 @@ struct SfArgs {
     double *S;               // [nbins] sums of |rho_hat|^2 / (nx ny) per shell (zeroed by the caller)
 };
 
+// Lets kernel `kern` use the device's whole opt-in dynamic shared memory per CTA. The limit is
+// a property of the kernel function, not of a launch: a captured CUDA graph launches its
+// nodes later, when another launch of the same function (another simulation, another pass
+// with a different tile shape) may have set a smaller limit, so it is raised to the maximum
+// once and never lowered. The shared memory a launch actually uses (its occupancy) is its own
+// dynamic size.
+template <typename K> inline cudaError_t allow_smem(K kern) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    return e;
+}
+
 // launchers (kernels_*.cu); all return cudaGetLastError() of the launch
 template <typename R> cudaError_t launch_col(const ColArgs<R> &a, int njobs, size_t smem, cudaStream_t s);
 template <typename R> cudaError_t launch_macro(const MacroArgs<R> &a, size_t smem, cudaStream_t s);

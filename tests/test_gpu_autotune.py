@@ -70,3 +70,29 @@ def test_autotune_needs_state():
     with lbm.Simulation(32, 32, lbm.default_params(**PHASE)) as s:
         with pytest.raises(lbm.LbmError, match="call out of order"):
             s.autotune()
+
+
+def test_graph_with_unequal_tile_shapes():
+    # one step graph holds the column pass and the flux pass (the same kernel) with different
+    # tile widths, and a second simulation of the same size launches it with other shapes in
+    # between: every launch must still run (the kernel's shared-memory allowance is the
+    # device maximum), with results bit for bit those of the default shapes
+    n = 256
+    p = lbm.default_params(precision=lbm.LBM_MIXED, **PHASE)
+    fields = droplet(n)
+    with lbm.Simulation(n, n, p) as a, lbm.Simulation(n, n, p) as b, lbm.Simulation(n, n, p) as c:
+        for s in (a, b, c):
+            s.init(*fields)
+        a.set_geometry((64, 1, 1, 4))
+        b.set_geometry((4, 2, 2, 64))
+        assert a.geometry() == (64, 1, 1, 4)
+        for _ in range(3):
+            a.step(2)
+            b.step(2)
+            c.step(2)
+        ref = c.get_f()
+        assert np.array_equal(a.get_f(), ref) and np.array_equal(b.get_f(), ref)
+        with pytest.raises(lbm.LbmError, match="not valid"):
+            a.set_geometry((3, 1, 1, 4))
+        with pytest.raises(lbm.LbmError, match="not valid"):
+            a.set_geometry((64, 1, 3, 4))
