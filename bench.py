@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -220,6 +222,45 @@ def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream):
             "ms_per_step": ms / steps, "nodes": nodes, "finite": ok, "launch_shapes": shapes}
 
 
+LARGE_N = 4096
+
+
+def large_run(lbm, torch, synthetic, steps, stream):
+    """The large single run: a 4096^2 spinodal quench (rho = 1 +/- 1%, T = 0.9, seed 5) in
+    LBM_MIXED, timed over `steps` graph-launched steps (inputs far larger than L2), then the
+    circularly averaged structure factor after those steps against the FP64 path from the
+    same seed."""
+    fields = synthetic.spinodal(LARGE_N, LARGE_N, 1.0, 0.01, 0.9, seed=5)
+    n = LARGE_N * LARGE_N
+    nbins = 256
+    out = {"workload": f"spinodal quench {LARGE_N}x{LARGE_N}, rho = 1 +/- 1% (seed 5), T = 0.9", "steps": steps}
+    S = {}
+    for prec, name in ((lbm.LBM_MIXED, "mixed"), (lbm.LBM_FP64, "fp64")):
+        p = lbm.default_params(precision=prec, **PARAMS)
+        with lbm.Simulation(LARGE_N, LARGE_N, p, stream=stream.cuda_stream) as sim:
+            sim.init(*fields)
+            sim.autotune()
+            with torch.cuda.stream(stream):
+                sim.step(2)
+                stream.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(steps)
+                e1.record(stream)
+                stream.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            S[name] = sim.structure_factor(nbins)[0]
+            out[name] = {"value": n / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+                         "launch_shapes": list(sim.geometry())}
+    out["mixed"]["step_frac_of_hbm_roofline"] = (ELEMS_PER_NODE_STEP * 4 * n / (out["mixed"]["ms_per_step"] * 1e-3)
+                                                 / 1e9 / peaks()[0])
+    k = int(np.argmax(S["fp64"][1:])) + 1
+    out["structure_factor"] = {"shells": nbins, "peak_shell_fp64": k,
+                               "rel_l2_mixed_vs_fp64": float(np.linalg.norm(S["mixed"] - S["fp64"])
+                                                             / np.linalg.norm(S["fp64"]))}
+    return out
+
+
 ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
@@ -361,6 +402,7 @@ def main():
             from paper_1403_3746_gb300 import accuracy
             tab = accuracy.error_table()
             sl, dr = tab["slab"]["rows"], tab["droplet"]["rows"]
+            extras["large_run"] = large_run(lbm, torch, synthetic, max(20, args.steps // 2), stream)
             extras["accuracy_mixed_vs_fp64"] = {
                 "coexistence_rel_err_max": max(max(r["rel_err_rho_l"], r["rel_err_rho_v"]) for r in sl),
                 "mass_drift_mixed_max": max(abs(r["mass_drift_mixed"]) for r in sl + dr),

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
 template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R> &a, int njobs, size_t smem,
                                                                   cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N>;
+    if (smem < (size_t)(a.W / 2) * F::STRIDE * sizeof(typename F::CT)) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(col_deriv_kernel<R, LOG2N>);
     if (e != cudaSuccess) return e;
     dim3 grid(a.nx / a.W, njobs, a.nb > 0 ? a.nb : 1);

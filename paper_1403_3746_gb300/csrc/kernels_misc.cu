@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) row_deriv_kernel(const _
 template <typename R, int LOG2N> static cudaError_t launch_row_deriv_n(const RowDerivArgs<R> &a, size_t smem,
                                                                        cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N>;
+    if (smem < (size_t)((a.nin + 1) / 2) * a.rows * F::STRIDE * sizeof(typename F::CT)) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(row_deriv_kernel<R, LOG2N>);
     if (e != cudaSuccess) return e;
     row_deriv_kernel<R, LOG2N><<<a.ny / a.rows, ((a.nin + 1) / 2) * a.rows * F::G, smem, s>>>(a);

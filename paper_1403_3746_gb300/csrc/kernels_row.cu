@@ -47,7 +47,11 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
 // d_x(div u) term. A second round of lines, (Q_x + i S_xx) and (S_xy + i div u), gives
 // d_x Q_x, d_x S_xx, d_x S_xy and d_x(div u), which completes that numerator.
 // ---------------------------------------------------------------------------------------
-template <typename R, int LOG2N>
+// SERIAL = false: the two lines of a row are transformed side by side by two groups of G
+// threads (the B group waits while A computes d_xx rho). SERIAL = true (rows too long for two
+// groups, float64 at nx = 4096): one group transforms A, then B, and K rho d_x rho waits in the
+// global slot of d_x S_xy (free until round 2 writes it) instead of shared memory.
+template <typename R, int LOG2N, bool SERIAL>
 __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R, LOG2N>::min_blocks) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N, true>;
     using CT = typename F::CT;
@@ -58,42 +62,46 @@ __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R,
     // per row three line buffers: A1, A2 (line A) and B1 (line B); then K rho d_x rho per node.
     // The partial numerator of C waits in its own global slot (M_CNUM) between the rounds.
     CT *lines = sb;                                            // [NR][3 SM]
-    R *krx = reinterpret_cast<R *>(sb + (size_t)3 * NR * SM);  // [NR][NX]
+    R *krx = reinterpret_cast<R *>(sb + (size_t)3 * NR * SM);  // [NR][NX] (not SERIAL)
     const int y0 = blockIdx.x * NR;
     const int slot = threadIdx.x / G, t = threadIdx.x % G;
-    const int kind = slot / NR, r = slot % NR;
-    CT *O1 = lines + (size_t)r * 3 * SM + (kind == 0 ? 0 : 2 * SM), *O2 = O1 + SM;  // O2: line A only
+    const int my_kind = SERIAL ? 0 : slot / NR, r = SERIAL ? slot : slot % NR;
     R *mrow = a.m + (size_t)(y0 + r) * NF_M * NX;  // this line's row of the macroscopic block
+    auto buf1 = [&](int kind) { return lines + (size_t)r * 3 * SM + (kind == 0 ? 0 : 2 * SM); };
+    CT *O2 = lines + (size_t)r * 3 * SM + SM;  // line A's second buffer
 
     if (threadIdx.x < NR)  // the node loop's inputs from the column pass start moving into L2
         prefetch_l2(a.m + ((size_t)(y0 + threadIdx.x) * NF_M + M_RY) * NX, 5 * NX * sizeof(R));
 
     // round 1: derivatives of the moments along x
     CT v[E];
+    for (int kind = my_kind; kind <= (SERIAL ? 1 : my_kind); ++kind) {
+        CT *O1 = buf1(kind);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int x = t + G * e;
-        v[e] = kind == 0 ? reg::mk<R>(mrow[M_RHO * NX + x], mrow[M_T * NX + x])
-                         : reg::mk<R>(mrow[M_UX * NX + x], mrow[M_UY * NX + x]);
-    }
-    F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
-    if (kind == 0) F::storeF(v, O2, t);  // keep the spectrum of A for d_xx rho (thread-private slots)
-    F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
-    F::template inverse<reg::SyncCta>(v, O1, t, a.ax.tw);
-    __syncthreads();
+        for (int e = 0; e < E; ++e) {
+            const int x = t + G * e;
+            v[e] = kind == 0 ? reg::mk<R>(mrow[M_RHO * NX + x], mrow[M_T * NX + x])
+                             : reg::mk<R>(mrow[M_UX * NX + x], mrow[M_UY * NX + x]);
+        }
+        F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
+        if (kind == 0) F::storeF(v, O2, t);  // keep the spectrum of A for d_xx rho (thread-private slots)
+        F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+        F::template inverse<reg::SyncCta>(v, O1, t, a.ax.tw);
+        reg::cta_barrier();
 #pragma unroll
-    for (int e = 0; e < E; ++e) O1[t + G * e] = v[e];
-    if (kind == 0) {
-        F::loadF(v, O2, t);
-        F::multiply(v, t, 2, R(1), a.ax.k1, a.ax.k2);
-        F::template inverse<reg::SyncCta>(v, O2, t, a.ax.tw);
-    } else {
-        F::template idle<reg::SyncCta>();
-    }
-    __syncthreads();
-    if (kind == 0) {
+        for (int e = 0; e < E; ++e) O1[t + G * e] = v[e];
+        if (kind == 0) {
+            F::loadF(v, O2, t);
+            F::multiply(v, t, 2, R(1), a.ax.k1, a.ax.k2);
+            F::template inverse<reg::SyncCta>(v, O2, t, a.ax.tw);
+        } else if (!SERIAL) {
+            F::template idle<reg::SyncCta>();
+        }
+        reg::cta_barrier();
+        if (kind == 0) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) O2[t + G * e] = v[e];
+            for (int e = 0; e < E; ++e) O2[t + G * e] = v[e];
+        }
     }
     __syncthreads();
 
@@ -130,7 +138,8 @@ __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R,
         const R r_gradu_r = rx * (dux_dx * rx + duy_dx * ry) + ry * (dux_dy * rx + duy_dy * ry);
         mn[M_CNUM * NX] = (Pw - rT) * divu + L_gradu - zeta * divu * divu + R(1.125) * rho * rho * divu +
                           K * (-R(0.5) * grr * divu - r_gradu_r);
-        krx[idx] = K * rho * rx;
+        if constexpr (SERIAL) mn[M_DSXY * NX] = K * rho * rx;
+        else krx[idx] = K * rho * rx;
         mn[M_QY * NX] = Qy;
         mn[M_SXY * NX] = Sxy;
         mn[M_SYY * NX] = Syy;
@@ -141,21 +150,25 @@ __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R,
     __syncthreads();
 
     // round 2: d_x of (Q_x, S_xx) on line A and of (S_xy, div u) on line B
+    for (int kind = my_kind; kind <= (SERIAL ? 1 : my_kind); ++kind) {
+        CT *O1 = buf1(kind);
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = O1[t + G * e];
-    F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
-    F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
-    F::template inverse<reg::SyncCta>(v, O1, t, a.ax.tw);
+        for (int e = 0; e < E; ++e) v[e] = O1[t + G * e];
+        F::template forward<reg::SyncCta>(v, O1, t, a.ax.tw);
+        F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+        F::template inverse<reg::SyncCta>(v, O1, t, a.ax.tw);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int x = t + G * e;
-        if (kind == 0) {
-            mrow[M_DQX * NX + x] = v[e].x;
-            mrow[M_DSXX * NX + x] = v[e].y;
-        } else {
-            mrow[M_DSXY * NX + x] = v[e].x;
-            // - K rho d_x rho d_x(div u); the partial value was written by this CTA's node loop
-            mrow[M_CNUM * NX + x] -= krx[r * NX + x] * v[e].y;
+        for (int e = 0; e < E; ++e) {
+            const int x = t + G * e;
+            if (kind == 0) {
+                mrow[M_DQX * NX + x] = v[e].x;
+                mrow[M_DSXX * NX + x] = v[e].y;
+            } else {
+                // - K rho d_x rho d_x(div u); the partial value was written by this CTA's node loop
+                const R k = SERIAL ? mrow[M_DSXY * NX + x] : krx[r * NX + x];
+                mrow[M_DSXY * NX + x] = v[e].x;
+                mrow[M_CNUM * NX + x] -= k * v[e].y;
+            }
         }
     }
 }
@@ -335,6 +348,9 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
     const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
     const bool same_base = a.fbase == a.fs;
     const bool iso = a.flags & LBM_FLAG_ISOTHERMAL;
+    // d_x f_i from global memory instead of the row transforms: only float64 rows of 4096 need it
+    constexpr bool AX_POSSIBLE = sizeof(R) == 8 && LOG2N == 12;
+    const bool ax_mode = AX_POSSIBLE && a.Ax != nullptr;
 
     // the node loop's other inputs start moving into L2 while the lines are transformed
     if (threadIdx.x < NR) {
@@ -342,11 +358,12 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         prefetch_l2(a.fs + y * NF_F * NX, NF_F * NX * sizeof(R));
         if (adv) prefetch_l2(a.Ay + y * NF_A * NX, NF_A * NX * sizeof(R));
         if (!same_base) prefetch_l2(a.fbase + y * NF_F * NX, NF_F * NX * sizeof(R));
+        if (adv && ax_mode) prefetch_l2(a.Ax + y * NF_F * NX, NF_F * NX * sizeof(R));
         prefetch_l2(a.m + y * NF_M * NX, (M_RY + 1) * NX * sizeof(R));
         if (frc) prefetch_l2(a.m + (y * NF_M + M_DQX) * NX, (NF_M - M_DQX) * NX * sizeof(R));
     }
 
-    if (adv) {
+    if (adv && !ax_mode) {
         // 6 lines per row (the 12 fields with v_x != 0, paired); LB lines per batch (LB divides
         // 6 NR); threads past LB G only take part in the barriers
         const int LB = a.lines_per_batch;
@@ -420,8 +437,12 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
                 R ad = 0;
                 constexpr int xs = xslot(i), ys = yslot(i);
                 if constexpr (xs >= 0) {
-                    const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + x];
-                    ad += R(vel_x(i)) * ((xs & 1) ? d.y : d.x);
+                    if (ax_mode) {
+                        ad += R(vel_x(i)) * ldcg(a.Ax + (y * NF_F + i) * NX + x);
+                    } else {
+                        const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + x];
+                        ad += R(vel_x(i)) * ((xs & 1) ? d.y : d.x);
+                    }
                 }
                 if constexpr (ys >= 0) ad += ldcg(an + ys * NX);
                 dfo -= h * ad;
@@ -531,6 +552,11 @@ template <typename R, int LOG2N> static cudaError_t launch_update_n(const Update
     constexpr bool MS = sizeof(R) == 4;  // float32: moment-space collision
     cudaError_t e = allow_smem(update_row_kernel<R, LOG2N, MS>);
     if (e != cudaSuccess) return e;
+    // the in-kernel row transforms need 6 line buffers per row; refuse a launch without them
+    const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
+    if (adv && a.Ax == nullptr && smem < (size_t)6 * a.rows * F::STRIDE * sizeof(typename F::CT))
+        return cudaErrorInvalidValue;
+    if (a.Ax != nullptr && !(sizeof(R) == 8 && LOG2N == 12)) return cudaErrorInvalidValue;
     // LB line transforms at a time; at least one thread per node of the CTA's rows (up to the cap)
     constexpr int cap = PassThreads<R>::value;
     UpdateArgs<R> b = a;
@@ -545,9 +571,22 @@ template <typename R, int LOG2N> static cudaError_t launch_update_n(const Update
 template <typename R, int LOG2N> static cudaError_t launch_macro_n(const MacroArgs<R> &a, size_t smem,
                                                                    cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N>;
-    cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N>);
+    // three line buffers per row, plus K rho d_x rho per node unless serial; refuse less
+    const size_t need = (size_t)3 * a.rows * F::STRIDE * sizeof(typename F::CT) +
+                        (a.serial ? 0 : (size_t)a.rows * F::N * sizeof(R));
+    if (smem < need) return cudaErrorInvalidValue;
+    if constexpr (sizeof(R) == 8 && LOG2N == 12) {  // the only shape that needs the serial form
+        if (a.serial) {
+            cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, true>);
+            if (e != cudaSuccess) return e;
+            macro_row_kernel<R, LOG2N, true><<<a.ny / a.rows, a.rows * F::G, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    if (a.serial) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, false>);
     if (e != cudaSuccess) return e;
-    macro_row_kernel<R, LOG2N><<<a.ny / a.rows, 2 * a.rows * F::G, smem, s>>>(a);
+    macro_row_kernel<R, LOG2N, false><<<a.ny / a.rows, 2 * a.rows * F::G, smem, s>>>(a);
     return cudaGetLastError();
 }
 

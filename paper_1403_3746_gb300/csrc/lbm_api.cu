@@ -108,6 +108,7 @@ struct lbm_ctx {
     void *f0 = nullptr, *f1 = nullptr;  // [nb ny][16][nx]: f^n (then f^{n+1}) and f^{n+1/2}
     void *Ay = nullptr;                 // [nb ny][12][nx]
     void *m = nullptr;                  // [nb ny][NF_M][nx]
+    void *Ax = nullptr;                 // [nb ny][16][nx]: d_x f_i, only when geo.upd_ax
     double *partial = nullptr;
     int diag_blocks = 0;
     // per-axis tables
@@ -241,6 +242,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
             MacroArgs<R> a{};
             a.m = m;
             a.nx = nx; a.ny = rows; a.rows = c->geo.rows_macro;
+            a.serial = c->geo.macro_serial ? 1 : 0;
             a.ax = axis<R>(c, true);
             a.K = (R)p.K; a.H = (R)p.H; a.q = (R)p.q; a.zeta = (R)p.zeta;
             LaunchTimer t(c, LBM_K_MACRO);
@@ -258,9 +260,28 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
             CU_TRY(launch_col<R>(a, 4, c->geo.flux_smem, c->stream));
         }
     }
+    if ((passes & PASS_UPDATE) && adv && c->geo.upd_ax) {
+        // d_x f_i of the 12 fields with v_x != 0 into Ax, two fields per complex line
+        for (int k = 0; k < 12; k += 2) {
+            RowDerivArgs<R> ra{};
+            ra.in[0] = fs + (size_t)xfield(k) * nx;
+            ra.in[1] = fs + (size_t)xfield(k + 1) * nx;
+            ra.out[0] = static_cast<R *>(c->Ax) + (size_t)xfield(k) * nx;
+            ra.out[1] = static_cast<R *>(c->Ax) + (size_t)xfield(k + 1) * nx;
+            ra.ld = ldf;
+            ra.nin = 2;
+            ra.nx = nx;
+            ra.ny = rows;
+            ra.rows = c->geo.rows_rowd;
+            ra.ax = axis<R>(c, true);
+            LaunchTimer t(c, LBM_K_UPDATE);
+            CU_TRY(launch_row_deriv<R>(ra, c->geo.rowd_smem, c->stream));
+        }
+    }
     if (passes & PASS_UPDATE) {
         UpdateArgs<R> a{};
         a.fs = fs;
+        a.Ax = (adv && c->geo.upd_ax) ? static_cast<const R *>(c->Ax) : nullptr;
         a.fbase = f0;
         a.fout = stage == 0 ? f1 : f0;  // stage 2 (Euler): in place, same node, same thread
         a.Ay = Ay;
@@ -333,12 +354,12 @@ std::vector<int> col_candidates(const lbm_ctx *c) {
             out.push_back(W);
     return out;
 }
-// Candidate rows per CTA of the update pass (6 line buffers per row, at most 200 KB).
+// Candidate rows per CTA of the update pass (6 line buffers per row within a CTA's shared memory).
 std::vector<int> upd_candidates(const lbm_ctx *c) {
     std::vector<int> out;
     const size_t SM = (size_t)line_smem(c->lx) * 2 * c->fsize;
     for (int r = 1; r <= c->ny && r * c->nx <= 4096; r *= 2)
-        if (6 * r * SM <= 200 * 1024) out.push_back(r);
+        if (6 * r * SM <= kMaxCtaSmem) out.push_back(r);
     return out;
 }
 // Candidate rows per CTA of the macro pass (two lines per row within its thread bound).
@@ -347,7 +368,7 @@ std::vector<int> macro_candidates(const lbm_ctx *c) {
     const size_t SM = (size_t)line_smem(c->lx) * 2 * c->fsize;
     for (int r = 1; r <= c->ny && r * c->nx <= 4096; r *= 2)
         if (2 * r * line_G(c->lx) <= macro_threads(c->fsize, c->lx) &&
-            3 * r * SM + (size_t)r * c->nx * c->fsize <= 200 * 1024)
+            3 * r * SM + (size_t)r * c->nx * c->fsize <= kMaxCtaSmem)
             out.push_back(r);
     return out;
 }
@@ -422,7 +443,7 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
     }
     const size_t SM = (size_t)line_smem(c->lx) * 2 * es;
     best_ms[1] = 0;
-    if (frc) {
+    if (frc && !c->geo.macro_serial) {
         int bestr = c->geo.rows_macro;
         float bt = 1e30f;
         for (int r : macro_candidates(c)) {
@@ -433,9 +454,10 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
         }
         c->geo.rows_macro = bestr;
         c->geo.macro_smem = 3 * bestr * SM + (size_t)bestr * c->nx * es;
-        best_ms[1] = bt;
+        best_ms[1] = bt < 1e30f ? bt : 0.0f;
     }
-    {
+    best_ms[2] = 0;
+    if (!c->geo.upd_ax) {
         int bestr = c->geo.rows_upd;
         float bt = 1e30f;
         for (int r : upd_candidates(c)) {
@@ -446,7 +468,7 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
         }
         c->geo.rows_upd = bestr;
         c->geo.upd_smem = 6 * bestr * SM;
-        best_ms[2] = bt;
+        best_ms[2] = bt < 1e30f ? bt : 0.0f;
     }
     if (cudaMemcpy2DAsync(c->m, NF_M * c->nx * es, save, 4 * c->nx * es, 4 * c->nx * es, rows,
                           cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
@@ -552,6 +574,7 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     parts.push_back({&c->f1, 16 * plane_f});
     parts.push_back({&c->Ay, 12 * plane_f});
     parts.push_back({&c->m, (size_t)NF_M * plane_f});
+    if (c->geo.upd_ax) parts.push_back({&c->Ax, 16 * plane_f});
     parts.push_back({reinterpret_cast<void **>(&c->partial), (size_t)c->diag_blocks * 5 * 8});
     parts.push_back({reinterpret_cast<void **>(&c->tw64x), (size_t)nx * 16});
     parts.push_back({reinterpret_cast<void **>(&c->tw64y), (size_t)ny * 16});
@@ -1014,18 +1037,25 @@ int lbm_set_geometry(lbm_handle c, const int geometry[4]) {
     if (!has(cw, geometry[0]) || !has(cw, geometry[3]))
         return fail(LBM_ERR_ARG, "column tile widths %d, %d are not valid for %d x %d", geometry[0], geometry[3], c->nx,
                     c->ny);
-    if (!has(macro_candidates(c), geometry[1])) return fail(LBM_ERR_ARG, "macro rows per CTA %d not valid", geometry[1]);
-    if (!has(upd_candidates(c), geometry[2])) return fail(LBM_ERR_ARG, "update rows per CTA %d not valid", geometry[2]);
+    // the macro and update shapes are fixed where their serial / separate-row-pass forms run
+    if (c->geo.macro_serial ? geometry[1] != c->geo.rows_macro : !has(macro_candidates(c), geometry[1]))
+        return fail(LBM_ERR_ARG, "macro rows per CTA %d not valid", geometry[1]);
+    if (c->geo.upd_ax ? geometry[2] != c->geo.rows_upd : !has(upd_candidates(c), geometry[2]))
+        return fail(LBM_ERR_ARG, "update rows per CTA %d not valid", geometry[2]);
     CU_TRY(cudaStreamSynchronize(c->stream));
     const size_t es = c->fsize, SMc = (size_t)line_smem(c->ly) * 2 * es, SMr = (size_t)line_smem(c->lx) * 2 * es;
     c->geo.colW = geometry[0];
     c->geo.col_smem = (size_t)(geometry[0] / 2) * SMc;
     c->geo.fluxW = geometry[3];
     c->geo.flux_smem = (size_t)(geometry[3] / 2) * SMc;
-    c->geo.rows_macro = geometry[1];
-    c->geo.macro_smem = 3 * geometry[1] * SMr + (size_t)geometry[1] * c->nx * es;
-    c->geo.rows_upd = geometry[2];
-    c->geo.upd_smem = 6 * geometry[2] * SMr;
+    if (!c->geo.macro_serial) {
+        c->geo.rows_macro = geometry[1];
+        c->geo.macro_smem = 3 * geometry[1] * SMr + (size_t)geometry[1] * c->nx * es;
+    }
+    if (!c->geo.upd_ax) {
+        c->geo.rows_upd = geometry[2];
+        c->geo.upd_smem = 6 * geometry[2] * SMr;
+    }
     if (c->graph) {  // recaptured with the new shapes at the next step
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -1325,6 +1355,10 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     while (r > 1 && 6 * r * SM > 200 * 1024) r >>= 1;  // update: 6 line buffers per row
     g->rows_upd = r;
     g->upd_smem = 6 * (size_t)r * SM;
+    // a row whose 6 line buffers exceed a CTA's shared memory (float64, nx = 4096: 418 KB) takes
+    // its x-derivatives from a separate row pass instead (float32 at 4096 needs 209 KB and fits)
+    g->upd_ax = g->upd_smem > kMaxCtaSmem;
+    if (g->upd_ax) g->upd_smem = 0;
     r = r0;
     // macro: 2 lines per row with 3 buffers, plus 1 value per node
     auto macro_bytes = [&](int rr) { return 3 * (size_t)rr * SM + (size_t)rr * nx * esize; };
@@ -1332,6 +1366,10 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     while (r > 1 && (2 * r * G > mact || macro_bytes(r) > 200 * 1024)) r >>= 1;
     g->rows_macro = r;
     g->macro_smem = macro_bytes(r);
+    // one row's two thread groups do not fit (float64, nx = 4096): one group, lines in turn,
+    // and K rho d_x rho in a global slot instead of shared memory
+    g->macro_serial = 2 * G > mact || g->macro_smem > kMaxCtaSmem;
+    if (g->macro_serial) g->macro_smem = 3 * (size_t)SM;
     r = r0;
     while (r > 1 && r * G > maxt) r >>= 1;  // one line per row (diagnostics)
     g->rows_rowd = r;

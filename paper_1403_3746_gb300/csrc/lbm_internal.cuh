@@ -92,6 +92,9 @@ void derivative_tables(int N, double d, double win_alpha, double win_p, double *
 
 // Launch geometry of the four passes for an nx x ny grid and an element size (lbm_api.cu):
 // column tile width and shared memory, rows per CTA and shared memory of the row kernels.
+// opt-in dynamic shared memory per CTA on sm_100 / sm_103 (227 KB)
+constexpr size_t kMaxCtaSmem = 232448;
+
 struct Geometry {
     int colW = 2;            // column pass of the f and macroscopic fields
     size_t col_smem = 0;
@@ -99,6 +102,8 @@ struct Geometry {
     size_t flux_smem = 0;
     int rows_upd = 1, rows_macro = 1, rows_rowd = 1;
     size_t upd_smem = 0, macro_smem = 0, rowd_smem = 0;
+    bool upd_ax = false;        // update pass takes d_x f from a separate row pass (Ax)
+    bool macro_serial = false;  // macro pass transforms a row's two lines in turn
 };
 void pass_geometry(int nx, int ny, size_t esize, Geometry *g);
 
@@ -149,6 +154,7 @@ template <typename R> struct ColArgs {
 template <typename R> struct MacroArgs {
     R *m;  // macroscopic block [ny][NF_M][nx]
     int nx, ny, rows;
+    int serial;  // one thread group transforms both lines of a row in turn (float64, nx = 4096)
     Axis<R> ax;
     R K, H, q, zeta;
 };
@@ -159,6 +165,8 @@ template <typename R> struct UpdateArgs {
     const R *fbase;  // f^n (the stage starts from it)
     R *fout;         // f^{n+1/2} or f^{n+1}; may alias fbase (same node, same thread)
     const R *Ay;     // [ny][12][nx]: v_iy d_y f_i
+    const R *Ax;     // nullptr: the kernel transforms its rows; else [ny][16][nx]: d_x f_i from a
+                     // separate row pass (rows too long for the kernel's shared memory)
     R *m;            // macroscopic block; moments of fs in, moments of fout out
     int nx, ny, rows;
     int lines_per_batch;  // line transforms in flight per batch (the other threads wait)
