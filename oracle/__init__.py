@@ -12,7 +12,8 @@ float64 numpy over whole fields:
   model.py    Sec. 2.2, Eqs. (1)-(2): van der Waals EOS, stress Lambda, the forcing
               term I_i; Sec. 2.3: the two-stage Runge-Kutta step
   maxwell.py  Sec. 3.1: Maxwell construction for the van der Waals coexistence curve
-  diag.py     Sec. 2.2 / 3.2: total mass, momentum, total energy e_T, max |u|
+  diag.py     Sec. 2.2 / 3.2: total mass, momentum, total energy e_T, max |u|, and the
+              circularly averaged structure factor of the density
 
 Readings of silent or garbled passages are listed where they are used.
 Parity status: every function here is pinned by `tests/test_oracle_*.py` except the

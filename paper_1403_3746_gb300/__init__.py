@@ -137,6 +137,17 @@ def diagnostics_noalloc(params, rho, ux, uy, T, stream=None):
     return dict(zip(("mass", "px", "py", "energy", "umax"), list(out)))
 
 
+def _host_out(out, shape):
+    """Four writable host arrays for a moments call: new ones, or the caller's after a check."""
+    if out is None:
+        return [np.empty(shape) for _ in range(4)]
+    out = list(out)
+    if len(out) != 4 or not all(isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == tuple(shape)
+                                and a.flags.c_contiguous and a.flags.writeable for a in out):
+        raise ValueError(f"out: four writable C-contiguous float64 arrays of shape {tuple(shape)}")
+    return out
+
+
 def _host(a, shape):
     a = np.ascontiguousarray(a, dtype=np.float64)
     if a.shape != shape:
@@ -204,9 +215,10 @@ class Simulation:
     def synchronize(self):
         _check(lib().lbm_synchronize(self._h))
 
-    def moments(self):
-        """(rho, u_x, u_y, T) as host numpy arrays."""
-        out = [np.empty(self.shape) for _ in range(4)]
+    def moments(self, out=None):
+        """(rho, u_x, u_y, T) as host numpy arrays; `out`: four C-contiguous float64 arrays of
+        shape (ny, nx) to fill instead (pinned ones take the fast copy path)."""
+        out = _host_out(out, self.shape)
         _check(lib().lbm_moments(self._h, *[_ptr(a) for a in out]))
         return tuple(out)
 
@@ -313,8 +325,8 @@ class Batch:
     def step(self, n=1):
         _check(lib().lbm_batch_step(self._h, int(n)))
 
-    def moments(self, k):
-        out = [np.empty(self._shape(k)) for _ in range(4)]
+    def moments(self, k, out=None):
+        out = _host_out(out, self._shape(k))
         _check(lib().lbm_batch_moments(self._h, int(k), *[_ptr(a) for a in out]))
         return tuple(out)
 

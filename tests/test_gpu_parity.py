@@ -188,6 +188,10 @@ def test_set_get_roundtrip_and_errors():
         mo = oracle.moments(d, f, 2.0)
         for a, b in zip(m, mo):
             assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b)) + 1e-16
+        own = [np.full((32, 32), np.nan) for _ in range(4)]
+        assert all(x is y for x, y in zip(s.moments(out=own), own))
+        for a, b in zip(own, m):
+            assert np.array_equal(a, b)
         bad = f.copy()
         bad[3, 4, 5] = np.nan
         with pytest.raises(lbm.LbmError, match="not finite"):

@@ -101,3 +101,16 @@ def test_variant_defaults(L):
     p = lbm.default_params()
     assert p.keff_terms == 8 and p.T_iso == 0.0 and p.reserved == 0
     assert ctypes.sizeof(lbm.lbm_params) == 12 * 8 + 2 * 4 + 8 + 2 * 4
+
+
+def test_moments_out_arrays_are_checked():
+    from paper_1403_3746_gb300 import _host_out
+    assert [a.shape for a in _host_out(None, (4, 8))] == [(4, 8)] * 4
+    good = [np.zeros((4, 8)) for _ in range(4)]
+    assert _host_out(good, (4, 8)) == good
+    ro = np.zeros((4, 8))
+    ro.flags.writeable = False
+    for bad in (good[:3], [np.zeros((4, 8), np.float32)] + good[1:], [np.zeros((8, 4))] + good[1:],
+                [ro] + good[1:], [np.zeros((4, 16))[:, ::2]] + good[1:]):
+        with pytest.raises(ValueError, match="four writable"):
+            _host_out(bad, (4, 8))
