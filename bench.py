@@ -298,6 +298,23 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x, device):
+    """The largest of every rank's x (the job time of replicas is the slowest rank's); x itself
+    outside an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank, steps, world, job_ms):
+    """All ranks' node updates over the job time, in millions per second."""
+    return world * nodes_per_rank * steps / (job_ms * 1e-3) / 1e6
+
+
 def reference_main(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -361,13 +378,9 @@ def main():
         step_ms, kern, wall, diag, step_ms_b, geom = time_path(lbm, torch, lbm.LBM_MIXED, args.steps, args.warmup,
                                                                 fields, stream, not args.no_autotune)
     clocks = clk.summary()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), "cuda")
     n = N_GRID * N_GRID
-    value = world * n * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_mlups(n, args.steps, world, total_ms)
 
     # FP64 path on the same workload (plain method)
     k64 = args.fp64_steps or max(3, args.steps // 10)
