@@ -403,7 +403,16 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
     void *save = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = LBM_OK;
+    const Geometry geo0 = c->geo;
+    bool saved = false;
     auto done = [&](int code) {
+        if (code != LBM_OK) {  // failed midway: the previous shapes and, if possible, the moments
+            c->geo = geo0;
+            if (saved)
+                cudaMemcpy2DAsync(c->m, NF_M * c->nx * es, save, 4 * c->nx * es, 4 * c->nx * es, rows,
+                                  cudaMemcpyDeviceToDevice, c->stream);
+            cudaStreamSynchronize(c->stream);
+        }
         if (save) cudaFree(save);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -420,6 +429,7 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
     if (cudaMemcpy2DAsync(save, 4 * c->nx * es, c->m, NF_M * c->nx * es, 4 * c->nx * es, rows,
                           cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
         return done(fail(LBM_ERR_CUDA, "autotune: saving the moments failed"));
+    saved = true;
     if ((rc = run_stage<R>(c, 0, PASS_ALL))) return done(rc);
     const bool frc = !(c->p.flags & LBM_FLAG_NO_FORCE);
 
@@ -470,6 +480,7 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
         c->geo.upd_smem = 6 * bestr * SM;
         best_ms[2] = bt < 1e30f ? bt : 0.0f;
     }
+    saved = false;  // restored here, on success as on failure
     if (cudaMemcpy2DAsync(c->m, NF_M * c->nx * es, save, 4 * c->nx * es, 4 * c->nx * es, rows,
                           cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
         return done(fail(LBM_ERR_CUDA, "autotune: restoring the moments failed"));
@@ -1208,12 +1219,16 @@ static int build_batch_graph(lbm_batch b) {
     const size_t G = b->groups.size();
     if (!b->cap) CU_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     if (!b->fork) CU_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-    while (b->branch.size() < G) {
+    while (b->branch.size() < G) {  // a branch stream and its join event, both or neither
         cudaStream_t s;
-        CU_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-        b->branch.push_back(s);
         cudaEvent_t e;
-        CU_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CU_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        const cudaError_t ee = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (ee != cudaSuccess) {
+            cudaStreamDestroy(s);
+            return fail(LBM_ERR_CUDA, "batch graph: cudaEventCreateWithFlags: %s", cudaGetErrorString(ee));
+        }
+        b->branch.push_back(s);
         b->join.push_back(e);
     }
     CU_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
