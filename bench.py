@@ -76,7 +76,8 @@ def ncu_traffic(kernel_key, precision):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while running; entering waits
+    (up to 5 s) for the first sample, so the timed region that follows is covered."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -85,24 +86,38 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.p = None
+        self.lines = []
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line)
+            self.first.set()
+        self.first.set()
 
     def __enter__(self):
+        import threading
+        self.first = threading.Event()
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+            return self
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        self.first.wait(timeout=5)
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
         if self.p:
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except Exception:
                 self.p.kill()
+            self.reader.join(timeout=5)
+        self.out = "".join(self.lines)
 
     def summary(self):
         rows = []
@@ -420,6 +435,7 @@ def main():
                 "mass_drift_fp64_max": max(abs(r["mass_drift_fp64"]) for r in sl + dr),
                 "spurious_velocity_rel_err_max": max(r["rel_err_umax"] for r in dr),
                 "pressure_jump_rel_err_max": max(r["rel_err_dp"] for r in dr),
+                "laplace_dp_R_over_sigma_fp64": {r["R"]: r.get("laplace_fp64") for r in dr},
                 "runs": f"slabs 256x2 at T={[r['T'] for r in sl]}, {tab['slab']['steps']} steps; droplets "
                         f"R={[r['R'] for r in dr]} on 128^2 at T=0.9, {tab['droplet']['steps']} steps"}
 

@@ -5,7 +5,11 @@ stated per physical result of Sec. 3 on the same seeded inputs:
 * relative mass drift over the run;
 * pressure jump P_in - P_out of the van der Waals pressure across a static circular droplet
   (the relaxed state of the droplet runs of Sec. 3.3; Laplace law);
-* spurious (parasitic) velocity max |u| around that droplet.
+* spurious (parasitic) velocity max |u| around that droplet;
+* the Laplace law in 2D, P_in - P_out = sigma / R, with the surface tension of the flat
+  interface sigma = K * integral of (d rho / dn)^2 across it (the gradient energy of the
+  Korteweg stress of Sec. 2.2), taken from the slab at the droplets' temperature, and R the
+  droplet's equimolar radius.
 
 Both paths run through the library (each instance set advanced as one batch); the float64
 path agrees with the oracle to round-off on short runs, so it stands in for it on runs of
@@ -26,11 +30,29 @@ def vdw_pressure(rho, T):
     return 3.0 * rho * T / (3.0 - rho) - 1.125 * rho * rho
 
 
+def surface_tension(profile, dx, K):
+    """sigma = K * integral (d rho/dx)^2 dx per interface, for a periodic profile rho(x) with
+    two interfaces (the slab); the derivative is spectral (exact for the band-limited profile)."""
+    n = profile.size
+    k = 2.0 * np.pi * np.fft.fftfreq(n, d=dx)
+    k[n // 2] = 0.0  # no first derivative at the Nyquist frequency
+    d = np.real(np.fft.ifft(1j * k * np.fft.fft(profile)))
+    return 0.5 * K * float(np.sum(d * d) * dx)
+
+
+def equimolar_radius(rho, rho_in, rho_out):
+    """Radius (cells) of the disc holding the droplet's excess mass at the inner density."""
+    area = float(np.sum((rho - rho_out) / (rho_in - rho_out)))
+    return float(np.sqrt(area / np.pi))
+
+
 def slab_runs(temps, precision, nx=256, ny=2, steps=20000, params=None):
     """Flat slabs (liquid in the middle half of x) at each temperature, advanced `steps` steps.
-    Returns per temperature (rho_l, rho_v, mass drift): bulk means over the central nx/8 of the
-    liquid and the outer nx/8 of the vapour."""
-    p = default_params(precision=precision, **(params or PHASE))
+    Returns per temperature (rho_l, rho_v, mass drift, sigma): bulk means over the central nx/8
+    of the liquid and the outer nx/8 of the vapour, and the surface tension of the final
+    profile."""
+    kw = dict(params or PHASE)
+    p = default_params(precision=precision, **kw)
     out = []
     with Batch([(nx, ny)] * len(temps), p) as b:
         mass0 = []
@@ -46,14 +68,14 @@ def slab_runs(temps, precision, nx=256, ny=2, steps=20000, params=None):
             rho_l = float(rho[nx // 2 - w: nx // 2 + w].mean())
             rho_v = float(np.concatenate([rho[:w], rho[nx - w:]]).mean())
             drift = (b.diagnostics(k)["mass"] - mass0[k]) / mass0[k]
-            out.append((rho_l, rho_v, drift))
+            out.append((rho_l, rho_v, drift, surface_tension(rho, kw["dx"], kw["K"])))
     return out
 
 
 def droplet_runs(radii, precision, n=128, T=0.9, steps=10000, params=None):
     """Static droplets of radius R (cells) centred in an n x n box at temperature T.
-    Returns per radius (P_in - P_out, max |u|, mass drift); P_in at the centre node,
-    P_out averaged over the four corner nodes."""
+    Returns per radius (P_in - P_out, max |u|, mass drift, equimolar radius in cells); P_in and
+    rho_in at the centre node, P_out and rho_out averaged over the four corner nodes."""
     p = default_params(precision=precision, **(params or PHASE))
     rl, rv = maxwell(T)
     out = []
@@ -66,11 +88,13 @@ def droplet_runs(radii, precision, n=128, T=0.9, steps=10000, params=None):
         for k in range(len(radii)):
             rho, ux, uy, Tf = b.moments(k)
             P = vdw_pressure(rho, Tf)
+            corners = ((0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1))
             p_in = float(P[n // 2, n // 2])
-            p_out = float(np.mean([P[0, 0], P[0, n - 1], P[n - 1, 0], P[n - 1, n - 1]]))
+            p_out = float(np.mean([P[c] for c in corners]))
+            r_eq = equimolar_radius(rho, float(rho[n // 2, n // 2]), float(np.mean([rho[c] for c in corners])))
             umax = float(np.sqrt(ux * ux + uy * uy).max())
             drift = (b.diagnostics(k)["mass"] - mass0[k]) / mass0[k]
-            out.append((p_in - p_out, umax, drift))
+            out.append((p_in - p_out, umax, drift, r_eq))
     return out
 
 
@@ -87,10 +111,23 @@ def error_table(temps=(0.85, 0.9, 0.95), radii=(8, 12, 16, 24, 32), slab_steps=2
                      "rel_err_rho_l": abs(m[0] - a[0]) / abs(a[0]), "rel_err_rho_v": abs(m[1] - a[1]) / abs(a[1]),
                      "maxwell_rho_l": rl, "maxwell_rho_v": rv,
                      "mass_drift_fp64": a[2], "mass_drift_mixed": m[2]})
+    # surface tension of the flat interface at the droplets' temperature (a slab of the same set)
+    T_drop = 0.9
+    sig = {"fp64": None, "mixed": None}
+    if T_drop in temps:
+        j = list(temps).index(T_drop)
+        sig = {"fp64": s64[j][3], "mixed": s32[j][3]}
+    dx = PHASE["dx"]
     drops = []
     for R, a, m in zip(radii, d64, d32):
-        drops.append({"R": R, "dp_fp64": a[0], "dp_mixed": m[0], "rel_err_dp": abs(m[0] - a[0]) / abs(a[0]),
-                      "umax_fp64": a[1], "umax_mixed": m[1], "rel_err_umax": abs(m[1] - a[1]) / abs(a[1]),
-                      "mass_drift_fp64": a[2], "mass_drift_mixed": m[2]})
+        row = {"R": R, "dp_fp64": a[0], "dp_mixed": m[0], "rel_err_dp": abs(m[0] - a[0]) / abs(a[0]),
+               "umax_fp64": a[1], "umax_mixed": m[1], "rel_err_umax": abs(m[1] - a[1]) / abs(a[1]),
+               "mass_drift_fp64": a[2], "mass_drift_mixed": m[2], "R_eq_fp64": a[3], "R_eq_mixed": m[3]}
+        if sig["fp64"]:
+            # Laplace in 2D: dp R / sigma = 1 (R in physical units)
+            row["laplace_fp64"] = a[0] * a[3] * dx / sig["fp64"]
+            row["laplace_mixed"] = m[0] * m[3] * dx / sig["mixed"]
+        drops.append(row)
     return {"slab": {"nx": 256, "ny": 2, "steps": slab_steps, "rows": coex},
-            "droplet": {"n": 128, "T": 0.9, "steps": drop_steps, "rows": drops}}
+            "droplet": {"n": 128, "T": T_drop, "steps": drop_steps, "rows": drops},
+            "surface_tension": sig}

@@ -296,3 +296,52 @@ def test_benchmark_workload_stays_bounded():
               f"umax {d1['umax']:.3e}, energy drift {abs(d1['energy'] / d0['energy'] - 1):.2e}")
         assert abs(d1["mass"] / d0["mass"] - 1) < 1e-6
         assert d1["umax"] < 0.1
+
+
+# Degenerate cases of the method.
+
+@pytest.mark.parametrize("precision,tol", [(lbm.LBM_FP64, 1e-13), (lbm.LBM_MIXED, 2e-6)])
+def test_uniform_state_is_a_fixed_point(precision, tol):
+    # A uniform state (here a uniform flow above the critical temperature, so it is also
+    # stable) has no gradients: every derivative vanishes, I_i = 0 (Eq. (2)) and f = f^eq
+    # makes the right-hand side of Eq. (1) zero. f and the moments stay put; the library's
+    # f^eq matches the oracle's. tol: FP64 rounding; for the mixed path, float32 f^eq and its
+    # moments (cond(M) ~ 2e3 times 2^-24, relative to the largest f_i).
+    nx, ny = 32, 16
+    state = (1.0, 0.01, -0.02, 1.1)
+    fields = tuple(np.full((ny, nx), v) for v in state)
+    p = oracle_params()
+    feq = init_feq(D2V16(p.eta0), *fields, p)
+    with lbm.Simulation(nx, ny, lib_params(precision=precision)) as s:
+        s.init(*fields)
+        f0 = s.get_f()
+        s.step(10)
+        f1 = s.get_f()
+        m = s.moments()
+    scale = np.max(np.abs(feq))
+    assert np.max(np.abs(f0 - feq)) <= tol * scale
+    assert np.max(np.abs(f1 - f0)) <= tol * scale
+    for a, v in zip(m, state):
+        assert np.max(np.abs(a - v)) <= tol * max(abs(v), 1.0)
+
+
+@pytest.mark.parametrize("precision,tol", [(lbm.LBM_FP64, 1e-13), (lbm.LBM_MIXED, 1e-6)])
+def test_nyquist_modes_do_not_advect(precision, tol):
+    # The first-derivative multiplier is zero at the Nyquist frequency m = -N/2 on both axes
+    # (a real field needs it), so under advection alone a distribution made of the mean and the
+    # two Nyquist modes (-1)^x, (-1)^y does not move; the oracle agrees.
+    nx, ny = 16, 8
+    p = oracle_params(flags=lbm.LBM_FLAG_NO_COLLISION | lbm.LBM_FLAG_NO_FORCE)
+    d = D2V16(p.eta0)
+    base = init_feq(d, *(np.full((ny, nx), v) for v in (1.0, 0.0, 0.0, 1.1)), p)
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    f = base * (1.0 + 0.01 * (-1.0) ** x + 0.02 * (-1.0) ** y)
+    fo = rk2_step(d, rk2_step(d, f, p), p)
+    assert np.max(np.abs(fo - f)) <= 1e-13 * np.max(np.abs(f))
+    with lbm.Simulation(nx, ny, lib_params(precision=precision,
+                                           flags=lbm.LBM_FLAG_NO_COLLISION | lbm.LBM_FLAG_NO_FORCE)) as s:
+        s.set_f(f)
+        f0 = s.get_f()
+        s.step(2)
+        assert np.max(np.abs(s.get_f() - f0)) <= tol * np.max(np.abs(f))

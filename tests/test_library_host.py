@@ -114,3 +114,17 @@ def test_moments_out_arrays_are_checked():
                 [ro] + good[1:], [np.zeros((4, 16))[:, ::2]] + good[1:]):
         with pytest.raises(ValueError, match="four writable"):
             _host_out(bad, (4, 8))
+
+
+def test_surface_tension_and_equimolar_radius_reducers():
+    # host-side reducers of the Laplace check, against closed forms
+    from paper_1403_3746_gb300.accuracy import equimolar_radius, surface_tension
+    n, dx, K, w, a = 256, 1 / 256, 5e-6, 3.0, 0.6
+    x = np.arange(n)
+    prof = 1.0 + a * (np.tanh((x - 64) / w) - np.tanh((x - 192) / w))
+    # integral of (a/w)^2 sech^4(x/w) over x (cells) is (a/w)^2 w 4/3; per unit length: / dx
+    assert surface_tension(prof, dx, K) == pytest.approx(K * (a / w) ** 2 * w * 4 / 3 / dx, rel=1e-8)
+    Y, X = np.mgrid[0:128, 0:128]
+    rho = 0.4 + 1.2 * (np.hypot(X - 63.5, Y - 63.5) < 20.0)
+    assert equimolar_radius(rho, 1.6, 0.4) == pytest.approx(20.0, rel=2e-2)
+    assert equimolar_radius(np.full((8, 8), 0.4), 1.6, 0.4) == 0.0
