@@ -429,13 +429,17 @@ def main():
             tab = accuracy.error_table()
             sl, dr = tab["slab"]["rows"], tab["droplet"]["rows"]
             extras["large_run"] = large_run(lbm, torch, synthetic, max(20, args.steps // 2), stream)
+            lp = accuracy.laplace_check()
+            extras["laplace_law"] = {
+                "runs": f"mixed droplets R={[r['R'] for r in lp['rows']]} on 128^2 at T={lp['T']}, "
+                        f"{lp['steps']} steps; sigma from a 256x2 slab",
+                "sigma": lp["sigma"], "dp_R_over_sigma": {r["R"]: r["dp_R_over_sigma"] for r in lp["rows"]}}
             extras["accuracy_mixed_vs_fp64"] = {
                 "coexistence_rel_err_max": max(max(r["rel_err_rho_l"], r["rel_err_rho_v"]) for r in sl),
                 "mass_drift_mixed_max": max(abs(r["mass_drift_mixed"]) for r in sl + dr),
                 "mass_drift_fp64_max": max(abs(r["mass_drift_fp64"]) for r in sl + dr),
                 "spurious_velocity_rel_err_max": max(r["rel_err_umax"] for r in dr),
                 "pressure_jump_rel_err_max": max(r["rel_err_dp"] for r in dr),
-                "laplace_dp_R_over_sigma_fp64": {r["R"]: r.get("laplace_fp64") for r in dr},
                 "runs": f"slabs 256x2 at T={[r['T'] for r in sl]}, {tab['slab']['steps']} steps; droplets "
                         f"R={[r['R'] for r in dr]} on 128^2 at T=0.9, {tab['droplet']['steps']} steps"}
 

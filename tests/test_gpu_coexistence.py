@@ -38,3 +38,19 @@ def test_stepwise_protocol_runs():
     assert abs(r0["rho_l"] / r0["maxwell_rho_l"] - 1) < 2e-3 and abs(r0["rho_v"] / r0["maxwell_rho_v"] - 1) < 5e-3
     # after lowering T the phases move apart, towards the new Maxwell pair
     assert rows[1]["rho_l"] > r0["rho_l"] and rows[1]["rho_v"] < r0["rho_v"]
+
+
+def test_laplace_law():
+    # Static droplets relaxed for 1e5 steps: the pressure jump times the equimolar radius equals
+    # the surface tension of the flat interface of the same fluid, within 10% (corrections of
+    # order interface width / R, a few cells out of 16-32, and the slowly decaying temperature
+    # non-uniformity of the thermal model); the jump falls with the radius.
+    from paper_1403_3746_gb300 import accuracy
+    res = accuracy.laplace_check(radii=(16, 24, 32))
+    print(res)
+    assert res["sigma"] > 0
+    for row in res["rows"]:
+        assert abs(row["dp_R_over_sigma"] - 1.0) < 0.1, row
+        assert abs(row["R_eq"] / row["R"] - 1.0) < 0.05, row
+    dps = [row["dp"] for row in res["rows"]]
+    assert all(a > b for a, b in zip(dps, dps[1:])), dps
