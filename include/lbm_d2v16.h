@@ -162,12 +162,14 @@ size_t lbm_device_bytes(lbm_handle h);
  * columns of the column-pass tiles; geometry[1], geometry[2]: rows per CTA of the macro and
  * update row passes; geometry[3]: width of the flux column-pass tiles. lbm_autotune times
  * every legal candidate of each (column tiles with at most 100 KB of line buffers; row CTAs
- * of at most 4096 nodes and 200 KB) on the handle's own buffers with the passes of a
- * Runge-Kutta stage, keeps the fastest, and reports the chosen shapes and the measured time
- * of each pass with them (ms: column, macro, update, flux; either pointer may be NULL). The
- * state is unchanged (the moment fields the update pass rewrites are saved and restored) and
- * results do not depend on the shapes. Needs an initialised state; allocates a temporary
- * device buffer of 4 fields; synchronises the stream. */
+ * of at most 4096 nodes whose line buffers fit the 227 KB of shared memory a CTA can have)
+ * on the handle's own buffers with the passes of a Runge-Kutta stage, keeps the fastest, and
+ * reports the chosen shapes and the measured time of each pass with them (ms: column, macro,
+ * update, flux; either pointer may be NULL). The state is unchanged (the moment fields the
+ * update pass rewrites are saved and restored) and results do not depend on the shapes. If it
+ * fails midway, the previous shapes and the saved moment fields are put back before it
+ * returns the error. Needs an initialised state; allocates a temporary device buffer of 4
+ * fields; synchronises the stream. */
 int lbm_geometry(lbm_handle h, int geometry[4]);
 /* Sets the launch shapes (same meaning as lbm_geometry) to any of the autotuner's legal
  * candidates (LBM_ERR_ARG otherwise); results do not depend on them. Synchronises. */
