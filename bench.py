@@ -41,6 +41,10 @@ ELEMS_PER_NODE_STEP = 2 * (34 + 17 + 8) + 61 + 77  # 256
 KERNEL_NAMES = {"col": "col_deriv_kernel", "macro": "macro_row_kernel", "flux": "col_deriv_kernel",
                 "update": "update_row_kernel"}
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (no tensor path for this work)
+# FP64 flops of one step of the FP64 path per node (DADD + DMUL + 2 DFMA thread instructions
+# of its four kernels, counted by ncu at 1024^2: 5.50 GFLOP per step; the count does not
+# depend on the launch shapes)
+FP64_FLOP_PER_NODE_STEP = 5.50e9 / (1024 * 1024)
 
 
 def peaks():
@@ -465,7 +469,13 @@ def main():
             "fp64_path": {"value": fp64_mlups, "unit": "MLUPS", "steps": k64, "launch_shapes": list(geom64),
                           "ms_per_step": sum(step64) / k64,
                           "kernels_ms_per_step": {k: v[0] / k64 for k, v in kern64.items()},
-                          "bound": "alu (fp64)", "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS},
+                          "bound": "alu (fp64)", "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS,
+                          "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                                       "peak_source": "nominal (GB300 FP64)",
+                                       "achieved": FP64_FLOP_PER_NODE_STEP * n / (sum(step64) / k64 * 1e-3) / 1e12,
+                                       "frac": FP64_FLOP_PER_NODE_STEP * n / (sum(step64) / k64 * 1e-3) / 1e12
+                                               / FP64_PEAK_TFLOPS,
+                                       "flop_source": "ncu FP64 thread-instruction counts per step (DFMA = 2)"}},
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
             "roofline": roofline, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
             "ms_per_step_kernel_timed_loop": sum(step_ms_b) / args.steps,
