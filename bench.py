@@ -459,8 +459,10 @@ def main():
             "metric": "MLUPS of D2V16 RK2 step at 1024^2", "value": value, "unit": "MLUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (moment sums compensated)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "LBM_MIXED", "l2": "flushed between steps (256 MiB write)",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "precision": "LBM_MIXED (f32 storage and arithmetic, f64 tables, compensated moment sums)",
+                       "l2": "flushed between steps (256 MiB write)",
                        "launch": "lbm_step: one CUDA graph per step (8 kernels)",
                        "launch_shapes": {"col_tile_width": geom[0], "macro_rows_per_cta": geom[1],
                                          "update_rows_per_cta": geom[2], "flux_tile_width": geom[3],
