@@ -345,3 +345,33 @@ def test_nyquist_modes_do_not_advect(precision, tol):
         f0 = s.get_f()
         s.step(2)
         assert np.max(np.abs(s.get_f() - f0)) <= tol * np.max(np.abs(f))
+
+
+def test_argument_and_state_errors():
+    # sizes outside powers of two in [2, 4096], states outside the van der Waals range, calls
+    # out of order and bad counts are refused with an error (nothing is launched); n = 0 steps
+    # is a no-op
+    for nx, ny in ((3, 8), (1, 8), (8, 8192), (0, 8)):
+        with pytest.raises(lbm.LbmError, match="power of two"):
+            lbm.Simulation(nx, ny, lib_params())
+    with lbm.Simulation(16, 8, lib_params()) as s:
+        with pytest.raises(lbm.LbmError, match="out of order"):
+            s.moments()
+        with pytest.raises(lbm.LbmError, match="out of order"):
+            s.diagnostics()
+        fields = [np.full((8, 16), v) for v in (1.0, 0.0, 0.0, 0.9)]
+        for k, bad in ((0, 3.5), (0, 0.0), (3, -0.1), (1, np.nan)):
+            f = [a.copy() for a in fields]
+            f[k][2, 3] = bad
+            with pytest.raises(lbm.LbmError, match="invalid argument"):
+                s.init(*f)
+        s.init(*fields)
+        f0 = s.get_f()
+        s.step(0)
+        assert np.array_equal(s.get_f(), f0)
+        with pytest.raises(lbm.LbmError, match="invalid argument"):
+            s.step(-1)
+        for nbins in (0, 8193):
+            with pytest.raises(lbm.LbmError, match="nbins"):
+                s.structure_factor(nbins)
+        assert np.array_equal(s.get_f(), f0)
