@@ -307,3 +307,27 @@ def test_structure_factor_of_single_modes_and_parseval():
     S, cnt = structure_factor(r, 64)
     assert np.sum(S * cnt) == pytest.approx(np.sum((r - r.mean()) ** 2), rel=1e-12)
     assert cnt.sum() == 16 * 32
+
+
+def test_diagnostics_of_a_single_density_mode(dvm):
+    # rho = rho0 + a sin(k x) with uniform u and T: every total is a closed form over the
+    # periodic box of area A (sin averages to 0, sin^2 and cos^2 to 1/2; the spectral
+    # derivative of a low mode is k cos(k x) to 1e-14 for the 16th-order k_eff):
+    # mass = rho0 A, p = rho0 u A, e_T = A [rho0 T - 9/8 (rho0^2 + a^2/2) + K a^2 k^2 / 4
+    # + rho0 |u|^2 / 2], max |u| = |u|.
+    nx, ny, rho0, a, T, u = 32, 8, 1.1, 0.2, 0.95, (0.03, -0.04)
+    p = Params()
+    x = np.arange(nx)[None, :] * p.dx * np.ones((ny, 1))
+    L = nx * p.dx
+    k = 2 * np.pi / L
+    rho = rho0 + a * np.sin(k * x)
+    f = feq(dvm, rho, np.full_like(rho, u[0]), np.full_like(rho, u[1]), np.full_like(rho, T), p.b)
+    d = diagnostics(dvm, f, p)
+    A = L * ny * p.dy
+    u2 = u[0] ** 2 + u[1] ** 2
+    assert d["mass"] == pytest.approx(rho0 * A, rel=1e-13)
+    assert d["px"] == pytest.approx(rho0 * u[0] * A, rel=1e-12)
+    assert d["py"] == pytest.approx(rho0 * u[1] * A, rel=1e-12)
+    eT = A * (rho0 * T - 9 / 8 * (rho0 ** 2 + a * a / 2) + p.K * a * a * k * k / 4 + rho0 * u2 / 2)
+    assert d["energy"] == pytest.approx(eT, rel=1e-12)
+    assert d["umax"] == pytest.approx(np.sqrt(u2), rel=1e-12)
