@@ -56,23 +56,31 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# the device code of the passes (kernels, FFT engine, shared layouts and launch limits); the
+# host orchestration (lbm_api.cu, lbm_noalloc.cu) is not part of it, and the launch shapes a
+# profile was taken with are checked separately
+DEVICE_SOURCES = ("fft_reg.cuh", "kernels_col.cu", "kernels_misc.cu", "kernels_row.cu", "kernels_sf.cu",
+                  "lbm_internal.cuh")
+
+
 def source_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1403_3746_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in DEVICE_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key, precision):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+def ncu_traffic(kernel_key, precision, shapes):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    device sources with the same launch shapes."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
         e = d[f"{precision}:{kernel_key}"]
-        if e.get("source_digest") != source_digest():
+        if e.get("source_digest") != source_digest() or list(e.get("launch_shapes", [])) != list(shapes):
             return None
         return e["dram_bytes_per_launch_full_size"]
     except Exception:
@@ -413,7 +421,7 @@ def main():
     alg_bytes = ELEMS_PER_NODE[dom] * 4 * n
     achieved = alg_bytes / per_launch_s / 1e9
     roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom] + "<float>", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": ncu_traffic(dom, "mixed"),
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": ncu_traffic(dom, "mixed", geom),
                 "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
                 "duration_source": "mean CUDA-event time per launch in a second timed loop of the same steps "
                                    "with an event pair around every kernel",

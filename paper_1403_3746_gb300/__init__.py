@@ -81,6 +81,7 @@ _SIGS = {
     "lbm_autotune": (ctypes.c_int, [_P, _P, _P]),
     "lbm_batch_autotune": (ctypes.c_int, [_P]),
     "lbm_batch_geometry": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "lbm_launch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
 }
 
 
@@ -135,6 +136,19 @@ def diagnostics_noalloc(params, rho, ux, uy, T, stream=None):
     _check(lib().lbm_diagnostics_noalloc(nx, ny, params.dx, params.dy, params.K, params.win_alpha,
                                          params.win_p, *ps, s, out))
     return dict(zip(("mass", "px", "py", "energy", "umax"), list(out)))
+
+
+PLAN_KEYS = ("col_width", "col_threads", "col_smem", "macro_rows", "macro_threads", "macro_smem", "macro_serial",
+             "update_rows", "update_smem", "update_ax", "rowd_rows", "rowd_threads", "rowd_smem",
+             "pass_thread_cap", "macro_thread_cap", "cta_smem_cap")
+
+
+def launch_plan(nx, ny, precision=LBM_FP64):
+    """lbm_launch_plan: the default launch shapes of an nx x ny grid and what each pass needs,
+    computed on the host (a dict keyed by PLAN_KEYS)."""
+    out = (ctypes.c_int * 16)()
+    _check(lib().lbm_launch_plan(int(nx), int(ny), int(precision), out))
+    return dict(zip(PLAN_KEYS, list(out)))
 
 
 def _host_out(out, shape):

@@ -128,3 +128,46 @@ def test_surface_tension_and_equimolar_radius_reducers():
     rho = 0.4 + 1.2 * (np.hypot(X - 63.5, Y - 63.5) < 20.0)
     assert equimolar_radius(rho, 1.6, 0.4) == pytest.approx(20.0, rel=2e-2)
     assert equimolar_radius(np.full((8, 8), 0.4), 1.6, 0.4) == 0.0
+
+
+def _line_G(n):
+    # threads per line of the register FFT engine: 16 points per thread (all points for n < 16)
+    return n // 16 if n >= 16 else 1
+
+
+@pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_MIXED])
+def test_launch_plan_of_every_size_fits_the_kernels(L, precision):
+    # host-side launch plan (no device) of every supported grid: each pass's CTA within its
+    # thread and shared-memory limits, tiles and row groups dividing the grid, and the
+    # separate-row-pass / serial-macro forms only where the kernels implement them (float64
+    # rows of 4096)
+    es = 8 if precision == lbm.LBM_FP64 else 4
+    sizes = [1 << k for k in range(1, 13)]
+    for nx in sizes:
+        for ny in sizes:
+            pl = lbm.launch_plan(nx, ny, precision)
+            cap_smem = pl["cta_smem_cap"]
+            assert cap_smem == 232448
+            assert nx % pl["col_width"] == 0 and pl["col_width"] >= 2
+            assert pl["col_threads"] == (pl["col_width"] // 2) * _line_G(ny) <= pl["pass_thread_cap"]
+            for k in ("col_smem", "macro_smem", "update_smem", "rowd_smem"):
+                assert 0 <= pl[k] <= cap_smem, (nx, ny, k, pl)
+            for k in ("macro_rows", "update_rows", "rowd_rows"):
+                assert ny % pl[k] == 0, (nx, ny, k)
+            assert pl["macro_threads"] <= pl["macro_thread_cap"]
+            assert pl["rowd_threads"] <= (384 if es == 8 else 768)
+            special = es == 8 and nx == 4096
+            assert pl["update_ax"] == (1 if special else 0), (nx, ny, pl)
+            assert pl["macro_serial"] == (1 if special else 0), (nx, ny, pl)
+            if not pl["update_ax"]:
+                # six line buffers per row of the update CTA
+                line = (nx + nx // 16 + 2) * 2 * es
+                assert pl["update_smem"] == 6 * pl["update_rows"] * line
+
+
+def test_launch_plan_rejects_bad_sizes(L):
+    for nx, ny in ((3, 8), (8, 8192), (1, 2)):
+        with pytest.raises(lbm.LbmError, match="power of two"):
+            lbm.launch_plan(nx, ny)
+    with pytest.raises(lbm.LbmError, match="precision"):
+        lbm.launch_plan(8, 8, 7)
