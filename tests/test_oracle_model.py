@@ -192,7 +192,10 @@ def test_mass_and_momentum_conservation_slab(dvm):
         f = rk2_step(dvm, f, p)
     d1 = diagnostics(dvm, f, p)
     assert abs(d1["mass"] - d0["mass"]) < 1e-13 * d0["mass"]
-    assert abs(d1["px"]) < 1e-14 * d0["mass"] and abs(d1["py"]) < 1e-14 * d0["mass"]
+    # momentum is conserved to rounding only (the forcing's momentum part is the spectral
+    # divergence of S, which sums to zero on the periodic box): 1e-13 of the mass is a
+    # rounding-level bound on any platform, far below what a wrong sign or term would give
+    assert abs(d1["px"]) < 1e-13 * d0["mass"] and abs(d1["py"]) < 1e-13 * d0["mass"]
     # total energy drifts only slightly (the paper reports |de_T| ~ 1e-9 for this model)
     assert abs(d1["energy"] - d0["energy"]) < 1e-6 * abs(d0["energy"])
 
