@@ -375,3 +375,21 @@ def test_argument_and_state_errors():
             with pytest.raises(lbm.LbmError, match="nbins"):
                 s.structure_factor(nbins)
         assert np.array_equal(s.get_f(), f0)
+
+
+@pytest.mark.parametrize("precision,tol", [(lbm.LBM_FP64, 1e-12), (lbm.LBM_MIXED, 2e-6)])
+def test_full_4096_grid_conserves_mass_and_momentum(precision, tol):
+    # the largest grid (4096^2, the large-run workload: spinodal quench at T = 0.9, seed 5),
+    # beyond what the oracle can step: properties that hold at any size. Mass is conserved and
+    # momentum stays zero to rounding (FP64) or to the float32 storage of f (mixed, relative to
+    # the mass; the moment sums are compensated), and the state stays finite.
+    n = 4096
+    fields = synthetic.spinodal(n, n, 1.0, 0.01, 0.9, seed=5)
+    with lbm.Simulation(n, n, lib_params(precision=precision)) as s:
+        s.init(*fields)
+        d0 = s.diagnostics()
+        s.step(2)
+        d1 = s.diagnostics()
+    assert abs(d1["mass"] / d0["mass"] - 1) < tol
+    assert abs(d1["px"]) < tol * d0["mass"] and abs(d1["py"]) < tol * d0["mass"]
+    assert np.isfinite(d1["energy"]) and d1["umax"] < 0.1
