@@ -3,7 +3,7 @@ the circularly averaged structure factor of the density.
 
 Total energy density (Sec. 2.2, after the recovered equations):
     e_T = rho T - 9 rho^2 / 8 + K |grad rho|^2 / 2 + rho u^2 / 2,
-with grad rho taken by the spectral scheme of Eq. (3). Totals are sums over nodes
+with grad rho taken by the spectral scheme of Eq. (3) (the run's k_eff series and window). Totals are sums over nodes
 times the cell area dx dy.
 """
 import numpy as np
@@ -37,8 +37,8 @@ def structure_factor(rho, nbins):
 
 def diagnostics(dvm, f, p):
     rho, ux, uy, T = moments(dvm, f, p.b)
-    rx = spectral_deriv(rho, 1, 0, p.dx, p.dy, p.win_alpha, p.win_p)
-    ry = spectral_deriv(rho, 0, 1, p.dx, p.dy, p.win_alpha, p.win_p)
+    rx = spectral_deriv(rho, 1, 0, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms, p.deriv)
+    ry = spectral_deriv(rho, 0, 1, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms, p.deriv)
     u2 = ux * ux + uy * uy
     eT = rho * T - 9.0 / 8.0 * rho * rho + 0.5 * p.K * (rx * rx + ry * ry) + 0.5 * rho * u2
     cell = p.dx * p.dy

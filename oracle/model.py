@@ -51,7 +51,9 @@ class Params:
     """Model and discretisation parameters (Sec. 2.2, Sec. 3). The defaults are the
     phase-separation set of Sec. 3.2 (tau = dt = 1e-4, dx = dy = 1/256, K = 5e-6) with
     q = -0.004 and b = 2 from Sec. 3.1. `force`, `collide` and `advect` switch the
-    three terms of Eq. (1) on or off (test hooks)."""
+    three terms of Eq. (1) on or off (test hooks). `deriv` selects how the derivative
+    operator of Eq. (3) is applied: "fft" (numpy's FFT of the field) or "dft" (explicit DFT
+    sums along each axis, the same operator with O(N) work per value)."""
     tau: float = 1e-4
     dt: float = 1e-4
     dx: float = 1.0 / 256.0
@@ -70,6 +72,7 @@ class Params:
     keff_terms: int = 8
     scheme: str = "rk2"
     T_iso: float = 0.0
+    deriv: str = "fft"
 
     @staticmethod
     def phase_separation():
@@ -96,7 +99,7 @@ def forcing_terms(dvm, rho, ux, uy, T, fe, p):
     """Eq. (2) and the coefficient definitions after it. Returns I (16, ny, nx) and a dict
     of the intermediate fields (A, B_x, B_y, C, C_q, ...)."""
     def D(h, ox, oy):
-        return spectral_deriv(h, ox, oy, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms)
+        return spectral_deriv(h, ox, oy, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms, p.deriv)
 
     # spatial derivatives of the macroscopic fields
     rx, ry = D(rho, 1, 0), D(rho, 0, 1)
@@ -147,8 +150,8 @@ def advection(dvm, f, p):
     """v_i . grad f_i for all 16 fields (Eq. (1) left side), by the FFT scheme of Eq. (3)."""
     out = np.empty_like(f)
     for i in range(16):
-        out[i] = dvm.vx[i] * spectral_deriv(f[i], 1, 0, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms) \
-            + dvm.vy[i] * spectral_deriv(f[i], 0, 1, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms)
+        out[i] = dvm.vx[i] * spectral_deriv(f[i], 1, 0, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms, p.deriv) \
+            + dvm.vy[i] * spectral_deriv(f[i], 0, 1, p.dx, p.dy, p.win_alpha, p.win_p, p.keff_terms, p.deriv)
     return out
 
 

@@ -57,22 +57,41 @@ def deriv_multiplier(N, dx, alpha=0.0, p=36.0, terms=8):
     return d
 
 
-def spectral_deriv(h, ox, oy, dx, dy, alpha=0.0, p=36.0, terms=8):
+def spectral_deriv(h, ox, oy, dx, dy, alpha=0.0, p=36.0, terms=8, backend="fft"):
     """Spectral derivative d^(ox) / dx^(ox) d^(oy) / dy^(oy) of a real field h of shape (ny, nx):
-    the composition of the first-derivative operators of each axis."""
+    the composition of the first-derivative operators of each axis. backend "fft": numpy's FFT
+    of the whole field; "dft": the same operator as explicit DFT sums along each axis
+    (dft_deriv_matrix, O(N) work per output value, no FFT)."""
     ny, nx = h.shape
+    if backend == "dft":
+        out = h
+        if ox:
+            out = out @ dft_deriv_matrix(nx, dx, ox, alpha, p, terms).T
+        if oy:
+            out = dft_deriv_matrix(ny, dy, oy, alpha, p, terms) @ out
+        return np.array(out, dtype=np.float64, copy=True)
     mult = (deriv_multiplier(nx, dx, alpha, p, terms)[None, :] ** ox
             * deriv_multiplier(ny, dy, alpha, p, terms)[:, None] ** oy)
     return np.fft.ifft2(mult * np.fft.fft2(h)).real
 
 
-def dft_deriv_matrix(N, dx, order=1):
-    """Brute-force real N x N matrix of the same operator along one axis, built from the DFT
-    sums (no FFT): D[a, b] = (1/N) sum_m d(m)^order exp(2 pi i m (a - b) / N)."""
-    m = dft_indices(N)
-    d = deriv_multiplier(N, dx) ** order
-    a = np.arange(N)
-    D = np.zeros((N, N), dtype=np.complex128)
-    for j in range(N):
-        D += d[j] * np.exp(2j * np.pi * m[j] * (a[:, None] - a[None, :]) / N)
-    return (D / N).real
+_DFT_CACHE = {}
+
+
+def dft_deriv_matrix(N, dx, order=1, alpha=0.0, p=36.0, terms=8):
+    """Real N x N matrix of the same operator along one axis, built from the DFT sums (no FFT):
+    D[a, b] = (1/N) sum_m d(m)^order exp(2 pi i m (a - b) / N). It is circulant, so its first
+    column c[k] = (1/N) sum_m d(m)^order exp(2 pi i m k / N) is summed directly (N terms for
+    each of the N values of k) and D[a, b] = c[(a - b) mod N]."""
+    key = (N, float(dx), order, float(alpha), float(p), terms)
+    if key not in _DFT_CACHE:
+        m = dft_indices(N)
+        d = deriv_multiplier(N, dx, alpha, p, terms) ** order
+        k = np.arange(N)
+        c = np.zeros(N, dtype=np.complex128)
+        for j in range(N):
+            c += d[j] * np.exp(2j * np.pi * ((m[j] * k) % N) / N)
+        c = (c / N).real
+        a = np.arange(N)
+        _DFT_CACHE[key] = c[(a[:, None] - a[None, :]) % N]
+    return _DFT_CACHE[key]

@@ -78,19 +78,65 @@ def test_multiplier_is_odd_and_purely_imaginary():
                 assert abs(d[jj[0]] + d[j]) <= 1e-15 * abs(d[j]) or (m[j] == -N // 2 and d[j] == 0)
 
 
-@pytest.mark.parametrize("nx,ny", [(8, 8), (16, 4), (4, 32), (2, 8)])
+def _brute_force_deriv(h, ox, oy, dx, dy, alpha=0.0, p=36.0, terms=8):
+    # sum_m d(m)^o exp(2 pi i m (a - b) / N) / N written out per output value, one axis at a
+    # time: no FFT and no matrix shared with the oracle
+    def axis_op(N, d, order):
+        m = np.rint(np.fft.fftfreq(N) * N)
+        phi = np.sin(np.pi * m / N)
+        ke = (2.0 / d) * sum(c * phi ** (2 * n + 1) for n, c in enumerate(C_KEFF[:terms]))
+        w = np.exp(-alpha * (np.abs(m) / (N / 2)) ** p) if alpha else np.ones(N)
+        mult = (1j * ke * w) ** order
+        mult[m == -N // 2] = 0.0
+        a = np.arange(N)
+        return np.array([[np.sum(mult * np.exp(2j * np.pi * m * (i - j) / N)).real / N for j in a] for i in a])
+    out = h
+    if ox:
+        out = out @ axis_op(h.shape[1], dx, ox).T
+    if oy:
+        out = axis_op(h.shape[0], dy, oy) @ out
+    return out
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 8), (16, 4), (4, 32), (2, 8), (128, 2), (64, 64)])
 def test_fft_derivative_matches_brute_force_dft(nx, ny):
+    # at N = 64 and 128 the operator is checked at the sizes the GPU parity tests run
     rng = np.random.default_rng(7)
     h = rng.standard_normal((ny, nx))
     dx, dy = 0.3, 0.7
     for ox, oy in [(1, 0), (0, 1), (2, 0), (0, 2), (1, 1)]:
-        ref = h
-        if ox:
-            ref = ref @ dft_deriv_matrix(nx, dx, ox).T
-        if oy:
-            ref = dft_deriv_matrix(ny, dy, oy) @ ref
+        ref = _brute_force_deriv(h, ox, oy, dx, dy)
         got = spectral_deriv(h, ox, oy, dx, dy)
-        assert np.allclose(got, ref, rtol=0, atol=1e-11 * max(1.0, np.abs(ref).max()))
+        tol = 1e-11 * max(1.0, np.abs(ref).max())
+        assert np.allclose(got, ref, rtol=0, atol=tol)
+        # the oracle's explicit-DFT back-end is the same operator
+        assert np.allclose(spectral_deriv(h, ox, oy, dx, dy, backend="dft"), ref, rtol=0, atol=tol)
+        if nx >= 64:
+            assert np.allclose(spectral_deriv(h, ox, oy, dx, dy, 36.0, 36.0, 4, "dft"),
+                               _brute_force_deriv(h, ox, oy, dx, dy, 36.0, 36.0, 4), rtol=0, atol=tol)
+
+
+def test_dft_matrix_is_the_brute_force_sum():
+    for N, order in ((16, 1), (32, 2), (128, 1)):
+        D = dft_deriv_matrix(N, 0.25, order)
+        ref = _brute_force_deriv(np.eye(N), order, 0, 0.25, 1.0)
+        assert np.allclose(D.T, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_rk2_step_same_with_both_derivative_back_ends(dvm):
+    # one Runge-Kutta step of a 32 x 16 noisy slab: the FFT and the explicit DFT back-ends
+    # of Eq. (3) agree to round-off through the whole step (advection and forcing chain)
+    import synthetic
+    from oracle.model import Params, init_feq, rk2_step
+    from oracle.maxwell import coexistence
+    rl, rv = coexistence(0.9)
+    fields = synthetic.slab(32, 16, rl, rv, 0.9, half_width=8, noise=1e-3, seed=3)
+    p = Params()
+    f = init_feq(dvm, *fields, p)
+    a = rk2_step(dvm, f, p)
+    p.deriv = "dft"
+    b = rk2_step(dvm, f, p)
+    assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(a))
 
 
 def test_windowed_derivative_of_single_modes():
