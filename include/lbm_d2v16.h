@@ -188,28 +188,32 @@ int lbm_set_geometry(lbm_handle h, const int geometry[4]);
 int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
 
 /* lbm_diagnostics for callers that cannot allocate device memory. The paper has no
- * counterpart: this is a library service. Examples: code running while a stream is being
- * captured into a CUDA graph (cudaMalloc is not permitted during capture), host applications
- * or plugins whose GPU memory belongs to another allocator or is budgeted at start-up, and
- * services that must not grow their footprint later. It computes out[5] = total mass,
- * x and y momentum, total energy (as lbm_diagnostics, whose out[0..4] it reproduces) and
- * max |u| from the moment fields rho, u_x, u_y, T given as caller-owned float64 device
- * arrays [ny][nx] on the grid nx x ny with spacings dx, dy, surface-tension coefficient K
- * and window (win_alpha, win_p; win_alpha = 0 for none). out is a caller-owned host array.
+ * counterpart: this is a library service. Examples: host applications or plugins whose GPU
+ * memory belongs to another allocator or is budgeted at start-up, and services that must not
+ * grow their footprint later. It computes out[5] = total mass, x and y momentum, total energy
+ * and max |u| (the quantities of lbm_diagnostics out[0..4]) from the moment fields rho, u_x,
+ * u_y, T given as caller-owned float64 device arrays [ny][nx] on the grid nx x ny with
+ * spacings dx, dy, surface-tension coefficient K, window (win_alpha, win_p; win_alpha = 0 for
+ * none) and keff_terms terms of the series of Eq. (3) (1..8, as lbm_params.keff_terms). out is
+ * a caller-owned host array. For a handle's state taken with lbm_moments_device and the
+ * handle's own parameters, the result equals lbm_diagnostics to about 1e-12 (relative) for
+ * LBM_FP64; for LBM_MIXED, lbm_diagnostics differentiates the float32 density instead, and the
+ * energy agrees to about 1e-6 (relative), the other values to about 1e-12.
  * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch (d_x rho,
  * d_y rho, per-block partial sums, derivative tables) is one file-scope device array of
- * about 16.3 MiB, which every GPU that loads this library holds until the process exits.
- * Limits: nx, ny powers of two in [2, 4096] and nx * ny <= 1048576 (e.g. 1024 x 1024);
- * larger sizes return LBM_ERR_ARG with the reason in lbm_last_error(). The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. Work is issued on `stream`
- * (a cudaStream_t, NULL = legacy default stream), which the call synchronises before it
- * returns. Every call rewrites the whole scratch it reads (nothing needs to start at
- * zero), but all calls share the one array: calls that overlap on the GPU (other streams,
- * other host threads) race. */
+ * about 16.3 MiB, which every GPU that loads this library holds until the process exits; its
+ * device address is looked up (cudaGetSymbolAddress) on every call, in the current device's
+ * context. Limits: nx, ny powers of two in [2, 4096] and nx * ny <= 1048576 (e.g. 1024 x 1024);
+ * larger sizes return LBM_ERR_ARG with the reason in lbm_last_error(). Work is issued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream), which the call synchronises before
+ * it returns; it also copies its tables from host memory. It therefore must not be called on a
+ * stream that is being captured into a CUDA graph: there it returns LBM_ERR_STATE without
+ * issuing work (the capture stays valid). Every call rewrites the whole scratch it reads
+ * (nothing needs to start at zero), but all calls share the one array: calls that overlap on
+ * the GPU (other streams, other host threads) race. */
 int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, double K, double win_alpha, double win_p,
-                            const double *rho, const double *ux, const double *uy, const double *T,
-                            void *stream, double out[5]);
+                            int keff_terms, const double *rho, const double *ux, const double *uy,
+                            const double *T, void *stream, double out[5]);
 
 /* ---- batches of independent simulations ------------------------------------------------
  * Many independent runs of Eq. (1) (parameter scans, ensembles over initial states, the

@@ -63,7 +63,7 @@ _SIGS = {
     "lbm_timing_read": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_device_bytes": (ctypes.c_size_t, [_P]),
     "lbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                _P, _P, _P, _P, _P, _D]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.POINTER(lbm_params), _P,
                                         ctypes.POINTER(_P)]),
@@ -128,13 +128,14 @@ def maxwell(T):
 def diagnostics_noalloc(params, rho, ux, uy, T, stream=None):
     """lbm_diagnostics_noalloc: mass, px, py, energy, umax of moment fields held in CUDA
     float64 tensors (ny, nx), for callers that cannot allocate device memory; the library
-    uses its built-in scratch array (nx * ny <= 2^20)."""
+    uses its built-in scratch array (nx * ny <= 2^20). The grid spacings, K, window and k_eff
+    series length come from `params`. Not for a stream under graph capture (LbmError)."""
     ny, nx = tuple(rho.shape)
     ps = [_dev_ptr(a, (ny, nx)) for a in (rho, ux, uy, T)]
     out = (ctypes.c_double * 5)()
     s = ctypes.c_void_p(stream) if isinstance(stream, int) else (stream or ctypes.c_void_p())
     _check(lib().lbm_diagnostics_noalloc(nx, ny, params.dx, params.dy, params.K, params.win_alpha,
-                                         params.win_p, *ps, s, out))
+                                         params.win_p, params.keff_terms, *ps, s, out))
     return dict(zip(("mass", "px", "py", "energy", "umax"), list(out)))
 
 

@@ -1,17 +1,17 @@
 // Global diagnostics without any device allocation.
 //
-// Some callers cannot allocate device memory at the time they need a diagnostic: code
-// running while a stream is being captured into a CUDA graph (cudaMalloc is not allowed
-// there), host applications or plugins whose GPU memory is owned by another allocator or
-// budgeted up front, and long-running services that must not grow their footprint after
-// start-up. lbm_diagnostics_noalloc serves them. Its scratch (the spectral d_x rho and
-// d_y rho fields, the per-block partial sums and the derivative tables) lives in the
-// file-scope array below, which every GPU that loads this library holds until the process
-// exits. The caller still passes the inputs (device fields) and the output (host array).
+// Some callers cannot allocate device memory at the time they need a diagnostic: host
+// applications or plugins whose GPU memory is owned by another allocator or budgeted up
+// front, and long-running services that must not grow their footprint after start-up.
+// lbm_diagnostics_noalloc serves them. Its scratch (the spectral d_x rho and d_y rho fields,
+// the per-block partial sums and the derivative tables) lives in the file-scope array below,
+// which every GPU that loads this library holds until the process exits. The caller still
+// passes the inputs (device fields) and the output (host array). The call copies its tables
+// from host memory and waits for its stream, so it cannot be recorded into a CUDA graph: on a
+// stream that is being captured it returns LBM_ERR_STATE before issuing any work.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -36,10 +36,6 @@ constexpr size_t kScratchDoubles = kOffTw32 + 2 * kMaxN;  // about 16.3 MiB in t
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-std::mutex g_mu;
-constexpr int kMaxDevices = 64;
-double *g_addr[kMaxDevices] = {};
-
 // errors are reported through lbm_last_error(), like every other entry point
 int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -51,21 +47,17 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
-// Device address of the scratch array on the current device; looked up once per device.
+// Device address of the scratch array in the current device's context. In host code the
+// array's name stands for a host-side shadow, not a device address, so a kernel must be given
+// this address instead. It is looked up on every call (a cheap runtime query that allocates
+// nothing), so a context that was reset and recreated since an earlier call is never handed a
+// stale address.
 int scratch_address(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(LBM_ERR_ARG, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(LBM_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
-        g_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(LBM_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+    *out = static_cast<double *>(p);
     return LBM_OK;
 }
 
@@ -84,8 +76,8 @@ int log2i(int n) {
 }  // namespace
 
 extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, double K, double win_alpha,
-                                       double win_p, const double *rho, const double *ux, const double *uy,
-                                       const double *T, void *stream, double out[5]) {
+                                       double win_p, int keff_terms, const double *rho, const double *ux,
+                                       const double *uy, const double *T, void *stream, double out[5]) {
     if (!rho || !ux || !uy || !T || !out) return fail(LBM_ERR_ARG, "NULL argument");
     if (!pow2(nx) || !pow2(ny) || nx > kMaxN || ny > kMaxN)
         return fail(LBM_ERR_ARG, "nx=%d, ny=%d: each must be a power of two in [2, %d]", nx, ny, kMaxN);
@@ -95,7 +87,13 @@ extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, dou
     if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(K) ||
         !(win_alpha >= 0) || !(win_p > 0))
         return fail(LBM_ERR_ARG, "bad dx, dy, K or window parameters");
+    if (keff_terms < 1 || keff_terms > 8) return fail(LBM_ERR_ARG, "keff_terms must be in [1, 8]");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(LBM_ERR_STATE, "lbm_diagnostics_noalloc cannot run on a stream that is being captured "
+                                   "(it copies from host memory and synchronises); no work was issued");
     double *sc = nullptr;
     int rc = scratch_address(&sc);
     if (rc) return rc;
@@ -107,8 +105,8 @@ extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, dou
     NA_TRY(launch_twiddles(twx, twx32, nx, s));
     NA_TRY(launch_twiddles(twy, twy32, ny, s));
     std::vector<double> tab(4 * (size_t)kMaxN);
-    derivative_tables(nx, dx, win_alpha, win_p, tab.data(), tab.data() + kMaxN);
-    derivative_tables(ny, dy, win_alpha, win_p, tab.data() + 2 * kMaxN, tab.data() + 3 * kMaxN);
+    derivative_tables(nx, dx, win_alpha, win_p, tab.data(), tab.data() + kMaxN, keff_terms);
+    derivative_tables(ny, dy, win_alpha, win_p, tab.data() + 2 * kMaxN, tab.data() + 3 * kMaxN, keff_terms);
     NA_TRY(cudaMemcpyAsync(k1x, tab.data(), 4 * (size_t)kMaxN * sizeof(double), cudaMemcpyHostToDevice, s));
 
     // d_y rho (column pass) and d_x rho (row pass) into the scratch fields
