@@ -115,6 +115,32 @@ int lbm_moments_device(lbm_handle h, double *rho, double *ux, double *uy, double
 int lbm_get_f(lbm_handle h, double *f16);
 int lbm_set_f(lbm_handle h, const double *f16);
 
+/* ---- checkpoint and resume ---------------------------------------------------------
+ * A state blob holds everything a step reads from the previous one, bit for bit: the 16
+ * distributions and the 4 moment fields in the handle's storage precision and device layout,
+ * the step counter, and a hash of the parameters, so that k steps, lbm_get_state, then k more
+ * steps from lbm_set_state (on the same or another handle of the same size and parameters)
+ * give exactly the state of 2k uninterrupted steps. Layout: a 64-byte header
+ * {char magic[8] = "LBMSTATE"; uint32 version = 1; int32 nx, ny, precision; int64 steps;
+ * uint64 params_hash; uint64 payload_bytes; uint32 element_size; uint32 reserved[3]},
+ * then the payload: rows y = 0..ny-1, each the 16 distributions then the moments rho, u_x,
+ * u_y, T of that row (nx values each, element_size bytes per value, host byte order). The
+ * paper has no counterpart (a library service). */
+
+/* Bytes of the blob of an nx x ny simulation in `precision` (host only; 0 for bad sizes). */
+size_t lbm_state_bytes(int nx, int ny, int precision);
+/* 64-bit FNV-1a hash of the parameters (every field of lbm_params in order, doubles by their
+ * bit patterns; host only, 0 for NULL). */
+unsigned long long lbm_params_hash(const lbm_params *params);
+/* Writes the current state into the caller's host buffer of `bytes` >= lbm_state_bytes(...)
+ * (LBM_ERR_ARG if smaller). Synchronises the stream. */
+int lbm_get_state(lbm_handle h, void *blob, size_t bytes);
+/* Replaces the state (distributions, moments, step counter) by a blob from lbm_get_state.
+ * LBM_ERR_ARG if the blob is short, its header is not a version-1 state, or its size,
+ * precision or parameter hash differ from the handle's; nothing is changed then.
+ * LBM_ERR_NONFINITE if a value of the payload is not finite. Synchronises the stream. */
+int lbm_set_state(lbm_handle h, const void *blob, size_t bytes);
+
 /* Global diagnostics (host out[6]): total mass, x and y momentum, total energy
  * sum(e_T) dx dy with e_T = rho T - 9 rho^2/8 + K |grad rho|^2 / 2 + rho u^2 / 2 (Sec. 2.2),
  * max |u|, and the number of steps taken. Synchronises the stream. */
@@ -248,6 +274,10 @@ int lbm_batch_step(lbm_batch b, int n);
 int lbm_batch_moments(lbm_batch b, int k, double *rho, double *ux, double *uy, double *T);
 int lbm_batch_get_f(lbm_batch b, int k, double *f16);
 int lbm_batch_diagnostics(lbm_batch b, int k, double out[6]);
+
+/* lbm_get_state / lbm_set_state of instance k (its own step count). */
+int lbm_batch_get_state(lbm_batch b, int k, void *blob, size_t bytes);
+int lbm_batch_set_state(lbm_batch b, int k, const void *blob, size_t bytes);
 
 /* lbm_autotune for every size group of the batch (all instances initialised); the launch
  * shapes of instance k's group via lbm_batch_geometry. */

@@ -82,6 +82,12 @@ _SIGS = {
     "lbm_batch_autotune": (ctypes.c_int, [_P]),
     "lbm_batch_geometry": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lbm_launch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "lbm_state_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_params_hash": (ctypes.c_ulonglong, [ctypes.POINTER(lbm_params)]),
+    "lbm_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "lbm_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "lbm_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+    "lbm_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
 }
 
 
@@ -137,6 +143,21 @@ def diagnostics_noalloc(params, rho, ux, uy, T, stream=None):
     _check(lib().lbm_diagnostics_noalloc(nx, ny, params.dx, params.dy, params.K, params.win_alpha,
                                          params.win_p, params.keff_terms, *ps, s, out))
     return dict(zip(("mass", "px", "py", "energy", "umax"), list(out)))
+
+
+def state_bytes(nx, ny, precision=LBM_FP64):
+    """lbm_state_bytes: size of the checkpoint blob of an nx x ny simulation (0 for bad sizes)."""
+    return int(lib().lbm_state_bytes(int(nx), int(ny), int(precision)))
+
+
+def params_hash(params):
+    """lbm_params_hash: the 64-bit parameter hash a checkpoint blob carries."""
+    return int(lib().lbm_params_hash(ctypes.byref(params)))
+
+
+def _blob_in(blob):
+    b = bytes(blob)
+    return ctypes.create_string_buffer(b, len(b)), len(b)
 
 
 PLAN_KEYS = ("col_width", "col_threads", "col_smem", "macro_rows", "macro_threads", "macro_smem", "macro_serial",
@@ -250,6 +271,18 @@ class Simulation:
         f = _host(f, (16,) + self.shape)
         _check(lib().lbm_set_f(self._h, _ptr(f)))
 
+    def get_state(self):
+        """Checkpoint blob (bytes): distributions, moments, step counter, parameter hash."""
+        n = state_bytes(self.nx, self.ny, self.params.precision)
+        buf = ctypes.create_string_buffer(n)
+        _check(lib().lbm_get_state(self._h, buf, n))
+        return buf.raw
+
+    def set_state(self, blob):
+        """Resume from a blob of get_state (same size and parameters)."""
+        buf, n = _blob_in(blob)
+        _check(lib().lbm_set_state(self._h, buf, n))
+
     def diagnostics(self):
         """dict(mass, px, py, energy, umax, steps)."""
         out = (ctypes.c_double * 6)()
@@ -349,6 +382,17 @@ class Batch:
         f = np.empty((16,) + self._shape(k))
         _check(lib().lbm_batch_get_f(self._h, int(k), _ptr(f)))
         return f
+
+    def get_state(self, k):
+        nx, ny = self.sizes[k]
+        n = state_bytes(nx, ny, self.params.precision)
+        buf = ctypes.create_string_buffer(n)
+        _check(lib().lbm_batch_get_state(self._h, int(k), buf, n))
+        return buf.raw
+
+    def set_state(self, k, blob):
+        buf, n = _blob_in(blob)
+        _check(lib().lbm_batch_set_state(self._h, int(k), buf, n))
 
     def diagnostics(self, k):
         out = (ctypes.c_double * 6)()

@@ -762,6 +762,123 @@ int set_f_host(lbm_ctx *c, int k, const double *f16) {
     return LBM_OK;
 }
 
+// ---- checkpoint blobs: header, then per row the 16 distributions and the 4 moments --------
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t nx, ny, precision;
+    int64_t steps;
+    uint64_t params_hash;
+    uint64_t payload_bytes;
+    uint32_t element_size;
+    uint32_t reserved[3];
+};
+static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', 'E'};
+
+// FNV-1a (64-bit) over the parameter fields in declaration order, each value's bytes taken
+// least significant first (the same on every host)
+uint64_t hash_params(const lbm_params &p) {
+    uint64_t h = 1469598103934665603ULL;
+    auto bytes = [&h](uint64_t v, int n) {
+        for (int k = 0; k < n; ++k) {
+            h ^= (v >> (8 * k)) & 0xffu;
+            h *= 1099511628211ULL;
+        }
+    };
+    auto dbl = [&bytes](double d) {
+        uint64_t u;
+        std::memcpy(&u, &d, 8);
+        bytes(u, 8);
+    };
+    auto i32 = [&bytes](int v) { bytes((uint32_t)v, 4); };
+    for (double d : {p.tau, p.dt, p.dx, p.dy, p.K, p.H, p.q, p.zeta, p.b, p.eta0, p.win_alpha, p.win_p}) dbl(d);
+    i32(p.precision);
+    i32(p.flags);
+    dbl(p.T_iso);
+    i32(p.keff_terms);
+    i32(p.reserved);
+    return h;
+}
+
+size_t state_payload(int nx, int ny, size_t es) { return (size_t)ny * (NF_F + 4) * nx * es; }
+
+int get_state_host(lbm_ctx *c, int k, long long steps, void *blob, size_t bytes) {
+    const size_t es = c->fsize, nx = c->nx, ny = c->ny, pay = state_payload(c->nx, c->ny, es);
+    if (!blob) return fail(LBM_ERR_ARG, "NULL blob");
+    if (bytes < sizeof(StateHeader) + pay)
+        return fail(LBM_ERR_ARG, "blob of %zu bytes, the state needs %zu", bytes, sizeof(StateHeader) + pay);
+    StateHeader hd{};
+    std::memcpy(hd.magic, kStateMagic, 8);
+    hd.version = 1;
+    hd.nx = c->nx;
+    hd.ny = c->ny;
+    hd.precision = c->p.precision;
+    hd.steps = steps;
+    hd.params_hash = hash_params(c->p);
+    hd.payload_bytes = pay;
+    hd.element_size = (uint32_t)es;
+    std::memcpy(blob, &hd, sizeof hd);
+    char *dst = static_cast<char *>(blob) + sizeof hd;
+    const size_t row = (NF_F + 4) * nx * es;
+    const char *f = static_cast<const char *>(c->f0) + c->row0(k) * NF_F * nx * es;
+    const char *m = static_cast<const char *>(c->m) + c->row0(k) * NF_M * nx * es;
+    CU_TRY(cudaMemcpy2DAsync(dst, row, f, NF_F * nx * es, NF_F * nx * es, ny, cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaMemcpy2DAsync(dst + NF_F * nx * es, row, m, NF_M * nx * es, 4 * nx * es, ny, cudaMemcpyDeviceToHost,
+                             c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+// validates a blob against context c; on success *steps is its step counter
+int check_state(const lbm_ctx *c, const void *blob, size_t bytes, long long *steps) {
+    const size_t es = c->fsize, pay = state_payload(c->nx, c->ny, es);
+    if (!blob) return fail(LBM_ERR_ARG, "NULL blob");
+    if (bytes < sizeof(StateHeader)) return fail(LBM_ERR_ARG, "blob of %zu bytes has no header", bytes);
+    StateHeader hd;
+    std::memcpy(&hd, blob, sizeof hd);
+    if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != 1)
+        return fail(LBM_ERR_ARG, "not a version-1 state blob");
+    if (hd.nx != c->nx || hd.ny != c->ny || hd.precision != c->p.precision || hd.element_size != es ||
+        hd.payload_bytes != pay)
+        return fail(LBM_ERR_ARG, "blob of a %d x %d state in precision %d, the handle is %d x %d in %d", hd.nx, hd.ny,
+                    hd.precision, c->nx, c->ny, c->p.precision);
+    if (hd.params_hash != hash_params(c->p))
+        return fail(LBM_ERR_ARG, "blob was written with other parameters (hash %016llx, handle %016llx)",
+                    (unsigned long long)hd.params_hash, (unsigned long long)hash_params(c->p));
+    if (bytes < sizeof hd + pay) return fail(LBM_ERR_ARG, "blob of %zu bytes is truncated", bytes);
+    if (hd.steps < 0) return fail(LBM_ERR_ARG, "negative step count in the blob");
+    const char *src = static_cast<const char *>(blob) + sizeof hd;
+    const size_t vals = pay / es;
+    for (size_t j = 0; j < vals; ++j) {
+        double v;
+        if (es == 4) {
+            float x;
+            std::memcpy(&x, src + j * 4, 4);
+            v = x;
+        } else {
+            std::memcpy(&v, src + j * 8, 8);
+        }
+        if (!std::isfinite(v)) return fail(LBM_ERR_NONFINITE, "blob value %zu is not finite", j);
+    }
+    *steps = hd.steps;
+    return LBM_OK;
+}
+
+int set_state_host(lbm_ctx *c, int k, const void *blob) {
+    const size_t es = c->fsize, nx = c->nx, ny = c->ny;
+    const size_t row = (NF_F + 4) * nx * es;
+    const char *src = static_cast<const char *>(blob) + sizeof(StateHeader);
+    char *f = static_cast<char *>(c->f0) + c->row0(k) * NF_F * nx * es;
+    char *m = static_cast<char *>(c->m) + c->row0(k) * NF_M * nx * es;
+    CU_TRY(cudaMemcpy2DAsync(f, NF_F * nx * es, src, row, NF_F * nx * es, ny, cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaMemcpy2DAsync(m, NF_M * nx * es, src + NF_F * nx * es, row, 4 * nx * es, ny, cudaMemcpyHostToDevice,
+                             c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    c->initialized[k] = 1;
+    return LBM_OK;
+}
+
 template <typename R> int diag_launch(lbm_ctx *c, int k) {
     // d_y rho into M_RY, d_x rho into M_DQX of instance k (stage scratch, rebuilt by the next stage)
     const int nx = c->nx, ldm = NF_M * nx;
@@ -991,6 +1108,31 @@ int lbm_get_f(lbm_handle c, double *f16) {
 int lbm_set_f(lbm_handle c, const double *f16) {
     if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
     return set_f_host(c, 0, f16);
+}
+
+size_t lbm_state_bytes(int nx, int ny, int precision) {
+    if (!is_pow2(nx) || !is_pow2(ny) || nx > 4096 || ny > 4096) return 0;
+    if (precision != LBM_FP64 && precision != LBM_MIXED) return 0;
+    return sizeof(StateHeader) + state_payload(nx, ny, precision == LBM_MIXED ? 4 : 8);
+}
+
+unsigned long long lbm_params_hash(const lbm_params *params) { return params ? hash_params(*params) : 0ULL; }
+
+int lbm_get_state(lbm_handle c, void *blob, size_t bytes) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
+    return get_state_host(c, 0, c->steps, blob, bytes);
+}
+
+int lbm_set_state(lbm_handle c, const void *blob, size_t bytes) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    long long steps = 0;
+    int rc = check_state(c, blob, bytes, &steps);
+    if (rc) return rc;
+    rc = set_state_host(c, 0, blob);
+    if (rc) return rc;
+    c->steps = steps;
+    return LBM_OK;
 }
 
 int lbm_diagnostics(lbm_handle c, double out[6]) {
@@ -1305,6 +1447,27 @@ int lbm_batch_get_f(lbm_batch b, int k, double *f16) {
     if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
     CU_TRY(cudaStreamSynchronize(b->stream));
     return get_f_host(c, b->where[k].second, f16);
+}
+
+int lbm_batch_get_state(lbm_batch b, int k, void *blob, size_t bytes) {
+    if (!b || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
+    lbm_ctx *c = b->groups[b->where[k].first];
+    if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    return get_state_host(c, b->where[k].second, b->steps[k], blob, bytes);
+}
+
+int lbm_batch_set_state(lbm_batch b, int k, const void *blob, size_t bytes) {
+    if (!b || k < 0 || k >= (int)b->where.size()) return fail(LBM_ERR_ARG, "bad batch or instance");
+    lbm_ctx *c = b->groups[b->where[k].first];
+    long long steps = 0;
+    int rc = check_state(c, blob, bytes, &steps);
+    if (rc) return rc;
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    rc = set_state_host(c, b->where[k].second, blob);
+    if (rc) return rc;
+    b->steps[k] = steps;
+    return LBM_OK;
 }
 
 int lbm_batch_diagnostics(lbm_batch b, int k, double out[6]) {

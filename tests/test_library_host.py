@@ -171,3 +171,25 @@ def test_launch_plan_rejects_bad_sizes(L):
             lbm.launch_plan(nx, ny)
     with pytest.raises(lbm.LbmError, match="precision"):
         lbm.launch_plan(8, 8, 7)
+
+
+def test_state_blob_size_and_params_hash(L):
+    # header of 64 bytes, then per row 16 distributions + 4 moments in the storage precision
+    assert lbm.state_bytes(64, 32, lbm.LBM_FP64) == 64 + 32 * 20 * 64 * 8
+    assert lbm.state_bytes(64, 32, lbm.LBM_MIXED) == 64 + 32 * 20 * 64 * 4
+    assert lbm.state_bytes(63, 32) == 0 and lbm.state_bytes(64, 32, 7) == 0
+    a, b = lbm.default_params(), lbm.default_params()
+    assert lbm.params_hash(a) == lbm.params_hash(b) != 0
+    for field, value in (("tau", 2e-4), ("K", 5.000001e-6), ("precision", lbm.LBM_MIXED), ("flags", 8),
+                         ("keff_terms", 4), ("win_alpha", 36.0)):
+        c = lbm.default_params(**{field: value})
+        assert lbm.params_hash(c) != lbm.params_hash(a), field
+    # FNV-1a over the field bytes, least significant first, written out here independently
+    import struct
+    h = 1469598103934665603
+    raw = struct.pack("<12d", a.tau, a.dt, a.dx, a.dy, a.K, a.H, a.q, a.zeta, a.b, a.eta0, a.win_alpha, a.win_p)
+    raw += struct.pack("<ii", a.precision, a.flags) + struct.pack("<d", a.T_iso)
+    raw += struct.pack("<ii", a.keff_terms, a.reserved)
+    for byte in raw:
+        h = ((h ^ byte) * 1099511628211) % (1 << 64)
+    assert lbm.params_hash(a) == h
