@@ -213,6 +213,31 @@ int lbm_launch_plan(int nx, int ny, int precision, int out[16]);
 int lbm_set_geometry(lbm_handle h, const int geometry[4]);
 int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
 
+/* Form of the two column passes (no counterpart in the paper: a performance choice that does
+ * not change any result). kinds[0]: the column pass, kinds[1]: the flux column pass;
+ * LBM_COL_DIRECT: each CTA loads its column tile straight from global memory, transforms and
+ * stores it; LBM_COL_TMA: a persistent grid whose CTAs stage the next tile in shared memory with
+ * tiled bulk tensor copies (TMA) while they transform the current one. lbm_autotune chooses
+ * the kinds together with the tile widths. lbm_set_pass_kinds returns LBM_ERR_ARG if the TMA form
+ * cannot take the current width (rows of fewer than 16 bytes, or staging buffers beyond a CTA's
+ * shared memory); where a launch still cannot use it, the direct form runs. */
+#define LBM_COL_DIRECT 0
+#define LBM_COL_TMA 1
+int lbm_pass_kinds(lbm_handle h, int kinds[2]);
+int lbm_set_pass_kinds(lbm_handle h, const int kinds[2]);
+
+/* Fault injection for tests (no counterpart in the paper). Every device-side wait of the
+ * library (the TMA column pass waiting for its copies) is bounded by `wait_cycles` clock
+ * cycles (<= 0: the default, about one second); a wait that runs out makes its kernel record
+ * the failure in the handle's device error word and return, and the next synchronising call
+ * (lbm_synchronize, lbm_moments, lbm_get_f, lbm_get_state, lbm_diagnostics) returns
+ * LBM_ERR_TIMEOUT once. LBM_FAULT_STARVE_COPIES makes the TMA column pass arm its barriers
+ * without issuing the copies, so that its first wait runs out (nothing is copied, nothing
+ * faults); LBM_FAULT_NONE restores normal operation. */
+#define LBM_FAULT_NONE 0
+#define LBM_FAULT_STARVE_COPIES 1
+int lbm_fault_inject(lbm_handle h, int what, long long wait_cycles);
+
 /* lbm_diagnostics for callers that cannot allocate device memory. The paper has no
  * counterpart: this is a library service. Examples: host applications or plugins whose GPU
  * memory belongs to another allocator or is budgeted at start-up, and services that must not

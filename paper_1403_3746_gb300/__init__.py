@@ -23,12 +23,19 @@ LBM_FLAG_NO_FORCE = 4
 LBM_FLAG_EULER = 8
 LBM_FLAG_ISOTHERMAL = 16
 KERNELS = {"col": 0, "macro": 1, "flux": 2, "update": 3}
+LBM_COL_DIRECT = 0
+LBM_COL_TMA = 1
+LBM_FAULT_NONE = 0
+LBM_FAULT_STARVE_COPIES = 1
+LBM_ERR_TIMEOUT = -5
 
 _lib = None
 
 
 class LbmError(RuntimeError):
-    pass
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 class lbm_params(ctypes.Structure):
@@ -83,6 +90,9 @@ _SIGS = {
     "lbm_batch_geometry": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lbm_launch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "lbm_state_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_pass_kinds": (ctypes.c_int, [_P, _P]),
+    "lbm_set_pass_kinds": (ctypes.c_int, [_P, _P]),
+    "lbm_fault_inject": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong]),
     "lbm_params_hash": (ctypes.c_ulonglong, [ctypes.POINTER(lbm_params)]),
     "lbm_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "lbm_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
@@ -110,7 +120,7 @@ def lib():
 def _check(rc):
     if rc != LBM_OK:
         L = lib()
-        raise LbmError(f"{L.lbm_strerror(rc).decode()} ({rc}): {L.lbm_last_error().decode()}")
+        raise LbmError(f"{L.lbm_strerror(rc).decode()} ({rc}): {L.lbm_last_error().decode()}", rc)
 
 
 def default_params(**kw):
@@ -316,6 +326,20 @@ class Simulation:
     def set_geometry(self, geometry):
         g = (ctypes.c_int * 4)(*[int(v) for v in geometry])
         _check(lib().lbm_set_geometry(self._h, ctypes.cast(g, _P)))
+
+    def pass_kinds(self):
+        """(column pass kind, flux column pass kind): LBM_COL_DIRECT or LBM_COL_TMA."""
+        k = (ctypes.c_int * 2)()
+        _check(lib().lbm_pass_kinds(self._h, ctypes.cast(k, _P)))
+        return tuple(k)
+
+    def set_pass_kinds(self, kinds):
+        k = (ctypes.c_int * 2)(*[int(v) for v in kinds])
+        _check(lib().lbm_set_pass_kinds(self._h, ctypes.cast(k, _P)))
+
+    def fault_inject(self, what, wait_cycles=0):
+        """Test hook: LBM_FAULT_STARVE_COPIES makes the TMA column pass's bounded wait run out."""
+        _check(lib().lbm_fault_inject(self._h, int(what), int(wait_cycles)))
 
     def autotune(self):
         """Times the launch-shape candidates on this simulation and keeps the fastest;

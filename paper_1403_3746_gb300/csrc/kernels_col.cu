@@ -7,6 +7,11 @@
 // segment of W values is one coalesced access. Forward transform, derivative multiplier
 // and inverse transform run in registers with shared-memory exchanges (fft_reg.cuh); the
 // result is written back in the same layout. blockIdx.y selects the job (input, output).
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -48,6 +53,181 @@ template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R
     col_deriv_kernel<R, LOG2N><<<grid, (a.W / 2) * F::G, smem, s>>>(a);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------------------
+// TMA-fed column pass. A persistent CTA walks the work items it + k gridDim (item = tile of W
+// columns of one job's field in one instance). Item k is staged in buffer k & 1: thread 0
+// arms that buffer's barrier with the tile's byte count and issues ny / boxr tiled copies of
+// (W x boxr) boxes; the copies of item k + 1 land while item k is transformed. Once every
+// thread has read its points of item k into registers, the same buffer serves as the line
+// buffers of item k's transforms (it is at least as large as both); after the CTA barrier
+// that ends item k it is handed back to the copy engine for item k + 2. Results are written
+// from registers, as in col_deriv_kernel, so every output value is bit for bit the same.
+// ---------------------------------------------------------------------------------------
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks)
+    col_tma_kernel(const __grid_constant__ ColTmaArgs<R> a) {
+    using F = reg::LineFFT<R, LOG2N, true>;
+    using CT = typename F::CT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const ColArgs<R> &c = a.c;
+    const int W = c.W, L = W >> 1;
+    const int l = threadIdx.x & (L - 1), t = threadIdx.x >> (c.log2W - 1);
+    unsigned char *stage0 = smem_raw, *stage1 = smem_raw + a.stage_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * (size_t)a.stage_bytes);
+    volatile int *flag = reinterpret_cast<volatile int *>(bar + 2);
+    const int tiles = c.nx / W, nb = c.nb > 0 ? c.nb : 1;
+    const unsigned tile_bytes = (unsigned)c.ny * (unsigned)W * (unsigned)sizeof(R);
+    // item -> (job, instance, tile), tile fastest
+    auto job_of = [&](int it) { return it / (tiles * nb); };
+    auto z_of = [&](int it) { return (it % (tiles * nb)) / tiles; };
+    auto tile_of = [&](int it) { return it % tiles; };
+    auto issue = [&](int it, int b) {  // thread 0
+        tma::bar_arrive_expect_tx(&bar[b], tile_bytes);
+        if (a.starve) return;  // fault injection: the barrier is armed, no copy will complete it
+        unsigned char *dst = b ? stage1 : stage0;
+        const int job = job_of(it), y0 = z_of(it) * c.ny, x0 = tile_of(it) * W;
+        for (int r0 = 0; r0 < c.ny; r0 += a.boxr)
+            tma::load_2d(dst + (size_t)r0 * W * sizeof(R), &a.map[job], x0, y0 + r0, &bar[b]);
+    };
+    bool pend0 = false, pend1 = false;  // thread 0: copies in flight per buffer
+    if (threadIdx.x == 0) {
+        tma::bar_init(&bar[0], 1);
+        tma::bar_init(&bar[1], 1);
+        tma::fence_bar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (blockIdx.x < a.items) issue(blockIdx.x, 0), pend0 = true;
+        if (blockIdx.x + gridDim.x < a.items) issue(blockIdx.x + gridDim.x, 1), pend1 = true;
+    }
+    int k = 0;
+    for (int it = blockIdx.x; it < a.items; it += gridDim.x, ++k) {
+        const int b = k & 1;
+        if (threadIdx.x == 0) {
+            bool ok = tma::bar_wait_bounded(&bar[b], (k >> 1) & 1, a.wait_cycles);
+            if (b) pend1 = false; else pend0 = false;
+            if (!ok) {
+                atomicOr(a.err, tma::kErrTimeout);
+                // the other buffer's copies (item k + 1) may still land: wait for them, bounded
+                if (b ? pend0 : pend1) tma::bar_wait_bounded(&bar[b ^ 1], ((k + 1) >> 1) & 1, a.wait_cycles);
+            }
+            *flag = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!*flag) return;  // uniform: every thread read the same flag
+        const ColJob<R> &jb = c.jobs[job_of(it)];
+        CT *st = reinterpret_cast<CT *>(b ? stage1 : stage0);
+        CT v[F::E];
+#pragma unroll
+        for (int e = 0; e < F::E; ++e) v[e] = st[(size_t)(t + F::G * e) * L + l];  // row t + G e, columns 2l, 2l+1
+        CT *buf = st + l * F::STRIDE;
+        F::template forward<reg::SyncCta>(v, buf, t, c.ay.tw);
+        F::multiply(v, t, jb.order, jb.c, c.ay.k1, c.ay.k2);
+        F::template inverse<reg::SyncCta>(v, buf, t, c.ay.tw);
+        const size_t rso = (size_t)(jb.ld_out >> 1);
+        CT *out = reinterpret_cast<CT *>(jb.out + (size_t)z_of(it) * c.ny * jb.ld_out + tile_of(it) * W + 2 * l);
+#pragma unroll
+        for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rso] = v[e];
+        reg::cta_barrier();  // every thread is done with this buffer
+        if (threadIdx.x == 0 && it + 2 * (int)gridDim.x < a.items) {
+            tma::fence_proxy_async_smem();
+            issue(it + 2 * gridDim.x, b);
+            if (b) pend1 = true; else pend0 = true;
+        }
+    }
+}
+
+size_t col_tma_smem(int nx, int ny, int W, size_t esize) {
+    if (W < 2 || W > nx || (W * esize) % 16 != 0 || (W * esize) > 256) return 0;
+    int l2 = 0;
+    while ((1 << l2) < ny) ++l2;
+    const size_t lines = (size_t)(W / 2) * line_smem(l2) * 2 * esize;
+    const size_t tile = (size_t)ny * W * esize;
+    const size_t sb = (std::max(lines, tile) + 127) & ~(size_t)127;
+    return 2 * sb + 32;
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    return g_encode;
+}
+}  // namespace
+
+template <typename R, int LOG2N>
+static cudaError_t launch_col_tma_n(const ColTmaArgs<R> &a, size_t smem, cudaStream_t s) {
+    using F = reg::LineFFT<R, LOG2N>;
+    const int threads = (a.c.W / 2) * F::G;
+    if (threads > PassThreads<R>::value || a.stage_bytes < (unsigned)((a.c.W / 2) * F::STRIDE * sizeof(typename F::CT)))
+        return cudaErrorNotSupported;
+    cudaError_t e = allow_smem(col_tma_kernel<R, LOG2N>);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, col_tma_kernel<R, LOG2N>, threads, smem)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    const int grid = std::min(a.items, sms * per_sm);
+    col_tma_kernel<R, LOG2N><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_col_tma(const ColArgs<R> &c, int njobs, int *err, long long wait_cycles, int starve,
+                           cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    const size_t es = sizeof(R);
+    const size_t smem = col_tma_smem(c.nx, c.ny, c.W, es);
+    if (smem == 0 || smem > kMaxCtaSmem || !err) return cudaErrorNotSupported;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    ColTmaArgs<R> a{};
+    a.c = c;
+    a.boxr = std::min(c.ny, 256);
+    const int nb = c.nb > 0 ? c.nb : 1;
+    a.items = njobs * (c.nx / c.W) * nb;
+    a.stage_bytes = (unsigned)((smem - 32) / 2);
+    a.err = err;
+    a.wait_cycles = wait_cycles;
+    a.starve = starve;
+    for (int j = 0; j < njobs; ++j) {
+        const ColJob<R> &jb = c.jobs[j];
+        const cuuint64_t dims[2] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny * nb};
+        const cuuint64_t strides[1] = {(cuuint64_t)jb.ld_in * es};
+        const cuuint32_t box[2] = {(cuuint32_t)c.W, (cuuint32_t)a.boxr};
+        const cuuint32_t estr[2] = {1, 1};
+        if ((reinterpret_cast<uintptr_t>(jb.in) & 15) || (strides[0] & 15)) return cudaErrorNotSupported;
+        const CUresult r = enc(&a.map[j], es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                               2, const_cast<R *>(jb.in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorNotSupported;
+    }
+    switch (c.ay.log2n) {
+#define LBM_CASE(L2) \
+    case L2: return launch_col_tma_n<R, L2>(a, smem, s);
+        LBM_FOR_LOG2N(LBM_CASE)
+#undef LBM_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_col_tma<double>(const ColArgs<double> &, int, int *, long long, int, cudaStream_t);
+template cudaError_t launch_col_tma<float>(const ColArgs<float> &, int, int *, long long, int, cudaStream_t);
 
 template <typename R>
 cudaError_t launch_col(const ColArgs<R> &a, int njobs, size_t smem, cudaStream_t s) {

@@ -111,6 +111,9 @@ struct lbm_ctx {
     void *Ax = nullptr;                 // [nb ny][16][nx]: d_x f_i, only when geo.upd_ax
     double *partial = nullptr;
     int diag_blocks = 0;
+    int *err = nullptr;               // device error word of the bounded waits (tma::kErrTimeout)
+    long long wait_cycles = 1LL << 31;  // budget of one device-side wait (about a second)
+    int starve = 0;                   // fault-injection hook (lbm_fault_inject)
     // per-axis tables
     double2 *tw64x = nullptr, *tw64y = nullptr;
     float2 *tw32x = nullptr, *tw32y = nullptr;
@@ -205,6 +208,18 @@ template <typename R> ColArgs<R> col_args(const lbm_ctx *c, int nb, int W) {
 // pass selection for run_stage (all by default; the autotuner times them one at a time)
 enum { PASS_COL = 1, PASS_MACRO = 2, PASS_FLUX = 4, PASS_UPDATE = 8, PASS_ALL = 15 };
 
+// A column pass in the chosen form: the TMA-fed kernel, or direct loads (also where TMA cannot
+// serve the shape: rows narrower than 16 bytes, misaligned fields)
+template <typename R>
+cudaError_t launch_col_pass(const lbm_ctx *c, const ColArgs<R> &a, int nj, bool tma, size_t direct_smem) {
+    if (tma) {
+        const cudaError_t e = launch_col_tma<R>(a, nj, c->err, c->wait_cycles, c->starve, c->stream);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
+    }
+    return launch_col<R>(a, nj, direct_smem, c->stream);
+}
+
 template <typename R>
 int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
     const lbm_params &p = c->p;
@@ -234,7 +249,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
         }
         if (nj && (passes & PASS_COL)) {
             LaunchTimer t(c, LBM_K_COL);
-            CU_TRY(launch_col<R>(a, nj, c->geo.col_smem, c->stream));
+            CU_TRY(launch_col_pass<R>(c, a, nj, c->geo.col_tma, c->geo.col_smem));
         }
     }
     if (frc && (passes & PASS_MACRO)) {
@@ -257,7 +272,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
             a.jobs[2] = ColJob<R>{M(M_SYY), M(M_DSYY), ldm, ldm, 1, R(1)};
             a.jobs[3] = ColJob<R>{M(M_DIVU), M(M_DDIVUY), ldm, ldm, 1, R(1)};
             LaunchTimer t(c, LBM_K_FLUX);
-            CU_TRY(launch_col<R>(a, 4, c->geo.flux_smem, c->stream));
+            CU_TRY(launch_col_pass<R>(c, a, 4, c->geo.flux_tma, c->geo.flux_smem));
         }
     }
     if ((passes & PASS_UPDATE) && adv && c->geo.upd_ax) {
@@ -354,6 +369,12 @@ std::vector<int> col_candidates(const lbm_ctx *c) {
             out.push_back(W);
     return out;
 }
+// Whether the TMA-fed column kernel can take tiles of W columns: rows of at least 16 bytes,
+// aligned field rows, its staging buffers within a CTA's shared memory.
+bool col_tma_ok(const lbm_ctx *c, int W) {
+    const size_t sm = col_tma_smem(c->nx, c->ny, W, c->fsize);
+    return sm > 0 && sm <= kMaxCtaSmem && (c->nx * c->fsize) % 16 == 0;
+}
 // Candidate rows per CTA of the update pass (6 line buffers per row within a CTA's shared memory).
 std::vector<int> upd_candidates(const lbm_ctx *c) {
     std::vector<int> out;
@@ -439,15 +460,22 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
         if (pass == PASS_FLUX && !frc) continue;
         int &Wg = pass == PASS_COL ? c->geo.colW : c->geo.fluxW;
         size_t &Sg = pass == PASS_COL ? c->geo.col_smem : c->geo.flux_smem;
+        bool &Kg = pass == PASS_COL ? c->geo.col_tma : c->geo.flux_tma;
         int bestW = Wg;
+        bool bestK = Kg;
         float bt = 1e30f;
-        for (int W : col_candidates(c)) {
-            Wg = W;
-            Sg = (size_t)(W / 2) * line_smem(c->ly) * 2 * es;
-            if ((rc = time_passes<R>(c, pass, e0, e1, &t))) return done(rc);
-            if (t < bt) bt = t, bestW = W;
+        for (bool kind : {false, true}) {
+            for (int W : col_candidates(c)) {
+                if (kind && !col_tma_ok(c, W)) continue;
+                Wg = W;
+                Kg = kind;
+                Sg = (size_t)(W / 2) * line_smem(c->ly) * 2 * es;
+                if ((rc = time_passes<R>(c, pass, e0, e1, &t))) return done(rc);
+                if (t < bt) bt = t, bestW = W, bestK = kind;
+            }
         }
         Wg = bestW;
+        Kg = bestK;
         Sg = (size_t)(bestW / 2) * line_smem(c->ly) * 2 * es;
         best_ms[pass == PASS_COL ? 0 : 3] = bt;
     }
@@ -587,6 +615,7 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     parts.push_back({&c->m, (size_t)NF_M * plane_f});
     if (c->geo.upd_ax) parts.push_back({&c->Ax, 16 * plane_f});
     parts.push_back({reinterpret_cast<void **>(&c->partial), (size_t)c->diag_blocks * 5 * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->err), sizeof(int)});
     parts.push_back({reinterpret_cast<void **>(&c->tw64x), (size_t)nx * 16});
     parts.push_back({reinterpret_cast<void **>(&c->tw64y), (size_t)ny * 16});
     parts.push_back({reinterpret_cast<void **>(&c->tw32x), (size_t)nx * 8});
@@ -613,7 +642,8 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     }
 
     // tables: twiddles on the device (sincospi), multipliers on the host (Eq. (3))
-    cudaError_t e = launch_twiddles(c->tw64x, c->tw32x, nx, c->stream);
+    cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_twiddles(c->tw64x, c->tw32x, nx, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->tw64y, c->tw32y, ny, c->stream);
     for (int ax = 0; ax < 2 && e == cudaSuccess; ++ax) {
         const int N = ax == 0 ? nx : ny;
@@ -640,6 +670,20 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     }
     *out = c;
     return LBM_OK;
+}
+
+// After a synchronisation of the context's stream: the error word of the bounded device
+// waits. A set word is reported once (and cleared) as LBM_ERR_TIMEOUT.
+int check_device_error(lbm_ctx *c) {
+    int v = 0;
+    CU_TRY(cudaMemcpyAsync(&v, c->err, sizeof v, cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    if (v == 0) return LBM_OK;
+    CU_TRY(cudaMemsetAsync(c->err, 0, sizeof v, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    return fail(LBM_ERR_TIMEOUT, "a bounded device-side wait gave up (error word %d): the steps since the last "
+                "check did not complete and the state is not valid",
+                v);
 }
 
 // f_i := f_i^eq(rho, u, T) for instance k from device arrays [ny][nx]
@@ -708,7 +752,7 @@ int moments_host(lbm_ctx *c, int k, double *rho, double *ux, double *uy, double 
     for (int j = 0; j < 4; ++j)
         if (host[j]) CU_TRY(cudaMemcpyAsync(host[j], dev[j], (size_t)c->n * 8, cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 // the API's [16][ny][nx] float64 layout <-> the device block [ny][16][nx] of instance k
@@ -718,6 +762,7 @@ int get_f_host(lbm_ctx *c, int k, double *f16) {
     const char *src0 = static_cast<const char *>(c->f0) + c->row0(k) * NF_F * nx * c->fsize;
     CU_TRY(cudaMemcpyAsync(tmp.data(), src0, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
+    if (int rc = check_device_error(c)) return rc;
     for (size_t y = 0; y < ny; ++y)
         for (size_t i = 0; i < 16; ++i) {
             const size_t src = (y * 16 + i) * nx, dst = (i * ny + y) * nx;
@@ -827,7 +872,7 @@ int get_state_host(lbm_ctx *c, int k, long long steps, void *blob, size_t bytes)
     CU_TRY(cudaMemcpy2DAsync(dst + NF_F * nx * es, row, m, NF_M * nx * es, 4 * nx * es, ny, cudaMemcpyDeviceToHost,
                              c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 // validates a blob against context c; on success *steps is its step counter
@@ -919,6 +964,7 @@ int diagnostics_instance(lbm_ctx *c, int k, long long steps, double out[6]) {
     std::vector<double> part((size_t)c->diag_blocks * 5);
     CU_TRY(cudaMemcpyAsync(part.data(), c->partial, part.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
+    if ((rc = check_device_error(c))) return rc;
     double s[4] = {0, 0, 0, 0}, mx = 0;
     for (int b = 0; b < c->diag_blocks; ++b) {
         for (int j = 0; j < 4; ++j) s[j] += part[b * 5 + j];
@@ -1144,6 +1190,43 @@ int lbm_diagnostics(lbm_handle c, double out[6]) {
 int lbm_synchronize(lbm_handle c) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
     CU_TRY(cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+}
+
+int lbm_pass_kinds(lbm_handle c, int kinds[2]) {
+    if (!c || !kinds) return fail(LBM_ERR_ARG, "NULL argument");
+    kinds[0] = c->geo.col_tma ? LBM_COL_TMA : LBM_COL_DIRECT;
+    kinds[1] = c->geo.flux_tma ? LBM_COL_TMA : LBM_COL_DIRECT;
+    return LBM_OK;
+}
+
+int lbm_set_pass_kinds(lbm_handle c, const int kinds[2]) {
+    if (!c || !kinds) return fail(LBM_ERR_ARG, "NULL argument");
+    for (int j = 0; j < 2; ++j) {
+        if (kinds[j] != LBM_COL_DIRECT && kinds[j] != LBM_COL_TMA) return fail(LBM_ERR_ARG, "unknown pass kind");
+        const int W = j == 0 ? c->geo.colW : c->geo.fluxW;
+        if (kinds[j] == LBM_COL_TMA && !col_tma_ok(c, W))
+            return fail(LBM_ERR_ARG, "the TMA column pass cannot take %d-column tiles of %d x %d", W, c->nx, c->ny);
+    }
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    c->geo.col_tma = kinds[0] == LBM_COL_TMA;
+    c->geo.flux_tma = kinds[1] == LBM_COL_TMA;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
+int lbm_fault_inject(lbm_handle c, int what, long long wait_cycles) {
+    if (!c || (what != LBM_FAULT_NONE && what != LBM_FAULT_STARVE_COPIES)) return fail(LBM_ERR_ARG, "bad argument");
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    c->starve = what == LBM_FAULT_STARVE_COPIES ? 1 : 0;
+    c->wait_cycles = wait_cycles > 0 ? wait_cycles : (1LL << 31);
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     return LBM_OK;
 }
 

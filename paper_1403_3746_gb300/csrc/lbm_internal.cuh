@@ -18,6 +18,7 @@
 
 #include "fft_reg.cuh"
 #include "lbm_d2v16.h"
+#include "tma.cuh"
 
 namespace lbm {
 
@@ -104,6 +105,8 @@ struct Geometry {
     size_t upd_smem = 0, macro_smem = 0, rowd_smem = 0;
     bool upd_ax = false;        // update pass takes d_x f from a separate row pass (Ax)
     bool macro_serial = false;  // macro pass transforms a row's two lines in turn
+    bool col_tma = false;       // column pass: TMA-fed persistent kernel (width colW) instead of direct loads
+    bool flux_tma = false;      // flux column pass: the same choice (width fluxW)
 };
 void pass_geometry(int nx, int ny, size_t esize, Geometry *g);
 
@@ -149,6 +152,29 @@ template <typename R> struct ColArgs {
     int nb;                // instances stacked along y (grid.z); row k ny + y of a field = instance k, row y
     Axis<R> ay;
 };
+
+// TMA-fed column pass (kernels_col.cu): a persistent grid of CTAs walks the work items
+// (job, tile of W columns, instance); each CTA stages its next item's whole column tile in
+// shared memory with tiled bulk tensor copies while it transforms the current one, and the
+// staging buffer of the current item doubles as its transforms' line buffers.
+template <typename R> struct ColTmaArgs {
+    CUtensorMap map[LBM_MAX_COLJOBS];  // per job: the input field as a 2D tensor (nx, nb ny), box (W, boxr)
+    ColArgs<R> c;
+    int boxr;             // rows per copy (<= 256)
+    int items;            // jobs x tiles x instances
+    unsigned stage_bytes; // one staging buffer (also the item's line buffers), multiple of 128
+    int *err;             // device error word (tma::kErrTimeout when a bounded wait gives up)
+    long long wait_cycles;  // budget of one wait
+    int starve;           // fault-injection hook: arm the barriers but issue no copies
+};
+// Shared memory of the TMA column pass for a tile of W columns of ny rows (two staging buffers
+// and two barriers); 0 if TMA cannot serve the shape.
+size_t col_tma_smem(int nx, int ny, int W, size_t esize);
+// Encodes the job tensor maps and launches on a persistent grid (at most `max_ctas` CTAs, 0 =
+// as many as fit); cudaErrorNotSupported when the shape or the driver cannot use TMA.
+template <typename R>
+cudaError_t launch_col_tma(const ColArgs<R> &a, int njobs, int *err, long long wait_cycles, int starve,
+                           cudaStream_t s);
 
 // ---- row pass of the macroscopic chain ---------------------------------------------
 template <typename R> struct MacroArgs {
