@@ -175,11 +175,15 @@ __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R,
 
 // ---------------------------------------------------------------------------------------
 // Moment sums of the new f (Sec. 2.1): rho = sum f, j = sum f v, E = sum f psi.
-// float64 path: plain sums. float32 path: each sum is accumulated with error-free
-// transformations (Knuth's TwoSum and the FMA-based TwoProduct, as in the compensated
-// dot product "Dot2" of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)), so the
-// sums of the stored float32 values are as accurate as in twice the working precision;
-// the irrational weights sqrt2 and 3/sqrt2 enter as float32 pairs (hi + lo).
+// float64 path: plain sums. float32 path: a fixed-quantum split makes the sums of the stored
+// float32 values exact up to one final rounding (as accurate as float64 sums, then rounded).
+// Each value is split as f = h 2^-16 + l: t = f + 192 rounds f to a multiple of 2^-16 (t lies in
+// [128, 256), whose float32 spacing is 2^-16, for |f| < 64), the bit pattern of t minus that of
+// 192 is the integer h exactly (float32 bit patterns are linear in the value within a binade),
+// and l = f - (t - 192) is exact with |l| <= 2^-17. The integer parts are summed exactly in
+// 32-bit integers (velocity weights 1, 6 and psi 36, 4, 9 are integers; the sqrt2-type weights
+// are applied to the integer group sums as float pairs), the small parts in float32 (rounding
+// below 2^-36 of the sum), and the two are combined once.
 // ---------------------------------------------------------------------------------------
 template <typename R> struct MomentSums;
 
@@ -200,66 +204,88 @@ template <> struct MomentSums<double> {
     }
 };
 
-__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
-    const float t = __fadd_rn(s, x);
-    const float bp = __fsub_rn(t, s);
-    c += __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-    s = t;
-}
-__device__ __forceinline__ void dot2_acc(float &s, float &c, float f, float wh, float wl) {
-    const float p = __fmul_rn(f, wh);
-    const float e = fmaf(f, wh, -p);  // exact: f*wh = p + e
-    two_sum_acc(s, c, p);
-    c += fmaf(f, wl, e);
-}
-
-// Knuth's TwoSum and TwoDiff: a + b = s + e and a - b = d + e exactly (no fused operations).
+// Knuth's TwoSum: a + b = s + e exactly (no fused operations).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
     const float bp = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
-__device__ __forceinline__ void two_diff(float a, float b, float &d, float &e) { two_sum(a, -b, d, e); }
+
+// speed group of velocity i: 0 (|v| = 1, carries eta), 1 (6), 2 (sqrt2 diagonals), 3 (3/sqrt2)
+__host__ __device__ constexpr int speed_group(int i) { return i >> 2; }
 
 template <> struct MomentSums<float> {
-    float rs = 0, rc = 0, xs = 0, xc = 0, ys = 0, yc = 0, es = 0, ec = 0;
-    // Velocities i and i + 2 are opposite: their contributions enter through the exact pair
-    // sum fi + fk = S + eS (to rho and E, weight psi_i) and difference fi - fk = D + eD (to j,
-    // weight v_i); the rounding terms eS, eD are added to the compensations.
+    static constexpr float kMagic = 192.0f;  // 1.5 2^7: f + 192 in [128, 256) for |f| < 64
+    static constexpr float kQ = 1.0f / 65536.0f;
+    // integer parts (offset bit patterns for the sums of the groups, plain for the differences)
+    unsigned sg[4] = {0u, 0u, 0u, 0u};  // per speed group: sum of bits(t) (offset 2 bits(192) per pair)
+    int xab = 0, yab = 0;               // x / y momentum of groups 0 and 1 (weights +-1, +-6)
+    int xc = 0, yc = 0, xd = 0, yd = 0; // signed unit-weight sums of groups 2 and 3
+    // small parts
+    float lr = 0.f, le = 0.f, lx = 0.f, ly = 0.f;
+    float psiA_hi = 0.f, psiA_lo = 0.f;  // psi of group 0 (1 + eta0^2) as a float pair
+
+    static __device__ __forceinline__ unsigned bits(float x) { return __float_as_uint(x); }
+
+    // Velocities i and i + 2 are opposite: their contributions enter as the integer pair sum
+    // (to rho and E) and difference (to j, weight v_i), and the same for the small parts.
     template <int I> __device__ __forceinline__ void add_pair(float fi, float fk, float psi_hi, float psi_lo) {
-        float S, eS, D, eD;
-        two_sum(fi, fk, S, eS);
-        two_diff(fi, fk, D, eD);
-        two_sum_acc(rs, rc, S);
-        rc += eS;
-        dot2_acc(es, ec, S, psi_hi, psi_lo);
-        ec = fmaf(psi_hi, eS, ec);
+        constexpr int g = speed_group(I);
+        const float ti = __fadd_rn(fi, kMagic), tk = __fadd_rn(fk, kMagic);
+        const float li = __fsub_rn(fi, __fsub_rn(ti, kMagic)), lk = __fsub_rn(fk, __fsub_rn(tk, kMagic));
+        const unsigned bi = bits(ti), bk = bits(tk);
+        sg[g] += bi + bk;
+        const int d = (int)(bi - bk);
+        const float ls = __fadd_rn(li, lk), ld = __fsub_rn(li, lk);
+        lr = __fadd_rn(lr, ls);
+        le = fmaf(psi_hi, ls, le);
+        if (g == 0) {
+            psiA_hi = psi_hi;
+            psiA_lo = psi_lo;
+        }
         if constexpr (vel_x(I) != 0.0) {
-            constexpr float wh = (float)vel_x(I), wl = (float)(vel_x(I) - (double)(float)vel_x(I));
-            dot2_acc(xs, xc, D, wh, wl);
-            xc = fmaf(wh, eD, xc);
+            if constexpr (g < 2) xab += (vel_x(I) > 0 ? 1 : -1) * (g == 0 ? 1 : 6) * d;
+            else if constexpr (g == 2) xc += vel_x(I) > 0 ? d : -d;
+            else xd += vel_x(I) > 0 ? d : -d;
+            lx = fmaf((float)vel_x(I), ld, lx);
         }
         if constexpr (vel_y(I) != 0.0) {
-            constexpr float wh = (float)vel_y(I), wl = (float)(vel_y(I) - (double)(float)vel_y(I));
-            dot2_acc(ys, yc, D, wh, wl);
-            yc = fmaf(wh, eD, yc);
+            if constexpr (g < 2) yab += (vel_y(I) > 0 ? 1 : -1) * (g == 0 ? 1 : 6) * d;
+            else if constexpr (g == 2) yc += vel_y(I) > 0 ? d : -d;
+            else yd += vel_y(I) > 0 ? d : -d;
+            ly = fmaf((float)vel_y(I), ld, ly);
         }
     }
-    __device__ __forceinline__ void add(int i, float f, float psi_hi, float psi_lo) {
-        two_sum_acc(rs, rc, f);
-        if (vel_x(i) != 0.0) {
-            const float wh = (float)vel_x(i), wl = (float)(vel_x(i) - (double)(float)vel_x(i));
-            dot2_acc(xs, xc, f, wh, wl);
-        }
-        if (vel_y(i) != 0.0) {
-            const float wh = (float)vel_y(i), wl = (float)(vel_y(i) - (double)(float)vel_y(i));
-            dot2_acc(ys, yc, f, wh, wl);
-        }
-        dot2_acc(es, ec, f, psi_hi, psi_lo);
+
+    // sum of the integer part a + sc sqrt2 + sd 3/sqrt2 (scaled by 2^-16) and the small part l
+    static __device__ __forceinline__ float momentum(int a, int sc, int sd, float l) {
+        constexpr float s2h = (float)LBM_SQ2, s2l = (float)(LBM_SQ2 - (double)(float)LBM_SQ2);
+        constexpr float d3h = (float)LBM_D3S2, d3l = (float)(LBM_D3S2 - (double)(float)LBM_D3S2);
+        const float fa = (float)a, fc = (float)sc, fd = (float)sd;  // exact: |values| < 2^24
+        const float pc = fc * s2h, ec = fmaf(fc, s2h, -pc);
+        const float pd = fd * d3h, ed = fmaf(fd, d3h, -pd);
+        float s1, t1, s2, t2;
+        two_sum(fa, pc, s1, t1);
+        two_sum(s1, pd, s2, t2);
+        const float corr = fmaf(fd, d3l, fmaf(fc, s2l, t1 + t2 + ec + ed));
+        return fmaf(s2, kQ, fmaf(corr, kQ, l));
     }
+
     __device__ __forceinline__ void finish(float b, float &rho, float &ux, float &uy, float &T) const {
-        rho = rs + rc;
-        const float jx = xs + xc, jy = ys + yc, E = es + ec;
+        const unsigned off = 4u * bits(kMagic);  // four values per group
+        const int SA = (int)(sg[0] - off), SB = (int)(sg[1] - off), SC = (int)(sg[2] - off), SD = (int)(sg[3] - off);
+        rho = fmaf((float)(SA + SB + SC + SD), kQ, lr);  // integer sum below 2^24: exact as float
+        // E: integer weights psi = 36, 4, 9 of groups 1-3, exact in int32, as an exact float pair
+        const int Ei = 36 * SB + 4 * SC + 9 * SD;
+        const float e1 = __int2float_rz(Ei);
+        const float e2 = (float)(Ei - __float2int_rz(e1));
+        const float fa = (float)SA;
+        const float pa = fa * psiA_hi, ea = fmaf(fa, psiA_hi, -pa);
+        float s, t;
+        two_sum(e1, pa, s, t);
+        const float corr = fmaf(fa, psiA_lo, t + e2 + ea);
+        const float E = fmaf(s, kQ, fmaf(corr, kQ, le));
+        const float jx = momentum(xab, xc, xd, lx), jy = momentum(yab, yc, yd, ly);
         const float ir = __fdividef(1.0f, rho);
         ux = jx * ir;
         uy = jy * ir;
@@ -379,7 +405,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(ldcg(fa + t + G * e), ldcg(fb + t + G * e));
                 F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
-                F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+                F::multiply(v, t, 1, a.cx[p], a.ax.k1, a.ax.k2);  // -h v_x folded in
                 F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
                 reg::cta_barrier();
 #pragma unroll
@@ -434,18 +460,18 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
             constexpr int i = decltype(I)::value;
             R dfo = 0;  // h R_i
             if (adv) {
-                R ad = 0;
+                // -h v_i . grad f_i: both parts come with -h v folded into their multipliers (the
+                // row line's second field has the opposite v_x, hence the sign of its part)
                 constexpr int xs = xslot(i), ys = yslot(i);
                 if constexpr (xs >= 0) {
                     if (ax_mode) {
-                        ad += R(vel_x(i)) * ldcg(a.Ax + (y * NF_F + i) * NX + x);
+                        dfo = -h * (R(vel_x(i)) * ldcg(a.Ax + (y * NF_F + i) * NX + x));
                     } else {
                         const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + x];
-                        ad += R(vel_x(i)) * ((xs & 1) ? d.y : d.x);
+                        dfo = (xs & 1) ? -d.y : d.x;
                     }
                 }
-                if constexpr (ys >= 0) ad += ldcg(an + ys * NX);
-                dfo -= h * ad;
+                if constexpr (ys >= 0) dfo += ldcg(an + ys * NX);
             }
             if (col) dfo += htau * ne;
             if (frc) dfo -= q * (fsv[i] + ne);

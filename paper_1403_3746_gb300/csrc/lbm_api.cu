@@ -235,10 +235,12 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
     {
         ColArgs<R> a = col_args<R>(c, c->nb, c->geo.colW);
         int nj = 0;
+        // Ay = -h v_iy d_y f_i: the stage's time step and the velocity folded into the multiplier
+        const double hs = stage == 0 ? 0.5 * p.dt : p.dt;
         if (adv)
             for (int k = 0; k < 12; ++k) {
                 const int i = yfield(k);
-                a.jobs[nj++] = ColJob<R>{fs + (size_t)i * nx, Ay + (size_t)k * nx, ldf, lda, 1, (R)vel_y(i)};
+                a.jobs[nj++] = ColJob<R>{fs + (size_t)i * nx, Ay + (size_t)k * nx, ldf, lda, 1, (R)(-hs * vel_y(i))};
             }
         if (frc) {
             a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RY), ldm, ldm, 1, R(1)};
@@ -305,6 +307,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
         a.ax = axis<R>(c, true);
         a.tau_inv = (R)(1.0 / p.tau);
         a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
+        for (int q = 0; q < 6; ++q) a.cx[q] = (R)(-(stage == 0 ? 0.5 * p.dt : p.dt) * vel_x(xfield(2 * q)));
         a.T_iso = (R)p.T_iso;
         a.K = (R)p.K;
         a.b = (R)p.b;

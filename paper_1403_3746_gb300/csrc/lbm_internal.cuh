@@ -190,7 +190,7 @@ template <typename R> struct UpdateArgs {
     const R *fs;     // f of this stage (derivatives, BGK, f^eq moments), [ny][16][nx]
     const R *fbase;  // f^n (the stage starts from it)
     R *fout;         // f^{n+1/2} or f^{n+1}; may alias fbase (same node, same thread)
-    const R *Ay;     // [ny][12][nx]: v_iy d_y f_i
+    const R *Ay;     // [ny][12][nx]: -h v_iy d_y f_i (the stage's h folded in by the column pass)
     const R *Ax;     // nullptr: the kernel transforms its rows; else [ny][16][nx]: d_x f_i from a
                      // separate row pass (rows too long for the kernel's shared memory)
     R *m;            // macroscopic block; moments of fs in, moments of fout out
@@ -198,6 +198,7 @@ template <typename R> struct UpdateArgs {
     int lines_per_batch;  // line transforms in flight per batch (the other threads wait)
     Axis<R> ax;
     R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
+    R cx[6];  // multiplier of row-transform line q: -h v_x of its first field (the second has -v_x)
     R T_iso;                   // LBM_FLAG_ISOTHERMAL: T at every node
     R psi_hi[16], psi_lo[16];  // psi_i = |v_i|^2 + eta_i^2 as a two-term sum (hi + lo)
     int flags;
