@@ -213,18 +213,22 @@ int lbm_launch_plan(int nx, int ny, int precision, int out[16]);
 int lbm_set_geometry(lbm_handle h, const int geometry[4]);
 int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
 
-/* Form of the two column passes (no counterpart in the paper: a performance choice that does
- * not change any result). kinds[0]: the column pass, kinds[1]: the flux column pass;
- * LBM_COL_DIRECT: each CTA loads its column tile straight from global memory, transforms and
- * stores it; LBM_COL_TMA: a persistent grid whose CTAs stage the next tile in shared memory with
- * tiled bulk tensor copies (TMA) while they transform the current one. lbm_autotune chooses
- * the kinds together with the tile widths. lbm_set_pass_kinds returns LBM_ERR_ARG if the TMA form
- * cannot take the current width (rows of fewer than 16 bytes, or staging buffers beyond a CTA's
- * shared memory); where a launch still cannot use it, the direct form runs. */
+/* Form of the passes (no counterpart in the paper: performance choices that do not change any
+ * result). kinds[0]: the column pass, kinds[1]: the flux column pass; LBM_COL_DIRECT: each CTA
+ * loads its column tile straight from global memory, transforms and stores it (tiles wider
+ * than one CTA's threads split every line over a thread-block cluster of 2 or 4 CTAs that
+ * exchange points through distributed shared memory); LBM_COL_TMA: a persistent grid whose CTAs
+ * stage the next tile in shared memory with tiled bulk tensor copies (TMA) while they transform
+ * the current one. kinds[2]: CTAs per row of the update pass, 1 or 2 (a cluster of two splits
+ * each row's transforms and node loop; float32 rows of 2048 or more, one row per cluster).
+ * lbm_autotune chooses them together with the tile widths and rows per CTA. lbm_set_pass_kinds
+ * returns LBM_ERR_ARG for a choice the current shapes cannot take (TMA: rows of fewer than 16
+ * bytes, cluster-split widths, staging buffers beyond a CTA's shared memory); where a launch
+ * still cannot use TMA, the direct form runs. */
 #define LBM_COL_DIRECT 0
 #define LBM_COL_TMA 1
-int lbm_pass_kinds(lbm_handle h, int kinds[2]);
-int lbm_set_pass_kinds(lbm_handle h, const int kinds[2]);
+int lbm_pass_kinds(lbm_handle h, int kinds[3]);
+int lbm_set_pass_kinds(lbm_handle h, const int kinds[3]);
 
 /* Fault injection for tests (no counterpart in the paper). Every device-side wait of the
  * library (the TMA column pass waiting for its copies) is bounded by `wait_cycles` clock

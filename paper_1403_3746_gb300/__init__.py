@@ -328,13 +328,18 @@ class Simulation:
         _check(lib().lbm_set_geometry(self._h, ctypes.cast(g, _P)))
 
     def pass_kinds(self):
-        """(column pass kind, flux column pass kind): LBM_COL_DIRECT or LBM_COL_TMA."""
-        k = (ctypes.c_int * 2)()
+        """(column pass kind, flux column pass kind, update CTAs per row): LBM_COL_DIRECT or
+        LBM_COL_TMA, LBM_COL_DIRECT or LBM_COL_TMA, 1 or 2."""
+        k = (ctypes.c_int * 3)()
         _check(lib().lbm_pass_kinds(self._h, ctypes.cast(k, _P)))
         return tuple(k)
 
     def set_pass_kinds(self, kinds):
-        k = (ctypes.c_int * 2)(*[int(v) for v in kinds])
+        """kinds: (column, flux) or (column, flux, update CTAs per row; default: unchanged)."""
+        kinds = list(kinds)
+        if len(kinds) == 2:
+            kinds.append(self.pass_kinds()[2])
+        k = (ctypes.c_int * 3)(*[int(v) for v in kinds])
         _check(lib().lbm_set_pass_kinds(self._h, ctypes.cast(k, _P)))
 
     def fault_inject(self, what, wait_cycles=0):

@@ -158,6 +158,39 @@ struct SyncWarp {
     static __device__ __forceinline__ void run() { __syncwarp(); }
 };
 
+// ---- thread-block clusters: a line split over CS CTAs of one cluster ----------------------
+// rank of this CTA in its cluster
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// barrier over every thread of every CTA of the cluster, with release / acquire ordering of
+// shared-memory accesses at cluster scope (non-aligned form: threads may arrive from different
+// branches)
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// shared::cluster address of the same shared-memory offset as p in the CTA of the given rank
+__device__ __forceinline__ uint32_t cluster_map(const void *p, unsigned rank) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, double2 v) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ void ld_cluster(uint32_t a, float2 &v) {
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ld_cluster(uint32_t a, double2 &v) {
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+}
+
 // Twiddle table of a line length n = 2^log2n: for each radix-16 pass P (span S = n / 16^P,
 // M = S / 16 sub-sequences, M > 1) the roots w_n^(16^P j k) for k = 1..15, j = 0..M-1 at
 // index twiddle_offset(n, P) + (k - 1) M + j, so the threads of a pass (consecutive j)
@@ -178,19 +211,34 @@ __host__ __device__ inline int twiddle_exponent(int n, int idx) {
     return -1;
 }
 
-template <typename R, int LOG2N, bool PK = false> struct LineFFT {
+// CS > 1: the line is split over the CS CTAs of a thread-block cluster. Thread t of the line
+// (0 <= t < G, numbered across the cluster) lives in the CTA of rank t / (G / CS), and each CTA's
+// line buffer holds the positions [rank N/CS, (rank + 1) N/CS) (padded). Every exchange but one
+// stays inside a CTA: the points of the first radix-16 pass (stride G) are spread over the whole
+// line, so the forward transform writes them into the other CTAs' buffers (distributed shared
+// memory) between two cluster barriers, and the inverse reads them back from there; an inverse
+// ends with a cluster barrier so that no CTA reuses or releases a buffer another still reads.
+template <typename R, int LOG2N, bool PK = false, int CS = 1> struct LineFFT {
     static constexpr int N = 1 << LOG2N;
     static constexpr int E = N < 16 ? N : 16;                // points per thread
     static constexpr int G = N / E;                          // threads per line
     static constexpr int NP16 = LOG2N >= 4 ? LOG2N / 4 : 0;  // radix-16 passes
     static constexpr int RL = LOG2N >= 4 ? (1 << (LOG2N & 3)) : N;  // final radix (1 = none)
-    static constexpr int SMEM = N + (N >> 4);                // padded line buffer, complex elements
+    static_assert(CS == 1 || (NP16 >= 2 && CS <= 16 && G % CS == 0), "cluster split needs lines of 256+ points");
+    static constexpr int NL = N / CS;                        // positions held by one CTA
+    static constexpr int GL = G / CS;                        // threads of a line in one CTA
+    static constexpr int SMEM = NL + (NL >> 4);              // padded line buffer, complex elements
     // distance between consecutive line buffers: two extra elements shift each buffer by 16 or
     // 32 bytes, so lines that share a warp (column tiles) do not collide on the same banks
     static constexpr int STRIDE = SMEM + 2;
     typedef C<R> CT;
 
     static __device__ __forceinline__ int pad(int p) { return p + (p >> 4); }
+    // padded index of this CTA's first position (0 without a cluster split)
+    static __device__ __forceinline__ int pad_base() {
+        if constexpr (CS == 1) return 0;
+        else return pad((int)cluster_rank() * NL);
+    }
     // position of point e of thread t in the input layout of radix-16 pass P
     template <int P> static __device__ __forceinline__ int pos16(int t, int e) {
         constexpr int S = N >> (4 * P), M = S >> 4;
@@ -216,39 +264,84 @@ template <typename R, int LOG2N, bool PK = false> struct LineFFT {
         }
     }
 
-    template <int P> static __device__ __forceinline__ void store16(const CT v[E], CT *buf, int t) {
+    template <int P> static __device__ __forceinline__ void store16(const CT v[E], CT *buf, int t, int pb = 0) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) buf[pad(pos16<P>(t, e))] = v[e];
+        for (int e = 0; e < E; ++e) buf[pad(pos16<P>(t, e)) - pb] = v[e];
     }
-    template <int P> static __device__ __forceinline__ void load16(CT v[E], const CT *buf, int t) {
+    template <int P> static __device__ __forceinline__ void load16(CT v[E], const CT *buf, int t, int pb = 0) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = buf[pad(pos16<P>(t, e))];
+        for (int e = 0; e < E; ++e) v[e] = buf[pad(pos16<P>(t, e)) - pb];
     }
-    static __device__ __forceinline__ void storeF(const CT v[E], CT *buf, int t) {
+    static __device__ __forceinline__ void storeF(const CT v[E], CT *buf, int t, int pb = 0) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) buf[pad(t * E + e)] = v[e];
+        for (int e = 0; e < E; ++e) buf[pad(t * E + e) - pb] = v[e];
     }
-    static __device__ __forceinline__ void loadF(CT v[E], const CT *buf, int t) {
+    static __device__ __forceinline__ void loadF(CT v[E], const CT *buf, int t, int pb = 0) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = buf[pad(t * E + e)];
+        for (int e = 0; e < E; ++e) v[e] = buf[pad(t * E + e) - pb];
+    }
+    // the layout of the first radix-16 pass across the cluster: position t + G e is held by the
+    // CTA of rank e CS / 16 (a compile-time value per e once the loop is unrolled)
+    // (the E / CS points bound for one rank are consecutive in e, so one mapped base at a time)
+    static __device__ __forceinline__ void store0_remote(const CT v[E], CT *buf, int t) {
+        const uint32_t off = (uint32_t)pad(t) * (uint32_t)sizeof(CT);
+#pragma unroll
+        for (int r = 0; r < CS; ++r) {
+            const uint32_t base = cluster_map(buf, r) + off;
+#pragma unroll
+            for (int e = r * (E / CS); e < (r + 1) * (E / CS); ++e)
+                st_cluster(base + (uint32_t)(pad(t + G * e) - pad(t) - pad(r * NL)) * (uint32_t)sizeof(CT), v[e]);
+        }
+    }
+    static __device__ __forceinline__ void load0_remote(CT v[E], const CT *buf, int t) {
+        const uint32_t off = (uint32_t)pad(t) * (uint32_t)sizeof(CT);
+#pragma unroll
+        for (int r = 0; r < CS; ++r) {
+            const uint32_t base = cluster_map(buf, r) + off;
+#pragma unroll
+            for (int e = r * (E / CS); e < (r + 1) * (E / CS); ++e)
+                ld_cluster(base + (uint32_t)(pad(t + G * e) - pad(t) - pad(r * NL)) * (uint32_t)sizeof(CT), v[e]);
+        }
+    }
+    // results in natural order x = t + G e, unpadded, into the line buffer of the CTA that holds x
+    // (a plain local store without a cluster split); the caller synchronises before reading
+    static __device__ __forceinline__ void store_natural(const CT v[E], CT *buf, int t) {
+        if constexpr (CS == 1) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) buf[t + G * e] = v[e];
+        } else {
+#pragma unroll
+            for (int r = 0; r < CS; ++r) {
+                const uint32_t base = cluster_map(buf + t, r);
+#pragma unroll
+                for (int e = r * (E / CS); e < (r + 1) * (E / CS); ++e)
+                    st_cluster(base + (uint32_t)(G * e - r * NL) * (uint32_t)sizeof(CT), v[e]);
+            }
+        }
     }
 
     template <int P, class SYNC> static __device__ __forceinline__ void fwd_from(CT v[E], CT *buf, int t,
-                                                                                const CT *__restrict__ tw) {
+                                                                                const CT *__restrict__ tw, int pb) {
         if constexpr (P < NP16) {
             pass16<P, false>(v, t, tw);
             if constexpr (P + 1 < NP16) {
-                SYNC::run();
-                store16<P>(v, buf, t);
-                SYNC::run();
-                load16<P + 1>(v, buf, t);
+                if constexpr (P == 0 && CS > 1) {  // the one exchange across the cluster
+                    cluster_barrier();
+                    store0_remote(v, buf, t);
+                    cluster_barrier();
+                } else {
+                    SYNC::run();
+                    store16<P>(v, buf, t, pb);
+                    SYNC::run();
+                }
+                load16<P + 1>(v, buf, t, pb);
             } else if constexpr (RL > 1) {
                 SYNC::run();
-                store16<P>(v, buf, t);
+                store16<P>(v, buf, t, pb);
                 SYNC::run();
-                loadF(v, buf, t);
+                loadF(v, buf, t, pb);
             }
-            fwd_from<P + 1, SYNC>(v, buf, t, tw);
+            fwd_from<P + 1, SYNC>(v, buf, t, tw, pb);
         } else if constexpr (RL > 1) {
 #pragma unroll
             for (int kb = 0; kb < E / RL; ++kb) dft_small<R, false, RL, PK>(v + kb * RL);
@@ -256,50 +349,82 @@ template <typename R, int LOG2N, bool PK = false> struct LineFFT {
     }
 
     template <int P, class SYNC> static __device__ __forceinline__ void inv_from(CT v[E], CT *buf, int t,
-                                                                                const CT *__restrict__ tw) {
+                                                                                const CT *__restrict__ tw, int pb) {
         if constexpr (P >= 0) {
             pass16<P, true>(v, t, tw);
             if constexpr (P > 0) {
                 SYNC::run();
-                store16<P>(v, buf, t);
-                SYNC::run();
-                load16<P - 1>(v, buf, t);
-                inv_from<P - 1, SYNC>(v, buf, t, tw);
+                store16<P>(v, buf, t, pb);
+                if constexpr (P == 1 && CS > 1) {  // read the first pass's layout across the cluster
+                    cluster_barrier();
+                    load0_remote(v, buf, t);
+                } else {
+                    SYNC::run();
+                    load16<P - 1>(v, buf, t, pb);
+                }
+                inv_from<P - 1, SYNC>(v, buf, t, tw, pb);
             }
         }
     }
 
     // Forward DFT of a line held as v[e] = x[t + G e]; on return v[e] = X at digit-reversed
     // position E t + e. buf: this line's shared buffer of SMEM elements. Every thread of the
-    // block (SyncCta) or warp (SyncWarp) must call it.
+    // block (SyncCta) or warp (SyncWarp) must call it; with a cluster split, every thread of
+    // the cluster.
     template <class SYNC> static __device__ __forceinline__ void forward(CT v[E], CT *buf, int t,
                                                                         const CT *__restrict__ tw) {
-        fwd_from<0, SYNC>(v, buf, t, tw);
+        fwd_from<0, SYNC>(v, buf, t, tw, pad_base());
     }
 
     // Inverse (N times the inverse DFT) of a spectrum held at positions E t + e; on return
     // v[e] = x[t + G e].
     template <class SYNC> static __device__ __forceinline__ void inverse(CT v[E], CT *buf, int t,
                                                                         const CT *__restrict__ tw) {
+        const int pb = pad_base();
         if constexpr (RL > 1) {
 #pragma unroll
             for (int kb = 0; kb < E / RL; ++kb) dft_small<R, true, RL, PK>(v + kb * RL);
             if constexpr (NP16 > 0) {
                 SYNC::run();
-                storeF(v, buf, t);
+                storeF(v, buf, t, pb);
                 SYNC::run();
-                load16<NP16 - 1>(v, buf, t);
+                load16<NP16 - 1>(v, buf, t, pb);
             }
         }
-        inv_from<NP16 - 1, SYNC>(v, buf, t, tw);
+        inv_from<NP16 - 1, SYNC>(v, buf, t, tw, pb);
+        if constexpr (CS > 1) cluster_barrier();
     }
 
     // Barriers only: a thread with no line in this transform calls it so that the block's
     // barrier count matches the threads that run forward() or inverse() (same count each).
     static constexpr int EXCHANGES = (NP16 > 1 ? NP16 - 1 : 0) + ((RL > 1 && NP16 > 0) ? 1 : 0);
     template <class SYNC> static __device__ __forceinline__ void idle() {
+        static_assert(CS == 1, "with a cluster split use idle_forward / idle_inverse");
 #pragma unroll
         for (int k = 0; k < 2 * EXCHANGES; ++k) SYNC::run();
+    }
+    // the barrier sequence of forward() / inverse() (CTA barriers and, with a cluster split,
+    // cluster barriers in the same order)
+    template <class SYNC> static __device__ __forceinline__ void idle_forward() {
+        if constexpr (CS == 1) {
+            idle<SYNC>();
+        } else {
+            cluster_barrier();
+            cluster_barrier();
+#pragma unroll
+            for (int k = 0; k < 2 * (EXCHANGES - 1); ++k) SYNC::run();
+        }
+    }
+    template <class SYNC> static __device__ __forceinline__ void idle_inverse() {
+        if constexpr (CS == 1) {
+            idle<SYNC>();
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2 * (EXCHANGES - 1); ++k) SYNC::run();
+            SYNC::run();
+            cluster_barrier();
+            cluster_barrier();
+        }
     }
 
     // v <- d^order * c * v at positions E t + e (tables k1 = W k_eff / N, k2 = -(W k_eff)^2 / N,

@@ -16,17 +16,20 @@
 
 namespace lbm {
 
-template <typename R, int LOG2N>
-__global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) col_deriv_kernel(const __grid_constant__ ColArgs<R> a) {
-    using F = reg::LineFFT<R, LOG2N, true>;
+// One CTA's share of a column tile: CS = 1 (whole lines in one CTA) or the CTA of rank `rank`
+// in a cluster of CS that splits every line of the tile (fft_reg.cuh); tile = the tile index.
+template <typename R, int LOG2N, int CS>
+__device__ __forceinline__ void col_tile(const ColArgs<R> &a, int tile, unsigned rank) {
+    using F = reg::LineFFT<R, LOG2N, true, CS>;
     using CT = typename F::CT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sbuf = reinterpret_cast<CT *>(smem_raw);
     const ColJob<R> &job = a.jobs[blockIdx.y];
     const int L = a.W >> 1;
-    const int l = threadIdx.x & (L - 1), t = threadIdx.x >> (a.log2W - 1);
+    const int l = threadIdx.x & (L - 1);
+    const int t = (int)rank * F::GL + (threadIdx.x >> (a.log2W - 1));  // thread of the line, across the cluster
     const size_t rsi = (size_t)(job.ld_in >> 1), rso = (size_t)(job.ld_out >> 1);  // row strides, complex units
-    const int x = blockIdx.x * a.W + 2 * l;
+    const int x = tile * a.W + 2 * l;
     // blockIdx.z: instance of a batch stacked along y (ny rows each)
     const size_t z = blockIdx.z;
     const CT *in = reinterpret_cast<const CT *>(job.in + z * a.ny * job.ld_in + x);
@@ -43,15 +46,45 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
     for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rso] = v[e];
 }
 
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) col_deriv_kernel(const __grid_constant__ ColArgs<R> a) {
+    col_tile<R, LOG2N, 1>(a, blockIdx.x, 0u);
+}
+
+// Column tiles wider than one CTA's threads can transform: each line is split over the CS CTAs
+// of a cluster (consecutive blockIdx.x), which exchange points through distributed shared memory.
+template <typename R, int LOG2N, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks)
+    col_cluster_kernel(const __grid_constant__ ColArgs<R> a) {
+    col_tile<R, LOG2N, CS>(a, blockIdx.x / CS, reg::cluster_rank());
+}
+
+template <typename R, int LOG2N, int CS> static cudaError_t launch_col_cs(const ColArgs<R> &a, int njobs, size_t smem,
+                                                                           cudaStream_t s) {
+    using F = reg::LineFFT<R, LOG2N, true, CS>;
+    if (smem < (size_t)(a.W / 2) * F::STRIDE * sizeof(typename F::CT)) return cudaErrorInvalidValue;
+    dim3 grid((a.nx / a.W) * CS, njobs, a.nb > 0 ? a.nb : 1);
+    if constexpr (CS == 1) {
+        cudaError_t e = allow_smem(col_deriv_kernel<R, LOG2N>);
+        if (e != cudaSuccess) return e;
+        col_deriv_kernel<R, LOG2N><<<grid, (a.W / 2) * F::GL, smem, s>>>(a);
+    } else {
+        cudaError_t e = allow_smem(col_cluster_kernel<R, LOG2N, CS>);
+        if (e != cudaSuccess) return e;
+        col_cluster_kernel<R, LOG2N, CS><<<grid, (a.W / 2) * F::GL, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R> &a, int njobs, size_t smem,
                                                                   cudaStream_t s) {
-    using F = reg::LineFFT<R, LOG2N>;
-    if (smem < (size_t)(a.W / 2) * F::STRIDE * sizeof(typename F::CT)) return cudaErrorInvalidValue;
-    cudaError_t e = allow_smem(col_deriv_kernel<R, LOG2N>);
-    if (e != cudaSuccess) return e;
-    dim3 grid(a.nx / a.W, njobs, a.nb > 0 ? a.nb : 1);
-    col_deriv_kernel<R, LOG2N><<<grid, (a.W / 2) * F::G, smem, s>>>(a);
-    return cudaGetLastError();
+    const int cs = col_cluster(a.W, LOG2N, sizeof(R));
+    if constexpr (LOG2N >= 9) {
+        if (cs == 2) return launch_col_cs<R, LOG2N, 2>(a, njobs, smem, s);
+        if (cs == 4) return launch_col_cs<R, LOG2N, 4>(a, njobs, smem, s);
+    }
+    if (cs != 1) return cudaErrorInvalidValue;
+    return launch_col_cs<R, LOG2N, 1>(a, njobs, smem, s);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -360,40 +360,56 @@ __host__ __device__ constexpr bool minv_zero(int i, int j) {
 __host__ __device__ constexpr int pair_rep(int p) { return 4 * (p >> 1) + (p & 1); }
 __host__ __device__ constexpr bool mom_odd(int j) { return (mom_px(j) + mom_py(j)) & 1; }
 
-template <typename R, int LOG2N, bool MOMENT_SPACE>
-__global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
-    using F = reg::LineFFT<R, LOG2N, true>;
+// CS = 1: a CTA owns `rows` whole rows. CS > 1 (float32 rows of 2048 or more, one row per
+// cluster): the CS CTAs of a cluster split the row's line transforms (fft_reg.cuh) and CTA
+// `rank` runs the node loop over its x-range [rank N/CS, (rank + 1) N/CS), whose derivatives the
+// transforms leave in its own shared memory.
+template <typename R, int LOG2N, bool MOMENT_SPACE, int CS>
+__device__ __forceinline__ void update_rows(const UpdateArgs<R> &a, int blk, unsigned rank) {
+    using F = reg::LineFFT<R, LOG2N, true, CS>;
     using CT = typename F::CT;
-    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE;
+    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE, NL = F::NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *sb = reinterpret_cast<CT *>(smem_raw);
-    const int NR = a.rows, nodes = NR * NX;
-    const int y0 = blockIdx.x * NR;
+    const int NR = a.rows, nodes = NR * NL;  // nodes of this CTA
+    const int y0 = blk * NR, x0 = (int)rank * NL;
     const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
     const bool col = !(a.flags & LBM_FLAG_NO_COLLISION);
     const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
     const bool same_base = a.fbase == a.fs;
     const bool iso = a.flags & LBM_FLAG_ISOTHERMAL;
     // d_x f_i from global memory instead of the row transforms: only float64 rows of 4096 need it
-    constexpr bool AX_POSSIBLE = sizeof(R) == 8 && LOG2N == 12;
+    constexpr bool AX_POSSIBLE = sizeof(R) == 8 && LOG2N == 12 && CS == 1;
     const bool ax_mode = AX_POSSIBLE && a.Ax != nullptr;
 
     // the node loop's other inputs start moving into L2 while the lines are transformed
-    if (threadIdx.x < NR) {
-        const size_t y = y0 + threadIdx.x;
-        prefetch_l2(a.fs + y * NF_F * NX, NF_F * NX * sizeof(R));
-        if (adv) prefetch_l2(a.Ay + y * NF_A * NX, NF_A * NX * sizeof(R));
-        if (!same_base) prefetch_l2(a.fbase + y * NF_F * NX, NF_F * NX * sizeof(R));
-        if (adv && ax_mode) prefetch_l2(a.Ax + y * NF_F * NX, NF_F * NX * sizeof(R));
-        prefetch_l2(a.m + y * NF_M * NX, (M_RY + 1) * NX * sizeof(R));
-        if (frc) prefetch_l2(a.m + (y * NF_M + M_DQX) * NX, (NF_M - M_DQX) * NX * sizeof(R));
+    if constexpr (CS == 1) {
+        if (threadIdx.x < NR) {
+            const size_t y = y0 + threadIdx.x;
+            prefetch_l2(a.fs + y * NF_F * NX, NF_F * NX * sizeof(R));
+            if (adv) prefetch_l2(a.Ay + y * NF_A * NX, NF_A * NX * sizeof(R));
+            if (!same_base) prefetch_l2(a.fbase + y * NF_F * NX, NF_F * NX * sizeof(R));
+            if (adv && ax_mode) prefetch_l2(a.Ax + y * NF_F * NX, NF_F * NX * sizeof(R));
+            prefetch_l2(a.m + y * NF_M * NX, (M_RY + 1) * NX * sizeof(R));
+            if (frc) prefetch_l2(a.m + (y * NF_M + M_DQX) * NX, (NF_M - M_DQX) * NX * sizeof(R));
+        }
+    } else {  // this CTA's x-range of every field of the row (NR = 1)
+        const int k = threadIdx.x;
+        const size_t y = y0, bytes = NL * sizeof(R);
+        if (k < NF_F) prefetch_l2(a.fs + (y * NF_F + k) * NX + x0, bytes);
+        else if (k < NF_F + NF_A) { if (adv) prefetch_l2(a.Ay + (y * NF_A + k - NF_F) * NX + x0, bytes); }
+        else if (k < 2 * NF_F + NF_A) { if (!same_base) prefetch_l2(a.fbase + (y * NF_F + k - NF_F - NF_A) * NX + x0, bytes); }
+        else if (k < 2 * NF_F + NF_A + NF_M) {
+            const int j = k - 2 * NF_F - NF_A;
+            if (j <= M_RY || (frc && j >= M_DQX)) prefetch_l2(a.m + (y * NF_M + j) * NX + x0, bytes);
+        }
     }
 
     if (adv && !ax_mode) {
         // 6 lines per row (the 12 fields with v_x != 0, paired); LB lines per batch (LB divides
-        // 6 NR); threads past LB G only take part in the barriers
+        // 6 NR); threads past LB G/CS only take part in the barriers
         const int LB = a.lines_per_batch;
-        const int ls = threadIdx.x / G, t = threadIdx.x % G;
+        const int ls = threadIdx.x / F::GL, t = (int)rank * F::GL + threadIdx.x % F::GL;
         for (int b0 = 0; b0 < 6 * NR; b0 += LB) {
             if (ls < LB) {
                 const int line = b0 + ls;
@@ -407,21 +423,21 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
                 F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
                 F::multiply(v, t, 1, a.cx[p], a.ax.k1, a.ax.k2);  // -h v_x folded in
                 F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
-                reg::cta_barrier();
-#pragma unroll
-                for (int e = 0; e < E; ++e) buf[t + G * e] = v[e];
+                if constexpr (CS == 1) reg::cta_barrier();  // (a split inverse ends with a cluster barrier)
+                F::store_natural(v, buf, t);
             } else {
-                F::template idle<reg::SyncCta>();
-                F::template idle<reg::SyncCta>();
-                reg::cta_barrier();
+                F::template idle_forward<reg::SyncCta>();
+                F::template idle_inverse<reg::SyncCta>();
+                if constexpr (CS == 1) reg::cta_barrier();
             }
         }
-        __syncthreads();
+        if constexpr (CS == 1) __syncthreads();
+        else reg::cluster_barrier();  // every CTA's part of every line has landed
     }
 
     const R b = a.b, K = a.K, tau_inv = a.tau_inv, h = a.h;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
-        const int r = idx / NX, x = idx % NX;
+        const int r = idx / NL, xl = idx % NL, x = x0 + xl;  // xl: index in this CTA's line buffers
         const size_t y = y0 + r;
         const R *fn = a.fs + y * NF_F * NX + x;       // field i at fn[i * NX]
         const R *an = a.Ay + y * NF_A * NX + x;       // slot k at an[k * NX]
@@ -467,7 +483,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
                     if (ax_mode) {
                         dfo = -h * (R(vel_x(i)) * ldcg(a.Ax + (y * NF_F + i) * NX + x));
                     } else {
-                        const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + x];
+                        const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + xl];
                         dfo = (xs & 1) ? -d.y : d.x;
                     }
                 }
@@ -564,6 +580,18 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
     }
 }
 
+template <typename R, int LOG2N, bool MOMENT_SPACE>
+__global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) update_row_kernel(const __grid_constant__ UpdateArgs<R> a) {
+    update_rows<R, LOG2N, MOMENT_SPACE, 1>(a, blockIdx.x, 0u);
+}
+
+// one row per cluster of CS CTAs (consecutive blockIdx.x)
+template <typename R, int LOG2N, bool MOMENT_SPACE, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks)
+    update_cluster_kernel(const __grid_constant__ UpdateArgs<R> a) {
+    update_rows<R, LOG2N, MOMENT_SPACE, CS>(a, blockIdx.x / CS, reg::cluster_rank());
+}
+
 // lines per batch of the update kernel: the largest divisor of the CTA's lines with LB G <= maxt
 static inline int update_lines_per_batch(int nlines, int G, int maxt) {
     int best = 1;
@@ -572,26 +600,42 @@ static inline int update_lines_per_batch(int nlines, int G, int maxt) {
     return best;
 }
 
-template <typename R, int LOG2N> static cudaError_t launch_update_n(const UpdateArgs<R> &a, size_t smem,
-                                                                    cudaStream_t s) {
-    using F = reg::LineFFT<R, LOG2N>;
+template <typename R, int LOG2N, int CS> static cudaError_t launch_update_cs(const UpdateArgs<R> &a, size_t smem,
+                                                                              cudaStream_t s) {
+    using F = reg::LineFFT<R, LOG2N, true, CS>;
     constexpr bool MS = sizeof(R) == 4;  // float32: moment-space collision
-    cudaError_t e = allow_smem(update_row_kernel<R, LOG2N, MS>);
+    cudaError_t e = CS == 1 ? allow_smem(update_row_kernel<R, LOG2N, MS>)
+                            : allow_smem(update_cluster_kernel<R, LOG2N, MS, CS>);
     if (e != cudaSuccess) return e;
     // the in-kernel row transforms need 6 line buffers per row; refuse a launch without them
     const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
     if (adv && a.Ax == nullptr && smem < (size_t)6 * a.rows * F::STRIDE * sizeof(typename F::CT))
         return cudaErrorInvalidValue;
-    if (a.Ax != nullptr && !(sizeof(R) == 8 && LOG2N == 12)) return cudaErrorInvalidValue;
+    if (a.Ax != nullptr && !(sizeof(R) == 8 && LOG2N == 12 && CS == 1)) return cudaErrorInvalidValue;
+    if (CS > 1 && a.rows != 1) return cudaErrorInvalidValue;
     // LB line transforms at a time; at least one thread per node of the CTA's rows (up to the cap)
     constexpr int cap = PassThreads<R>::value;
     UpdateArgs<R> b = a;
-    b.lines_per_batch = update_lines_per_batch(6 * a.rows, F::G, cap);
-    const int nodes = a.rows * F::N;
-    int threads = b.lines_per_batch * F::G;
+    b.lines_per_batch = update_lines_per_batch(6 * a.rows, F::GL, cap);
+    const int nodes = a.rows * F::NL;
+    int threads = b.lines_per_batch * F::GL;
     if (threads < nodes) threads = nodes < cap ? ((nodes + 31) & ~31) : cap;
-    update_row_kernel<R, LOG2N, MS><<<a.ny / a.rows, threads, smem, s>>>(b);
+    if constexpr (CS == 1) {
+        update_row_kernel<R, LOG2N, MS><<<a.ny / a.rows, threads, smem, s>>>(b);
+    } else {
+        if (threads < 2 * NF_F + NF_A + NF_M) threads = 2 * NF_F + NF_A + NF_M;  // one prefetching thread per field
+        update_cluster_kernel<R, LOG2N, MS, CS><<<(a.ny / a.rows) * CS, threads, smem, s>>>(b);
+    }
     return cudaGetLastError();
+}
+
+template <typename R, int LOG2N> static cudaError_t launch_update_n(const UpdateArgs<R> &a, size_t smem,
+                                                                    cudaStream_t s) {
+    if constexpr (sizeof(R) == 4 && LOG2N >= 11) {
+        if (a.cs == 2) return launch_update_cs<R, LOG2N, 2>(a, smem, s);
+    }
+    if (a.cs != 1 && a.cs != 0) return cudaErrorInvalidValue;
+    return launch_update_cs<R, LOG2N, 1>(a, smem, s);
 }
 
 template <typename R, int LOG2N> static cudaError_t launch_macro_n(const MacroArgs<R> &a, size_t smem,

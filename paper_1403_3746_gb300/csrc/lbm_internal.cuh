@@ -73,6 +73,28 @@ template <typename R> struct PassThreads {
     static constexpr int min_blocks = sizeof(R) == 8 ? 1 : 2;
 };
 __host__ __device__ constexpr int pass_threads(size_t esize) { return esize == 8 ? 384 : 512; }
+// CTAs per cluster for a column tile of W columns of lines of 2^log2n points: 1 when the tile's
+// W/2 lines fit one CTA's threads, else the split (2 or 4, lines of 512+ points) that makes
+// them fit; 0 when no split serves the width
+__host__ __device__ constexpr int col_cluster(int W, int log2n, size_t esize) {
+    return (W / 2) * line_G(log2n) <= pass_threads(esize) ? 1
+           : (log2n < 9)                                 ? 0
+           : (W / 2) * line_G(log2n) <= 2 * pass_threads(esize) ? 2
+           : (W / 2) * line_G(log2n) <= 4 * pass_threads(esize) ? 4
+                                                                 : 0;
+}
+// shared memory of an update-pass CTA: 6 line buffers per row of its share (1 / cs) of the row
+__host__ __device__ constexpr size_t upd_smem(int rows, int log2n, size_t esize, int cs) {
+    return (size_t)6 * rows * (((1 << log2n) / cs) + (((1 << log2n) / cs) >> 4) + 2) * 2 * esize;
+}
+// shared memory of a direct column-pass CTA: W/2 line buffers of its share of each line
+__host__ __device__ constexpr size_t col_smem(int W, int log2n, size_t esize) {
+    return col_cluster(W, log2n, esize) == 0
+               ? 0
+               : (size_t)(W / 2) *
+                     (((1 << log2n) / col_cluster(W, log2n, esize)) + (((1 << log2n) / col_cluster(W, log2n, esize)) >> 4) + 2) *
+                     2 * esize;
+}
 // macroscopic row pass (two lines of G threads per row): float32 CTAs of max(128, 2 G)
 // threads; at 128 (nx <= 1024) seven are resident per SM (<= 72 registers per thread), so
 // that 1024 rows fit in one wave of 152 SMs
@@ -105,6 +127,7 @@ struct Geometry {
     size_t upd_smem = 0, macro_smem = 0, rowd_smem = 0;
     bool upd_ax = false;        // update pass takes d_x f from a separate row pass (Ax)
     bool macro_serial = false;  // macro pass transforms a row's two lines in turn
+    int upd_cs = 1;             // update pass: CTAs per row (2: a cluster splits each row)
     bool col_tma = false;       // column pass: TMA-fed persistent kernel (width colW) instead of direct loads
     bool flux_tma = false;      // flux column pass: the same choice (width fluxW)
 };
@@ -196,6 +219,7 @@ template <typename R> struct UpdateArgs {
     R *m;            // macroscopic block; moments of fs in, moments of fout out
     int nx, ny, rows;
     int lines_per_batch;  // line transforms in flight per batch (the other threads wait)
+    int cs;               // CTAs per row: 1, or 2 (a cluster splits the row; float32 rows of 2048+)
     Axis<R> ax;
     R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
     R cx[6];  // multiplier of row-transform line q: -h v_x of its first field (the second has -v_x)
