@@ -199,15 +199,16 @@ size_t lbm_device_bytes(lbm_handle h);
 int lbm_geometry(lbm_handle h, int geometry[4]);
 /* The default launch plan of an nx x ny grid in the given precision, computed on the host
  * (no device, no handle): what lbm_create will choose before any tuning, and what each pass
- * needs. out[16] (caller-owned): [0] column tile width, [1] its CTA threads, [2] its shared
+ * needs. out[18] (caller-owned): [0] column tile width, [1] its CTA threads, [2] its shared
  * memory (bytes); [3] macro rows per CTA, [4] macro CTA threads, [5] macro shared memory,
  * [6] 1 if the macro pass transforms a row's two lines in turn; [7] update rows per CTA,
  * [8] update shared memory, [9] 1 if the update takes d_x f from a separate row pass (then
  * [8] is 0); [10] rows per CTA, [11] CTA threads and [12] shared memory of the row-derivative
  * pass; limits: [13] CTA threads of the column and update passes, [14] CTA threads of the
- * macro pass, [15] shared memory per CTA. LBM_ERR_ARG for sizes or precision outside the
+ * macro pass, [15] shared memory per CTA; [16] CTAs per row of the update pass (a cluster of two
+ * splits float32 rows of 4096), [17] CTAs per cluster of the column pass. LBM_ERR_ARG for sizes or precision outside the
  * library's range; LBM_ERR_UNSUPPORTED (out filled) if a pass would exceed [15]. */
-int lbm_launch_plan(int nx, int ny, int precision, int out[16]);
+int lbm_launch_plan(int nx, int ny, int precision, int out[18]);
 /* Sets the launch shapes (same meaning as lbm_geometry) to any of the autotuner's legal
  * candidates (LBM_ERR_ARG otherwise); results do not depend on them. Synchronises. */
 int lbm_set_geometry(lbm_handle h, const int geometry[4]);

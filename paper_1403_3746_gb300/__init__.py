@@ -172,13 +172,13 @@ def _blob_in(blob):
 
 PLAN_KEYS = ("col_width", "col_threads", "col_smem", "macro_rows", "macro_threads", "macro_smem", "macro_serial",
              "update_rows", "update_smem", "update_ax", "rowd_rows", "rowd_threads", "rowd_smem",
-             "pass_thread_cap", "macro_thread_cap", "cta_smem_cap")
+             "pass_thread_cap", "macro_thread_cap", "cta_smem_cap", "update_ctas_per_row", "col_ctas_per_cluster")
 
 
 def launch_plan(nx, ny, precision=LBM_FP64):
     """lbm_launch_plan: the default launch shapes of an nx x ny grid and what each pass needs,
     computed on the host (a dict keyed by PLAN_KEYS)."""
-    out = (ctypes.c_int * 16)()
+    out = (ctypes.c_int * 18)()
     _check(lib().lbm_launch_plan(int(nx), int(ny), int(precision), out))
     return dict(zip(PLAN_KEYS, list(out)))
 

@@ -1274,7 +1274,7 @@ int lbm_timing_read(lbm_handle c, int kernel, double *ms, long long *launches) {
 
 size_t lbm_device_bytes(lbm_handle c) { return c ? c->slab_bytes : 0; }
 
-int lbm_launch_plan(int nx, int ny, int precision, int out[16]) {
+int lbm_launch_plan(int nx, int ny, int precision, int out[18]) {
     if (!out) return fail(LBM_ERR_ARG, "NULL argument");
     if (!is_pow2(nx) || !is_pow2(ny) || nx > 4096 || ny > 4096)
         return fail(LBM_ERR_ARG, "nx=%d, ny=%d: each must be a power of two in [2, 4096]", nx, ny);
@@ -1284,13 +1284,14 @@ int lbm_launch_plan(int nx, int ny, int precision, int out[16]) {
     const int lx = ilog2(nx), ly = ilog2(ny);
     Geometry g;
     pass_geometry(nx, ny, es, &g);
-    const int v[16] = {g.colW, (g.colW / 2) * line_G(ly) / std::max(1, col_cluster(g.colW, ly, es)), (int)g.col_smem,
+    const int v[18] = {g.colW, (g.colW / 2) * line_G(ly) / std::max(1, col_cluster(g.colW, ly, es)), (int)g.col_smem,
                        g.rows_macro, g.rows_macro * line_G(lx) * (g.macro_serial ? 1 : 2), (int)g.macro_smem,
                        g.macro_serial ? 1 : 0,
                        g.rows_upd, (int)g.upd_smem, g.upd_ax ? 1 : 0,
                        g.rows_rowd, g.rows_rowd * line_G(lx), (int)g.rowd_smem,
-                       pass_threads(es), macro_threads(es, lx), (int)kMaxCtaSmem};
-    for (int k = 0; k < 16; ++k) out[k] = v[k];
+                       pass_threads(es), macro_threads(es, lx), (int)kMaxCtaSmem,
+                       g.upd_cs, std::max(1, col_cluster(g.colW, ly, es))};
+    for (int k = 0; k < 18; ++k) out[k] = v[k];
     const size_t need = std::max(std::max(g.upd_smem, g.macro_smem), std::max(g.col_smem, g.rowd_smem));
     if (need > kMaxCtaSmem)
         return fail(LBM_ERR_UNSUPPORTED, "nx=%d ny=%d needs %zu B of shared memory per block", nx, ny, need);
