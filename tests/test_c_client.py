@@ -17,7 +17,7 @@ C_SOURCE = r"""
 
 int main(void) {
     double rl = 0.0, rv = 0.0;
-    int plan[16];
+    int plan[18];
     int rc = lbm_maxwell(0.95, &rl, &rv);
     printf("maxwell %d %.7f %.7f\n", rc, rl, rv);
     rc = lbm_launch_plan(1024, 1024, LBM_MIXED, plan);
