@@ -316,6 +316,33 @@ int lbm_batch_autotune(lbm_batch b);
 int lbm_batch_structure_factor(lbm_batch b, int k, int nbins, double *S, double *count);
 int lbm_batch_geometry(lbm_batch b, int k, int geometry[4]);
 
+/* How lbm_batch_step advances the batch (no counterpart in the paper: a performance choice that
+ * does not change any result). LBM_BATCH_GRAPH (the default): one CUDA graph per step whose
+ * size groups run as parallel branches of the per-pass kernels. LBM_BATCH_PERSISTENT: one
+ * persistent kernel launch per step (captured in a CUDA graph after a reset of its control
+ * words) whose CTAs take work items (stage, pass, size group, instance, tile) from a global
+ * queue; each item waits, bounded, until every tile of the previous pass of its own instance
+ * has completed (per-instance counters), so instances move through the passes independently.
+ * The persistent form takes LBM_MIXED batches of at most 4 sizes with nx and ny in 128..1024
+ * and flags 0 or LBM_FLAG_ISOTHERMAL (LBM_ERR_UNSUPPORTED otherwise); it allocates its control
+ * words (a few ints per instance) on its first step. A wait that runs out (budget: the
+ * wait_cycles of lbm_batch_fault_inject, about a second by default) makes every CTA leave the
+ * launch; the next lbm_batch_synchronize / lbm_batch_moments / lbm_batch_get_f /
+ * lbm_batch_diagnostics / lbm_batch_get_state returns LBM_ERR_TIMEOUT once and the states must be
+ * re-initialised. */
+#define LBM_BATCH_GRAPH 0
+#define LBM_BATCH_PERSISTENT 1
+int lbm_batch_set_form(lbm_batch b, int form);
+int lbm_batch_form(lbm_batch b); /* -1 for NULL */
+/* Waits for all work of the batch; LBM_ERR_TIMEOUT if a bounded device wait gave up. */
+int lbm_batch_synchronize(lbm_batch b);
+/* Fault injection for tests (no counterpart in the paper): LBM_FAULT_WITHHOLD_COMPLETION makes
+ * the persistent kernel's first work item never report its completion, so the items that wait
+ * for it run out their budget of wait_cycles clock cycles (<= 0: the default); nothing faults.
+ * LBM_FAULT_NONE restores normal operation. */
+#define LBM_FAULT_WITHHOLD_COMPLETION 2
+int lbm_batch_fault_inject(lbm_batch b, int what, long long wait_cycles);
+
 /* Frees all device memory of the batch (synchronises first). NULL is ignored. */
 void lbm_batch_destroy(lbm_batch b);
 

@@ -27,6 +27,9 @@ LBM_COL_DIRECT = 0
 LBM_COL_TMA = 1
 LBM_FAULT_NONE = 0
 LBM_FAULT_STARVE_COPIES = 1
+LBM_FAULT_WITHHOLD_COMPLETION = 2
+LBM_BATCH_GRAPH = 0
+LBM_BATCH_PERSISTENT = 1
 LBM_ERR_TIMEOUT = -5
 
 _lib = None
@@ -91,6 +94,10 @@ _SIGS = {
     "lbm_launch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "lbm_state_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_pass_kinds": (ctypes.c_int, [_P, _P]),
+    "lbm_batch_set_form": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lbm_batch_form": (ctypes.c_int, [_P]),
+    "lbm_batch_synchronize": (ctypes.c_int, [_P]),
+    "lbm_batch_fault_inject": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong]),
     "lbm_set_pass_kinds": (ctypes.c_int, [_P, _P]),
     "lbm_fault_inject": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong]),
     "lbm_params_hash": (ctypes.c_ulonglong, [ctypes.POINTER(lbm_params)]),
@@ -430,6 +437,20 @@ class Batch:
 
     def autotune(self):
         _check(lib().lbm_batch_autotune(self._h))
+
+    def set_form(self, form):
+        """LBM_BATCH_GRAPH or LBM_BATCH_PERSISTENT (one persistent kernel launch per step)."""
+        _check(lib().lbm_batch_set_form(self._h, int(form)))
+
+    def form(self):
+        return int(lib().lbm_batch_form(self._h))
+
+    def synchronize(self):
+        _check(lib().lbm_batch_synchronize(self._h))
+
+    def fault_inject(self, what, wait_cycles=0):
+        """Test hook: LBM_FAULT_WITHHOLD_COMPLETION makes the persistent kernel's waits run out."""
+        _check(lib().lbm_batch_fault_inject(self._h, int(what), int(wait_cycles)))
 
     def structure_factor(self, k, nbins):
         S, cnt = np.empty(nbins), np.empty(nbins)

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbm_d2v16.so")
-SOURCES = ["lbm_api.cu", "kernels_col.cu", "kernels_row.cu", "kernels_misc.cu", "kernels_sf.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "kernels_col.cu", "kernels_row.cu", "kernels_misc.cu", "kernels_sf.cu", "lbm_noalloc.cu",
+           "kernels_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "--extended-lambda",
          "-I" + CSRC, "-I" + INCLUDE]

@@ -12,43 +12,13 @@
 #include <algorithm>
 #include <mutex>
 
-#include "lbm_internal.cuh"
+#include "pass_bodies.cuh"
 
 namespace lbm {
 
-// One CTA's share of a column tile: CS = 1 (whole lines in one CTA) or the CTA of rank `rank`
-// in a cluster of CS that splits every line of the tile (fft_reg.cuh); tile = the tile index.
-template <typename R, int LOG2N, int CS>
-__device__ __forceinline__ void col_tile(const ColArgs<R> &a, int tile, unsigned rank) {
-    using F = reg::LineFFT<R, LOG2N, true, CS>;
-    using CT = typename F::CT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CT *sbuf = reinterpret_cast<CT *>(smem_raw);
-    const ColJob<R> &job = a.jobs[blockIdx.y];
-    const int L = a.W >> 1;
-    const int l = threadIdx.x & (L - 1);
-    const int t = (int)rank * F::GL + (threadIdx.x >> (a.log2W - 1));  // thread of the line, across the cluster
-    const size_t rsi = (size_t)(job.ld_in >> 1), rso = (size_t)(job.ld_out >> 1);  // row strides, complex units
-    const int x = tile * a.W + 2 * l;
-    // blockIdx.z: instance of a batch stacked along y (ny rows each)
-    const size_t z = blockIdx.z;
-    const CT *in = reinterpret_cast<const CT *>(job.in + z * a.ny * job.ld_in + x);
-    CT *out = reinterpret_cast<CT *>(job.out + z * a.ny * job.ld_out + x);
-
-    CT v[F::E];
-#pragma unroll
-    for (int e = 0; e < F::E; ++e) v[e] = __ldcg(in + (size_t)(t + F::G * e) * rsi);  // L2 only: single use
-    CT *buf = sbuf + l * F::STRIDE;
-    F::template forward<reg::SyncCta>(v, buf, t, a.ay.tw);
-    F::multiply(v, t, job.order, job.c, a.ay.k1, a.ay.k2);
-    F::template inverse<reg::SyncCta>(v, buf, t, a.ay.tw);
-#pragma unroll
-    for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rso] = v[e];
-}
-
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) col_deriv_kernel(const __grid_constant__ ColArgs<R> a) {
-    col_tile<R, LOG2N, 1>(a, blockIdx.x, 0u);
+    col_tile<R, LOG2N, 1>(a, blockIdx.y, blockIdx.z, blockIdx.x, 0u);
 }
 
 // Column tiles wider than one CTA's threads can transform: each line is split over the CS CTAs
@@ -56,7 +26,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
 template <typename R, int LOG2N, int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks)
     col_cluster_kernel(const __grid_constant__ ColArgs<R> a) {
-    col_tile<R, LOG2N, CS>(a, blockIdx.x / CS, reg::cluster_rank());
+    col_tile<R, LOG2N, CS>(a, blockIdx.y, blockIdx.z, blockIdx.x / CS, reg::cluster_rank());
 }
 
 template <typename R, int LOG2N, int CS> static cudaError_t launch_col_cs(const ColArgs<R> &a, int njobs, size_t smem,

@@ -154,6 +154,13 @@ struct lbm_batch_ctx {
     cudaEvent_t fork = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::vector<long long> steps;                // per instance, since its lbm_batch_init
+    // persistent form (kernels_batch.cu): one launch per step over all instances
+    int form = LBM_BATCH_GRAPH;
+    cudaGraphExec_t pgraph = nullptr;            // memset of the control words + the persistent kernel
+    int *bctrl = nullptr;                        // queue counter, abort flag, completion counters; then
+    size_t bctrl_ints = 0;                       // the error word at bctrl[bctrl_ints]
+    long long wait_cycles = 1LL << 31;
+    int withhold = 0;
 };
 
 namespace {
@@ -220,62 +227,112 @@ cudaError_t launch_col_pass(const lbm_ctx *c, const ColArgs<R> &a, int nj, bool 
     return launch_col<R>(a, nj, direct_smem, c->stream);
 }
 
+// Arguments of the passes of one stage (stage 0 / 1: the two Runge-Kutta stages; 2: a forward
+// Euler step in place), shared by the per-pass launches and the persistent batch kernel.
+template <typename R> int column_jobs(const lbm_ctx *c, int stage, ColArgs<R> &a) {
+    const lbm_params &p = c->p;
+    const int nx = c->nx, ldf = NF_F * nx, lda = NF_A * nx, ldm = NF_M * nx;
+    R *m = static_cast<R *>(c->m), *Ay = static_cast<R *>(c->Ay);
+    const R *fs = static_cast<const R *>(stage == 1 ? c->f1 : c->f0);
+    auto M = [m, nx](int k) { return m + (size_t)k * nx; };  // first row of macro field k
+    int nj = 0;
+    // Ay = -h v_iy d_y f_i: the stage's time step and the velocity folded into the multiplier
+    const double hs = stage == 0 ? 0.5 * p.dt : p.dt;
+    if (!(p.flags & LBM_FLAG_NO_ADVECTION))
+        for (int k = 0; k < 12; ++k) {
+            const int i = yfield(k);
+            a.jobs[nj++] = ColJob<R>{fs + (size_t)i * nx, Ay + (size_t)k * nx, ldf, lda, 1, (R)(-hs * vel_y(i))};
+        }
+    if (!(p.flags & LBM_FLAG_NO_FORCE)) {
+        a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RY), ldm, ldm, 1, R(1)};
+        a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RYY), ldm, ldm, 2, R(1)};
+        a.jobs[nj++] = ColJob<R>{M(M_UX), M(M_UXY), ldm, ldm, 1, R(1)};
+        a.jobs[nj++] = ColJob<R>{M(M_UY), M(M_UYY), ldm, ldm, 1, R(1)};
+        a.jobs[nj++] = ColJob<R>{M(M_T), M(M_TY), ldm, ldm, 1, R(1)};
+    }
+    return nj;
+}
+
+template <typename R> void flux_jobs(const lbm_ctx *c, ColArgs<R> &a) {
+    const int nx = c->nx, ldm = NF_M * nx;
+    R *m = static_cast<R *>(c->m);
+    auto M = [m, nx](int k) { return m + (size_t)k * nx; };
+    a.jobs[0] = ColJob<R>{M(M_QY), M(M_DQY), ldm, ldm, 1, R(1)};
+    a.jobs[1] = ColJob<R>{M(M_SXY), M(M_DSXYY), ldm, ldm, 1, R(1)};
+    a.jobs[2] = ColJob<R>{M(M_SYY), M(M_DSYY), ldm, ldm, 1, R(1)};
+    a.jobs[3] = ColJob<R>{M(M_DIVU), M(M_DDIVUY), ldm, ldm, 1, R(1)};
+}
+
+template <typename R> MacroArgs<R> macro_args(const lbm_ctx *c, int rows_per_cta) {
+    const lbm_params &p = c->p;
+    MacroArgs<R> a{};
+    a.m = static_cast<R *>(c->m);
+    a.nx = c->nx;
+    a.ny = c->nb * c->ny;
+    a.rows = rows_per_cta;
+    a.serial = c->geo.macro_serial ? 1 : 0;
+    a.ax = axis<R>(c, true);
+    a.K = (R)p.K; a.H = (R)p.H; a.q = (R)p.q; a.zeta = (R)p.zeta;
+    return a;
+}
+
+template <typename R> UpdateArgs<R> update_args(const lbm_ctx *c, int stage, int rows_per_cta) {
+    const lbm_params &p = c->p;
+    const bool adv = !(p.flags & LBM_FLAG_NO_ADVECTION);
+    R *f0 = static_cast<R *>(c->f0), *f1 = static_cast<R *>(c->f1);
+    UpdateArgs<R> a{};
+    a.fs = stage == 1 ? f1 : f0;
+    a.Ax = (adv && c->geo.upd_ax) ? static_cast<const R *>(c->Ax) : nullptr;
+    a.fbase = f0;
+    a.fout = stage == 0 ? f1 : f0;  // stage 2 (Euler): in place, same node, same thread
+    a.Ay = static_cast<const R *>(c->Ay);
+    a.m = static_cast<R *>(c->m);
+    a.nx = c->nx; a.ny = c->nb * c->ny; a.rows = rows_per_cta;
+    a.cs = c->geo.upd_cs;
+    a.ax = axis<R>(c, true);
+    a.tau_inv = (R)(1.0 / p.tau);
+    a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
+    for (int q = 0; q < 6; ++q) a.cx[q] = (R)(-(stage == 0 ? 0.5 * p.dt : p.dt) * vel_x(xfield(2 * q)));
+    a.T_iso = (R)p.T_iso;
+    a.K = (R)p.K;
+    a.b = (R)p.b;
+    a.eta2 = (R)(p.eta0 * p.eta0);
+    for (int i = 0; i < 16; ++i) {
+        const double psi = vel_sq(i) + (i < 4 ? p.eta0 * p.eta0 : 0.0);
+        a.k.psi_hi[i] = (R)psi;
+        a.k.psi_lo[i] = (R)(psi - (double)a.k.psi_hi[i]);
+    }
+    a.flags = p.flags;
+    for (int k = 0; k < 256; ++k) a.k.minv[k] = (R)c->minv[k];
+    return a;
+}
+
 template <typename R>
 int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
     const lbm_params &p = c->p;
     const bool adv = !(p.flags & LBM_FLAG_NO_ADVECTION);
     const bool frc = !(p.flags & LBM_FLAG_NO_FORCE);
     const int nx = c->nx, rows = c->nb * c->ny;
-    R *f0 = static_cast<R *>(c->f0), *f1 = static_cast<R *>(c->f1);
-    R *Ay = static_cast<R *>(c->Ay), *m = static_cast<R *>(c->m);
-    const R *fs = stage == 1 ? f1 : f0;
-    const int ldf = NF_F * nx, lda = NF_A * nx, ldm = NF_M * nx;
-    auto M = [m, nx](int k) { return m + (size_t)k * nx; };  // first row of macro field k
-
+    const R *fs = static_cast<const R *>(stage == 1 ? c->f1 : c->f0);
+    const int ldf = NF_F * nx;
     {
         ColArgs<R> a = col_args<R>(c, c->nb, c->geo.colW);
-        int nj = 0;
-        // Ay = -h v_iy d_y f_i: the stage's time step and the velocity folded into the multiplier
-        const double hs = stage == 0 ? 0.5 * p.dt : p.dt;
-        if (adv)
-            for (int k = 0; k < 12; ++k) {
-                const int i = yfield(k);
-                a.jobs[nj++] = ColJob<R>{fs + (size_t)i * nx, Ay + (size_t)k * nx, ldf, lda, 1, (R)(-hs * vel_y(i))};
-            }
-        if (frc) {
-            a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RY), ldm, ldm, 1, R(1)};
-            a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RYY), ldm, ldm, 2, R(1)};
-            a.jobs[nj++] = ColJob<R>{M(M_UX), M(M_UXY), ldm, ldm, 1, R(1)};
-            a.jobs[nj++] = ColJob<R>{M(M_UY), M(M_UYY), ldm, ldm, 1, R(1)};
-            a.jobs[nj++] = ColJob<R>{M(M_T), M(M_TY), ldm, ldm, 1, R(1)};
-        }
+        const int nj = column_jobs<R>(c, stage, a);
         if (nj && (passes & PASS_COL)) {
             LaunchTimer t(c, LBM_K_COL);
             CU_TRY(launch_col_pass<R>(c, a, nj, c->geo.col_tma, c->geo.col_smem));
         }
     }
     if (frc && (passes & PASS_MACRO)) {
-        {
-            MacroArgs<R> a{};
-            a.m = m;
-            a.nx = nx; a.ny = rows; a.rows = c->geo.rows_macro;
-            a.serial = c->geo.macro_serial ? 1 : 0;
-            a.ax = axis<R>(c, true);
-            a.K = (R)p.K; a.H = (R)p.H; a.q = (R)p.q; a.zeta = (R)p.zeta;
-            LaunchTimer t(c, LBM_K_MACRO);
-            CU_TRY(launch_macro<R>(a, c->geo.macro_smem, c->stream));
-        }
+        const MacroArgs<R> a = macro_args<R>(c, c->geo.rows_macro);
+        LaunchTimer t(c, LBM_K_MACRO);
+        CU_TRY(launch_macro<R>(a, c->geo.macro_smem, c->stream));
     }
     if (frc && (passes & PASS_FLUX)) {
-        {
-            ColArgs<R> a = col_args<R>(c, c->nb, c->geo.fluxW);
-            a.jobs[0] = ColJob<R>{M(M_QY), M(M_DQY), ldm, ldm, 1, R(1)};
-            a.jobs[1] = ColJob<R>{M(M_SXY), M(M_DSXYY), ldm, ldm, 1, R(1)};
-            a.jobs[2] = ColJob<R>{M(M_SYY), M(M_DSYY), ldm, ldm, 1, R(1)};
-            a.jobs[3] = ColJob<R>{M(M_DIVU), M(M_DDIVUY), ldm, ldm, 1, R(1)};
-            LaunchTimer t(c, LBM_K_FLUX);
-            CU_TRY(launch_col_pass<R>(c, a, 4, c->geo.flux_tma, c->geo.flux_smem));
-        }
+        ColArgs<R> a = col_args<R>(c, c->nb, c->geo.fluxW);
+        flux_jobs<R>(c, a);
+        LaunchTimer t(c, LBM_K_FLUX);
+        CU_TRY(launch_col_pass<R>(c, a, 4, c->geo.flux_tma, c->geo.flux_smem));
     }
     if ((passes & PASS_UPDATE) && adv && c->geo.upd_ax) {
         // d_x f_i of the 12 fields with v_x != 0 into Ax, two fields per complex line
@@ -296,30 +353,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
         }
     }
     if (passes & PASS_UPDATE) {
-        UpdateArgs<R> a{};
-        a.fs = fs;
-        a.Ax = (adv && c->geo.upd_ax) ? static_cast<const R *>(c->Ax) : nullptr;
-        a.fbase = f0;
-        a.fout = stage == 0 ? f1 : f0;  // stage 2 (Euler): in place, same node, same thread
-        a.Ay = Ay;
-        a.m = m;
-        a.nx = nx; a.ny = rows; a.rows = c->geo.rows_upd;
-        a.cs = c->geo.upd_cs;
-        a.ax = axis<R>(c, true);
-        a.tau_inv = (R)(1.0 / p.tau);
-        a.h = (R)(stage == 0 ? 0.5 * p.dt : p.dt);
-        for (int q = 0; q < 6; ++q) a.cx[q] = (R)(-(stage == 0 ? 0.5 * p.dt : p.dt) * vel_x(xfield(2 * q)));
-        a.T_iso = (R)p.T_iso;
-        a.K = (R)p.K;
-        a.b = (R)p.b;
-        a.eta2 = (R)(p.eta0 * p.eta0);
-        for (int i = 0; i < 16; ++i) {
-            const double psi = vel_sq(i) + (i < 4 ? p.eta0 * p.eta0 : 0.0);
-            a.psi_hi[i] = (R)psi;
-            a.psi_lo[i] = (R)(psi - (double)a.psi_hi[i]);
-        }
-        a.flags = p.flags;
-        for (int k = 0; k < 256; ++k) a.minv[k] = (R)c->minv[k];
+        const UpdateArgs<R> a = update_args<R>(c, stage, c->geo.rows_upd);
         LaunchTimer t(c, LBM_K_UPDATE);
         CU_TRY(launch_update<R>(a, c->geo.upd_smem, c->stream));
     }
@@ -1443,6 +1477,8 @@ void lbm_batch_destroy(lbm_batch b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
+    if (b->bctrl) cudaFree(b->bctrl);
     for (cudaStream_t s : b->branch) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -1523,11 +1559,184 @@ static int build_batch_graph(lbm_batch b) {
     return LBM_OK;
 }
 
+// Whether the persistent kernel can take the batch: float32, the full two-stage model (or the
+// thermostat), at most kBatchGroups sizes, lines of 128 to 1024 points.
+static bool batch_persistent_ok(lbm_batch b) {
+    if (b->groups.empty() || (int)b->groups.size() > kBatchGroups) return false;
+    for (lbm_ctx *c : b->groups)
+        if (!c->mixed || (c->p.flags & ~LBM_FLAG_ISOTHERMAL) || c->lx < 7 || c->lx > 10 || c->ly < 7 || c->ly > 10)
+            return false;
+    return true;
+}
+
+// Work items and tile shapes of the persistent kernel (512-thread CTAs): column tiles of W =
+// min(nx, 1024 / G) columns (W/2 lines of G threads fill the CTA), macro and update row blocks
+// as large as 512 threads and 100 KB of shared memory allow.
+static int batch_args(lbm_batch b, BatchArgs<float> &A, size_t &smem) {
+    constexpr int T = 512;
+    constexpr size_t es = 4, cap = 100 * 1024;
+    A.ngroups = (int)b->groups.size();
+    smem = 0;
+    int inst = 0;
+    for (int gi = 0; gi < A.ngroups; ++gi) {
+        lbm_ctx *c = b->groups[gi];
+        BatchGroup<float> &G = A.g[gi];
+        const int Gy = line_G(c->ly), Gx = line_G(c->lx);
+        const int W = std::min(c->nx, 2 * T / Gy);
+        int nrm = 1;
+        while (2 * nrm <= c->ny && 2 * (2 * nrm) * Gx <= T &&
+               3 * (size_t)(2 * nrm) * line_smem(c->lx) * 2 * es + (size_t)(2 * nrm) * c->nx * es <= cap)
+            nrm *= 2;
+        int nru = 1;
+        while (2 * nru <= c->ny && 2 * nru * c->nx <= 4096 && upd_smem(2 * nru, c->lx, es, 1) <= cap) nru *= 2;
+        int nj = 0;
+        for (int st = 0; st < 2; ++st) {
+            G.col[st] = col_args<float>(c, c->nb, W);
+            nj = column_jobs<float>(c, st, G.col[st]);
+            G.flux[st] = col_args<float>(c, c->nb, W);
+            flux_jobs<float>(c, G.flux[st]);
+            G.upd[st] = update_args<float>(c, st, nru);
+            G.upd[st].cs = 1;
+            G.upd[st].lines_per_batch = update_lines_per_batch(6 * nru, Gx, T);
+        }
+        G.macro = macro_args<float>(c, nrm);
+        G.tiles_x[0] = G.tiles_x[1] = c->nx / W;
+        G.ntile[0] = nj * (c->nx / W);
+        G.ntile[1] = c->ny / nrm;
+        G.ntile[2] = 4 * (c->nx / W);
+        G.ntile[3] = c->ny / nru;
+        G.inst0 = inst;
+        inst += c->nb;
+        smem = std::max(smem, col_smem(W, c->ly, es));
+        smem = std::max(smem, 3 * (size_t)nrm * line_smem(c->lx) * 2 * es + (size_t)nrm * c->nx * es);
+        smem = std::max(smem, upd_smem(nru, c->lx, es, 1));
+    }
+    int q = 0;
+    for (int chain = 0; chain < kBatchPasses; ++chain)
+        for (int gi = 0; gi < A.ngroups; ++gi) {
+            A.seg[chain * A.ngroups + gi] = q;
+            q += b->groups[gi]->nb * A.g[gi].ntile[chain & 3];
+        }
+    A.seg[kBatchPasses * A.ngroups] = q;
+    const size_t ints = 2 + (size_t)inst * kBatchPasses;
+    if (!b->bctrl || b->bctrl_ints != ints) {
+        if (b->bctrl) cudaFree(b->bctrl);
+        b->bctrl = nullptr;
+        if (cudaMalloc(&b->bctrl, (ints + 1) * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ERR_NOMEM, "persistent batch: no device memory for its control words");
+        }
+        b->bctrl_ints = ints;
+        CU_TRY(cudaMemset(b->bctrl, 0, (ints + 1) * sizeof(int)));
+    }
+    A.ctrl = b->bctrl;
+    A.err = b->bctrl + ints;
+    A.wait_cycles = b->wait_cycles;
+    A.withhold = b->withhold;
+    return LBM_OK;
+}
+
+static int build_batch_persistent_graph(lbm_batch b) {
+    BatchArgs<float> *A = new (std::nothrow) BatchArgs<float>();
+    if (!A) return fail(LBM_ERR_NOMEM, "host allocation failed");
+    struct Del {
+        BatchArgs<float> *p;
+        ~Del() { delete p; }
+    } del{A};
+    size_t smem = 0;
+    int rc = batch_args(b, *A, smem);
+    if (rc) return rc;
+    int dev = 0, sms = 0;
+    CU_TRY(cudaGetDevice(&dev));
+    CU_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 0;
+    const cudaError_t eo = batch_step_ctas_per_sm<float>(smem, &per_sm);
+    if (eo != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return fail(LBM_ERR_UNSUPPORTED, "persistent batch: no CTA fits an SM (%zu B of shared memory; %s)", smem,
+                    cudaGetErrorString(eo));
+    }
+    if (!b->cap) CU_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    CU_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = cudaMemsetAsync(b->bctrl, 0, b->bctrl_ints * sizeof(int), b->cap);  // not the error word
+    if (e == cudaSuccess) e = launch_batch_step<float>(*A, smem, per_sm * sms, b->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
+    if (e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(LBM_ERR_CUDA, "persistent batch graph: %s", cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->pgraph, graph, 0);
+    cudaGraphDestroy(graph);
+    CU_TRY(ei);
+    return LBM_OK;
+}
+
+// After a synchronisation of the batch's stream: the persistent kernel's error word and every
+// size group's own (TMA) error word; a set word is reported once as LBM_ERR_TIMEOUT.
+static int check_batch_error(lbm_batch b) {
+    if (b->bctrl) {
+        int v = 0;
+        CU_TRY(cudaMemcpy(&v, b->bctrl + b->bctrl_ints, sizeof v, cudaMemcpyDeviceToHost));
+        if (v) {
+            CU_TRY(cudaMemset(b->bctrl + b->bctrl_ints, 0, sizeof v));
+            return fail(LBM_ERR_TIMEOUT, "a bounded wait of the persistent batch kernel gave up (error word %d): the "
+                        "steps since the last check did not complete and the states are not valid",
+                        v);
+        }
+    }
+    for (lbm_ctx *c : b->groups) {
+        const int rc = check_device_error(c);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_synchronize(lbm_batch b) {
+    if (!b) return fail(LBM_ERR_ARG, "NULL batch");
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    return check_batch_error(b);
+}
+
+int lbm_batch_form(lbm_batch b) { return b ? b->form : -1; }
+
+int lbm_batch_set_form(lbm_batch b, int form) {
+    if (!b || (form != LBM_BATCH_GRAPH && form != LBM_BATCH_PERSISTENT)) return fail(LBM_ERR_ARG, "bad argument");
+    if (form == LBM_BATCH_PERSISTENT && !batch_persistent_ok(b))
+        return fail(LBM_ERR_UNSUPPORTED, "the persistent form takes float32 batches of at most %d sizes with lines "
+                    "of 128 to 1024 points and no test flags",
+                    kBatchGroups);
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    b->form = form;
+    return LBM_OK;
+}
+
+int lbm_batch_fault_inject(lbm_batch b, int what, long long wait_cycles) {
+    if (!b || (what != LBM_FAULT_NONE && what != LBM_FAULT_WITHHOLD_COMPLETION)) return fail(LBM_ERR_ARG, "bad argument");
+    CU_TRY(cudaStreamSynchronize(b->stream));
+    b->withhold = what == LBM_FAULT_WITHHOLD_COMPLETION ? 1 : 0;
+    b->wait_cycles = wait_cycles > 0 ? wait_cycles : (1LL << 31);
+    if (b->pgraph) {
+        cudaGraphExecDestroy(b->pgraph);
+        b->pgraph = nullptr;
+    }
+    return LBM_OK;
+}
+
 int lbm_batch_step(lbm_batch b, int n) {
     if (!b || n < 0) return fail(LBM_ERR_ARG, "bad batch or n < 0");
     for (lbm_ctx *c : b->groups)
         if (!c->all_initialized()) return fail(LBM_ERR_STATE, "lbm_batch_step before every instance is initialised");
     if (n == 0) return LBM_OK;
+    if (b->form == LBM_BATCH_PERSISTENT) {
+        if (!b->pgraph) {
+            int rc = build_batch_persistent_graph(b);
+            if (rc) return rc;
+        }
+        for (int s = 0; s < n; ++s) CU_TRY(cudaGraphLaunch(b->pgraph, b->stream));
+        for (long long &s : b->steps) s += n;
+        return LBM_OK;
+    }
     if (!b->graph) {
         int rc = build_batch_graph(b);
         if (rc) return rc;
@@ -1542,6 +1751,7 @@ int lbm_batch_moments(lbm_batch b, int k, double *rho, double *ux, double *uy, d
     lbm_ctx *c = b->groups[b->where[k].first];
     if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
     CU_TRY(cudaStreamSynchronize(b->stream));
+    if (int rc = check_batch_error(b)) return rc;
     return moments_host(c, b->where[k].second, rho, ux, uy, T);
 }
 
@@ -1550,6 +1760,7 @@ int lbm_batch_get_f(lbm_batch b, int k, double *f16) {
     lbm_ctx *c = b->groups[b->where[k].first];
     if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
     CU_TRY(cudaStreamSynchronize(b->stream));
+    if (int rc = check_batch_error(b)) return rc;
     return get_f_host(c, b->where[k].second, f16);
 }
 
@@ -1558,6 +1769,7 @@ int lbm_batch_get_state(lbm_batch b, int k, void *blob, size_t bytes) {
     lbm_ctx *c = b->groups[b->where[k].first];
     if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
     CU_TRY(cudaStreamSynchronize(b->stream));
+    if (int rc = check_batch_error(b)) return rc;
     return get_state_host(c, b->where[k].second, b->steps[k], blob, bytes);
 }
 
@@ -1579,6 +1791,7 @@ int lbm_batch_diagnostics(lbm_batch b, int k, double out[6]) {
     lbm_ctx *c = b->groups[b->where[k].first];
     if (!c->initialized[b->where[k].second]) return fail(LBM_ERR_STATE, "instance %d has no state yet", k);
     CU_TRY(cudaStreamSynchronize(b->stream));
+    if (int rc = check_batch_error(b)) return rc;
     return diagnostics_instance(c, b->where[k].second, b->steps[k], out);
 }
 

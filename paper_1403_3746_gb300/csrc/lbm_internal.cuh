@@ -209,6 +209,12 @@ template <typename R> struct MacroArgs {
 };
 
 // ---- fused update row pass -----------------------------------------------------------
+// tables of the model read with compile-time indices by the node loop (kernel parameters, so
+// they are operands from the constant bank)
+template <typename R> struct UpdateConst {
+    R psi_hi[16], psi_lo[16];  // psi_i = |v_i|^2 + eta_i^2 as a two-term sum (hi + lo)
+    R minv[256];               // inverse of the 16x16 moment matrix, row-major
+};
 template <typename R> struct UpdateArgs {
     const R *fs;     // f of this stage (derivatives, BGK, f^eq moments), [ny][16][nx]
     const R *fbase;  // f^n (the stage starts from it)
@@ -224,10 +230,42 @@ template <typename R> struct UpdateArgs {
     R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
     R cx[6];  // multiplier of row-transform line q: -h v_x of its first field (the second has -v_x)
     R T_iso;                   // LBM_FLAG_ISOTHERMAL: T at every node
-    R psi_hi[16], psi_lo[16];  // psi_i = |v_i|^2 + eta_i^2 as a two-term sum (hi + lo)
     int flags;
-    R minv[256];  // inverse of the 16x16 moment matrix, row-major
+    UpdateConst<R> k;          // the model's tables (a batch kernel passes one copy for all groups)
 };
+
+// lines per batch of the update pass: the largest divisor of the CTA's lines with LB G <= maxt
+inline int update_lines_per_batch(int nlines, int G, int maxt) {
+    int best = 1;
+    for (int d = 1; d <= nlines; ++d)
+        if (nlines % d == 0 && d * G <= maxt) best = d;
+    return best;
+}
+
+// ---- persistent batch kernel (kernels_batch.cu) ----------------------------------------
+constexpr int kBatchGroups = 4;  // size groups one persistent launch takes
+constexpr int kBatchPasses = 8;  // passes of a step per instance: (column, macro, flux, update) x 2 stages
+template <typename R> struct BatchGroup {
+    ColArgs<R> col[2], flux[2];  // per stage
+    MacroArgs<R> macro;          // the same for both stages
+    UpdateArgs<R> upd[2];        // per stage (lines_per_batch set for the batch kernel's CTA)
+    int ntile[4];                // items per instance: column (jobs x column tiles), macro row blocks,
+                                 // flux (4 jobs x column tiles), update row blocks
+    int tiles_x[2];              // column tiles of the column and flux passes
+    int inst0;                   // the group's first instance in the completion counters
+};
+template <typename R> struct BatchArgs {
+    BatchGroup<R> g[kBatchGroups];
+    int ngroups;
+    int seg[kBatchPasses * kBatchGroups + 1];  // first queue index of each (pass of the chain, group)
+    int *ctrl;              // [0] queue counter, [1] abort flag, then [instances][kBatchPasses]
+                            // completed items (all zeroed before each launch)
+    int *err;               // device error word (tma::kErrTimeout)
+    long long wait_cycles;  // budget of one wait
+    int withhold;           // fault-injection hook: item 0 never reports completion
+};
+template <typename R> cudaError_t launch_batch_step(const BatchArgs<R> &a, size_t smem, int grid, cudaStream_t s);
+template <typename R> cudaError_t batch_step_ctas_per_sm(size_t smem, int *n);
 
 struct InitArgs {
     const double *rho, *ux, *uy, *T;  // inputs, [ny][nx]
@@ -289,9 +327,12 @@ struct SfArgs {
 // dynamic size.
 template <typename K> inline cudaError_t allow_smem(K kern) {
     int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);  // static shared memory counts against the limit
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
     return e;
 }
 
