@@ -139,11 +139,35 @@ def test_grid_shapes(nx, ny):
     assert_parity(fg, mg, fo, mo, TOL64, f"{nx}x{ny}")
 
 
-def test_spinodal_256_20_steps():
+def test_spinodal_256_200_steps():
     fields = synthetic.spinodal(256, 256, 1.0, 0.01, 0.9, seed=2)
-    fo, mo = run_oracle(fields, 20)
-    fg, mg = run_gpu(fields, 20)
-    assert_parity(fg, mg, fo, mo, TOL64, "spinodal 256^2 x 20")
+    fo, mo = run_oracle(fields, 200)
+    fg, mg = run_gpu(fields, 200)
+    assert_parity(fg, mg, fo, mo, TOL64, "spinodal 256^2 x 200")
+
+
+def test_spinodal_256_2000_steps_against_stored_oracle():
+    # The 256^2 quench through 2000 steps (t = 0.2; the density contrast grows from 1% to 3%,
+    # still the linear stage) against the oracle's state stored by tests/golden/make_spinodal256.py
+    # (sampled rows). f, rho and T stay within 1e-10. The velocity is a small difference of large
+    # momentum sums measured against a 1e-3 floor; its GPU-oracle difference grows with the
+    # unstable modes and reaches about 7e-10 of the floor by step 2000 (1.3e-10 at step 300), so
+    # it is held to 1e-9 here and to 1e-10 in the 200-step test above.
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "spinodal256_2000.npz"))
+    fields = synthetic.spinodal(256, 256, 1.0, 0.01, 0.9, seed=int(g["seed"]))
+    fg, mg = run_gpu(fields, int(g["steps"]))
+    rows, frows = g["moment_rows"], g["f_rows"]
+    fo = g["f"]
+    floor = 1e-2 * np.max(np.abs(fo))
+    ef = max(field_err(fg[i][frows], fo[i], floor) for i in range(16))
+    er = field_err(mg[0][rows], g["rho"])
+    eT = field_err(mg[3][rows], g["T"])
+    us = max(float(g["u_scale"]), 1e-3)
+    eu = max(float(np.max(np.abs(mg[1][rows] - g["ux"]))), float(np.max(np.abs(mg[2][rows] - g["uy"])))) / us
+    print(f"spinodal 256^2 x 2000 vs stored oracle: f {ef:.2e}, rho {er:.2e}, T {eT:.2e}, u {eu:.2e}")
+    assert ef <= TOL64 and er <= TOL64 and eT <= TOL64
+    assert eu <= 1e-9
 
 
 def test_droplet_1024_one_step():
