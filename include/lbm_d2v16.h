@@ -146,6 +146,20 @@ int lbm_set_state(lbm_handle h, const void *blob, size_t bytes);
  * max |u|, and the number of steps taken. Synchronises the stream. */
 int lbm_diagnostics(lbm_handle h, double out[6]);
 
+/* lbm_diagnostics in two halves, so that a caller reading the diagnostics of every step does
+ * not stall the stream (no counterpart in the paper: a library service). lbm_diagnostics_begin
+ * issues the diagnostics of the current state on the stream, with an asynchronous copy of the
+ * per-block partial sums into a pinned host slot the handle owns (allocated at the first call),
+ * and returns at once; lbm_diagnostics_end waits for the oldest pending request only and
+ * reduces it into out[6] (as lbm_diagnostics; out[5] = the step count when it was issued). At
+ * most two requests may be pending (LBM_ERR_STATE otherwise; also for an end without a
+ * request). Typical use: step, begin, end of the previous step's request; stepping between a
+ * begin and its end is expected, since a request reads the state at the point of the stream
+ * where it was issued. An end reports LBM_ERR_TIMEOUT if a bounded device wait gave up before
+ * its request. */
+int lbm_diagnostics_begin(lbm_handle h);
+int lbm_diagnostics_end(lbm_handle h, double out[6]);
+
 /* Circularly averaged structure factor of the density (the domain-growth measure of the
  * phase-separation runs, Sec. 3.2), computed on the device in float64 from the current
  * density: S[b] = mean over shell b of |rho_hat(m)|^2 / (nx ny) for b < nbins (1..8192),

@@ -95,6 +95,8 @@ _SIGS = {
     "lbm_state_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_pass_kinds": (ctypes.c_int, [_P, _P]),
     "lbm_batch_set_form": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lbm_diagnostics_begin": (ctypes.c_int, [_P]),
+    "lbm_diagnostics_end": (ctypes.c_int, [_P, _D]),
     "lbm_batch_form": (ctypes.c_int, [_P]),
     "lbm_batch_synchronize": (ctypes.c_int, [_P]),
     "lbm_batch_fault_inject": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong]),
@@ -304,6 +306,16 @@ class Simulation:
         """dict(mass, px, py, energy, umax, steps)."""
         out = (ctypes.c_double * 6)()
         _check(lib().lbm_diagnostics(self._h, out))
+        return dict(zip(("mass", "px", "py", "energy", "umax", "steps"), list(out)))
+
+    def diagnostics_begin(self):
+        """Issue the diagnostics of the current state without waiting (lbm_diagnostics_begin)."""
+        _check(lib().lbm_diagnostics_begin(self._h))
+
+    def diagnostics_end(self):
+        """Wait for the oldest pending request and return its dict (lbm_diagnostics_end)."""
+        out = (ctypes.c_double * 6)()
+        _check(lib().lbm_diagnostics_end(self._h, out))
         return dict(zip(("mass", "px", "py", "energy", "umax", "steps"), list(out)))
 
     def timing(self, enable=True):

@@ -111,6 +111,12 @@ struct lbm_ctx {
     void *Ax = nullptr;                 // [nb ny][16][nx]: d_x f_i, only when geo.upd_ax
     double *partial = nullptr;
     int diag_blocks = 0;
+    // pipelined diagnostics (lbm_diagnostics_begin / _end): two pinned host slots, each the
+    // per-block partial sums and the error word of one request, and a ring of pending requests
+    double *hpart = nullptr;
+    cudaEvent_t dev_ev[2] = {nullptr, nullptr};
+    long long dsteps[2] = {0, 0};
+    int dhead = 0, dcount = 0;
     int *err = nullptr;               // device error word of the bounded waits (tma::kErrTimeout)
     long long wait_cycles = 1LL << 31;  // budget of one device-side wait (about a second)
     int starve = 0;                   // fault-injection hook (lbm_fault_inject)
@@ -598,6 +604,9 @@ void free_ctx(lbm_ctx *c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->dev_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->hpart) cudaFreeHost(c->hpart);
     cudaFree(c->slab);
     delete c;
 }
@@ -1024,6 +1033,21 @@ int diagnostics_instance(lbm_ctx *c, int k, long long steps, double out[6]) {
     return LBM_OK;
 }
 
+// host reduction of one slot of per-block partial sums into out[0..4]
+int reduce_partials(const lbm_ctx *c, const double *part, double out[6]) {
+    double s[4] = {0, 0, 0, 0}, mx = 0;
+    for (int b = 0; b < c->diag_blocks; ++b) {
+        for (int j = 0; j < 4; ++j) s[j] += part[b * 5 + j];
+        mx = std::max(mx, part[b * 5 + 4]);
+    }
+    const double cell = c->p.dx * c->p.dy;
+    for (int j = 0; j < 4; ++j) out[j] = s[j] * cell;
+    out[4] = std::sqrt(mx);
+    for (int j = 0; j < 5; ++j)
+        if (!std::isfinite(out[j])) return fail(LBM_ERR_NONFINITE, "diagnostic %d is not finite", j);
+    return LBM_OK;
+}
+
 // Circularly averaged structure factor of instance k's density (kernels_sf.cu): the spectra
 // go to the half-step buffer f1 (16 bytes per node, free outside a step); the frequency
 // tables and shell sums to a temporary device buffer.
@@ -1230,6 +1254,50 @@ int lbm_diagnostics(lbm_handle c, double out[6]) {
     if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
     if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
     return diagnostics_instance(c, 0, c->steps, out);
+}
+
+int lbm_diagnostics_begin(lbm_handle c) {
+    if (!c) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
+    if (c->dcount == 2) return fail(LBM_ERR_STATE, "two requests pending: call lbm_diagnostics_end first");
+    const size_t slot_doubles = (size_t)c->diag_blocks * 5 + 1;  // partials, then the error word
+    if (!c->hpart) {
+        if (cudaHostAlloc(&c->hpart, 2 * slot_doubles * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            c->hpart = nullptr;
+            return fail(LBM_ERR_NOMEM, "no pinned host memory for the diagnostics slots");
+        }
+        for (cudaEvent_t &e : c->dev_ev) CU_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const int slot = (c->dhead + c->dcount) & 1;
+    double *h = c->hpart + slot * slot_doubles;
+    int rc = c->mixed ? diag_launch<float>(c, 0) : diag_launch<double>(c, 0);
+    if (rc) return rc;
+    CU_TRY(cudaMemcpyAsync(h, c->partial, (slot_doubles - 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaMemcpyAsync(h + slot_doubles - 1, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaEventRecord(c->dev_ev[slot], c->stream));
+    c->dsteps[slot] = c->steps;
+    ++c->dcount;
+    return LBM_OK;
+}
+
+int lbm_diagnostics_end(lbm_handle c, double out[6]) {
+    if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    if (c->dcount == 0) return fail(LBM_ERR_STATE, "no diagnostics request pending");
+    const size_t slot_doubles = (size_t)c->diag_blocks * 5 + 1;
+    const int slot = c->dhead;
+    c->dhead ^= 1;
+    --c->dcount;
+    CU_TRY(cudaEventSynchronize(c->dev_ev[slot]));
+    const double *h = c->hpart + slot * slot_doubles;
+    int err = 0;
+    std::memcpy(&err, h + slot_doubles - 1, sizeof err);
+    if (err) {
+        CU_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+        return fail(LBM_ERR_TIMEOUT, "a bounded device-side wait gave up (error word %d) before this request", err);
+    }
+    out[5] = (double)c->dsteps[slot];
+    return reduce_partials(c, h, out);
 }
 
 int lbm_synchronize(lbm_handle c) {

@@ -91,3 +91,29 @@ def test_foreign_blobs_are_refused():
         with pytest.raises(lbm.LbmError, match="not finite"):
             a.set_state(bytes(nan))
         assert np.array_equal(a.get_f(), f)  # refused blobs change nothing
+
+
+def test_pipelined_diagnostics_match_the_blocking_call():
+    nx, ny = 128, 64
+    p = lbm.default_params(precision=lbm.LBM_MIXED)
+    with lbm.Simulation(nx, ny, p) as a, lbm.Simulation(nx, ny, p) as b:
+        a.init(*_fields(nx, ny))
+        b.init(*_fields(nx, ny))
+        ref = []
+        for _ in range(4):
+            a.step(3)
+            ref.append(a.diagnostics())
+        got = []
+        for k in range(4):
+            b.step(3)
+            b.diagnostics_begin()
+            if k > 0:
+                got.append(b.diagnostics_end())  # the previous step's request, while this one runs
+        got.append(b.diagnostics_end())
+        assert got == ref
+        with pytest.raises(lbm.LbmError, match="pending"):
+            b.diagnostics_end()
+        b.diagnostics_begin()
+        b.diagnostics_begin()
+        with pytest.raises(lbm.LbmError, match="two requests"):
+            b.diagnostics_begin()
