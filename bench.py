@@ -59,8 +59,8 @@ def peaks():
 # the device code of the passes (kernels, FFT engine, shared layouts and launch limits); the
 # host orchestration (lbm_api.cu, lbm_noalloc.cu) is not part of it, and the launch shapes a
 # profile was taken with are checked separately
-DEVICE_SOURCES = ("fft_reg.cuh", "kernels_col.cu", "kernels_misc.cu", "kernels_row.cu", "kernels_sf.cu",
-                  "lbm_internal.cuh")
+DEVICE_SOURCES = ("fft_reg.cuh", "kernels_batch.cu", "kernels_col.cu", "kernels_misc.cu", "kernels_row.cu",
+                  "kernels_sf.cu", "lbm_internal.cuh", "pass_bodies.cuh", "tma.cuh")
 
 
 def source_digest():
