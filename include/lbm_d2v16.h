@@ -12,8 +12,9 @@
  *
  * Layouts. A scalar field is row-major [ny][nx] (x fastest), float64. The 16 distributions
  * are [16][ny][nx]. Velocity i (0-based) is: 0..3 -> (1,0),(0,1),(-1,0),(0,-1);
- * 4..7 -> 6x the same; 8..11 -> (s,s),(-s,s),(-s,-s),(s,-s) with s = sqrt2;
- * 12..15 -> the same with s = 3/sqrt2. eta_i = eta0 on 0..3 and 0 elsewhere (Sec. 2.1).
+ * 4..7 -> 6x the same; 8..11 -> (s,s),(-s,s),(-s,-s),(s,-s) with s = 1 (speed sqrt2);
+ * 12..15 -> the same with s = 1.5 (speed 3/sqrt2): the Kataoka-Tsutahara speeds 1, 6, sqrt2,
+ * 3/sqrt2. eta_i = eta0 on 0..3 and 0 elsewhere (Sec. 2.1).
  *
  * Errors. Every int-returning call returns LBM_OK (0) or a negative LBM_ERR_* code;
  * lbm_strerror() gives a message, lbm_last_error() a detailed one for the calling thread.

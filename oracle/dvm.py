@@ -2,10 +2,15 @@
 its discrete equilibrium f_i^eq.
 
 Readings (the paper cites the DVM but does not print it):
-* Velocities (not printed): i = 1..4 are (+-1, 0) and (0, +-1); i = 5..8 are (+-6, 0)
-  and (0, +-6); i = 9..12 are (+-sqrt2, +-sqrt2); i = 13..16 are (+-3/sqrt2, +-3/sqrt2).
-  Within each group the four vectors go counter-clockwise starting from the +x axis
-  (groups 1-2) or from the first quadrant (groups 3-4).
+* Velocities (not printed): the four speeds of Kataoka and Tsutahara's D2V16 set, 1, 6, sqrt2
+  and 3/sqrt2, the first two along the axes and the last two along the diagonals: i = 1..4 are
+  (+-1, 0) and (0, +-1); i = 5..8 are (+-6, 0) and (0, +-6); i = 9..12 are (+-1, +-1) (speed
+  sqrt2); i = 13..16 are (+-1.5, +-1.5) (speed 3/sqrt2). Within each group the four vectors go
+  counter-clockwise starting from the +x axis (groups 1-2) or from the first quadrant
+  (groups 3-4). (Reading the diagonal speeds as component values instead, i.e. speeds 2 and 3,
+  also gives an invertible moment system, but the droplet runs of Sec. 3.3 then diverge within
+  a few hundred steps, while the paper runs them for long times; with these speeds they stay
+  bounded.)
 * eta_i = eta0 = 2.5 on i = 1..4 and 0 on i = 5..16 (Sec. 2.1).
 * The moment definition of the energy in Sec. 2.1 lacks the factor rho; it is read as
   rho (b T + u^2) = sum f_i (v_i^2 + eta_i^2).
@@ -17,8 +22,6 @@ Readings (the paper cites the DVM but does not print it):
 """
 import numpy as np
 
-S2 = np.sqrt(2.0)
-
 
 class D2V16:
     """Velocity set and extra-degree-of-freedom parameters (Sec. 2.1)."""
@@ -27,7 +30,7 @@ class D2V16:
         v = []
         for c in (1.0, 6.0):
             v += [(c, 0.0), (0.0, c), (-c, 0.0), (0.0, -c)]
-        for c in (S2, 3.0 / S2):
+        for c in (1.0, 1.5):  # diagonal speeds sqrt2 and 3/sqrt2
             v += [(c, c), (-c, c), (-c, -c), (c, -c)]
         self.v = np.array(v, dtype=np.float64)          # (16, 2)
         self.vx = self.v[:, 0].copy()

@@ -59,9 +59,9 @@ __device__ __forceinline__ void batch_update(const UpdateArgs<R> &u, const Updat
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks)
-    batch_step_kernel(const __grid_constant__ BatchArgs<R> a) {
+// TPB threads per CTA (512 or 256), at least MINB CTAs per SM (the register budget)
+template <typename R, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) batch_step_kernel(const __grid_constant__ BatchArgs<R> a) {
     __shared__ int s_item, s_ok;
     const int total = a.seg[kBatchPasses * a.ngroups];
     int *queue = a.ctrl, *abort_flag = a.ctrl + 1, *done = a.ctrl + 2;
@@ -113,21 +113,36 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
     }
 }
 
-template <typename R> cudaError_t launch_batch_step(const BatchArgs<R> &a, size_t smem, int grid, cudaStream_t s) {
-    cudaError_t e = allow_smem(batch_step_kernel<R>);
+template <typename R, int TPB, int MINB> cudaError_t launch_batch_tpb(const BatchArgs<R> &a, size_t smem, int grid,
+                                                                       cudaStream_t s) {
+    cudaError_t e = allow_smem(batch_step_kernel<R, TPB, MINB>);
     if (e != cudaSuccess) return e;
-    batch_step_kernel<R><<<grid, PassThreads<R>::value, smem, s>>>(a);
+    batch_step_kernel<R, TPB, MINB><<<grid, TPB, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename R> cudaError_t batch_step_ctas_per_sm(size_t smem, int *n) {
-    *n = 0;
-    cudaError_t e = allow_smem(batch_step_kernel<R>);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, batch_step_kernel<R>, PassThreads<R>::value, smem);
+template <typename R> cudaError_t launch_batch_step(const BatchArgs<R> &a, size_t smem, int grid, int tpb,
+                                                   cudaStream_t s) {
+    if (tpb == 256) return launch_batch_tpb<R, 256, 3>(a, smem, grid, s);
+    if (tpb == 512) return launch_batch_tpb<R, 512, 2>(a, smem, grid, s);
+    return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_batch_step<float>(const BatchArgs<float> &, size_t, int, cudaStream_t);
-template cudaError_t batch_step_ctas_per_sm<float>(size_t, int *);
+template <typename R> cudaError_t batch_step_ctas_per_sm(size_t smem, int tpb, int *n) {
+    *n = 0;
+    cudaError_t e;
+    if (tpb == 256) {
+        if ((e = allow_smem(batch_step_kernel<R, 256, 3>)) != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, batch_step_kernel<R, 256, 3>, 256, smem);
+    }
+    if (tpb == 512) {
+        if ((e = allow_smem(batch_step_kernel<R, 512, 2>)) != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, batch_step_kernel<R, 512, 2>, 512, smem);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_batch_step<float>(const BatchArgs<float> &, size_t, int, int, cudaStream_t);
+template cudaError_t batch_step_ctas_per_sm<float>(size_t, int, int *);
 
 }  // namespace lbm

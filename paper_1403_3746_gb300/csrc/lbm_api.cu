@@ -167,6 +167,7 @@ struct lbm_batch_ctx {
     size_t bctrl_ints = 0;                       // the error word at bctrl[bctrl_ints]
     long long wait_cycles = 1LL << 31;
     int withhold = 0;
+    int ptpb = 512;                              // threads per CTA of the persistent kernel (256 or 512)
 };
 
 namespace {
@@ -1557,6 +1558,85 @@ void lbm_batch_destroy(lbm_batch b) {
 
 int lbm_batch_count(lbm_batch b) { return b ? (int)b->where.size() : 0; }
 
+static int build_batch_persistent_graph(lbm_batch b);
+static int check_batch_error(lbm_batch b);
+
+// The persistent form's CTA size (256 or 512 threads), by timing whole steps of each: the
+// distributions and the macroscopic block of every group (all a step reads from the one
+// before) are saved to a temporary device buffer first and put back afterwards, so the state
+// and every later result are unchanged.
+static int autotune_persistent(lbm_batch b) {
+    std::vector<size_t> fb, mb;
+    size_t total = 0;
+    for (lbm_ctx *c : b->groups) {
+        fb.push_back((size_t)c->n * c->nb * NF_F * c->fsize);
+        mb.push_back((size_t)c->n * c->nb * NF_M * c->fsize);
+        total += fb.back() + mb.back();
+    }
+    char *save = nullptr;
+    if (cudaMalloc(&save, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ERR_NOMEM, "batch autotune: no device memory to save the states");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LBM_OK;
+    auto copy_all = [&](bool to_save) {
+        size_t off = 0;
+        for (size_t g = 0; g < b->groups.size(); ++g) {
+            lbm_ctx *c = b->groups[g];
+            void *f = c->f0, *m = c->m;
+            cudaError_t e = to_save ? cudaMemcpyAsync(save + off, f, fb[g], cudaMemcpyDeviceToDevice, b->stream)
+                                    : cudaMemcpyAsync(f, save + off, fb[g], cudaMemcpyDeviceToDevice, b->stream);
+            off += fb[g];
+            if (e == cudaSuccess)
+                e = to_save ? cudaMemcpyAsync(save + off, m, mb[g], cudaMemcpyDeviceToDevice, b->stream)
+                            : cudaMemcpyAsync(m, save + off, mb[g], cudaMemcpyDeviceToDevice, b->stream);
+            off += mb[g];
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    const int tpb0 = b->ptpb;
+    int best = tpb0;
+    float bt = 1e30f;
+    if (copy_all(true) != cudaSuccess) rc = fail(LBM_ERR_CUDA, "batch autotune: saving the states failed");
+    if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = fail(LBM_ERR_CUDA, "batch autotune: cudaEventCreate failed");
+    for (int tpb : {512, 256}) {
+        if (rc) break;
+        b->ptpb = tpb;
+        if (b->pgraph) {
+            cudaGraphExecDestroy(b->pgraph);
+            b->pgraph = nullptr;
+        }
+        if ((rc = build_batch_persistent_graph(b))) break;
+        float t = 0;
+        cudaError_t e = cudaGraphLaunch(b->pgraph, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaGraphLaunch(b->pgraph, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e != cudaSuccess) {
+            rc = fail(LBM_ERR_CUDA, "batch autotune: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (t < bt) bt = t, best = tpb;
+    }
+    b->ptpb = rc ? tpb0 : best;
+    if (b->pgraph) {
+        cudaGraphExecDestroy(b->pgraph);
+        b->pgraph = nullptr;
+    }
+    if (copy_all(false) != cudaSuccess && rc == LBM_OK) rc = fail(LBM_ERR_CUDA, "batch autotune: restoring the states failed");
+    cudaStreamSynchronize(b->stream);
+    if (rc == LBM_OK) rc = check_batch_error(b);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    return rc;
+}
+
 int lbm_batch_autotune(lbm_batch b) {
     if (!b) return fail(LBM_ERR_ARG, "NULL batch");
     CU_TRY(cudaStreamSynchronize(b->stream));
@@ -1569,6 +1649,7 @@ int lbm_batch_autotune(lbm_batch b) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
+    if (b->form == LBM_BATCH_PERSISTENT) return autotune_persistent(b);
     return LBM_OK;
 }
 
@@ -1637,12 +1718,14 @@ static bool batch_persistent_ok(lbm_batch b) {
     return true;
 }
 
-// Work items and tile shapes of the persistent kernel (512-thread CTAs): column tiles of W =
-// min(nx, 1024 / G) columns (W/2 lines of G threads fill the CTA), macro and update row blocks
-// as large as 512 threads and 100 KB of shared memory allow.
+// Work items and tile shapes of the persistent kernel (CTAs of T = 512 or 256 threads): column
+// tiles of W = min(nx, 2T / G) columns (W/2 lines of G threads fill the CTA), macro and update
+// row blocks as large as T threads and the shared memory of two (T = 512) or three (T = 256)
+// CTAs per SM allow.
 static int batch_args(lbm_batch b, BatchArgs<float> &A, size_t &smem) {
-    constexpr int T = 512;
-    constexpr size_t es = 4, cap = 100 * 1024;
+    const int T = b->ptpb;
+    constexpr size_t es = 4;
+    const size_t cap = T == 512 ? 100 * 1024 : 72 * 1024;
     A.ngroups = (int)b->groups.size();
     smem = 0;
     int inst = 0;
@@ -1656,7 +1739,7 @@ static int batch_args(lbm_batch b, BatchArgs<float> &A, size_t &smem) {
                3 * (size_t)(2 * nrm) * line_smem(c->lx) * 2 * es + (size_t)(2 * nrm) * c->nx * es <= cap)
             nrm *= 2;
         int nru = 1;
-        while (2 * nru <= c->ny && 2 * nru * c->nx <= 4096 && upd_smem(2 * nru, c->lx, es, 1) <= cap) nru *= 2;
+        while (2 * nru <= c->ny && 2 * nru * c->nx <= 8 * T && upd_smem(2 * nru, c->lx, es, 1) <= cap) nru *= 2;
         int nj = 0;
         for (int st = 0; st < 2; ++st) {
             G.col[st] = col_args<float>(c, c->nb, W);
@@ -1718,7 +1801,7 @@ static int build_batch_persistent_graph(lbm_batch b) {
     CU_TRY(cudaGetDevice(&dev));
     CU_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int per_sm = 0;
-    const cudaError_t eo = batch_step_ctas_per_sm<float>(smem, &per_sm);
+    const cudaError_t eo = batch_step_ctas_per_sm<float>(smem, b->ptpb, &per_sm);
     if (eo != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return fail(LBM_ERR_UNSUPPORTED, "persistent batch: no CTA fits an SM (%zu B of shared memory; %s)", smem,
@@ -1727,7 +1810,7 @@ static int build_batch_persistent_graph(lbm_batch b) {
     if (!b->cap) CU_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     CU_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
     cudaError_t e = cudaMemsetAsync(b->bctrl, 0, b->bctrl_ints * sizeof(int), b->cap);  // not the error word
-    if (e == cudaSuccess) e = launch_batch_step<float>(*A, smem, per_sm * sms, b->cap);
+    if (e == cudaSuccess) e = launch_batch_step<float>(*A, smem, per_sm * sms, b->ptpb, b->cap);
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
     if (e != cudaSuccess || ee != cudaSuccess) {

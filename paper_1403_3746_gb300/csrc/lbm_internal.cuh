@@ -22,15 +22,14 @@
 
 namespace lbm {
 
-// D2V16 velocities (0-based), Sec. 2.1 (values: see the header comment of lbm_d2v16.h).
-#define LBM_SQ2 1.4142135623730950488016887
-#define LBM_D3S2 2.1213203435596425732025331  // 3/sqrt(2)
+// D2V16 velocities (0-based), Sec. 2.1 (values: see the header comment of lbm_d2v16.h): the
+// Kataoka-Tsutahara speeds 1 and 6 along the axes, sqrt2 and 3/sqrt2 along the diagonals.
 __host__ __device__ constexpr double vel_x(int i) {
     switch (i) {
         case 0: return 1.0;  case 2: return -1.0;
         case 4: return 6.0;  case 6: return -6.0;
-        case 8: return LBM_SQ2;  case 9: return -LBM_SQ2;  case 10: return -LBM_SQ2;  case 11: return LBM_SQ2;
-        case 12: return LBM_D3S2; case 13: return -LBM_D3S2; case 14: return -LBM_D3S2; case 15: return LBM_D3S2;
+        case 8: return 1.0;  case 9: return -1.0;  case 10: return -1.0;  case 11: return 1.0;
+        case 12: return 1.5; case 13: return -1.5; case 14: return -1.5; case 15: return 1.5;
         default: return 0.0;
     }
 }
@@ -38,14 +37,14 @@ __host__ __device__ constexpr double vel_y(int i) {
     switch (i) {
         case 1: return 1.0;  case 3: return -1.0;
         case 5: return 6.0;  case 7: return -6.0;
-        case 8: return LBM_SQ2;  case 9: return LBM_SQ2;  case 10: return -LBM_SQ2;  case 11: return -LBM_SQ2;
-        case 12: return LBM_D3S2; case 13: return LBM_D3S2; case 14: return -LBM_D3S2; case 15: return -LBM_D3S2;
+        case 8: return 1.0;  case 9: return 1.0;  case 10: return -1.0;  case 11: return -1.0;
+        case 12: return 1.5; case 13: return 1.5; case 14: return -1.5; case 15: return -1.5;
         default: return 0.0;
     }
 }
 // |v_i|^2 (without eta)
 __host__ __device__ constexpr double vel_sq(int i) {
-    return i < 4 ? 1.0 : (i < 8 ? 36.0 : (i < 12 ? 4.0 : 9.0));
+    return i < 4 ? 1.0 : (i < 8 ? 36.0 : (i < 12 ? 2.0 : 4.5));
 }
 // fields with v_x != 0, in the order of the 12 real rows of the update kernel's shared tile:
 // row k holds field XF(k); complex line p packs rows 2p (real part) and 2p+1 (imag part)
@@ -264,8 +263,10 @@ template <typename R> struct BatchArgs {
     long long wait_cycles;  // budget of one wait
     int withhold;           // fault-injection hook: item 0 never reports completion
 };
-template <typename R> cudaError_t launch_batch_step(const BatchArgs<R> &a, size_t smem, int grid, cudaStream_t s);
-template <typename R> cudaError_t batch_step_ctas_per_sm(size_t smem, int *n);
+// tpb: threads per CTA of the persistent kernel, 256 or 512
+template <typename R>
+cudaError_t launch_batch_step(const BatchArgs<R> &a, size_t smem, int grid, int tpb, cudaStream_t s);
+template <typename R> cudaError_t batch_step_ctas_per_sm(size_t smem, int tpb, int *n);
 
 struct InitArgs {
     const double *rho, *ux, *uy, *T;  // inputs, [ny][nx]

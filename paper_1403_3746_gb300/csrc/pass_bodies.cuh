@@ -237,9 +237,9 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
 // [128, 256), whose float32 spacing is 2^-16, for |f| < 64), the bit pattern of t minus that of
 // 192 is the integer h exactly (float32 bit patterns are linear in the value within a binade),
 // and l = f - (t - 192) is exact with |l| <= 2^-17. The integer parts are summed exactly in
-// 32-bit integers (velocity weights 1, 6 and psi 36, 4, 9 are integers; the sqrt2-type weights
-// are applied to the integer group sums as float pairs), the small parts in float32 (rounding
-// below 2^-36 of the sum), and the two are combined once.
+// 32-bit integers with the weights 2 v_i and 2 psi_i of velocities 4..15 (integers for this
+// velocity set), the small parts in float32 (rounding below 2^-36 of the sum), and the two are
+// combined once. psi of velocities 0..3 (1 + eta0^2, a parameter) enters as a float pair.
 // ---------------------------------------------------------------------------------------
 template <typename R> struct MomentSums;
 
@@ -267,18 +267,19 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
-// speed group of velocity i: 0 (|v| = 1, carries eta), 1 (6), 2 (sqrt2 diagonals), 3 (3/sqrt2)
+// speed group of velocity i: 0 (speed 1, carries eta), 1 (6), 2 (sqrt2 diagonals), 3 (3/sqrt2)
 __host__ __device__ constexpr int speed_group(int i) { return i >> 2; }
+// twice a velocity component and twice |v|^2, as integers (exact for this velocity set)
+__host__ __device__ constexpr int twice(double x) { return (int)(2.0 * x); }
+static_assert(2.0 * vel_x(12) == (double)twice(vel_x(12)) && 2.0 * vel_sq(12) == (double)twice(vel_sq(12)),
+              "the integer moment weights need 2 v and 2 |v|^2 integral");
 
 template <> struct MomentSums<float> {
     static constexpr float kMagic = 192.0f;  // 1.5 2^7: f + 192 in [128, 256) for |f| < 64
     static constexpr float kQ = 1.0f / 65536.0f;
-    // integer parts (offset bit patterns for the sums of the groups, plain for the differences)
-    unsigned sg[4] = {0u, 0u, 0u, 0u};  // per speed group: sum of bits(t) (offset 2 bits(192) per pair)
-    int xab = 0, yab = 0;               // x / y momentum of groups 0 and 1 (weights +-1, +-6)
-    int xc = 0, yc = 0, xd = 0, yd = 0; // signed unit-weight sums of groups 2 and 3
-    // small parts
-    float lr = 0.f, le = 0.f, lx = 0.f, ly = 0.f;
+    unsigned sA = 0u, sB = 0u, sC = 0u, sD = 0u;  // per speed group: sum of bits(t) (offset bits(192) per value)
+    int jx2 = 0, jy2 = 0;                // 2 v-weighted integer parts (pair differences: no offset)
+    float lr = 0.f, le = 0.f, lx = 0.f, ly = 0.f;  // small parts
     float psiA_hi = 0.f, psiA_lo = 0.f;  // psi of group 0 (1 + eta0^2) as a float pair
 
     static __device__ __forceinline__ unsigned bits(float x) { return __float_as_uint(x); }
@@ -289,59 +290,45 @@ template <> struct MomentSums<float> {
         constexpr int g = speed_group(I);
         const float ti = __fadd_rn(fi, kMagic), tk = __fadd_rn(fk, kMagic);
         const float li = __fsub_rn(fi, __fsub_rn(ti, kMagic)), lk = __fsub_rn(fk, __fsub_rn(tk, kMagic));
-        const unsigned bi = bits(ti), bk = bits(tk);
-        sg[g] += bi + bk;
+        const unsigned bi = bits(ti), bk = bits(tk), sp = bi + bk;
+        if constexpr (g == 0) sA += sp;
+        else if constexpr (g == 1) sB += sp;
+        else if constexpr (g == 2) sC += sp;
+        else sD += sp;
         const int d = (int)(bi - bk);
         const float ls = __fadd_rn(li, lk), ld = __fsub_rn(li, lk);
         lr = __fadd_rn(lr, ls);
         le = fmaf(psi_hi, ls, le);
-        if (g == 0) {
+        if constexpr (g == 0) {
             psiA_hi = psi_hi;
             psiA_lo = psi_lo;
         }
         if constexpr (vel_x(I) != 0.0) {
-            if constexpr (g < 2) xab += (vel_x(I) > 0 ? 1 : -1) * (g == 0 ? 1 : 6) * d;
-            else if constexpr (g == 2) xc += vel_x(I) > 0 ? d : -d;
-            else xd += vel_x(I) > 0 ? d : -d;
+            jx2 += twice(vel_x(I)) * d;
             lx = fmaf((float)vel_x(I), ld, lx);
         }
         if constexpr (vel_y(I) != 0.0) {
-            if constexpr (g < 2) yab += (vel_y(I) > 0 ? 1 : -1) * (g == 0 ? 1 : 6) * d;
-            else if constexpr (g == 2) yc += vel_y(I) > 0 ? d : -d;
-            else yd += vel_y(I) > 0 ? d : -d;
+            jy2 += twice(vel_y(I)) * d;
             ly = fmaf((float)vel_y(I), ld, ly);
         }
     }
 
-    // sum of the integer part a + sc sqrt2 + sd 3/sqrt2 (scaled by 2^-16) and the small part l
-    static __device__ __forceinline__ float momentum(int a, int sc, int sd, float l) {
-        constexpr float s2h = (float)LBM_SQ2, s2l = (float)(LBM_SQ2 - (double)(float)LBM_SQ2);
-        constexpr float d3h = (float)LBM_D3S2, d3l = (float)(LBM_D3S2 - (double)(float)LBM_D3S2);
-        const float fa = (float)a, fc = (float)sc, fd = (float)sd;  // exact: |values| < 2^24
-        const float pc = fc * s2h, ec = fmaf(fc, s2h, -pc);
-        const float pd = fd * d3h, ed = fmaf(fd, d3h, -pd);
-        float s1, t1, s2, t2;
-        two_sum(fa, pc, s1, t1);
-        two_sum(s1, pd, s2, t2);
-        const float corr = fmaf(fd, d3l, fmaf(fc, s2l, t1 + t2 + ec + ed));
-        return fmaf(s2, kQ, fmaf(corr, kQ, l));
-    }
-
     __device__ __forceinline__ void finish(float b, float &rho, float &ux, float &uy, float &T) const {
         const unsigned off = 4u * bits(kMagic);  // four values per group
-        const int SA = (int)(sg[0] - off), SB = (int)(sg[1] - off), SC = (int)(sg[2] - off), SD = (int)(sg[3] - off);
+        const int SA = (int)(sA - off), SB = (int)(sB - off), SC = (int)(sC - off), SD = (int)(sD - off);
         rho = fmaf((float)(SA + SB + SC + SD), kQ, lr);  // integer sum below 2^24: exact as float
-        // E: integer weights psi = 36, 4, 9 of groups 1-3, exact in int32, as an exact float pair
-        const int Ei = 36 * SB + 4 * SC + 9 * SD;
+        // E: 2 psi = 72, 4, 9 for groups 1..3, exact in int32, converted as an exact float pair
+        const int Ei = twice(vel_sq(4)) * SB + twice(vel_sq(8)) * SC + twice(vel_sq(12)) * SD;
         const float e1 = __int2float_rz(Ei);
-        const float e2 = (float)(Ei - __float2int_rz(e1));
+        const float e2v = (float)(Ei - __float2int_rz(e1));
         const float fa = (float)SA;
         const float pa = fa * psiA_hi, ea = fmaf(fa, psiA_hi, -pa);
         float s, t;
-        two_sum(e1, pa, s, t);
-        const float corr = fmaf(fa, psiA_lo, t + e2 + ea);
+        two_sum(0.5f * e1, pa, s, t);  // 0.5 e1: exact (a power-of-two scaling)
+        const float corr = fmaf(fa, psiA_lo, t + 0.5f * e2v + ea);
         const float E = fmaf(s, kQ, fmaf(corr, kQ, le));
-        const float jx = momentum(xab, xc, xd, lx), jy = momentum(yab, yc, yd, ly);
+        // j: 2 v-weighted integer sums below 2^24 (exact as floats), scaled by 2^-17
+        const float jx = fmaf((float)jx2, 0.5f * kQ, lx), jy = fmaf((float)jy2, 0.5f * kQ, ly);
         const float ir = __fdividef(1.0f, rho);
         ux = jx * ir;
         uy = jy * ir;

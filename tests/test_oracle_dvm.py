@@ -52,8 +52,11 @@ def test_moment_matrix_rows_match_velocity_functionals(dvm):
 
 
 def test_velocity_set_geometry(dvm):
+    # Kataoka-Tsutahara speeds 1, sqrt2, 3/sqrt2, 6: axes for 1 and 6, diagonals for the others
     speeds = np.sort(np.unique(np.round(np.hypot(dvm.vx, dvm.vy), 12)))
-    assert np.allclose(speeds, [1.0, 2.0, 3.0, 6.0])
+    assert np.allclose(speeds, [1.0, np.sqrt(2.0), 3.0 / np.sqrt(2.0), 6.0])
+    diag = np.abs(np.abs(dvm.vx) - np.abs(dvm.vy)) < 1e-15
+    assert list(diag) == [False] * 8 + [True] * 8
     assert np.allclose(dvm.v.sum(axis=0), 0.0)
     assert np.allclose(dvm.eta, [2.5] * 4 + [0.0] * 12)
 
