@@ -230,8 +230,9 @@ BATCH_WORKLOAD = ("96 independent spinodal quenches (32 each at 128^2, 256^2, 51
                   "T_k uniform in [0.80, 0.95]")
 
 
-def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream):
-    """The batched form: all instances advanced by one graph launch per step. The state
+def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream, form=None):
+    """The batched form: all instances advanced by one graph launch per step (form None: the
+    graph of per-pass kernels; LBM_BATCH_PERSISTENT: one persistent kernel per step). The state
     (about 2.9 GB in LBM_MIXED) is far larger than L2, so no flush is needed between steps."""
     p = lbm.default_params(precision=precision, **PARAMS)
     temps = synthetic.quench_temperatures(4, len(BATCH_SIZES))
@@ -239,7 +240,9 @@ def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream):
     with lbm.Batch([(n, n) for n in BATCH_SIZES], p, stream=stream.cuda_stream) as b:
         for k, n in enumerate(BATCH_SIZES):
             b.init(k, *synthetic.spinodal(n, n, 1.0, 0.01, float(temps[k]), seed=4000 + k))
-        b.autotune()  # launch shapes per size group, by measurement
+        if form is not None:
+            b.set_form(form)
+        b.autotune()  # launch shapes per size group (and the persistent kernel's CTA size), by measurement
         shapes = {f"{n}x{n}": list(b.geometry(BATCH_SIZES.index(n))) for n in sorted(set(BATCH_SIZES))}
         with torch.cuda.stream(stream):
             b.step(warmup)
@@ -249,10 +252,14 @@ def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream):
             b.step(steps)
             e1.record(stream)
             stream.synchronize()
+        b.synchronize()
         ms = e0.elapsed_time(e1)
         ok = all(abs(b.diagnostics(k)["mass"]) > 0 for k in (0, len(BATCH_SIZES) - 1))
-    return {"value": nodes * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "steps": steps,
-            "ms_per_step": ms / steps, "nodes": nodes, "finite": ok, "launch_shapes": shapes}
+    out = {"value": nodes * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "steps": steps,
+           "ms_per_step": ms / steps, "nodes": nodes, "finite": ok}
+    if form is None:
+        out["launch_shapes"] = shapes
+    return out
 
 
 LARGE_N = 4096
@@ -468,8 +475,12 @@ def main():
     if not args.no_extras:
         kb = max(5, args.steps // 10)
         extras["batched_form"] = {
-            "workload": BATCH_WORKLOAD, "launch": "one CUDA graph per step, size groups as parallel branches",
+            "workload": BATCH_WORKLOAD,
+            "launch": "mixed / fp64: one CUDA graph per step, size groups as parallel branches; mixed_persistent: "
+                      "one persistent kernel launch per step over a queue of (stage, pass, group, instance, tile)",
             "mixed": batch_path(lbm, torch, synthetic, lbm.LBM_MIXED, kb, 3, stream),
+            "mixed_persistent": batch_path(lbm, torch, synthetic, lbm.LBM_MIXED, kb, 3, stream,
+                                           lbm.LBM_BATCH_PERSISTENT),
             "fp64": batch_path(lbm, torch, synthetic, lbm.LBM_FP64, max(3, kb // 4), 3, stream)}
         if rank == 0:
             from paper_1403_3746_gb300 import accuracy
