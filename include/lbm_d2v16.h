@@ -76,13 +76,17 @@ typedef struct lbm_params {
     double T_iso;  /* temperature of LBM_FLAG_ISOTHERMAL (> 0 when the flag is set) */
     int keff_terms; /* terms of the series of Eq. (3), 1..8: 8 = 16th order (default), 4 = 8th order */
     int reserved;   /* 0 */
+    double filter_alpha; /* window of the solution: after every step, f_i <- the inverse transform of */
+    double filter_p;     /* W(m_x) W(m_y) times its spectrum, W(m) = exp(-filter_alpha (|m|/(N/2))^filter_p);
+                            filter_alpha = 0 (default): no filter */
 } lbm_params;
 
 typedef struct lbm_ctx *lbm_handle;
 
 /* Fills *p with the phase-separation set of Sec. 3.2 (tau = dt = 1e-4, dx = dy = 1/256,
  * K = 5e-6, H = 0, zeta = 0) with q = -0.004 and b = 2 (Sec. 3.1), eta0 = 2.5, no window
- * (win_alpha = 0, win_p = 36), FP64, no flags, T_iso = 0, keff_terms = 8. */
+ * (win_alpha = 0, win_p = 36), FP64, no flags, T_iso = 0, keff_terms = 8, no solution filter
+ * (filter_alpha = 0, filter_p = 36). */
 void lbm_default_params(lbm_params *p);
 
 /* Creates a simulation on the current CUDA device. nx, ny: powers of two, 2 <= n <= 4096

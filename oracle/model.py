@@ -34,7 +34,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from .dvm import D2V16, moment_matrix, feq, moments
-from .wfft import spectral_deriv
+from .wfft import spectral_deriv, window
 
 _MINV = {}
 
@@ -53,7 +53,8 @@ class Params:
     q = -0.004 and b = 2 from Sec. 3.1. `force`, `collide` and `advect` switch the
     three terms of Eq. (1) on or off (test hooks). `deriv` selects how the derivative
     operator of Eq. (3) is applied: "fft" (numpy's FFT of the field) or "dft" (explicit DFT
-    sums along each axis, the same operator with O(N) work per value)."""
+    sums along each axis, the same operator with O(N) work per value). `filter_alpha` > 0 ends
+    every step with the solution filter of window exponent (filter_alpha, filter_p)."""
     tau: float = 1e-4
     dt: float = 1e-4
     dx: float = 1.0 / 256.0
@@ -73,6 +74,8 @@ class Params:
     scheme: str = "rk2"
     T_iso: float = 0.0
     deriv: str = "fft"
+    filter_alpha: float = 0.0
+    filter_p: float = 36.0
 
     @staticmethod
     def phase_separation():
@@ -172,13 +175,25 @@ def rhs(dvm, f, p):
     return R
 
 
+def solution_filter(f, p):
+    """The window applied to the solution (a reading of the "windowed" FFT scheme, abstract and
+    Sec. 2.3): each f_i becomes the inverse transform of W(m_x) W(m_y) times its spectrum, with
+    the exponential window W of wfft.window (the Nyquist index included)."""
+    ny, nx = f.shape[1:]
+    W = window(ny, p.filter_alpha, p.filter_p)[:, None] * window(nx, p.filter_alpha, p.filter_p)[None, :]
+    return np.fft.ifft2(W[None] * np.fft.fft2(f, axes=(1, 2)), axes=(1, 2)).real
+
+
 def rk2_step(dvm, f, p):
     """Sec. 2.3: two-stage (midpoint) Runge-Kutta step of Eq. (1); the forward Euler step
-    f + dt R(f) when p.scheme == "euler"."""
+    f + dt R(f) when p.scheme == "euler". With p.filter_alpha > 0 the step ends with the
+    solution filter."""
     if p.scheme == "euler":
-        return f + p.dt * rhs(dvm, f, p)
-    fh = f + 0.5 * p.dt * rhs(dvm, f, p)
-    return f + p.dt * rhs(dvm, fh, p)
+        out = f + p.dt * rhs(dvm, f, p)
+    else:
+        fh = f + 0.5 * p.dt * rhs(dvm, f, p)
+        out = f + p.dt * rhs(dvm, fh, p)
+    return solution_filter(out, p) if p.filter_alpha > 0 else out
 
 
 def init_feq(dvm, rho, ux, uy, T, p):

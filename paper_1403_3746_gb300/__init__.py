@@ -47,7 +47,8 @@ class lbm_params(ctypes.Structure):
                 ("q", ctypes.c_double), ("zeta", ctypes.c_double), ("b", ctypes.c_double),
                 ("eta0", ctypes.c_double), ("win_alpha", ctypes.c_double), ("win_p", ctypes.c_double),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("T_iso", ctypes.c_double),
-                ("keff_terms", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("keff_terms", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("filter_alpha", ctypes.c_double), ("filter_p", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p

@@ -148,8 +148,10 @@ __global__ void field_out_kernel(const R *src, int ld, double *out, int nx, int 
     }
 }
 
-// Generic spectral x-derivative of up to 4 fields (paired into complex lines), `rows` rows
-// per CTA, G threads per line (fft_reg.cuh); row y of every field at + y * ld.
+// Generic spectral x-derivative (or, order 2, the real multiplier of table k2: a second
+// derivative or the solution filter) of up to 4 fields (paired into complex lines), `rows` rows
+// per CTA, G threads per line (fft_reg.cuh); row y of every field at + y * ld. A field may be
+// transformed in place (out = in): every thread reads its points before any is written back.
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(MaxThreads<R>::value) row_deriv_kernel(const __grid_constant__ RowDerivArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N>;
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) row_deriv_kernel(const _
     }
     CT *buf = sb + (size_t)slot * F::STRIDE;
     F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
-    F::multiply(v, t, 1, R(1), a.ax.k1, a.ax.k2);
+    F::multiply(v, t, a.order == 2 ? 2 : 1, R(1), a.ax.k1, a.ax.k2);
     F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) {

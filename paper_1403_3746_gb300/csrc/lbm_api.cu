@@ -125,6 +125,8 @@ struct lbm_ctx {
     float2 *tw32x = nullptr, *tw32y = nullptr;
     double *k1x = nullptr, *k2x = nullptr, *k1y = nullptr, *k2y = nullptr;
     float *k1x32 = nullptr, *k2x32 = nullptr, *k1y32 = nullptr, *k2y32 = nullptr;
+    double *kfx = nullptr, *kfy = nullptr;  // solution filter W(m) / N per axis (params filter_alpha > 0)
+    float *kfx32 = nullptr, *kfy32 = nullptr;
     double minv[256];
 
     Geometry geo;  // launch geometry
@@ -354,6 +356,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
             ra.nx = nx;
             ra.ny = rows;
             ra.rows = c->geo.rows_rowd;
+            ra.order = 1;
             ra.ax = axis<R>(c, true);
             LaunchTimer t(c, LBM_K_UPDATE);
             CU_TRY(launch_row_deriv<R>(ra, c->geo.rowd_smem, c->stream));
@@ -367,13 +370,67 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
     return LBM_OK;
 }
 
-int run_step_launches(lbm_ctx *c) {
-    if (c->p.flags & LBM_FLAG_EULER) return c->mixed ? run_stage<float>(c, 2) : run_stage<double>(c, 2);
-    for (int st = 0; st < 2; ++st) {
-        int rc = c->mixed ? run_stage<float>(c, st) : run_stage<double>(c, st);
-        if (rc) return rc;
+// The solution filter (params filter_alpha > 0): f_i <- the inverse transform of W(m_x) W(m_y)
+// times the spectrum of f_i for all 16 fields in place, as a row pass (four launches of four
+// fields) and a column pass (16 jobs), then the moments of the filtered f for the next step.
+template <typename R> Axis<R> filter_axis(const lbm_ctx *c, bool xdir);
+template <> Axis<double> filter_axis<double>(const lbm_ctx *c, bool xdir) {
+    return xdir ? Axis<double>{c->tw64x, c->k1x, c->kfx, c->lx} : Axis<double>{c->tw64y, c->k1y, c->kfy, c->ly};
+}
+template <> Axis<float> filter_axis<float>(const lbm_ctx *c, bool xdir) {
+    return xdir ? Axis<float>{c->tw32x, c->k1x32, c->kfx32, c->lx} : Axis<float>{c->tw32y, c->k1y32, c->kfy32, c->ly};
+}
+
+template <typename R> int run_filter(lbm_ctx *c) {
+    const int nx = c->nx, rows = c->nb * c->ny, ldf = NF_F * nx;
+    R *f = static_cast<R *>(c->f0);
+    // four fields (two lines per row) per launch where the threads allow it, else two
+    const int per = 2 * c->geo.rows_rowd * line_G(c->lx) <= max_threads(c->fsize) ? 4 : 2;
+    for (int k = 0; k < 16; k += per) {
+        RowDerivArgs<R> ra{};
+        for (int j = 0; j < per; ++j) {
+            ra.in[j] = f + (size_t)(k + j) * nx;
+            ra.out[j] = f + (size_t)(k + j) * nx;
+        }
+        ra.ld = ldf;
+        ra.nin = per;
+        ra.nx = nx;
+        ra.ny = rows;
+        ra.rows = c->geo.rows_rowd;
+        ra.order = 2;
+        ra.ax = filter_axis<R>(c, true);
+        LaunchTimer t(c, LBM_K_UPDATE);
+        CU_TRY(launch_row_deriv<R>(ra, (per / 2) * c->geo.rowd_smem, c->stream));
     }
+    ColArgs<R> a = col_args<R>(c, c->nb, c->geo.colW);
+    a.ay = filter_axis<R>(c, false);
+    for (int i = 0; i < 16; ++i) a.jobs[i] = ColJob<R>{f + (size_t)i * nx, f + (size_t)i * nx, ldf, ldf, 2, R(1)};
+    {
+        LaunchTimer t(c, LBM_K_COL);
+        CU_TRY(launch_col<R>(a, 16, c->geo.col_smem, c->stream));
+    }
+    MomArgs ma{};
+    ma.f = f;
+    ma.m = c->m;
+    ma.nx = nx;
+    ma.ny = rows;
+    ma.b = c->p.b;
+    ma.T_iso = (c->p.flags & LBM_FLAG_ISOTHERMAL) ? c->p.T_iso : 0.0;
+    for (int i = 0; i < 16; ++i) ma.psi[i] = vel_sq(i) + (i < 4 ? c->p.eta0 * c->p.eta0 : 0.0);
+    LaunchTimer t(c, LBM_K_UPDATE);
+    CU_TRY(launch_moments<R>(ma, c->stream));
     return LBM_OK;
+}
+
+int run_step_launches(lbm_ctx *c) {
+    int rc = LBM_OK;
+    if (c->p.flags & LBM_FLAG_EULER) {
+        rc = c->mixed ? run_stage<float>(c, 2) : run_stage<double>(c, 2);
+    } else {
+        for (int st = 0; st < 2 && rc == LBM_OK; ++st) rc = c->mixed ? run_stage<float>(c, st) : run_stage<double>(c, st);
+    }
+    if (rc == LBM_OK && c->p.filter_alpha > 0) rc = c->mixed ? run_filter<float>(c) : run_filter<double>(c);
+    return rc;
 }
 
 // Captures one step of the context (launches on `s`, then restores its stream) into a graph.
@@ -587,6 +644,8 @@ int check_params(const lbm_params *p) {
     if (p->tau <= 0 || p->dt <= 0 || p->dx <= 0 || p->dy <= 0 || p->b <= 0)
         return fail(LBM_ERR_ARG, "tau, dt, dx, dy and b must be positive");
     if (p->win_alpha < 0 || p->win_p <= 0) return fail(LBM_ERR_ARG, "need win_alpha >= 0 and win_p > 0");
+    if (!std::isfinite(p->filter_alpha) || !std::isfinite(p->filter_p) || p->filter_alpha < 0 || p->filter_p <= 0)
+        return fail(LBM_ERR_ARG, "need finite filter_alpha >= 0 and filter_p > 0");
     if (p->precision != LBM_FP64 && p->precision != LBM_MIXED)
         return fail(LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_MIXED");
     if (p->flags & ~(LBM_FLAG_NO_ADVECTION | LBM_FLAG_NO_COLLISION | LBM_FLAG_NO_FORCE | LBM_FLAG_EULER |
@@ -683,6 +742,10 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     parts.push_back({reinterpret_cast<void **>(&c->k2x32), (size_t)nx * 4});
     parts.push_back({reinterpret_cast<void **>(&c->k1y32), (size_t)ny * 4});
     parts.push_back({reinterpret_cast<void **>(&c->k2y32), (size_t)ny * 4});
+    parts.push_back({reinterpret_cast<void **>(&c->kfx), (size_t)nx * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->kfy), (size_t)ny * 8});
+    parts.push_back({reinterpret_cast<void **>(&c->kfx32), (size_t)nx * 4});
+    parts.push_back({reinterpret_cast<void **>(&c->kfy32), (size_t)ny * 4});
     for (auto &pp : parts) off += al(pp.second);
     if (cudaMalloc(&c->slab, off) != cudaSuccess) {
         cudaGetLastError();
@@ -716,6 +779,13 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
         if (e == cudaSuccess) e = cudaMemcpy(dk2, k2.data(), N * 8, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(fk1, k1f.data(), N * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(fk2, k2f.data(), N * 4, cudaMemcpyHostToDevice);
+        // the solution filter's table (unused while filter_alpha = 0)
+        std::vector<double> kf(N);
+        std::vector<float> kff(N);
+        filter_table(N, params->filter_alpha, params->filter_p, kf.data());
+        for (int pos = 0; pos < N; ++pos) kff[pos] = (float)kf[pos];
+        if (e == cudaSuccess) e = cudaMemcpy(ax == 0 ? c->kfx : c->kfy, kf.data(), N * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ax == 0 ? c->kfx32 : c->kfy32, kff.data(), N * 4, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -898,6 +968,8 @@ uint64_t hash_params(const lbm_params &p) {
     dbl(p.T_iso);
     i32(p.keff_terms);
     i32(p.reserved);
+    dbl(p.filter_alpha);
+    dbl(p.filter_p);
     return h;
 }
 
@@ -994,6 +1066,7 @@ template <typename R> int diag_launch(lbm_ctx *c, int k) {
     ra.nx = c->nx;
     ra.ny = c->ny;
     ra.rows = c->geo.rows_rowd;
+    ra.order = 1;
     ra.ax = axis<R>(c, true);
     CU_TRY(launch_row_deriv<R>(ra, c->geo.rowd_smem, c->stream));
     DiagArgs da{};
@@ -1144,6 +1217,8 @@ void lbm_default_params(lbm_params *p) {
     p->T_iso = 0.0;
     p->keff_terms = 8;
     p->reserved = 0;
+    p->filter_alpha = 0.0;
+    p->filter_p = 36.0;
 }
 
 const char *lbm_strerror(int code) {
@@ -1713,7 +1788,8 @@ static int build_batch_graph(lbm_batch b) {
 static bool batch_persistent_ok(lbm_batch b) {
     if (b->groups.empty() || (int)b->groups.size() > kBatchGroups) return false;
     for (lbm_ctx *c : b->groups)
-        if (!c->mixed || (c->p.flags & ~LBM_FLAG_ISOTHERMAL) || c->lx < 7 || c->lx > 10 || c->ly < 7 || c->ly > 10)
+        if (!c->mixed || (c->p.flags & ~LBM_FLAG_ISOTHERMAL) || c->p.filter_alpha > 0 || c->lx < 7 || c->lx > 10 ||
+            c->ly < 7 || c->ly > 10)
             return false;
     return true;
 }
@@ -1999,6 +2075,19 @@ void derivative_tables(int N, double d, double win_alpha, double win_p, double *
         const int at = G * (pos % E) + pos / E;
         k1[at] = ke / N;
         k2[at] = -ke * ke / N;
+    }
+}
+
+void filter_table(int N, double alpha, double p, double *kf) {
+    int l2 = 0;
+    while ((1 << l2) < N) ++l2;
+    const int first = l2 >= 4 ? 16 : N;
+    const int E = N < 16 ? N : 16, G = N / E;  // stored at G e + t for position E t + e
+    for (int pos = 0; pos < N; ++pos) {
+        const int k = freq_at(pos, N, first);
+        const int m = k < N / 2 ? k : k - N;
+        const double w = alpha > 0 ? std::exp(-alpha * std::pow(std::fabs((double)m) / (0.5 * N), p)) : 1.0;
+        kf[G * (pos % E) + pos / E] = w / N;
     }
 }
 

@@ -111,6 +111,9 @@ template <typename R, int LOG2N> struct MacroThreads {
 // transforms: k1[p] = W(m) k_eff(m) / N and k2[p] = -(W(m) k_eff(m))^2 / N for the DFT index m
 // held at position p (zero at the Nyquist index). Eq. (3) and the window W (lbm_api.cu).
 void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2, int terms = 8);
+// The solution filter W(m) / N of one axis in the same order (W(m) = exp(-alpha (|m|/(N/2))^p),
+// the Nyquist index included) (lbm_api.cu).
+void filter_table(int N, double alpha, double p, double *kf);
 
 // Launch geometry of the four passes for an nx x ny grid and an element size (lbm_api.cu):
 // column tile width and shared memory, rows per CTA and shared memory of the row kernels.
@@ -303,6 +306,7 @@ template <typename R> struct RowDerivArgs {
     int ld;  // row stride of every in / out field (elements)
     int nin;  // 1..4 inputs (paired two per complex line)
     int nx, ny, rows;
+    int order;  // 1: d_x (table k1); 2: the real multiplier of table k2 (a second derivative or a filter)
     Axis<R> ax;
 };
 

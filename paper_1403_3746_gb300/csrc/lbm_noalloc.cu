@@ -129,6 +129,7 @@ extern "C" int lbm_diagnostics_noalloc(int nx, int ny, double dx, double dy, dou
     ra.nx = nx;
     ra.ny = ny;
     ra.rows = geo.rows_rowd;
+    ra.order = 1;
     ra.ax = Axis<double>{twx, k1x, k2x, log2i(nx)};
     NA_TRY(launch_row_deriv<double>(ra, geo.rowd_smem, s));
 

@@ -116,3 +116,36 @@ def test_rectangular_droplet_protocol_against_oracle():
     ef, em = errors(fg, mg, fo, mo)
     print(f"droplet protocol mixed: f {ef:.2e}, moments {em}")
     assert ef <= 1e-4 and max(em[:3]) <= 1e-4
+
+
+@pytest.mark.parametrize("precision,tol", [(lbm.LBM_FP64, TOL64), (lbm.LBM_MIXED, 2e-6)])
+def test_solution_filter_against_oracle(precision, tol):
+    # the window applied to the solution after every step (filter_alpha = 36, filter_p = 36),
+    # on a slab (phase-separation set) and a droplet (droplet set of Sec. 3.3, T = 0.9)
+    rl, rv = oracle.coexistence(0.9)
+    cases = [(slab(), dict(PHASE)),
+             (synthetic.droplet(64, 64, 16, rl, rv, 0.9, width=2.0),
+              dict(tau=5e-4, dt=1e-4, dx=0.01, dy=0.01, K=1e-5, q=-0.05, b=2.0))]
+    for fields, kw in cases:
+        fg, mg, fo, mo = run_both(fields, 30, precision=precision, filter_alpha=36.0, filter_p=36.0, **kw)
+        ef, em = errors(fg, mg, fo, mo)
+        print(f"filter precision={precision}: f {ef:.2e}, moments {em}")
+        assert ef <= tol and max(em) <= tol
+
+
+def test_solution_filter_keeps_the_droplet_set_bounded():
+    # the droplet parameter set of Sec. 3.3 in the thermal mode (T = 0.9, R = 32 on 128^2)
+    # with the solution filter: bounded and mass-conserving through 3000 steps in both paths
+    rl, rv = oracle.coexistence(0.9)
+    fields = synthetic.droplet(128, 128, 32, rl, rv, 0.9, width=2.0)
+    kw = dict(tau=5e-4, dt=1e-4, dx=0.01, dy=0.01, K=1e-5, q=-0.05, b=2.0, filter_alpha=36.0, filter_p=36.0)
+    for precision in (lbm.LBM_FP64, lbm.LBM_MIXED):
+        with lbm.Simulation(128, 128, lbm.default_params(precision=precision, **kw)) as s:
+            s.init(*fields)
+            d0 = s.diagnostics()
+            s.step(3000)
+            d1 = s.diagnostics()
+            rho = s.moments()[0]
+        print(f"precision {precision}: umax {d1['umax']:.3e}, rho {rho.min():.4f}..{rho.max():.4f}")
+        assert d1["umax"] < 0.1 and abs(d1["mass"] / d0["mass"] - 1) < 1e-6
+        assert rv * 0.9 < rho.min() and rho.max() < rl * 1.1

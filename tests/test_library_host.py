@@ -100,7 +100,16 @@ def test_create_rejects_bad_variant_params(L, kw):
 def test_variant_defaults(L):
     p = lbm.default_params()
     assert p.keff_terms == 8 and p.T_iso == 0.0 and p.reserved == 0
-    assert ctypes.sizeof(lbm.lbm_params) == 12 * 8 + 2 * 4 + 8 + 2 * 4
+    assert p.filter_alpha == 0.0 and p.filter_p == 36.0
+    assert ctypes.sizeof(lbm.lbm_params) == 12 * 8 + 2 * 4 + 8 + 2 * 4 + 2 * 8
+
+
+@pytest.mark.parametrize("kw", [dict(filter_alpha=-1.0), dict(filter_p=0.0), dict(filter_alpha=float("nan"))])
+def test_create_rejects_bad_filter_params(L, kw):
+    p = lbm.default_params(**kw)
+    h = ctypes.c_void_p()
+    assert L.lbm_create(16, 16, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert not h.value
 
 
 def test_moments_out_arrays_are_checked():
@@ -185,7 +194,7 @@ def test_state_blob_size_and_params_hash(L):
     a, b = lbm.default_params(), lbm.default_params()
     assert lbm.params_hash(a) == lbm.params_hash(b) != 0
     for field, value in (("tau", 2e-4), ("K", 5.000001e-6), ("precision", lbm.LBM_MIXED), ("flags", 8),
-                         ("keff_terms", 4), ("win_alpha", 36.0)):
+                         ("keff_terms", 4), ("win_alpha", 36.0), ("filter_alpha", 36.0)):
         c = lbm.default_params(**{field: value})
         assert lbm.params_hash(c) != lbm.params_hash(a), field
     # FNV-1a over the field bytes, least significant first, written out here independently
@@ -193,7 +202,7 @@ def test_state_blob_size_and_params_hash(L):
     h = 1469598103934665603
     raw = struct.pack("<12d", a.tau, a.dt, a.dx, a.dy, a.K, a.H, a.q, a.zeta, a.b, a.eta0, a.win_alpha, a.win_p)
     raw += struct.pack("<ii", a.precision, a.flags) + struct.pack("<d", a.T_iso)
-    raw += struct.pack("<ii", a.keff_terms, a.reserved)
+    raw += struct.pack("<ii", a.keff_terms, a.reserved) + struct.pack("<dd", a.filter_alpha, a.filter_p)
     for byte in raw:
         h = ((h ^ byte) * 1099511628211) % (1 << 64)
     assert lbm.params_hash(a) == h

@@ -178,3 +178,27 @@ def test_keff_with_four_terms_is_eighth_order():
     ser = sympy.series(sympy.asin(x), x, 0, 9).removeO()
     mm = N * np.arcsin(phi) / np.pi
     assert keff(mm, N, 2.0, terms=4) == pytest.approx(float(ser.subs(x, phi)), rel=1e-14)
+
+
+def test_solution_filter_of_single_modes(dvm):
+    # the solution filter scales the 2D mode (m_x, m_y) of every field by W(m_x) W(m_y),
+    # W(m) = exp(-alpha (|m|/(N/2))^p), written out here from its definition; the Nyquist index
+    # is damped by exp(-alpha); a uniform field is untouched; the step ends with it
+    from oracle.model import Params, solution_filter, rk2_step, init_feq
+    nx, ny, alpha, p = 32, 16, 36.0, 8.0
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    P = Params(filter_alpha=alpha, filter_p=p)
+    for mx, my in ((3, 2), (11, 5), (16, 0), (0, 8)):
+        h = np.cos(2 * np.pi * (mx * x / nx + my * y / ny)) + 1.0
+        f = np.repeat(h[None], 16, axis=0)
+        w = np.exp(-alpha * (mx / (nx / 2)) ** p) * np.exp(-alpha * (my / (ny / 2)) ** p)
+        out = solution_filter(f, P)
+        ref = np.cos(2 * np.pi * (mx * x / nx + my * y / ny)) * w + 1.0
+        assert np.allclose(out, np.repeat(ref[None], 16, axis=0), rtol=0, atol=1e-13)
+    import oracle, synthetic
+    rl, rv = oracle.coexistence(0.9)
+    fields = synthetic.slab(32, 16, rl, rv, 0.9, half_width=8, noise=1e-3, seed=5)
+    f0 = init_feq(dvm, *fields, P)
+    P0 = Params()
+    assert np.allclose(rk2_step(dvm, f0, P), solution_filter(rk2_step(dvm, f0, P0), P), rtol=0, atol=1e-15)
