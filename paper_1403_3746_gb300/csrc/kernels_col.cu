@@ -128,10 +128,18 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         F::template forward<reg::SyncCta>(v, buf, t, c.ay.tw);
         F::multiply(v, t, jb.order, jb.c, c.ay.k1, c.ay.k2);
         F::template inverse<reg::SyncCta>(v, buf, t, c.ay.tw);
-        const size_t rso = (size_t)(jb.ld_out >> 1);
+        const size_t rso = (size_t)(jb.ld_out >> 1), rsi = (size_t)(jb.ld_in >> 1);
         CT *out = reinterpret_cast<CT *>(jb.out + (size_t)z_of(it) * c.ny * jb.ld_out + tile_of(it) * W + 2 * l);
+        const CT *inp = reinterpret_cast<const CT *>(jb.in + (size_t)z_of(it) * c.ny * jb.ld_in + tile_of(it) * W + 2 * l);
 #pragma unroll
-        for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rso] = v[e];
+        for (int e = 0; e < F::E; ++e) {
+            CT r = v[e];
+            if (jb.acc) {  // out = in + result (in place: this thread's own positions)
+                const CT o = __ldcg(inp + (size_t)(t + F::G * e) * rsi);
+                r = reg::mk<R>(o.x + r.x, o.y + r.y);
+            }
+            out[(size_t)(t + F::G * e) * rso] = r;
+        }
         reg::cta_barrier();  // every thread is done with this buffer
         if (threadIdx.x == 0 && it + 2 * (int)gridDim.x < a.items) {
             tma::fence_proxy_async_smem();

@@ -177,8 +177,13 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) row_deriv_kernel(const _
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const size_t g = row + t + G * e;
-        a.out[ka][g] = v[e].x;
-        if (kb < a.nin) a.out[kb][g] = v[e].y;
+        if (a.acc) {  // each position is read and written by this thread only, so in may alias out
+            a.out[ka][g] = a.in[ka][g] + v[e].x;
+            if (kb < a.nin) a.out[kb][g] = a.in[kb][g] + v[e].y;
+        } else {
+            a.out[ka][g] = v[e].x;
+            if (kb < a.nin) a.out[kb][g] = v[e].y;
+        }
     }
 }
 

@@ -371,8 +371,9 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
 }
 
 // The solution filter (params filter_alpha > 0): f_i <- the inverse transform of W(m_x) W(m_y)
-// times the spectrum of f_i for all 16 fields in place, as a row pass (four launches of four
-// fields) and a column pass (16 jobs), then the moments of the filtered f for the next step.
+// times the spectrum of f_i for all 16 fields in place, as a row pass (launches of four or two
+// fields) and a column pass (16 jobs), each adding the transform of the correction W - 1 to the
+// field, then the moments of the filtered f for the next step.
 template <typename R> Axis<R> filter_axis(const lbm_ctx *c, bool xdir);
 template <> Axis<double> filter_axis<double>(const lbm_ctx *c, bool xdir) {
     return xdir ? Axis<double>{c->tw64x, c->k1x, c->kfx, c->lx} : Axis<double>{c->tw64y, c->k1y, c->kfy, c->ly};
@@ -398,13 +399,14 @@ template <typename R> int run_filter(lbm_ctx *c) {
         ra.ny = rows;
         ra.rows = c->geo.rows_rowd;
         ra.order = 2;
+        ra.acc = 1;
         ra.ax = filter_axis<R>(c, true);
         LaunchTimer t(c, LBM_K_UPDATE);
         CU_TRY(launch_row_deriv<R>(ra, (per / 2) * c->geo.rowd_smem, c->stream));
     }
     ColArgs<R> a = col_args<R>(c, c->nb, c->geo.colW);
     a.ay = filter_axis<R>(c, false);
-    for (int i = 0; i < 16; ++i) a.jobs[i] = ColJob<R>{f + (size_t)i * nx, f + (size_t)i * nx, ldf, ldf, 2, R(1)};
+    for (int i = 0; i < 16; ++i) a.jobs[i] = ColJob<R>{f + (size_t)i * nx, f + (size_t)i * nx, ldf, ldf, 2, R(1), 1};
     {
         LaunchTimer t(c, LBM_K_COL);
         CU_TRY(launch_col<R>(a, 16, c->geo.col_smem, c->stream));
@@ -2087,7 +2089,7 @@ void filter_table(int N, double alpha, double p, double *kf) {
         const int k = freq_at(pos, N, first);
         const int m = k < N / 2 ? k : k - N;
         const double w = alpha > 0 ? std::exp(-alpha * std::pow(std::fabs((double)m) / (0.5 * N), p)) : 1.0;
-        kf[G * (pos % E) + pos / E] = w / N;
+        kf[G * (pos % E) + pos / E] = (w - 1.0) / N;
     }
 }
 

@@ -111,8 +111,10 @@ template <typename R, int LOG2N> struct MacroThreads {
 // transforms: k1[p] = W(m) k_eff(m) / N and k2[p] = -(W(m) k_eff(m))^2 / N for the DFT index m
 // held at position p (zero at the Nyquist index). Eq. (3) and the window W (lbm_api.cu).
 void derivative_tables(int N, double d, double win_alpha, double win_p, double *k1, double *k2, int terms = 8);
-// The solution filter W(m) / N of one axis in the same order (W(m) = exp(-alpha (|m|/(N/2))^p),
-// the Nyquist index included) (lbm_api.cu).
+// The correction of the solution filter, (W(m) - 1) / N, of one axis in the same order (W(m) =
+// exp(-alpha (|m|/(N/2))^p), the Nyquist index included): filtered = f + the inverse transform
+// of the correction times the spectrum, so the rounding of the transforms touches only the small
+// removed part and the mean (W(0) = 1) is kept exactly (lbm_api.cu).
 void filter_table(int N, double alpha, double p, double *kf);
 
 // Launch geometry of the four passes for an nx x ny grid and an element size (lbm_api.cu):
@@ -169,6 +171,7 @@ template <typename R> struct ColJob {
     int ld_in, ld_out;
     int order;
     R c;
+    int acc;  // 1: out = in + the transform's result (in place: the solution filter's correction)
 };
 #define LBM_MAX_COLJOBS 20
 template <typename R> struct ColArgs {
@@ -307,6 +310,7 @@ template <typename R> struct RowDerivArgs {
     int nin;  // 1..4 inputs (paired two per complex line)
     int nx, ny, rows;
     int order;  // 1: d_x (table k1); 2: the real multiplier of table k2 (a second derivative or a filter)
+    int acc;    // 1: out = in + the result (in place: the solution filter's correction)
     Axis<R> ax;
 };
 

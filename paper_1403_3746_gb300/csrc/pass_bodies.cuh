@@ -45,6 +45,14 @@ __device__ __forceinline__ void col_tile(const ColArgs<R> &a, int jobi, int z, i
     F::template forward<reg::SyncCta>(v, buf, t, a.ay.tw);
     F::multiply(v, t, job.order, job.c, a.ay.k1, a.ay.k2);
     F::template inverse<reg::SyncCta>(v, buf, t, a.ay.tw);
+    if (job.acc) {  // out = in + result; each position is read and written by this thread only
+#pragma unroll
+        for (int e = 0; e < F::E; ++e) {
+            const CT o = __ldcg(in + (size_t)(t + F::G * e) * rsi);
+            out[(size_t)(t + F::G * e) * rso] = reg::mk<R>(o.x + v[e].x, o.y + v[e].y);
+        }
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rso] = v[e];
 }
