@@ -469,7 +469,7 @@ def main():
                                    "with an event pair around every kernel",
                 "step_frac": ELEMS_PER_NODE_STEP * 4 * n / (total_ms * 1e-3 / args.steps) / 1e9 / hbm}
     launches = sum(c for _, c in kern.values())  # loop B; loop A's graphs hold the same kernels per step
-    e2e = e2e_path(lbm, torch, lbm.LBM_MIXED, max(50, args.steps // 4), fields) if rank == 0 else None
+    e2e = e2e_path(lbm, torch, lbm.LBM_MIXED, max(200, args.steps), fields) if rank == 0 else None
 
     extras = {}
     if not args.no_extras:
