@@ -178,6 +178,7 @@ def time_path(lbm, torch, precision, steps, warmup, fields, stream, autotune=Tru
     with lbm.Simulation(N_GRID, N_GRID, p, stream=stream.cuda_stream) as sim:
         sim.init(*fields)
         geometry = sim.autotune()[0] if autotune else sim.geometry()  # launch shapes, before any timed step
+        geometry = list(geometry) + list(sim.pass_kinds())  # + column, flux column kinds, update CTAs per row
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 sim.step(1)
@@ -526,6 +527,7 @@ def main():
                        "launch": "lbm_step: one CUDA graph per step (8 kernels)",
                        "launch_shapes": {"col_tile_width": geom[0], "macro_rows_per_cta": geom[1],
                                          "update_rows_per_cta": geom[2], "flux_tile_width": geom[3],
+                                         "col_kind": geom[4], "flux_kind": geom[5], "update_ctas_per_row": geom[6],
                                          "chosen_by": "defaults" if args.no_autotune else "lbm_autotune"},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "fp64_path": {"value": fp64_mlups, "unit": "MLUPS", "steps": k64, "launch_shapes": list(geom64),

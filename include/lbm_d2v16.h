@@ -208,13 +208,15 @@ size_t lbm_device_bytes(lbm_handle h);
  * update row passes; geometry[3]: width of the flux column-pass tiles. lbm_autotune times
  * every legal candidate of each (column tiles with at most 100 KB of line buffers; row CTAs
  * of at most 4096 nodes whose line buffers fit the 227 KB of shared memory a CTA can have)
- * on the handle's own buffers with the passes of a Runge-Kutta stage, keeps the fastest, and
- * reports the chosen shapes and the measured time of each pass with them (ms: column, macro,
- * update, flux; either pointer may be NULL). The state is unchanged (the moment fields the
+ * on the handle's own buffers by the time of a whole Runge-Kutta stage, each timed run after
+ * an L2 flush (the cold cache a step starts from), one pass's shape at a time, keeps the
+ * fastest, and reports the chosen shapes and the stage time with each pass's chosen shape (ms:
+ * column, macro, update, flux tuning; either pointer may be NULL). The state is unchanged (the moment fields the
  * update pass rewrites are saved and restored) and results do not depend on the shapes. If it
  * fails midway, the previous shapes and the saved moment fields are put back before it
- * returns the error. Needs an initialised state; allocates a temporary device buffer of 4
- * fields; synchronises the stream. */
+ * returns the error. Needs an initialised state; allocates temporary device buffers of 4
+ * fields and of twice the L2 size (the flush; without it the timings are taken warm);
+ * synchronises the stream. */
 int lbm_geometry(lbm_handle h, int geometry[4]);
 /* The default launch plan of an nx x ny grid in the given precision, computed on the host
  * (no device, no handle): what lbm_create will choose before any tuning, and what each pass
@@ -239,14 +241,17 @@ int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
  * than one CTA's threads split every line over a thread-block cluster of 2 or 4 CTAs that
  * exchange points through distributed shared memory); LBM_COL_TMA: a persistent grid whose CTAs
  * stage the next tile in shared memory with tiled bulk tensor copies (TMA) while they transform
- * the current one. kinds[2]: CTAs per row of the update pass, 1 or 2 (a cluster of two splits
- * each row's transforms and node loop; float32 rows of 2048 or more, one row per cluster).
- * lbm_autotune chooses them together with the tile widths and rows per CTA. lbm_set_pass_kinds
- * returns LBM_ERR_ARG for a choice the current shapes cannot take (TMA: rows of fewer than 16
- * bytes, cluster-split widths, staging buffers beyond a CTA's shared memory); where a launch
- * still cannot use TMA, the direct form runs. */
+ * the current one; LBM_COL_LOOKAHEAD: the direct form, each CTA first issuing bulk L2
+ * prefetches of the input rows of the CTA about one wave of resident CTAs after it, so that
+ * DRAM streams while the resident CTAs transform. kinds[2]: CTAs per row of the update pass, 1
+ * or 2 (a cluster of two splits each row's transforms and node loop; float32 rows of 2048 or
+ * more, one row per cluster). lbm_autotune chooses them together with the tile widths and rows
+ * per CTA. lbm_set_pass_kinds returns LBM_ERR_ARG for a choice the current shapes cannot take
+ * (TMA and lookahead: rows of fewer than 16 bytes or cluster-split widths; TMA: staging buffers
+ * beyond a CTA's shared memory); where a launch still cannot use TMA, the direct form runs. */
 #define LBM_COL_DIRECT 0
 #define LBM_COL_TMA 1
+#define LBM_COL_LOOKAHEAD 2
 int lbm_pass_kinds(lbm_handle h, int kinds[3]);
 int lbm_set_pass_kinds(lbm_handle h, const int kinds[3]);
 

@@ -25,6 +25,7 @@ LBM_FLAG_ISOTHERMAL = 16
 KERNELS = {"col": 0, "macro": 1, "flux": 2, "update": 3}
 LBM_COL_DIRECT = 0
 LBM_COL_TMA = 1
+LBM_COL_LOOKAHEAD = 2
 LBM_FAULT_NONE = 0
 LBM_FAULT_STARVE_COPIES = 1
 LBM_FAULT_WITHHOLD_COMPLETION = 2
@@ -348,8 +349,8 @@ class Simulation:
         _check(lib().lbm_set_geometry(self._h, ctypes.cast(g, _P)))
 
     def pass_kinds(self):
-        """(column pass kind, flux column pass kind, update CTAs per row): LBM_COL_DIRECT or
-        LBM_COL_TMA, LBM_COL_DIRECT or LBM_COL_TMA, 1 or 2."""
+        """(column pass kind, flux column pass kind, update CTAs per row): each column kind
+        LBM_COL_DIRECT, LBM_COL_TMA or LBM_COL_LOOKAHEAD; 1 or 2."""
         k = (ctypes.c_int * 3)()
         _check(lib().lbm_pass_kinds(self._h, ctypes.cast(k, _P)))
         return tuple(k)

@@ -16,34 +16,79 @@
 
 namespace lbm {
 
-template <typename R, int LOG2N>
+// L2 lookahead (a.pf > 0): CTAs start in linear block order, so the CTA a.pf blocks later
+// runs about one wave of resident CTAs after this one; its input rows are prefetched into L2
+// now, one bulk prefetch per row.
+template <typename R> __device__ __forceinline__ void col_lookahead(const ColArgs<R> &a) {
+    const long long per_z = (long long)gridDim.x * gridDim.y;
+    const long long b = blockIdx.x + (long long)gridDim.x * blockIdx.y + per_z * blockIdx.z + a.pf;
+    if (b >= per_z * gridDim.z) return;
+    const int z = (int)(b / per_z), rem = (int)(b % per_z), jn = rem / gridDim.x, tn = rem % gridDim.x;
+    const ColJob<R> &job = a.jobs[jn];
+    const unsigned bytes = (unsigned)(a.W * sizeof(R));
+    const R *in = job.in + (size_t)z * a.ny * job.ld_in + (size_t)tn * a.W;
+    for (int r = threadIdx.x; r < a.ny; r += blockDim.x) prefetch_l2(in + (size_t)r * job.ld_in, bytes);
+}
+
+// ACC: every job accumulates (out = in + result; the solution filter), instantiated apart.
+template <typename R, int LOG2N, bool ACC>
 __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks) col_deriv_kernel(const __grid_constant__ ColArgs<R> a) {
-    col_tile<R, LOG2N, 1>(a, blockIdx.y, blockIdx.z, blockIdx.x, 0u);
+    if (a.pf > 0) col_lookahead(a);
+    col_tile<R, LOG2N, 1, false, ACC>(a, blockIdx.y, blockIdx.z, blockIdx.x, 0u);
 }
 
 // Column tiles wider than one CTA's threads can transform: each line is split over the CS CTAs
 // of a cluster (consecutive blockIdx.x), which exchange points through distributed shared memory.
-template <typename R, int LOG2N, int CS>
+template <typename R, int LOG2N, int CS, bool ACC>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks)
     col_cluster_kernel(const __grid_constant__ ColArgs<R> a) {
-    col_tile<R, LOG2N, CS>(a, blockIdx.y, blockIdx.z, blockIdx.x / CS, reg::cluster_rank());
+    col_tile<R, LOG2N, CS, false, ACC>(a, blockIdx.y, blockIdx.z, blockIdx.x / CS, reg::cluster_rank());
+}
+
+// whether every job of a launch accumulates (1), none does (0), or they are mixed (-1: refused)
+template <typename R> static int jobs_acc(const ColArgs<R> &a, int njobs) {
+    for (int j = 1; j < njobs; ++j)
+        if ((a.jobs[j].acc != 0) != (a.jobs[0].acc != 0)) return -1;
+    return a.jobs[0].acc != 0 ? 1 : 0;
+}
+
+template <typename R, int LOG2N, int CS, bool ACC>
+static cudaError_t launch_col_cs_t(const ColArgs<R> &a, int njobs, size_t smem, cudaStream_t s) {
+    using F = reg::LineFFT<R, LOG2N, true, CS>;
+    dim3 grid((a.nx / a.W) * CS, njobs, a.nb > 0 ? a.nb : 1);
+    if constexpr (CS == 1) {
+        cudaError_t e = allow_smem(col_deriv_kernel<R, LOG2N, ACC>);
+        if (e != cudaSuccess) return e;
+        const int threads = (a.W / 2) * F::GL;
+        if (a.pf == 0) {
+            col_deriv_kernel<R, LOG2N, ACC><<<grid, threads, smem, s>>>(a);
+        } else {  // lookahead distance: the CTAs resident at once
+            int dev = 0, sms = 0, per_sm = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, col_deriv_kernel<R, LOG2N, ACC>, threads,
+                                                                    smem)) != cudaSuccess)
+                return e;
+            ColArgs<R> b = a;
+            b.pf = std::max(1, sms * per_sm);
+            col_deriv_kernel<R, LOG2N, ACC><<<grid, threads, smem, s>>>(b);
+        }
+    } else {
+        cudaError_t e = allow_smem(col_cluster_kernel<R, LOG2N, CS, ACC>);
+        if (e != cudaSuccess) return e;
+        col_cluster_kernel<R, LOG2N, CS, ACC><<<grid, (a.W / 2) * F::GL, smem, s>>>(a);
+    }
+    return cudaGetLastError();
 }
 
 template <typename R, int LOG2N, int CS> static cudaError_t launch_col_cs(const ColArgs<R> &a, int njobs, size_t smem,
                                                                            cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N, true, CS>;
     if (smem < (size_t)(a.W / 2) * F::STRIDE * sizeof(typename F::CT)) return cudaErrorInvalidValue;
-    dim3 grid((a.nx / a.W) * CS, njobs, a.nb > 0 ? a.nb : 1);
-    if constexpr (CS == 1) {
-        cudaError_t e = allow_smem(col_deriv_kernel<R, LOG2N>);
-        if (e != cudaSuccess) return e;
-        col_deriv_kernel<R, LOG2N><<<grid, (a.W / 2) * F::GL, smem, s>>>(a);
-    } else {
-        cudaError_t e = allow_smem(col_cluster_kernel<R, LOG2N, CS>);
-        if (e != cudaSuccess) return e;
-        col_cluster_kernel<R, LOG2N, CS><<<grid, (a.W / 2) * F::GL, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    const int acc = jobs_acc(a, njobs);
+    if (acc < 0) return cudaErrorInvalidValue;
+    return acc ? launch_col_cs_t<R, LOG2N, CS, true>(a, njobs, smem, s)
+               : launch_col_cs_t<R, LOG2N, CS, false>(a, njobs, smem, s);
 }
 
 template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R> &a, int njobs, size_t smem,
@@ -67,7 +112,7 @@ template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R
 // that ends item k it is handed back to the copy engine for item k + 2. Results are written
 // from registers, as in col_deriv_kernel, so every output value is bit for bit the same.
 // ---------------------------------------------------------------------------------------
-template <typename R, int LOG2N>
+template <typename R, int LOG2N, bool ACC>
 __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks)
     col_tma_kernel(const __grid_constant__ ColTmaArgs<R> a) {
     using F = reg::LineFFT<R, LOG2N, true>;
@@ -134,7 +179,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
 #pragma unroll
         for (int e = 0; e < F::E; ++e) {
             CT r = v[e];
-            if (jb.acc) {  // out = in + result (in place: this thread's own positions)
+            if constexpr (ACC) {  // out = in + result (in place: this thread's own positions)
                 const CT o = __ldcg(inp + (size_t)(t + F::G * e) * rsi);
                 r = reg::mk<R>(o.x + r.x, o.y + r.y);
             }
@@ -177,24 +222,31 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 }  // namespace
 
-template <typename R, int LOG2N>
-static cudaError_t launch_col_tma_n(const ColTmaArgs<R> &a, size_t smem, cudaStream_t s) {
+template <typename R, int LOG2N, bool ACC>
+static cudaError_t launch_col_tma_t(const ColTmaArgs<R> &a, size_t smem, cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N>;
     const int threads = (a.c.W / 2) * F::G;
     if (threads > PassThreads<R>::value || a.stage_bytes < (unsigned)((a.c.W / 2) * F::STRIDE * sizeof(typename F::CT)))
         return cudaErrorNotSupported;
-    cudaError_t e = allow_smem(col_tma_kernel<R, LOG2N>);
+    cudaError_t e = allow_smem(col_tma_kernel<R, LOG2N, ACC>);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, col_tma_kernel<R, LOG2N>, threads, smem)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, col_tma_kernel<R, LOG2N, ACC>, threads, smem)) !=
         cudaSuccess)
         return e;
     if (per_sm < 1) return cudaErrorNotSupported;
     const int grid = std::min(a.items, sms * per_sm);
-    col_tma_kernel<R, LOG2N><<<grid, threads, smem, s>>>(a);
+    col_tma_kernel<R, LOG2N, ACC><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename R, int LOG2N>
+static cudaError_t launch_col_tma_n(const ColTmaArgs<R> &a, int njobs, size_t smem, cudaStream_t s) {
+    const int acc = jobs_acc(a.c, njobs);
+    if (acc < 0) return cudaErrorInvalidValue;
+    return acc ? launch_col_tma_t<R, LOG2N, true>(a, smem, s) : launch_col_tma_t<R, LOG2N, false>(a, smem, s);
 }
 
 template <typename R>
@@ -230,7 +282,7 @@ cudaError_t launch_col_tma(const ColArgs<R> &c, int njobs, int *err, long long w
     }
     switch (c.ay.log2n) {
 #define LBM_CASE(L2) \
-    case L2: return launch_col_tma_n<R, L2>(a, smem, s);
+    case L2: return launch_col_tma_n<R, L2>(a, njobs, smem, s);
         LBM_FOR_LOG2N(LBM_CASE)
 #undef LBM_CASE
         default: return cudaErrorInvalidValue;

@@ -227,11 +227,16 @@ enum { PASS_COL = 1, PASS_MACRO = 2, PASS_FLUX = 4, PASS_UPDATE = 8, PASS_ALL = 
 // A column pass in the chosen form: the TMA-fed kernel, or direct loads (also where TMA cannot
 // serve the shape: rows narrower than 16 bytes, misaligned fields)
 template <typename R>
-cudaError_t launch_col_pass(const lbm_ctx *c, const ColArgs<R> &a, int nj, bool tma, size_t direct_smem) {
-    if (tma) {
+cudaError_t launch_col_pass(const lbm_ctx *c, const ColArgs<R> &a, int nj, int kind, size_t direct_smem) {
+    if (kind == LBM_COL_TMA) {
         const cudaError_t e = launch_col_tma<R>(a, nj, c->err, c->wait_cycles, c->starve, c->stream);
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
+    }
+    if (kind == LBM_COL_LOOKAHEAD && col_cluster(a.W, a.ay.log2n, sizeof(R)) == 1) {
+        ColArgs<R> b = a;
+        b.pf = 1;  // the launcher sets the distance
+        return launch_col<R>(b, nj, direct_smem, c->stream);
     }
     return launch_col<R>(a, nj, direct_smem, c->stream);
 }
@@ -329,7 +334,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
         const int nj = column_jobs<R>(c, stage, a);
         if (nj && (passes & PASS_COL)) {
             LaunchTimer t(c, LBM_K_COL);
-            CU_TRY(launch_col_pass<R>(c, a, nj, c->geo.col_tma, c->geo.col_smem));
+            CU_TRY(launch_col_pass<R>(c, a, nj, c->geo.col_kind, c->geo.col_smem));
         }
     }
     if (frc && (passes & PASS_MACRO)) {
@@ -341,7 +346,7 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
         ColArgs<R> a = col_args<R>(c, c->nb, c->geo.fluxW);
         flux_jobs<R>(c, a);
         LaunchTimer t(c, LBM_K_FLUX);
-        CU_TRY(launch_col_pass<R>(c, a, 4, c->geo.flux_tma, c->geo.flux_smem));
+        CU_TRY(launch_col_pass<R>(c, a, 4, c->geo.flux_kind, c->geo.flux_smem));
     }
     if ((passes & PASS_UPDATE) && adv && c->geo.upd_ax) {
         // d_x f_i of the 12 fields with v_x != 0 into Ax, two fields per complex line
@@ -478,6 +483,11 @@ bool col_tma_ok(const lbm_ctx *c, int W) {
     const size_t sm = col_tma_smem(c->nx, c->ny, W, c->fsize);
     return col_cluster(W, c->ly, c->fsize) == 1 && sm > 0 && sm <= kMaxCtaSmem && (c->nx * c->fsize) % 16 == 0;
 }
+// Whether the direct column kernel can prefetch tiles of W columns row by row: rows of at least
+// 16 bytes (the bulk prefetch granule), whole lines in one CTA.
+bool col_lookahead_ok(const lbm_ctx *c, int W) {
+    return col_cluster(W, c->ly, c->fsize) == 1 && W * c->fsize >= 16 && (c->nx * c->fsize) % 16 == 0;
+}
 // Whether a cluster of two CTAs may split the update pass's rows: float32 rows of 2048 or more.
 bool upd_split_ok(const lbm_ctx *c) { return c->fsize == 4 && c->lx >= 11 && !c->geo.upd_ax; }
 // Candidate rows per CTA of the update pass (6 line buffers per row within a CTA's shared memory).
@@ -501,81 +511,117 @@ std::vector<int> macro_candidates(const lbm_ctx *c) {
 
 template <typename R> int run_stage(lbm_ctx *c, int stage, int passes);
 
-// Times `passes` of Runge-Kutta stage 1 on the current buffers: one untimed launch, then the
-// mean of three.
-template <typename R> int time_passes(lbm_ctx *c, int passes, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
-    int rc = run_stage<R>(c, 0, passes);
+// Times one whole step as lbm_step runs it (the step's launches captured into a CUDA graph):
+// one untimed launch, then the mean of three, each after a write of `flush_bytes` to `flush`
+// (larger than L2, so every step starts from a cold cache, as in a long run of steps whose
+// working set exceeds L2; a working set that fits L2 would otherwise favour shapes that only
+// win when their inputs are already cached). The whole step is timed because a pass's shape
+// also changes what it leaves in L2 for the next pass. The steps advance the state, which the
+// caller saves and restores.
+int time_step(lbm_ctx *c, void *flush, size_t flush_bytes, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    int rc = build_step_graph(c);
     if (rc) return rc;
-    CU_TRY(cudaEventRecord(e0, c->stream));
-    for (int k = 0; k < 3 && rc == LBM_OK; ++k) rc = run_stage<R>(c, 0, passes);
-    if (rc) return rc;
-    CU_TRY(cudaEventRecord(e1, c->stream));
-    CU_TRY(cudaEventSynchronize(e1));
-    CU_TRY(cudaEventElapsedTime(ms, e0, e1));
-    *ms /= 3.0f;
+    CU_TRY(cudaGraphLaunch(c->graph, c->stream));
+    float sum = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        if (flush) CU_TRY(cudaMemsetAsync(flush, k, flush_bytes, c->stream));
+        CU_TRY(cudaEventRecord(e0, c->stream));
+        CU_TRY(cudaGraphLaunch(c->graph, c->stream));
+        CU_TRY(cudaEventRecord(e1, c->stream));
+        CU_TRY(cudaEventSynchronize(e1));
+        float t = 0.0f;
+        CU_TRY(cudaEventElapsedTime(&t, e0, e1));
+        sum += t;
+    }
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    *ms = sum / 3.0f;
     return LBM_OK;
 }
 
-// Chooses the column tile width and the rows per CTA of the macro and update passes by timing
-// every candidate on the context's own buffers. The passes of stage 1 read f^n and the
-// moments and write scratch (f^{n+1/2}, Ay, the derivative fields), except that the update
-// pass overwrites the moment fields: those are saved first and restored at the end, so the
-// state is unchanged. Per-row and per-column work does not depend on these shapes, so results
+// Chooses the column pass forms and tile widths, the macro pass's rows per CTA and the update
+// pass's split and rows per CTA by timing whole steps with every candidate, one pass's shape at
+// a time (the others at their current choice). The distributions f^n and the moment fields
+// are saved first and restored at the end, so the state is unchanged; the other buffers are
+// scratch of a step. Per-row and per-column work does not depend on these shapes, so results
 // stay bit for bit the same.
 template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
     const bool timing = c->timing;
     c->timing = false;
-    const size_t es = c->fsize, rows = (size_t)c->nb * c->ny;
-    void *save = nullptr;
+    const size_t es = c->fsize, rows = (size_t)c->nb * c->ny, fbytes = rows * NF_F * c->nx * es;
+    void *save = nullptr, *save_f = nullptr, *flush = nullptr;
+    size_t flush_bytes = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = LBM_OK;
     const Geometry geo0 = c->geo;
     bool saved = false;
+    auto restore = [&]() {
+        cudaError_t e = cudaMemcpy2DAsync(c->m, NF_M * c->nx * es, save, 4 * c->nx * es, 4 * c->nx * es, rows,
+                                          cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->f0, save_f, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+        return e;
+    };
     auto done = [&](int code) {
-        if (code != LBM_OK) {  // failed midway: the previous shapes and, if possible, the moments
+        if (code != LBM_OK) {  // failed midway: the previous shapes and, if possible, the state
             c->geo = geo0;
-            if (saved)
-                cudaMemcpy2DAsync(c->m, NF_M * c->nx * es, save, 4 * c->nx * es, 4 * c->nx * es, rows,
-                                  cudaMemcpyDeviceToDevice, c->stream);
+            if (saved) restore();
             cudaStreamSynchronize(c->stream);
         }
+        if (c->graph) {  // recaptured with the chosen shapes at the next step
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
         if (save) cudaFree(save);
+        if (save_f) cudaFree(save_f);
+        if (flush) cudaFree(flush);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         c->timing = timing;
         return code;
     };
-    if (cudaMalloc(&save, 4 * c->nx * es * rows) != cudaSuccess) {
+    if (cudaMalloc(&save, 4 * c->nx * es * rows) != cudaSuccess || cudaMalloc(&save_f, fbytes) != cudaSuccess) {
         cudaGetLastError();
-        return done(fail(LBM_ERR_NOMEM, "autotune: no scratch for the moment fields"));
+        return done(fail(LBM_ERR_NOMEM, "autotune: no scratch for the state"));
     }
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return done(fail(LBM_ERR_CUDA, "autotune: cudaEventCreate failed"));
+    {  // L2 flush buffer: twice the L2 size (without it, the timings are taken warm)
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
+            l2 > 0 && cudaMalloc(&flush, 2 * (size_t)l2) == cudaSuccess)
+            flush_bytes = 2 * (size_t)l2;
+        else
+            flush = nullptr, cudaGetLastError();
+    }
     // moment fields M_RHO..M_T: 4 nx contiguous elements per row of the macroscopic block
     if (cudaMemcpy2DAsync(save, 4 * c->nx * es, c->m, NF_M * c->nx * es, 4 * c->nx * es, rows,
-                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-        return done(fail(LBM_ERR_CUDA, "autotune: saving the moments failed"));
+                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(save_f, c->f0, fbytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return done(fail(LBM_ERR_CUDA, "autotune: saving the state failed"));
     saved = true;
-    if ((rc = run_stage<R>(c, 0, PASS_ALL))) return done(rc);
     const bool frc = !(c->p.flags & LBM_FLAG_NO_FORCE);
 
     float t = 0;
-    // column tile widths of the column pass and of the flux column pass
+    // column tile widths and forms of the column pass and of the flux column pass
     for (int pass : {PASS_COL, PASS_FLUX}) {
         if (pass == PASS_FLUX && !frc) continue;
         int &Wg = pass == PASS_COL ? c->geo.colW : c->geo.fluxW;
         size_t &Sg = pass == PASS_COL ? c->geo.col_smem : c->geo.flux_smem;
-        bool &Kg = pass == PASS_COL ? c->geo.col_tma : c->geo.flux_tma;
-        int bestW = Wg;
-        bool bestK = Kg;
+        int &Kg = pass == PASS_COL ? c->geo.col_kind : c->geo.flux_kind;
+        int bestW = Wg, bestK = Kg;
         float bt = 1e30f;
-        for (bool kind : {false, true}) {
+        for (int kind : {LBM_COL_DIRECT, LBM_COL_TMA, LBM_COL_LOOKAHEAD}) {
             for (int W : col_candidates(c)) {
-                if (kind && !col_tma_ok(c, W)) continue;
+                if (kind == LBM_COL_TMA && !col_tma_ok(c, W)) continue;
+                if (kind == LBM_COL_LOOKAHEAD && !col_lookahead_ok(c, W)) continue;
                 Wg = W;
                 Kg = kind;
                 Sg = col_smem(W, c->ly, es);
-                if ((rc = time_passes<R>(c, pass, e0, e1, &t))) return done(rc);
+                if ((rc = time_step(c, flush, flush_bytes, e0, e1, &t))) return done(rc);
                 if (t < bt) bt = t, bestW = W, bestK = kind;
             }
         }
@@ -592,7 +638,7 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
         for (int r : macro_candidates(c)) {
             c->geo.rows_macro = r;
             c->geo.macro_smem = 3 * r * SM + (size_t)r * c->nx * es;
-            if ((rc = time_passes<R>(c, PASS_MACRO, e0, e1, &t))) return done(rc);
+            if ((rc = time_step(c, flush, flush_bytes, e0, e1, &t))) return done(rc);
             if (t < bt) bt = t, bestr = r;
         }
         c->geo.rows_macro = bestr;
@@ -610,7 +656,7 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
                 c->geo.rows_upd = r;
                 c->geo.upd_cs = cs;
                 c->geo.upd_smem = upd_smem(r, c->lx, es, cs);
-                if ((rc = time_passes<R>(c, PASS_UPDATE, e0, e1, &t))) return done(rc);
+                if ((rc = time_step(c, flush, flush_bytes, e0, e1, &t))) return done(rc);
                 if (t < bt) bt = t, bestr = r, bestcs = cs;
             }
         }
@@ -620,15 +666,9 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
         best_ms[2] = bt < 1e30f ? bt : 0.0f;
     }
     saved = false;  // restored here, on success as on failure
-    if (cudaMemcpy2DAsync(c->m, NF_M * c->nx * es, save, 4 * c->nx * es, 4 * c->nx * es, rows,
-                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-        return done(fail(LBM_ERR_CUDA, "autotune: restoring the moments failed"));
+    if (restore() != cudaSuccess) return done(fail(LBM_ERR_CUDA, "autotune: restoring the state failed"));
     if (cudaStreamSynchronize(c->stream) != cudaSuccess)
         return done(fail(LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError())));
-    if (c->graph) {  // recaptured with the new shapes at the next step
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
     return done(LBM_OK);
 }
 
@@ -1386,8 +1426,8 @@ int lbm_synchronize(lbm_handle c) {
 
 int lbm_pass_kinds(lbm_handle c, int kinds[3]) {
     if (!c || !kinds) return fail(LBM_ERR_ARG, "NULL argument");
-    kinds[0] = c->geo.col_tma ? LBM_COL_TMA : LBM_COL_DIRECT;
-    kinds[1] = c->geo.flux_tma ? LBM_COL_TMA : LBM_COL_DIRECT;
+    kinds[0] = c->geo.col_kind;
+    kinds[1] = c->geo.flux_kind;
     kinds[2] = c->geo.upd_cs;
     return LBM_OK;
 }
@@ -1395,17 +1435,20 @@ int lbm_pass_kinds(lbm_handle c, int kinds[3]) {
 int lbm_set_pass_kinds(lbm_handle c, const int kinds[3]) {
     if (!c || !kinds) return fail(LBM_ERR_ARG, "NULL argument");
     for (int j = 0; j < 2; ++j) {
-        if (kinds[j] != LBM_COL_DIRECT && kinds[j] != LBM_COL_TMA) return fail(LBM_ERR_ARG, "unknown pass kind");
+        if (kinds[j] != LBM_COL_DIRECT && kinds[j] != LBM_COL_TMA && kinds[j] != LBM_COL_LOOKAHEAD)
+            return fail(LBM_ERR_ARG, "unknown pass kind");
         const int W = j == 0 ? c->geo.colW : c->geo.fluxW;
         if (kinds[j] == LBM_COL_TMA && !col_tma_ok(c, W))
             return fail(LBM_ERR_ARG, "the TMA column pass cannot take %d-column tiles of %d x %d", W, c->nx, c->ny);
+        if (kinds[j] == LBM_COL_LOOKAHEAD && !col_lookahead_ok(c, W))
+            return fail(LBM_ERR_ARG, "the lookahead column pass cannot take %d-column tiles of %d x %d", W, c->nx, c->ny);
     }
     if (kinds[2] != 1 && kinds[2] != 2) return fail(LBM_ERR_ARG, "update CTAs per row must be 1 or 2");
     if (kinds[2] == 2 && !(upd_split_ok(c) && c->geo.rows_upd == 1))
         return fail(LBM_ERR_ARG, "the update pass splits only float32 rows of 2048 or more, one row per cluster");
     CU_TRY(cudaStreamSynchronize(c->stream));
-    c->geo.col_tma = kinds[0] == LBM_COL_TMA;
-    c->geo.flux_tma = kinds[1] == LBM_COL_TMA;
+    c->geo.col_kind = kinds[0];
+    c->geo.flux_kind = kinds[1];
     c->geo.upd_cs = kinds[2];
     c->geo.upd_smem = upd_smem(c->geo.rows_upd, c->lx, c->fsize, c->geo.upd_cs);
     if (c->graph) {
@@ -1505,8 +1548,12 @@ int lbm_set_geometry(lbm_handle c, const int geometry[4]) {
     c->geo.col_smem = col_smem(geometry[0], c->ly, es);
     c->geo.fluxW = geometry[3];
     c->geo.flux_smem = col_smem(geometry[3], c->ly, es);
-    if (c->geo.col_tma && !col_tma_ok(c, c->geo.colW)) c->geo.col_tma = false;
-    if (c->geo.flux_tma && !col_tma_ok(c, c->geo.fluxW)) c->geo.flux_tma = false;
+    // a pass kind the new widths cannot take falls back to the direct form
+    auto kind_ok = [c](int kind, int W) {
+        return kind == LBM_COL_TMA ? col_tma_ok(c, W) : kind == LBM_COL_LOOKAHEAD ? col_lookahead_ok(c, W) : true;
+    };
+    if (!kind_ok(c->geo.col_kind, c->geo.colW)) c->geo.col_kind = LBM_COL_DIRECT;
+    if (!kind_ok(c->geo.flux_kind, c->geo.fluxW)) c->geo.flux_kind = LBM_COL_DIRECT;
     if (!c->geo.macro_serial) {
         c->geo.rows_macro = geometry[1];
         c->geo.macro_smem = 3 * geometry[1] * SMr + (size_t)geometry[1] * c->nx * es;

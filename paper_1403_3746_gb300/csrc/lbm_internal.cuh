@@ -132,8 +132,8 @@ struct Geometry {
     bool upd_ax = false;        // update pass takes d_x f from a separate row pass (Ax)
     bool macro_serial = false;  // macro pass transforms a row's two lines in turn
     int upd_cs = 1;             // update pass: CTAs per row (2: a cluster splits each row)
-    bool col_tma = false;       // column pass: TMA-fed persistent kernel (width colW) instead of direct loads
-    bool flux_tma = false;      // flux column pass: the same choice (width fluxW)
+    int col_kind = 0;           // column pass: LBM_COL_DIRECT, LBM_COL_TMA or LBM_COL_LOOKAHEAD (width colW)
+    int flux_kind = 0;          // flux column pass: the same choice (width fluxW)
 };
 void pass_geometry(int nx, int ny, size_t esize, Geometry *g);
 
@@ -179,6 +179,8 @@ template <typename R> struct ColArgs {
     int nx, ny, W, log2W;  // ny: rows of one instance
     int nb;                // instances stacked along y (grid.z); row k ny + y of a field = instance k, row y
     Axis<R> ay;
+    int pf;                // L2 lookahead of the direct kernel: CTA b first prefetches the input rows of
+                           // the tile of CTA b + pf (about one wave of resident CTAs later); 0: none
 };
 
 // TMA-fed column pass (kernels_col.cu): a persistent grid of CTAs walks the work items

@@ -12,8 +12,9 @@ namespace lbm {
 // in a cluster of CS that splits every line of the tile (fft_reg.cuh); tile = the tile index.
 // job: index into a.jobs; z: instance of a batch stacked along y (ny rows each). Threads beyond
 // the tile's lines (a CTA larger than the tile needs, as in the batch kernel) only keep the
-// barrier count.
-template <typename R, int LOG2N, int CS, bool EXTRA = false>
+// barrier count. ACC: every job of the launch accumulates (out = in + result, the solution
+// filter's correction), a separate instantiation so that the plain passes keep their registers.
+template <typename R, int LOG2N, int CS, bool EXTRA = false, bool ACC = false>
 __device__ __forceinline__ void col_tile(const ColArgs<R> &a, int jobi, int z, int tile, unsigned rank) {
     using F = reg::LineFFT<R, LOG2N, true, CS>;
     using CT = typename F::CT;
@@ -45,16 +46,16 @@ __device__ __forceinline__ void col_tile(const ColArgs<R> &a, int jobi, int z, i
     F::template forward<reg::SyncCta>(v, buf, t, a.ay.tw);
     F::multiply(v, t, job.order, job.c, a.ay.k1, a.ay.k2);
     F::template inverse<reg::SyncCta>(v, buf, t, a.ay.tw);
-    if (job.acc) {  // out = in + result; each position is read and written by this thread only
+    if constexpr (ACC) {  // out = in + result; each position is read and written by this thread only
 #pragma unroll
         for (int e = 0; e < F::E; ++e) {
             const CT o = __ldcg(in + (size_t)(t + F::G * e) * rsi);
             out[(size_t)(t + F::G * e) * rso] = reg::mk<R>(o.x + v[e].x, o.y + v[e].y);
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rso] = v[e];
+        for (int e = 0; e < F::E; ++e) out[(size_t)(t + F::G * e) * rso] = v[e];
+    }
 }
 
 
@@ -411,85 +412,21 @@ __host__ __device__ constexpr bool minv_zero(int i, int j) {
 __host__ __device__ constexpr int pair_rep(int p) { return 4 * (p >> 1) + (p & 1); }
 __host__ __device__ constexpr bool mom_odd(int j) { return (mom_px(j) + mom_py(j)) & 1; }
 
-// CS = 1: a CTA owns `rows` whole rows. CS > 1 (float32 rows of 2048 or more, one row per
-// cluster): the CS CTAs of a cluster split the row's line transforms (fft_reg.cuh) and CTA
-// `rank` runs the node loop over its x-range [rank N/CS, (rank + 1) N/CS), whose derivatives the
-// transforms leave in its own shared memory.
-template <typename R, int LOG2N, bool MOMENT_SPACE, int CS>
-__device__ __forceinline__ void update_rows(const UpdateArgs<R> &a, const UpdateConst<R> &kc, int blk, unsigned rank) {
-    using F = reg::LineFFT<R, LOG2N, true, CS>;
-    using CT = typename F::CT;
-    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE, NL = F::NL;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    CT *sb = reinterpret_cast<CT *>(smem_raw);
-    const int NR = a.rows, nodes = NR * NL;  // nodes of this CTA
-    const int y0 = blk * NR, x0 = (int)rank * NL;
+// One node (y, x) of the fused update pass: the body of its node loop. dl: the node's row of
+// d_x line buffers (line q at dl + q ls, natural order), xl: the node's index in them.
+template <typename R, int LOG2N, bool MOMENT_SPACE, bool AX_POSSIBLE>
+__device__ __forceinline__ void update_node(const UpdateArgs<R> &a, const UpdateConst<R> &kc, size_t y, int x,
+                                            const reg::C<R> *dl, size_t ls, int xl) {
+    using CT = reg::C<R>;
+    constexpr int NX = 1 << LOG2N;
+    const R b = a.b, K = a.K, tau_inv = a.tau_inv, h = a.h;
     const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
     const bool col = !(a.flags & LBM_FLAG_NO_COLLISION);
     const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
     const bool same_base = a.fbase == a.fs;
     const bool iso = a.flags & LBM_FLAG_ISOTHERMAL;
-    // d_x f_i from global memory instead of the row transforms: only float64 rows of 4096 need it
-    constexpr bool AX_POSSIBLE = sizeof(R) == 8 && LOG2N == 12 && CS == 1;
     const bool ax_mode = AX_POSSIBLE && a.Ax != nullptr;
-
-    // the node loop's other inputs start moving into L2 while the lines are transformed
-    if constexpr (CS == 1) {
-        if (threadIdx.x < NR) {
-            const size_t y = y0 + threadIdx.x;
-            prefetch_l2(a.fs + y * NF_F * NX, NF_F * NX * sizeof(R));
-            if (adv) prefetch_l2(a.Ay + y * NF_A * NX, NF_A * NX * sizeof(R));
-            if (!same_base) prefetch_l2(a.fbase + y * NF_F * NX, NF_F * NX * sizeof(R));
-            if (adv && ax_mode) prefetch_l2(a.Ax + y * NF_F * NX, NF_F * NX * sizeof(R));
-            prefetch_l2(a.m + y * NF_M * NX, (M_RY + 1) * NX * sizeof(R));
-            if (frc) prefetch_l2(a.m + (y * NF_M + M_DQX) * NX, (NF_M - M_DQX) * NX * sizeof(R));
-        }
-    } else {  // this CTA's x-range of every field of the row (NR = 1)
-        const int k = threadIdx.x;
-        const size_t y = y0, bytes = NL * sizeof(R);
-        if (k < NF_F) prefetch_l2(a.fs + (y * NF_F + k) * NX + x0, bytes);
-        else if (k < NF_F + NF_A) { if (adv) prefetch_l2(a.Ay + (y * NF_A + k - NF_F) * NX + x0, bytes); }
-        else if (k < 2 * NF_F + NF_A) { if (!same_base) prefetch_l2(a.fbase + (y * NF_F + k - NF_F - NF_A) * NX + x0, bytes); }
-        else if (k < 2 * NF_F + NF_A + NF_M) {
-            const int j = k - 2 * NF_F - NF_A;
-            if (j <= M_RY || (frc && j >= M_DQX)) prefetch_l2(a.m + (y * NF_M + j) * NX + x0, bytes);
-        }
-    }
-
-    if (adv && !ax_mode) {
-        // 6 lines per row (the 12 fields with v_x != 0, paired); LB lines per batch (LB divides
-        // 6 NR); threads past LB G/CS only take part in the barriers
-        const int LB = a.lines_per_batch;
-        const int ls = threadIdx.x / F::GL, t = (int)rank * F::GL + threadIdx.x % F::GL;
-        for (int b0 = 0; b0 < 6 * NR; b0 += LB) {
-            if (ls < LB) {
-                const int line = b0 + ls;
-                const int p = line / NR, r = line % NR;
-                CT *buf = sb + (size_t)line * SM;
-                const R *frow = a.fs + (size_t)(y0 + r) * NF_F * NX;
-                const R *fa = frow + xfield(2 * p) * NX, *fb = frow + xfield(2 * p + 1) * NX;
-                CT v[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(ldcg(fa + t + G * e), ldcg(fb + t + G * e));
-                F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
-                F::multiply(v, t, 1, a.cx[p], a.ax.k1, a.ax.k2);  // -h v_x folded in
-                F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
-                if constexpr (CS == 1) reg::cta_barrier();  // (a split inverse ends with a cluster barrier)
-                F::store_natural(v, buf, t);
-            } else {
-                F::template idle_forward<reg::SyncCta>();
-                F::template idle_inverse<reg::SyncCta>();
-                if constexpr (CS == 1) reg::cta_barrier();
-            }
-        }
-        if constexpr (CS == 1) __syncthreads();
-        else reg::cluster_barrier();  // every CTA's part of every line has landed
-    }
-
-    const R b = a.b, K = a.K, tau_inv = a.tau_inv, h = a.h;
-    for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
-        const int r = idx / NL, xl = idx % NL, x = x0 + xl;  // xl: index in this CTA's line buffers
-        const size_t y = y0 + r;
+    {
         const R *fn = a.fs + y * NF_F * NX + x;       // field i at fn[i * NX]
         const R *an = a.Ay + y * NF_A * NX + x;       // slot k at an[k * NX]
         R *mn = a.m + y * NF_M * NX + x;              // macro field k at mn[k * NX]
@@ -534,7 +471,7 @@ __device__ __forceinline__ void update_rows(const UpdateArgs<R> &a, const Update
                     if (ax_mode) {
                         dfo = -h * (R(vel_x(i)) * ldcg(a.Ax + (y * NF_F + i) * NX + x));
                     } else {
-                        const CT d = sb[(size_t)((xs >> 1) * NR + r) * SM + xl];
+                        const CT d = dl[(xs >> 1) * ls + xl];
                         dfo = (xs & 1) ? -d.y : d.x;
                     }
                 }
@@ -628,6 +565,86 @@ __device__ __forceinline__ void update_rows(const UpdateArgs<R> &a, const Update
         mn[M_UX * NX] = nux;
         mn[M_UY * NX] = nuy;
         mn[M_T * NX] = nT;
+    }
+}
+
+// CS = 1: a CTA owns `rows` whole rows. CS > 1 (float32 rows of 2048 or more, one row per
+// cluster): the CS CTAs of a cluster split the row's line transforms (fft_reg.cuh) and CTA
+// `rank` runs the node loop over its x-range [rank N/CS, (rank + 1) N/CS), whose derivatives the
+// transforms leave in its own shared memory.
+template <typename R, int LOG2N, bool MOMENT_SPACE, int CS>
+__device__ __forceinline__ void update_rows(const UpdateArgs<R> &a, const UpdateConst<R> &kc, int blk, unsigned rank) {
+    using F = reg::LineFFT<R, LOG2N, true, CS>;
+    using CT = typename F::CT;
+    constexpr int NX = F::N, G = F::G, E = F::E, SM = F::STRIDE, NL = F::NL;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    CT *sb = reinterpret_cast<CT *>(smem_raw);
+    const int NR = a.rows, nodes = NR * NL;  // nodes of this CTA
+    const int y0 = blk * NR, x0 = (int)rank * NL;
+    const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
+    const bool frc = !(a.flags & LBM_FLAG_NO_FORCE);
+    const bool same_base = a.fbase == a.fs;
+    // d_x f_i from global memory instead of the row transforms: only float64 rows of 4096 need it
+    constexpr bool AX_POSSIBLE = sizeof(R) == 8 && LOG2N == 12 && CS == 1;
+    const bool ax_mode = AX_POSSIBLE && a.Ax != nullptr;
+
+    // the node loop's other inputs start moving into L2 while the lines are transformed
+    if constexpr (CS == 1) {
+        if (threadIdx.x < NR) {
+            const size_t y = y0 + threadIdx.x;
+            prefetch_l2(a.fs + y * NF_F * NX, NF_F * NX * sizeof(R));
+            if (adv) prefetch_l2(a.Ay + y * NF_A * NX, NF_A * NX * sizeof(R));
+            if (!same_base) prefetch_l2(a.fbase + y * NF_F * NX, NF_F * NX * sizeof(R));
+            if (adv && ax_mode) prefetch_l2(a.Ax + y * NF_F * NX, NF_F * NX * sizeof(R));
+            prefetch_l2(a.m + y * NF_M * NX, (M_RY + 1) * NX * sizeof(R));
+            if (frc) prefetch_l2(a.m + (y * NF_M + M_DQX) * NX, (NF_M - M_DQX) * NX * sizeof(R));
+        }
+    } else {  // this CTA's x-range of every field of the row (NR = 1)
+        const int k = threadIdx.x;
+        const size_t y = y0, bytes = NL * sizeof(R);
+        if (k < NF_F) prefetch_l2(a.fs + (y * NF_F + k) * NX + x0, bytes);
+        else if (k < NF_F + NF_A) { if (adv) prefetch_l2(a.Ay + (y * NF_A + k - NF_F) * NX + x0, bytes); }
+        else if (k < 2 * NF_F + NF_A) { if (!same_base) prefetch_l2(a.fbase + (y * NF_F + k - NF_F - NF_A) * NX + x0, bytes); }
+        else if (k < 2 * NF_F + NF_A + NF_M) {
+            const int j = k - 2 * NF_F - NF_A;
+            if (j <= M_RY || (frc && j >= M_DQX)) prefetch_l2(a.m + (y * NF_M + j) * NX + x0, bytes);
+        }
+    }
+
+    if (adv && !ax_mode) {
+        // 6 lines per row (the 12 fields with v_x != 0, paired); LB lines per batch (LB divides
+        // 6 NR); threads past LB G/CS only take part in the barriers
+        const int LB = a.lines_per_batch;
+        const int ls = threadIdx.x / F::GL, t = (int)rank * F::GL + threadIdx.x % F::GL;
+        for (int b0 = 0; b0 < 6 * NR; b0 += LB) {
+            if (ls < LB) {
+                const int line = b0 + ls;
+                const int p = line / NR, r = line % NR;
+                CT *buf = sb + (size_t)line * SM;
+                const R *frow = a.fs + (size_t)(y0 + r) * NF_F * NX;
+                const R *fa = frow + xfield(2 * p) * NX, *fb = frow + xfield(2 * p + 1) * NX;
+                CT v[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[e] = reg::mk<R>(ldcg(fa + t + G * e), ldcg(fb + t + G * e));
+                F::template forward<reg::SyncCta>(v, buf, t, a.ax.tw);
+                F::multiply(v, t, 1, a.cx[p], a.ax.k1, a.ax.k2);  // -h v_x folded in
+                F::template inverse<reg::SyncCta>(v, buf, t, a.ax.tw);
+                if constexpr (CS == 1) reg::cta_barrier();  // (a split inverse ends with a cluster barrier)
+                F::store_natural(v, buf, t);
+            } else {
+                F::template idle_forward<reg::SyncCta>();
+                F::template idle_inverse<reg::SyncCta>();
+                if constexpr (CS == 1) reg::cta_barrier();
+            }
+        }
+        if constexpr (CS == 1) __syncthreads();
+        else reg::cluster_barrier();  // every CTA's part of every line has landed
+    }
+
+    for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
+        const int r = idx / NL, xl = idx % NL;  // xl: index in this CTA's line buffers
+        update_node<R, LOG2N, MOMENT_SPACE, AX_POSSIBLE>(a, kc, (size_t)(y0 + r), x0 + xl, sb + (size_t)r * SM,
+                                                         (size_t)NR * SM, xl);
     }
 }
 

@@ -1,6 +1,7 @@
-"""The TMA-fed column pass (LBM_COL_TMA) against the direct one: bit for bit the same states
-over every legal tile width, in both precisions, for single grids and stacked batch instances;
-its bounded waits end a starved launch with LBM_ERR_TIMEOUT instead of a hang."""
+"""The TMA-fed column pass (LBM_COL_TMA) and the direct pass with L2 lookahead
+(LBM_COL_LOOKAHEAD) against the direct one: bit for bit the same states over every legal tile
+width, in both precisions, for single grids and stacked batch instances; the TMA pass's bounded
+waits end a starved launch with LBM_ERR_TIMEOUT instead of a hang."""
 import numpy as np
 import pytest
 
@@ -34,9 +35,10 @@ def _run(nx, ny, precision, W, kinds, steps=3):
         return s.get_f()
 
 
+@pytest.mark.parametrize("kind", [lbm.LBM_COL_TMA, lbm.LBM_COL_LOOKAHEAD])
 @pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_MIXED])
 @pytest.mark.parametrize("nx,ny", [(64, 64), (256, 128), (32, 1024), (1024, 16)])
-def test_tma_column_pass_is_bitwise_the_direct_one(precision, nx, ny):
+def test_column_pass_kinds_are_bitwise_the_direct_one(kind, precision, nx, ny):
     es = 8 if precision == lbm.LBM_FP64 else 4
     plan = lbm.launch_plan(nx, ny, precision)
     widths = [w for w in (2, 4, 8, 16, 32) if w <= nx and w * es >= 16 and w * es <= 256]
@@ -44,7 +46,7 @@ def test_tma_column_pass_is_bitwise_the_direct_one(precision, nx, ny):
     tried = 0
     for W in widths:
         try:
-            got = _run(nx, ny, precision, W, (lbm.LBM_COL_TMA, lbm.LBM_COL_TMA))
+            got = _run(nx, ny, precision, W, (kind, kind))
         except lbm.LbmError as e:  # a width this shape cannot take (threads or shared memory)
             assert "not valid" in str(e) or "cannot take" in str(e), str(e)
             continue
@@ -120,3 +122,4 @@ def test_cluster_split_update_rows_are_bitwise_the_plain_ones(nx, ny):
         s.init(*_fields(256, 8))
         with pytest.raises(lbm.LbmError, match="2048"):
             s.set_pass_kinds((lbm.LBM_COL_DIRECT, lbm.LBM_COL_DIRECT, 2))
+
