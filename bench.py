@@ -187,7 +187,8 @@ def time_path(lbm, torch, precision, steps, warmup, fields, stream, autotune=Tru
             step_ms, wall = loop(sim)
             sim.timing(True)
             step_ms_b, _ = loop(sim)
-        kern = {k: sim.timing_read(k) for k in ELEMS_PER_NODE}
+        keys = list(ELEMS_PER_NODE) + (["rho64"] if precision == lbm.LBM_MIXED_RHO64 else [])
+        kern = {k: sim.timing_read(k) for k in keys}
         sim.timing(False)
         diag = sim.diagnostics()
     return step_ms, kern, wall, diag, step_ms_b, geometry
@@ -485,7 +486,7 @@ def main():
             "fp64": batch_path(lbm, torch, synthetic, lbm.LBM_FP64, max(3, kb // 4), 3, stream)}
         if rank == 0:
             from paper_1403_3746_gb300 import accuracy
-            tab = accuracy.error_table()
+            tab = accuracy.error_table(rho64=True)
             sl, dr = tab["slab"]["rows"], tab["droplet"]["rows"]
             extras["large_run"] = large_run(lbm, torch, synthetic, max(20, args.steps // 2), stream)
             lp = accuracy.laplace_check()
@@ -500,7 +501,22 @@ def main():
                 "spurious_velocity_rel_err_max": max(r["rel_err_umax"] for r in dr),
                 "pressure_jump_rel_err_max": max(r["rel_err_dp"] for r in dr),
                 "runs": f"slabs 256x2 at T={[r['T'] for r in sl]}, {tab['slab']['steps']} steps; droplets "
-                        f"R={[r['R'] for r in dr]} on 128^2 at T=0.9, {tab['droplet']['steps']} steps"}
+                        f"R={[r['R'] for r in dr]} on 128^2 at T=0.9, {tab['droplet']['steps']} steps",
+                "rho64": {  # LBM_MIXED_RHO64 against float64, same runs
+                    "coexistence_rel_err_max": max(max(r["rel_err_rho_l_rho64"], r["rel_err_rho_v_rho64"]) for r in sl),
+                    "mass_drift_max": max(abs(r["mass_drift_rho64"]) for r in sl + dr),
+                    "spurious_velocity_rel_err_max": max(r["rel_err_umax_rho64"] for r in dr),
+                    "pressure_jump_rel_err_max": max(r["rel_err_dp_rho64"] for r in dr)}}
+            # the same workload with the density chain in float64 (LBM_MIXED_RHO64)
+            kr = max(5, args.steps // 4)
+            step_r, kern_r, _, _, _, geom_r = time_path(lbm, torch, lbm.LBM_MIXED_RHO64, kr, 3, fields, stream,
+                                                        not args.no_autotune)
+            extras["rho64_path"] = {
+                "value": n * kr / (sum(step_r) * 1e-3) / 1e6, "unit": "MLUPS", "steps": kr,
+                "ms_per_step": sum(step_r) / kr, "launch_shapes": list(geom_r),
+                "kernels_ms_per_step": {k: v[0] / kr for k, v in kern_r.items()},
+                "note": "LBM_MIXED with rho as a float64 sum, its derivatives by float64 transforms and the "
+                        "pressure and Lambda terms in float64; kernels_ms_per_step.rho64 is the float64 chain"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -46,7 +46,12 @@ extern "C" {
 /* precision of the hot path */
 #define LBM_FP64 0   /* every step in float64 (the plain method) */
 #define LBM_MIXED 1  /* f storage, all transforms and the update in float32; float64 tables; moment
-                        sums compensated (float64-class); collision in moment space */
+                        sums of the stored values exact up to one rounding; collision in moment
+                        space */
+#define LBM_MIXED_RHO64 2 /* LBM_MIXED with the density chain in float64: rho as the float64 sum of
+                             the stored distributions, its first and second derivatives by float64
+                             transforms, and the van der Waals pressure and the Lambda terms of the
+                             macroscopic pass evaluated in float64 */
 
 /* test hooks: switch terms of Eq. (1) off */
 #define LBM_FLAG_NO_ADVECTION 1 /* drop v_i . grad f_i */
@@ -71,7 +76,7 @@ typedef struct lbm_params {
     double eta0;  /* extra-degree-of-freedom parameter of velocities 0..3 (Sec. 2.1: 2.5) */
     double win_alpha; /* window of the windowed FFT: W(m) = exp(-win_alpha (|m|/(N/2))^win_p) */
     double win_p;     /* along each derivative's axis; win_alpha = 0 (default): W = 1, Eq. (3) */
-    int precision; /* LBM_FP64 or LBM_MIXED */
+    int precision; /* LBM_FP64, LBM_MIXED or LBM_MIXED_RHO64 */
     int flags;     /* LBM_FLAG_* bits, 0 for the full model */
     double T_iso;  /* temperature of LBM_FLAG_ISOTHERMAL (> 0 when the flag is set) */
     int keff_terms; /* terms of the series of Eq. (3), 1..8: 8 = 16th order (default), 4 = 8th order */
@@ -196,7 +201,8 @@ int lbm_maxwell(double T, double *rho_l, double *rho_v);
 #define LBM_K_MACRO 1  /* row pass of the macroscopic chain (fluxes, x-derivatives) */
 #define LBM_K_FLUX 2   /* column pass of the flux divergences */
 #define LBM_K_UPDATE 3 /* fused row pass: x-derivatives of f, f^eq, I_i, BGK, RK stage, moments */
-#define LBM_K_COUNT 4
+#define LBM_K_RHO64 4  /* LBM_MIXED_RHO64: the float64 density sum and its float64 derivatives */
+#define LBM_K_COUNT 5
 int lbm_timing(lbm_handle h, int enable);
 int lbm_timing_read(lbm_handle h, int kernel, double *ms, long long *launches);
 

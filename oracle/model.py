@@ -28,6 +28,11 @@ f^{n+1} = f^n + dt R(f^n). Isothermal mode (the fixed temperature of the droplet
 Sec. 3.3): with T_iso > 0, f^eq and I_i of every stage use T = T_iso at every node instead of
 the temperature moment of f (the energy equation is replaced by a thermostat; mass and
 momentum stay conserved).
+
+Solution filter (filter_alpha > 0; a second reading of the "windowed" FFT scheme): after each
+step every f_i is replaced by the inverse transform of W(m_x) W(m_y) times its spectrum, with
+the window W of wfft.window. The paper prints no filter, so against the paper this is
+"parity unpinned"; tests pin it to this definition on single Fourier modes.
 """
 from dataclasses import dataclass
 

@@ -17,12 +17,13 @@ from .build import LIB as LIB_PATH
 LBM_OK = 0
 LBM_FP64 = 0
 LBM_MIXED = 1
+LBM_MIXED_RHO64 = 2
 LBM_FLAG_NO_ADVECTION = 1
 LBM_FLAG_NO_COLLISION = 2
 LBM_FLAG_NO_FORCE = 4
 LBM_FLAG_EULER = 8
 LBM_FLAG_ISOTHERMAL = 16
-KERNELS = {"col": 0, "macro": 1, "flux": 2, "update": 3}
+KERNELS = {"col": 0, "macro": 1, "flux": 2, "update": 3, "rho64": 4}
 LBM_COL_DIRECT = 0
 LBM_COL_TMA = 1
 LBM_COL_LOOKAHEAD = 2

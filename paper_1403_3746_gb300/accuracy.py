@@ -20,7 +20,7 @@ import numpy as np
 
 import synthetic
 
-from . import Batch, LBM_FP64, LBM_MIXED, default_params, maxwell
+from . import Batch, LBM_FP64, LBM_MIXED, LBM_MIXED_RHO64, default_params, maxwell
 
 PHASE = dict(tau=1e-4, dt=1e-4, dx=1 / 256, dy=1 / 256, K=5e-6, q=-0.004, b=2.0)
 
@@ -98,25 +98,38 @@ def droplet_runs(radii, precision, n=128, T=0.9, steps=10000, params=None):
     return out
 
 
-def error_table(temps=(0.85, 0.9, 0.95), radii=(8, 12, 16, 24, 32), slab_steps=20000, drop_steps=10000):
-    """Runs both precisions and returns the per-result comparison (plain dicts, JSON-ready)."""
+def error_table(temps=(0.85, 0.9, 0.95), radii=(8, 12, 16, 24, 32), slab_steps=20000, drop_steps=10000,
+                rho64=False):
+    """Runs both precisions and returns the per-result comparison (plain dicts, JSON-ready).
+    rho64: also LBM_MIXED_RHO64 (the density chain in float64), its errors against float64 in
+    the same rows under the suffix _rho64."""
     s64 = slab_runs(temps, LBM_FP64, steps=slab_steps)
     s32 = slab_runs(temps, LBM_MIXED, steps=slab_steps)
     d64 = droplet_runs(radii, LBM_FP64, steps=drop_steps)
     d32 = droplet_runs(radii, LBM_MIXED, steps=drop_steps)
+    sr = slab_runs(temps, LBM_MIXED_RHO64, steps=slab_steps) if rho64 else [None] * len(temps)
+    dr = droplet_runs(radii, LBM_MIXED_RHO64, steps=drop_steps) if rho64 else [None] * len(radii)
     coex = []
-    for T, a, m in zip(temps, s64, s32):
+    for T, a, m, r in zip(temps, s64, s32, sr):
         rl, rv = maxwell(T)
-        coex.append({"T": T, "rho_l_fp64": a[0], "rho_l_mixed": m[0], "rho_v_fp64": a[1], "rho_v_mixed": m[1],
-                     "rel_err_rho_l": abs(m[0] - a[0]) / abs(a[0]), "rel_err_rho_v": abs(m[1] - a[1]) / abs(a[1]),
-                     "maxwell_rho_l": rl, "maxwell_rho_v": rv,
-                     "mass_drift_fp64": a[2], "mass_drift_mixed": m[2]})
+        row = {"T": T, "rho_l_fp64": a[0], "rho_l_mixed": m[0], "rho_v_fp64": a[1], "rho_v_mixed": m[1],
+               "rel_err_rho_l": abs(m[0] - a[0]) / abs(a[0]), "rel_err_rho_v": abs(m[1] - a[1]) / abs(a[1]),
+               "maxwell_rho_l": rl, "maxwell_rho_v": rv,
+               "mass_drift_fp64": a[2], "mass_drift_mixed": m[2]}
+        if r is not None:
+            row.update({"rel_err_rho_l_rho64": abs(r[0] - a[0]) / abs(a[0]),
+                        "rel_err_rho_v_rho64": abs(r[1] - a[1]) / abs(a[1]), "mass_drift_rho64": r[2]})
+        coex.append(row)
     drops = []
-    for R, a, m in zip(radii, d64, d32):
-        drops.append({"R": R, "dp_fp64": a[0], "dp_mixed": m[0], "rel_err_dp": abs(m[0] - a[0]) / abs(a[0]),
-                      "umax_fp64": a[1], "umax_mixed": m[1], "rel_err_umax": abs(m[1] - a[1]) / abs(a[1]),
-                      "mass_drift_fp64": a[2], "mass_drift_mixed": m[2], "R_eq_fp64": a[3], "R_eq_mixed": m[3],
-                      "surface_tension_fp64": s64[list(temps).index(0.9)][3] if 0.9 in temps else None})
+    for R, a, m, r in zip(radii, d64, d32, dr):
+        row = {"R": R, "dp_fp64": a[0], "dp_mixed": m[0], "rel_err_dp": abs(m[0] - a[0]) / abs(a[0]),
+               "umax_fp64": a[1], "umax_mixed": m[1], "rel_err_umax": abs(m[1] - a[1]) / abs(a[1]),
+               "mass_drift_fp64": a[2], "mass_drift_mixed": m[2], "R_eq_fp64": a[3], "R_eq_mixed": m[3],
+               "surface_tension_fp64": s64[list(temps).index(0.9)][3] if 0.9 in temps else None}
+        if r is not None:
+            row.update({"rel_err_dp_rho64": abs(r[0] - a[0]) / abs(a[0]),
+                        "rel_err_umax_rho64": abs(r[1] - a[1]) / abs(a[1]), "mass_drift_rho64": r[2]})
+        drops.append(row)
     return {"slab": {"nx": 256, "ny": 2, "steps": slab_steps, "rows": coex},
             "droplet": {"n": 128, "T": 0.9, "steps": drop_steps, "rows": drops}}
 

@@ -85,6 +85,21 @@ __global__ void moments_kernel(const __grid_constant__ MomArgs a) {
     }
 }
 
+// LBM_MIXED_RHO64: rho of every node as the float64 sum of its 16 stored float32 values (exact:
+// the values span far fewer than the 29 bits a float64 has beyond a float32's significand).
+__global__ void rho64_kernel(const float *f, double *r64, int nx, int ny) {
+    const long long n = (long long)nx * ny;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long y = g / nx, x = g - y * nx;
+        const float *fn = f + y * NF_F * nx + x;
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) s += (double)__ldcg(fn + i * nx);
+        r64[(y * NR64 + R64_RHO) * nx + x] = s;
+    }
+}
+
 // Per-block partial sums of mass, x/y momentum, e_T (Sec. 2.2) and the max of |u|^2.
 template <typename R>
 __global__ void __launch_bounds__(256) diag_kernel(const __grid_constant__ DiagArgs a) {
@@ -200,6 +215,11 @@ template <typename R, int LOG2N> static cudaError_t launch_row_deriv_n(const Row
 static inline int grid_for(long long n) {
     long long b = (n + 255) / 256;
     return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+cudaError_t launch_rho64(const float *f, double *r64, int nx, int ny, cudaStream_t s) {
+    rho64_kernel<<<grid_for((long long)nx * ny), 256, 0, s>>>(f, r64, nx, ny);
+    return cudaGetLastError();
 }
 
 template <typename F> cudaError_t launch_init(const InitArgs &a, cudaStream_t s) {

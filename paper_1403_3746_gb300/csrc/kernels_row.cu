@@ -12,9 +12,9 @@
 
 namespace lbm {
 
-template <typename R, int LOG2N, bool SERIAL>
+template <typename R, int LOG2N, bool SERIAL, bool RHO64>
 __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R, LOG2N>::min_blocks) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
-    macro_rows<R, LOG2N, SERIAL>(a, blockIdx.x);
+    macro_rows<R, LOG2N, SERIAL, false, RHO64>(a, blockIdx.x);
 }
 
 template <typename R, int LOG2N, bool MOMENT_SPACE>
@@ -77,16 +77,26 @@ template <typename R, int LOG2N> static cudaError_t launch_macro_n(const MacroAr
     if (smem < need) return cudaErrorInvalidValue;
     if constexpr (sizeof(R) == 8 && LOG2N == 12) {  // the only shape that needs the serial form
         if (a.serial) {
-            cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, true>);
+            if (a.r64) return cudaErrorInvalidValue;
+            cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, true, false>);
             if (e != cudaSuccess) return e;
-            macro_row_kernel<R, LOG2N, true><<<a.ny / a.rows, a.rows * F::G, smem, s>>>(a);
+            macro_row_kernel<R, LOG2N, true, false><<<a.ny / a.rows, a.rows * F::G, smem, s>>>(a);
             return cudaGetLastError();
         }
     }
     if (a.serial) return cudaErrorInvalidValue;
-    cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, false>);
+    if constexpr (sizeof(R) == 4) {  // the float64 density chain (LBM_MIXED_RHO64)
+        if (a.r64) {
+            cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, false, true>);
+            if (e != cudaSuccess) return e;
+            macro_row_kernel<R, LOG2N, false, true><<<a.ny / a.rows, 2 * a.rows * F::G, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    if (a.r64) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, false, false>);
     if (e != cudaSuccess) return e;
-    macro_row_kernel<R, LOG2N, false><<<a.ny / a.rows, 2 * a.rows * F::G, smem, s>>>(a);
+    macro_row_kernel<R, LOG2N, false, false><<<a.ny / a.rows, 2 * a.rows * F::G, smem, s>>>(a);
     return cudaGetLastError();
 }
 

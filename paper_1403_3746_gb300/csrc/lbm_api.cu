@@ -99,6 +99,7 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     bool mixed = false;
+    bool rho64 = false;  // LBM_MIXED_RHO64: the density chain in float64 (r64, geo64)
     size_t fsize = 8;
 
     char *slab = nullptr;
@@ -109,6 +110,7 @@ struct lbm_ctx {
     void *Ay = nullptr;                 // [nb ny][12][nx]
     void *m = nullptr;                  // [nb ny][NF_M][nx]
     void *Ax = nullptr;                 // [nb ny][16][nx]: d_x f_i, only when geo.upd_ax
+    double *r64 = nullptr;              // [nb ny][NR64][nx]: the float64 density chain (rho64 only)
     double *partial = nullptr;
     int diag_blocks = 0;
     // pipelined diagnostics (lbm_diagnostics_begin / _end): two pinned host slots, each the
@@ -129,7 +131,8 @@ struct lbm_ctx {
     float *kfx32 = nullptr, *kfy32 = nullptr;
     double minv[256];
 
-    Geometry geo;  // launch geometry
+    Geometry geo;    // launch geometry
+    Geometry geo64;  // float64 launch geometry of the density chain's transforms (rho64 only)
 
     std::vector<char> initialized;  // per instance
     long long steps = 0;
@@ -258,8 +261,10 @@ template <typename R> int column_jobs(const lbm_ctx *c, int stage, ColArgs<R> &a
             a.jobs[nj++] = ColJob<R>{fs + (size_t)i * nx, Ay + (size_t)k * nx, ldf, lda, 1, (R)(-hs * vel_y(i))};
         }
     if (!(p.flags & LBM_FLAG_NO_FORCE)) {
-        a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RY), ldm, ldm, 1, R(1)};
-        a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RYY), ldm, ldm, 2, R(1)};
+        if (!c->rho64) {  // (LBM_MIXED_RHO64: the float64 density chain instead)
+            a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RY), ldm, ldm, 1, R(1)};
+            a.jobs[nj++] = ColJob<R>{M(M_RHO), M(M_RYY), ldm, ldm, 2, R(1)};
+        }
         a.jobs[nj++] = ColJob<R>{M(M_UX), M(M_UXY), ldm, ldm, 1, R(1)};
         a.jobs[nj++] = ColJob<R>{M(M_UY), M(M_UYY), ldm, ldm, 1, R(1)};
         a.jobs[nj++] = ColJob<R>{M(M_T), M(M_TY), ldm, ldm, 1, R(1)};
@@ -287,7 +292,37 @@ template <typename R> MacroArgs<R> macro_args(const lbm_ctx *c, int rows_per_cta
     a.serial = c->geo.macro_serial ? 1 : 0;
     a.ax = axis<R>(c, true);
     a.K = (R)p.K; a.H = (R)p.H; a.q = (R)p.q; a.zeta = (R)p.zeta;
+    a.K64 = p.K; a.H64 = p.H; a.q64 = p.q; a.zeta64 = p.zeta;
+    a.r64 = c->rho64 ? c->r64 : nullptr;
     return a;
+}
+
+// LBM_MIXED_RHO64: rho of the stage's f as a float64 sum, then its derivatives by float64
+// transforms: d_y rho, d_yy rho (one column launch) and d_x rho, d_xx rho (two row launches).
+int run_rho64_chain(lbm_ctx *c, const float *fs) {
+    const int nx = c->nx, rows = c->nb * c->ny, ld = NR64 * nx;
+    double *r = c->r64;
+    auto F = [r, nx](int k) { return r + (size_t)k * nx; };
+    LaunchTimer t(c, LBM_K_RHO64);
+    CU_TRY(launch_rho64(fs, r, nx, rows, c->stream));
+    ColArgs<double> ca = col_args<double>(c, c->nb, c->geo64.colW);
+    ca.jobs[0] = ColJob<double>{F(R64_RHO), F(R64_RY), ld, ld, 1, 1.0};
+    ca.jobs[1] = ColJob<double>{F(R64_RHO), F(R64_RYY), ld, ld, 2, 1.0};
+    CU_TRY(launch_col<double>(ca, 2, c->geo64.col_smem, c->stream));
+    for (int order = 1; order <= 2; ++order) {
+        RowDerivArgs<double> ra{};
+        ra.in[0] = F(R64_RHO);
+        ra.out[0] = F(order == 1 ? R64_RX : R64_RXX);
+        ra.ld = ld;
+        ra.nin = 1;
+        ra.nx = nx;
+        ra.ny = rows;
+        ra.rows = c->geo64.rows_rowd;
+        ra.order = order;
+        ra.ax = axis<double>(c, true);
+        CU_TRY(launch_row_deriv<double>(ra, c->geo64.rowd_smem, c->stream));
+    }
+    return LBM_OK;
 }
 
 template <typename R> UpdateArgs<R> update_args(const lbm_ctx *c, int stage, int rows_per_cta) {
@@ -335,6 +370,12 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
         if (nj && (passes & PASS_COL)) {
             LaunchTimer t(c, LBM_K_COL);
             CU_TRY(launch_col_pass<R>(c, a, nj, c->geo.col_kind, c->geo.col_smem));
+        }
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (c->rho64 && frc && (passes & PASS_COL)) {
+            const int rc = run_rho64_chain(c, reinterpret_cast<const float *>(fs));
+            if (rc) return rc;
         }
     }
     if (frc && (passes & PASS_MACRO)) {
@@ -688,8 +729,8 @@ int check_params(const lbm_params *p) {
     if (p->win_alpha < 0 || p->win_p <= 0) return fail(LBM_ERR_ARG, "need win_alpha >= 0 and win_p > 0");
     if (!std::isfinite(p->filter_alpha) || !std::isfinite(p->filter_p) || p->filter_alpha < 0 || p->filter_p <= 0)
         return fail(LBM_ERR_ARG, "need finite filter_alpha >= 0 and filter_p > 0");
-    if (p->precision != LBM_FP64 && p->precision != LBM_MIXED)
-        return fail(LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_MIXED");
+    if (p->precision != LBM_FP64 && p->precision != LBM_MIXED && p->precision != LBM_MIXED_RHO64)
+        return fail(LBM_ERR_ARG, "precision must be LBM_FP64, LBM_MIXED or LBM_MIXED_RHO64");
     if (p->flags & ~(LBM_FLAG_NO_ADVECTION | LBM_FLAG_NO_COLLISION | LBM_FLAG_NO_FORCE | LBM_FLAG_EULER |
                      LBM_FLAG_ISOTHERMAL))
         return fail(LBM_ERR_ARG, "unknown flag bits");
@@ -735,7 +776,8 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     c->n = (long long)nx * ny;
     c->p = *params;
     c->stream = stream;
-    c->mixed = params->precision == LBM_MIXED;
+    c->mixed = params->precision != LBM_FP64;
+    c->rho64 = params->precision == LBM_MIXED_RHO64;
     c->fsize = c->mixed ? 4 : 8;
     c->initialized.assign(nb, 0);
     if (cudaGetDevice(&c->device) != cudaSuccess) {
@@ -751,8 +793,12 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     pass_geometry(nx, ny, c->fsize, &c->geo);
-    const size_t need =
+    size_t need =
         std::max(std::max(c->geo.upd_smem, c->geo.macro_smem), std::max(c->geo.col_smem, c->geo.rowd_smem));  // flux = col
+    if (c->rho64) {  // the density chain's float64 column and row transforms
+        pass_geometry(nx, ny, 8, &c->geo64);
+        need = std::max(need, std::max(c->geo64.col_smem, c->geo64.rowd_smem));
+    }
     if (need > (size_t)smem_optin) {
         delete c;
         return fail(LBM_ERR_UNSUPPORTED, "nx=%d ny=%d needs %zu B of shared memory per block (device: %d)", nx,
@@ -770,6 +816,7 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     parts.push_back({&c->Ay, 12 * plane_f});
     parts.push_back({&c->m, (size_t)NF_M * plane_f});
     if (c->geo.upd_ax) parts.push_back({&c->Ax, 16 * plane_f});
+    if (c->rho64) parts.push_back({reinterpret_cast<void **>(&c->r64), (size_t)NR64 * c->n * nb * sizeof(double)});
     parts.push_back({reinterpret_cast<void **>(&c->partial), (size_t)c->diag_blocks * 5 * 8});
     parts.push_back({reinterpret_cast<void **>(&c->err), sizeof(int)});
     parts.push_back({reinterpret_cast<void **>(&c->tw64x), (size_t)nx * 16});
@@ -1345,8 +1392,8 @@ int lbm_set_f(lbm_handle c, const double *f16) {
 
 size_t lbm_state_bytes(int nx, int ny, int precision) {
     if (!is_pow2(nx) || !is_pow2(ny) || nx > 4096 || ny > 4096) return 0;
-    if (precision != LBM_FP64 && precision != LBM_MIXED) return 0;
-    return sizeof(StateHeader) + state_payload(nx, ny, precision == LBM_MIXED ? 4 : 8);
+    if (precision != LBM_FP64 && precision != LBM_MIXED && precision != LBM_MIXED_RHO64) return 0;
+    return sizeof(StateHeader) + state_payload(nx, ny, precision == LBM_FP64 ? 8 : 4);
 }
 
 unsigned long long lbm_params_hash(const lbm_params *params) { return params ? hash_params(*params) : 0ULL; }
@@ -1501,9 +1548,9 @@ int lbm_launch_plan(int nx, int ny, int precision, int out[18]) {
     if (!out) return fail(LBM_ERR_ARG, "NULL argument");
     if (!is_pow2(nx) || !is_pow2(ny) || nx > 4096 || ny > 4096)
         return fail(LBM_ERR_ARG, "nx=%d, ny=%d: each must be a power of two in [2, 4096]", nx, ny);
-    if (precision != LBM_FP64 && precision != LBM_MIXED)
-        return fail(LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_MIXED");
-    const size_t es = precision == LBM_MIXED ? 4 : 8;
+    if (precision != LBM_FP64 && precision != LBM_MIXED && precision != LBM_MIXED_RHO64)
+        return fail(LBM_ERR_ARG, "precision must be LBM_FP64, LBM_MIXED or LBM_MIXED_RHO64");
+    const size_t es = precision == LBM_FP64 ? 8 : 4;
     const int lx = ilog2(nx), ly = ilog2(ny);
     Geometry g;
     pass_geometry(nx, ny, es, &g);
@@ -1837,7 +1884,7 @@ static int build_batch_graph(lbm_batch b) {
 static bool batch_persistent_ok(lbm_batch b) {
     if (b->groups.empty() || (int)b->groups.size() > kBatchGroups) return false;
     for (lbm_ctx *c : b->groups)
-        if (!c->mixed || (c->p.flags & ~LBM_FLAG_ISOTHERMAL) || c->p.filter_alpha > 0 || c->lx < 7 || c->lx > 10 ||
+        if (!c->mixed || c->rho64 || (c->p.flags & ~LBM_FLAG_ISOTHERMAL) || c->p.filter_alpha > 0 || c->lx < 7 || c->lx > 10 ||
             c->ly < 7 || c->ly > 10)
             return false;
     return true;

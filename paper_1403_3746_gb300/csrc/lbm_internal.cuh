@@ -213,7 +213,16 @@ template <typename R> struct MacroArgs {
     int serial;  // one thread group transforms both lines of a row in turn (float64, nx = 4096)
     Axis<R> ax;
     R K, H, q, zeta;
+    // LBM_MIXED_RHO64: the float64 density chain [ny][NR64][nx] (nullptr otherwise) and the
+    // parameters in float64 for the terms evaluated in float64
+    const double *r64;
+    double K64, H64, q64, zeta64;
 };
+// fields of the float64 density chain (LBM_MIXED_RHO64): rho = the float64 sum of the stored f,
+// d_x rho, d_xx rho (row derivatives), d_y rho, d_yy rho (column derivatives)
+enum Rho64Field { R64_RHO, R64_RX, R64_RXX, R64_RY, R64_RYY, NR64 };
+// rho in float64 as the sum of the 16 stored distributions of each node (f: [ny][16][nx])
+cudaError_t launch_rho64(const float *f, double *r64, int nx, int ny, cudaStream_t s);
 
 // ---- fused update row pass -----------------------------------------------------------
 // tables of the model read with compile-time indices by the node loop (kernel parameters, so

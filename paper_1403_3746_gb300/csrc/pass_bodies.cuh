@@ -100,7 +100,11 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
 // global slot of d_x S_xy (free until round 2 writes it) instead of shared memory.
 // Threads beyond the row lines' groups (a CTA larger than the pass needs, as in the batch
 // kernel) only keep the barrier count. Inputs written by other passes are read L2-only.
-template <typename R, int LOG2N, bool SERIAL, bool EXTRA = false>
+// RHO64 (LBM_MIXED_RHO64): rho and its derivatives come from the float64 density chain
+// (a.r64) and the node loop's rho-dependent terms (P^w, Lambda, S, Q, the C numerator) are
+// evaluated in float64, then rounded to the path's type; d_y rho is also written to M_RY for the
+// update pass.
+template <typename R, int LOG2N, bool SERIAL, bool EXTRA = false, bool RHO64 = false>
 __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
     using F = reg::LineFFT<R, LOG2N, true>;
     using CT = typename F::CT;
@@ -120,8 +124,10 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
     auto buf1 = [&](int kind) { return lines + (size_t)r * 3 * SM + (kind == 0 ? 0 : 2 * SM); };
     CT *O2 = lines + (size_t)r * 3 * SM + SM;  // line A's second buffer
 
-    if (threadIdx.x < NR)  // the node loop's inputs from the column pass start moving into L2
+    if (threadIdx.x < NR) {  // the node loop's inputs from the column pass start moving into L2
         prefetch_l2(a.m + ((size_t)(y0 + threadIdx.x) * NF_M + M_RY) * NX, 5 * NX * sizeof(R));
+        if constexpr (RHO64) prefetch_l2(a.r64 + (size_t)(y0 + threadIdx.x) * NR64 * NX, NR64 * NX * sizeof(double));
+    }
 
     // round 1: derivatives of the moments along x
     CT v[E];
@@ -165,48 +171,65 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
     }
     __syncthreads();
 
-    const R K = a.K, H = a.H, q = a.q, zeta = a.zeta;
+    using D = std::conditional_t<RHO64, double, R>;  // type of the rho-dependent terms
+    const D K = RHO64 ? (D)a.K64 : (D)a.K, H = RHO64 ? (D)a.H64 : (D)a.H, q = RHO64 ? (D)a.q64 : (D)a.q,
+            zeta = RHO64 ? (D)a.zeta64 : (D)a.zeta;
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int rr = idx / NX, x = idx % NX;
         R *mn = a.m + (size_t)(y0 + rr) * NF_M * NX + x;  // this node: field k at mn[k * NX]
         CT *A1 = lines + (size_t)rr * 3 * SM, *A2 = A1 + SM, *B1 = A1 + 2 * SM;
-        const R rx = A1[x].x, Tx = A1[x].y, rxx = A2[x].x;
-        const R dux_dx = B1[x].x, duy_dx = B1[x].y;
-        const R rho = __ldcg(mn + M_RHO * NX), T = __ldcg(mn + M_T * NX);
-        const R ry = __ldcg(mn + M_RY * NX), ryy = __ldcg(mn + M_RYY * NX), dux_dy = __ldcg(mn + M_UXY * NX),
-                duy_dy = __ldcg(mn + M_UYY * NX);
-        const R Ty = __ldcg(mn + M_TY * NX);
+        const D Tx = A1[x].y;
+        const D dux_dx = B1[x].x, duy_dx = B1[x].y;
+        const D T = __ldcg(mn + M_T * NX);
+        const D dux_dy = __ldcg(mn + M_UXY * NX), duy_dy = __ldcg(mn + M_UYY * NX);
+        const D Ty = __ldcg(mn + M_TY * NX);
+        D rho, rx, rxx, ry, ryy;
+        if constexpr (RHO64) {
+            const double *rn = a.r64 + (size_t)(y0 + rr) * NR64 * NX + x;
+            rho = __ldcg(rn + R64_RHO * NX);
+            rx = __ldcg(rn + R64_RX * NX);
+            rxx = __ldcg(rn + R64_RXX * NX);
+            ry = __ldcg(rn + R64_RY * NX);
+            ryy = __ldcg(rn + R64_RYY * NX);
+            mn[M_RY * NX] = (R)ry;  // read by the update pass's C term
+        } else {
+            rho = __ldcg(mn + M_RHO * NX);
+            rx = A1[x].x;
+            rxx = A2[x].x;
+            ry = __ldcg(mn + M_RY * NX);
+            ryy = __ldcg(mn + M_RYY * NX);
+        }
 
-        const R lap = rxx + ryy;
-        const R divu = dux_dx + duy_dy;
+        const D lap = rxx + ryy;
+        const D divu = dux_dx + duy_dy;
         // van der Waals EOS (Sec. 2.2)
-        const R rT = rho * T;
-        const R Pw = quot(R(3) * rT, R(3) - rho) - R(1.125) * rho * rho;
+        const D rT = rho * T;
+        const D Pw = quot(D(3) * rT, D(3) - rho) - D(1.125) * rho * rho;
         // Lambda with M = K + H T and grad(M/T) = -K grad T / T^2
-        const R Mc = K + H * T;
-        const R iT2 = quot(R(1), T * T);
-        const R gx = -K * Tx * iT2, gy = -K * Ty * iT2;
-        const R grr = rx * rx + ry * ry;
-        const R iso = Mc * (rho * lap + R(0.5) * grr) + rT * (rx * gx + ry * gy);
-        const R Lxx = Mc * rx * rx - iso, Lxy = Mc * rx * ry, Lyy = Mc * ry * ry - iso;
-        const R Pn = Pw - rT - zeta * divu;
-        const R Sxx = Pn + Lxx, Sxy = Lxy, Syy = Pn + Lyy;
-        const R qrT = q * rT;
-        const R Qx = qrT * Tx, Qy = qrT * Ty;
+        const D Mc = K + H * T;
+        const D iT2 = quot(D(1), T * T);
+        const D gx = -K * Tx * iT2, gy = -K * Ty * iT2;
+        const D grr = rx * rx + ry * ry;
+        const D iso = Mc * (rho * lap + D(0.5) * grr) + rT * (rx * gx + ry * gy);
+        const D Lxx = Mc * rx * rx - iso, Lxy = Mc * rx * ry, Lyy = Mc * ry * ry - iso;
+        const D Pn = Pw - rT - zeta * divu;
+        const D Sxx = Pn + Lxx, Sxy = Lxy, Syy = Pn + Lyy;
+        const D qrT = q * rT;
+        const D Qx = qrT * Tx, Qy = qrT * Ty;
         // numerator of C without -K rho (d_x rho d_x(div u) + d_y rho d_y(div u)): the x term is
         // added after round 2 below, the y term by the update pass (after the flux pass)
-        const R L_gradu = Lxx * dux_dx + Lxy * (duy_dx + dux_dy) + Lyy * duy_dy;
-        const R r_gradu_r = rx * (dux_dx * rx + duy_dx * ry) + ry * (dux_dy * rx + duy_dy * ry);
-        mn[M_CNUM * NX] = (Pw - rT) * divu + L_gradu - zeta * divu * divu + R(1.125) * rho * rho * divu +
-                          K * (-R(0.5) * grr * divu - r_gradu_r);
-        if constexpr (SERIAL) mn[M_DSXY * NX] = K * rho * rx;
-        else krx[idx] = K * rho * rx;
-        mn[M_QY * NX] = Qy;
-        mn[M_SXY * NX] = Sxy;
-        mn[M_SYY * NX] = Syy;
-        mn[M_DIVU * NX] = divu;
-        A1[x] = reg::mk<R>(Qx, Sxx);  // round-2 lines, same node and thread as the reads above
-        B1[x] = reg::mk<R>(Sxy, divu);
+        const D L_gradu = Lxx * dux_dx + Lxy * (duy_dx + dux_dy) + Lyy * duy_dy;
+        const D r_gradu_r = rx * (dux_dx * rx + duy_dx * ry) + ry * (dux_dy * rx + duy_dy * ry);
+        mn[M_CNUM * NX] = (R)((Pw - rT) * divu + L_gradu - zeta * divu * divu + D(1.125) * rho * rho * divu +
+                              K * (-D(0.5) * grr * divu - r_gradu_r));
+        if constexpr (SERIAL) mn[M_DSXY * NX] = (R)(K * rho * rx);
+        else krx[idx] = (R)(K * rho * rx);
+        mn[M_QY * NX] = (R)Qy;
+        mn[M_SXY * NX] = (R)Sxy;
+        mn[M_SYY * NX] = (R)Syy;
+        mn[M_DIVU * NX] = (R)divu;
+        A1[x] = reg::mk<R>((R)Qx, (R)Sxx);  // round-2 lines, same node and thread as the reads above
+        B1[x] = reg::mk<R>((R)Sxy, (R)divu);
     }
     __syncthreads();
 

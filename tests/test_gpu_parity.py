@@ -257,6 +257,28 @@ def test_mixed_slab_64_200_steps():
     assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
 
 
+def test_mixed_rho64_slab_64_200_steps():
+    # the density chain in float64 (LBM_MIXED_RHO64): the mixed path's bounds
+    fields = slab_fields(64, 64)
+    fo, mo = run_oracle(fields, 200)
+    fg, mg = run_gpu(fields, 200, precision=lbm.LBM_MIXED_RHO64)
+    ef, er, eu, eT = mixed_errors(fg, mg, fo, mo)
+    print(f"mixed rho64 slab 64^2 x 200: f {ef:.2e}, rho {er:.2e}, |du| {eu:.2e}, T {eT:.2e}")
+    assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 32), (256, 64), (4096, 8)])
+def test_mixed_rho64_forcing_only(nx, ny):
+    # forcing term alone (no advection, no collision): what the float64 density chain feeds
+    fields = moving_fields(nx, ny)
+    flags = lbm.LBM_FLAG_NO_ADVECTION | lbm.LBM_FLAG_NO_COLLISION
+    fo, mo = run_oracle(fields, 2, flags=flags)
+    fg, mg = run_gpu(fields, 2, precision=lbm.LBM_MIXED_RHO64, flags=flags)
+    ef, er, eu, eT = mixed_errors(fg, mg, fo, mo)
+    print(f"mixed rho64 forcing {nx}x{ny} x 2: f {ef:.2e}, rho {er:.2e}, |du| {eu:.2e}, T {eT:.2e}")
+    assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
+
+
 def test_mixed_rows_of_4096():
     # float32 rows of 4096: the update pass's 6 line buffers take 209 KB of shared memory
     fields = slab_fields(4096, 8)

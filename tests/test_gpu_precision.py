@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def table():
     lbm_build.build()
-    t = accuracy.error_table()
+    t = accuracy.error_table(rho64=True)
     for row in t["slab"]["rows"]:
         print({k: f"{v:.6g}" for k, v in row.items()})
     for row in t["droplet"]["rows"]:
@@ -36,6 +36,15 @@ def test_mass_drift(table):
     for row in rows:
         assert abs(row["mass_drift_fp64"]) <= 1e-10, row
         assert abs(row["mass_drift_mixed"]) <= 2e-6, row
+        assert abs(row["mass_drift_rho64"]) <= 2e-6, row
+
+
+def test_float64_density_chain_keeps_the_bounds(table):
+    # LBM_MIXED_RHO64 against float64: the same bounds as LBM_MIXED
+    for row in table["slab"]["rows"]:
+        assert row["rel_err_rho_l_rho64"] <= 1e-4 and row["rel_err_rho_v_rho64"] <= 1e-4, row
+    for row in table["droplet"]["rows"]:
+        assert row["rel_err_dp_rho64"] <= 1e-3 and row["rel_err_umax_rho64"] <= 1e-3, row
 
 
 def test_droplet_pressure_jump_and_spurious_velocity(table):

@@ -144,7 +144,7 @@ def _line_G(n):
     return n // 16 if n >= 16 else 1
 
 
-@pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_MIXED])
+@pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_MIXED, lbm.LBM_MIXED_RHO64])
 def test_launch_plan_of_every_size_fits_the_kernels(L, precision):
     # host-side launch plan (no device) of every supported grid: each pass's CTA within its
     # thread and shared-memory limits, tiles and row groups dividing the grid, and the
@@ -190,10 +190,12 @@ def test_state_blob_size_and_params_hash(L):
     # header of 64 bytes, then per row 16 distributions + 4 moments in the storage precision
     assert lbm.state_bytes(64, 32, lbm.LBM_FP64) == 64 + 32 * 20 * 64 * 8
     assert lbm.state_bytes(64, 32, lbm.LBM_MIXED) == 64 + 32 * 20 * 64 * 4
+    assert lbm.state_bytes(64, 32, lbm.LBM_MIXED_RHO64) == lbm.state_bytes(64, 32, lbm.LBM_MIXED)
     assert lbm.state_bytes(63, 32) == 0 and lbm.state_bytes(64, 32, 7) == 0
     a, b = lbm.default_params(), lbm.default_params()
     assert lbm.params_hash(a) == lbm.params_hash(b) != 0
-    for field, value in (("tau", 2e-4), ("K", 5.000001e-6), ("precision", lbm.LBM_MIXED), ("flags", 8),
+    for field, value in (("tau", 2e-4), ("K", 5.000001e-6), ("precision", lbm.LBM_MIXED),
+                         ("precision", lbm.LBM_MIXED_RHO64), ("flags", 8),
                          ("keff_terms", 4), ("win_alpha", 36.0), ("filter_alpha", 36.0)):
         c = lbm.default_params(**{field: value})
         assert lbm.params_hash(c) != lbm.params_hash(a), field
