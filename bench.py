@@ -42,9 +42,9 @@ KERNEL_NAMES = {"col": "col_deriv_kernel", "macro": "macro_row_kernel", "flux": 
                 "update": "update_row_kernel"}
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (no tensor path for this work)
 # FP64 flops of one step of the FP64 path per node (DADD + DMUL + 2 DFMA thread instructions
-# of its four kernels, counted by ncu at 1024^2: 5.50 GFLOP per step; the count does not
+# of its four kernels, counted by ncu at 1024^2: 5.35 GFLOP per step; the count does not
 # depend on the launch shapes)
-FP64_FLOP_PER_NODE_STEP = 5.50e9 / (1024 * 1024)
+FP64_FLOP_PER_NODE_STEP = 5.353e9 / (1024 * 1024)
 
 
 def peaks():
@@ -413,6 +413,36 @@ def reference_main(args):
     return 0
 
 
+def profile_main(args):
+    """Launch sequences for ncu launch lists (the kernels and their order are fixed; nothing is
+    timed here and no number printed by a run under ncu is a bench value)."""
+    import torch
+    import paper_1403_3746_gb300 as lbm
+    from paper_1403_3746_gb300 import build as lbm_build
+    import synthetic
+
+    torch.cuda.set_device(0)
+    if not os.path.exists(lbm_build.LIB):
+        lbm_build.build()
+    p = lbm.default_params(precision=lbm.LBM_MIXED, **PARAMS)
+    if args.profile == "large":
+        fields = synthetic.spinodal(LARGE_N, LARGE_N, 1.0, 0.01, 0.9, seed=5)
+        with lbm.Simulation(LARGE_N, LARGE_N, p) as sim:
+            sim.init(*fields)
+            sim.step(1)
+            sim.step(2)
+            sim.synchronize()
+            out = {"profile": "large", "n": LARGE_N, "steps": 3, "launch_shapes": list(sim.geometry()) + list(sim.pass_kinds())}
+    else:
+        fields = make_fields(lbm, synthetic)
+        with lbm.Simulation(N_GRID, N_GRID, p) as sim:
+            sim.init(*fields)
+            sim.step(1)
+            d = [sim.diagnostics() for _ in range(3)]
+            out = {"profile": "diag", "n": N_GRID, "steps": 1, "diagnostics": 3, "mass": d[-1]["mass"]}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,9 +454,15 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched form and the error table")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (for profiler runs, whose timing would mislead the tuner)")
+    ap.add_argument("--profile", choices=["large", "diag"], default=None,
+                    help="a fixed short launch sequence for ncu launch lists (default shapes, no timing): "
+                         "large = 4096^2 mixed spinodal, init + 1 + 2 steps; diag = 1024^2 mixed droplet, "
+                         "init + 1 step + 3 diagnostics requests")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
+    if args.profile:
+        return profile_main(args)
 
     import torch
     import paper_1403_3746_gb300 as lbm

@@ -100,43 +100,131 @@ __global__ void rho64_kernel(const float *f, double *r64, int nx, int ny) {
     }
 }
 
+// A float32 value pair hi + lo (about 48 significant bits) and its exact-sum update (Knuth's
+// TwoSum for hi, the error into lo), for sums of float32 terms without float64 arithmetic.
+struct FPair {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(hi, x);
+        const float bp = __fsub_rn(t, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+        hi = t;
+    }
+    // x y added exactly: the product's rounding error from fmaf
+    __device__ __forceinline__ void add_prod(float x, float y) {
+        const float p = __fmul_rn(x, y);
+        add(p);
+        lo = __fadd_rn(lo, fmaf(x, y, -p));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ void merge(const FPair &o) {
+        add(o.hi);
+        lo = __fadd_rn(lo, o.lo);
+    }
+    // the larger of two non-negative pairs (by hi, then lo)
+    __device__ __forceinline__ void take_max(const FPair &o) {
+        if (o.hi > hi || (o.hi == hi && o.lo > lo)) hi = o.hi, lo = o.lo;
+    }
+};
+
 // Per-block partial sums of mass, x/y momentum, e_T (Sec. 2.2) and the max of |u|^2.
+// float64 states: float64 arithmetic. float32 states: the large terms (rho, rho u, rho T,
+// 9/8 rho^2, |u|^2) enter as exact products and sums in float pairs, the small ones (the
+// gradient and kinetic parts of e_T) in float32, so the sums agree with a float64 evaluation of
+// the same stored values to about 1e-14 of the large terms while the per-node work stays in the
+// float32 pipe (GB300's float64 rate is 1/64 of float32); the block's sums become float64 once.
 template <typename R>
 __global__ void __launch_bounds__(256) diag_kernel(const __grid_constant__ DiagArgs a) {
-    __shared__ double red[5][256];
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, mx = 0;
     const R *prho = static_cast<const R *>(a.rho), *pux = static_cast<const R *>(a.ux);
     const R *puy = static_cast<const R *>(a.uy), *pT = static_cast<const R *>(a.T);
     const R *prx = static_cast<const R *>(a.rx), *pry = static_cast<const R *>(a.ry);
-    const long long n = (long long)a.nx * a.ny;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
-         g += (long long)gridDim.x * blockDim.x) {
-        const long long y = g / a.nx, x = g - y * a.nx;
-        const long long o = y * a.ld + x;
-        const double rho = prho[o], ux = pux[o], uy = puy[o], T = pT[o];
-        const double rx = prx[o], ry = pry[o];
-        const double u2 = ux * ux + uy * uy;
-        s0 += rho;
-        s1 += rho * ux;
-        s2 += rho * uy;
-        s3 += rho * T - 1.125 * rho * rho + 0.5 * a.K * (rx * rx + ry * ry) + 0.5 * rho * u2;
-        mx = fmax(mx, u2);
-    }
-    const int t = threadIdx.x;
-    red[0][t] = s0; red[1][t] = s1; red[2][t] = s2; red[3][t] = s3; red[4][t] = mx;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (t < w) {
-            red[0][t] += red[0][t + w];
-            red[1][t] += red[1][t + w];
-            red[2][t] += red[2][t + w];
-            red[3][t] += red[3][t + w];
-            red[4][t] = fmax(red[4][t], red[4][t + w]);
+    if constexpr (sizeof(R) == 8) {
+        __shared__ double red[5][256];
+        double s0 = 0, s1 = 0, s2 = 0, s3 = 0, mx = 0;
+        const long long n = (long long)a.nx * a.ny;
+        for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
+             g += (long long)gridDim.x * blockDim.x) {
+            const long long y = g / a.nx, x = g - y * a.nx;
+            const long long o = y * a.ld + x;
+            const double rho = prho[o], ux = pux[o], uy = puy[o], T = pT[o];
+            const double rx = prx[o], ry = pry[o];
+            const double u2 = ux * ux + uy * uy;
+            s0 += rho;
+            s1 += rho * ux;
+            s2 += rho * uy;
+            s3 += rho * T - 1.125 * rho * rho + 0.5 * a.K * (rx * rx + ry * ry) + 0.5 * rho * u2;
+            mx = fmax(mx, u2);
+        }
+        const int t = threadIdx.x;
+        red[0][t] = s0; red[1][t] = s1; red[2][t] = s2; red[3][t] = s3; red[4][t] = mx;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (t < w) {
+                red[0][t] += red[0][t + w];
+                red[1][t] += red[1][t + w];
+                red[2][t] += red[2][t + w];
+                red[3][t] += red[3][t + w];
+                red[4][t] = fmax(red[4][t], red[4][t + w]);
+            }
+            __syncthreads();
+        }
+        if (t == 0)
+            for (int k = 0; k < 5; ++k) a.partial[blockIdx.x * 5 + k] = red[k][0];
+    } else {
+        // rows of the block (no 64-bit index division per node)
+        FPair S[5];  // mass, x and y momentum, e_T, max |u|^2
+        const float hK = (float)(0.5 * a.K);
+        for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
+            const long long ro = (long long)y * a.ld;
+            for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
+                const long long o = ro + x;
+                const float rho = prho[o], ux = pux[o], uy = puy[o], T = pT[o];
+                const float rx = prx[o], ry = pry[o];
+                S[0].add(rho);
+                S[1].add_prod(rho, ux);
+                S[2].add_prod(rho, uy);
+                FPair u2;  // |u|^2 exactly
+                u2.add_prod(ux, ux);
+                u2.add_prod(uy, uy);
+                S[3].add_prod(rho, T);
+                const float r2 = __fmul_rn(rho, rho), er2 = fmaf(rho, rho, -r2);  // rho^2 = r2 + er2
+                S[3].add_prod(-1.125f, r2);
+                S[3].lo = __fadd_rn(S[3].lo, fmaf(hK, fmaf(rx, rx, ry * ry), fmaf(-1.125f, er2, 0.5f * rho * u2.hi)));
+                S[4].take_max(u2);
+            }
+        }
+        // block reduction in float pairs (warp shuffles, then one warp over the warps' pairs);
+        // the block's pairs become float64 once
+        __shared__ float wpart[32][5][2];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            for (int d = 16; d > 0; d >>= 1) {
+                FPair o;
+                o.hi = __shfl_down_sync(0xffffffffu, S[k].hi, d);
+                o.lo = __shfl_down_sync(0xffffffffu, S[k].lo, d);
+                if (k < 4) S[k].merge(o);
+                else S[k].take_max(o);
+            }
+            if (lane == 0) wpart[warp][k][0] = S[k].hi, wpart[warp][k][1] = S[k].lo;
         }
         __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                FPair v;
+                if (lane < nw) v.hi = wpart[lane][k][0], v.lo = wpart[lane][k][1];
+                for (int d = 16; d > 0; d >>= 1) {
+                    FPair o;
+                    o.hi = __shfl_down_sync(0xffffffffu, v.hi, d);
+                    o.lo = __shfl_down_sync(0xffffffffu, v.lo, d);
+                    if (k < 4) v.merge(o);
+                    else v.take_max(o);
+                }
+                if (lane == 0) a.partial[blockIdx.x * 5 + k] = v.value();
+            }
+        }
     }
-    if (t == 0)
-        for (int k = 0; k < 5; ++k) a.partial[blockIdx.x * 5 + k] = red[k][0];
 }
 
 // Twiddle table in the per-pass layout of fft_reg.cuh: entry idx = exp(-2 pi i a / n) with

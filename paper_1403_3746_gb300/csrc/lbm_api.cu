@@ -1144,9 +1144,12 @@ template <typename R> int diag_launch(lbm_ctx *c, int k) {
     // d_y rho into M_RY, d_x rho into M_DQX of instance k (stage scratch, rebuilt by the next stage)
     const int nx = c->nx, ldm = NF_M * nx;
     R *m = static_cast<R *>(c->m) + c->row0(k) * ldm;
-    ColArgs<R> ca = col_args<R>(c, 1, c->geo.colW);
+    // one job: the narrowest tiles with 16-byte rows, so that its CTAs spread over the SMs
+    const int W = std::min(nx, std::max(2, 16 / (int)sizeof(R)));
+    const int Wd = col_cluster(W, c->ly, sizeof(R)) == 1 ? W : c->geo.colW;
+    ColArgs<R> ca = col_args<R>(c, 1, Wd);
     ca.jobs[0] = ColJob<R>{m + (size_t)M_RHO * nx, m + (size_t)M_RY * nx, ldm, ldm, 1, R(1)};
-    CU_TRY(launch_col<R>(ca, 1, c->geo.col_smem, c->stream));
+    CU_TRY(launch_col<R>(ca, 1, Wd == c->geo.colW ? c->geo.col_smem : col_smem(Wd, c->ly, sizeof(R)), c->stream));
     RowDerivArgs<R> ra{};
     ra.in[0] = m + (size_t)M_RHO * nx;
     ra.out[0] = m + (size_t)M_DQX * nx;
