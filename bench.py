@@ -203,8 +203,9 @@ def time_path(lbm, torch, precision, steps, warmup, fields, stream, autotune=Tru
 def e2e_path(lbm, torch, precision, steps, fields):
     """Through the C ABI with host buffers: init from pinned host memory, every step lbm_step and
     a diagnostics request whose per-block partial sums come back to pinned host memory
-    (lbm_diagnostics_begin; the previous step's request is reduced with lbm_diagnostics_end while
-    this step runs), and the final moments read back to pinned host memory."""
+    (lbm_diagnostics_begin: the request rides on the next step's first macro pass; the previous
+    step's request is reduced with lbm_diagnostics_end while this step runs), and the final
+    moments read back to pinned host memory."""
     p = lbm.default_params(precision=precision, **PARAMS)
     pinned = [torch.empty((N_GRID, N_GRID), dtype=torch.float64, pin_memory=True).numpy() for _ in range(8)]
     for dst, src in zip(pinned[:4], fields):
@@ -225,12 +226,12 @@ def e2e_path(lbm, torch, precision, steps, fields):
         sim.moments(out=pinned[4:])
         wall = time.perf_counter() - t0
     n = N_GRID * N_GRID
-    blocks = min(1024, (n + 255) // 256)  # the library's reduction blocks: 5 partial sums each, and its error word
+    blocks = N_GRID  # the fused requests' partial sums: 5 per macro-pass CTA (one row each), and the error word
     assert len(diags) == steps and diags[-1]["steps"] == steps
     return {"value": n * steps / wall / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": 4 * n * 8 / steps, "d2h_bytes_per_step": blocks * 5 * 8 + 4 + 4 * n * 8 / steps,
-            "note": "init from pinned host + per step lbm_step and a pipelined diagnostics read "
-                    "(lbm_diagnostics_begin / _end) + final moments"}
+            "note": "init from pinned host + per step lbm_step and a diagnostics read (lbm_diagnostics_begin "
+                    "/ _end; each request fused into the next step's macro pass) + final moments"}
 
 
 BATCH_SIZES = [128] * 32 + [256] * 32 + [512] * 32

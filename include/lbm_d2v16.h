@@ -158,15 +158,20 @@ int lbm_diagnostics(lbm_handle h, double out[6]);
 
 /* lbm_diagnostics in two halves, so that a caller reading the diagnostics of every step does
  * not stall the stream (no counterpart in the paper: a library service). lbm_diagnostics_begin
- * issues the diagnostics of the current state on the stream, with an asynchronous copy of the
- * per-block partial sums into a pinned host slot the handle owns (allocated at the first call),
- * and returns at once; lbm_diagnostics_end waits for the oldest pending request only and
- * reduces it into out[6] (as lbm_diagnostics; out[5] = the step count when it was issued). At
- * most two requests may be pending (LBM_ERR_STATE otherwise; also for an end without a
- * request). Typical use: step, begin, end of the previous step's request; stepping between a
- * begin and its end is expected, since a request reads the state at the point of the stream
- * where it was issued. An end reports LBM_ERR_TIMEOUT if a bounded device wait gave up before
- * its request. */
+ * requests the diagnostics of the current state and returns at once; lbm_diagnostics_end
+ * waits for the oldest pending request only and reduces it into out[6] (as lbm_diagnostics;
+ * out[5] = the step count when it was issued). A request's per-block partial sums come back by
+ * an asynchronous copy into a pinned host slot the handle owns (allocated at the first call).
+ * For LBM_MIXED handles with the forcing chain on, a request is fused into the next lbm_step:
+ * that step's first macroscopic pass, which holds the state's moments and density derivatives,
+ * also sums the diagnostics (no launch of their own); if no step comes before the end, or the
+ * state is replaced first (lbm_init, lbm_set_f, lbm_set_state, lbm_autotune), it is computed
+ * on its own then, from the same state. The fused form agrees with lbm_diagnostics to rounding
+ * (its d_x rho comes from the pass's own transform: the energy to ~1e-9). Other handles issue
+ * the computation at the begin (as lbm_diagnostics, bit for bit). At most two requests may be
+ * pending (LBM_ERR_STATE otherwise; also for an end without a request). Typical use: step,
+ * begin, end of the previous step's request. An end reports LBM_ERR_TIMEOUT if a bounded device
+ * wait gave up before its request. */
 int lbm_diagnostics_begin(lbm_handle h);
 int lbm_diagnostics_end(lbm_handle h, double out[6]);
 

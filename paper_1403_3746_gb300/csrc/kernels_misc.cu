@@ -100,33 +100,6 @@ __global__ void rho64_kernel(const float *f, double *r64, int nx, int ny) {
     }
 }
 
-// A float32 value pair hi + lo (about 48 significant bits) and its exact-sum update (Knuth's
-// TwoSum for hi, the error into lo), for sums of float32 terms without float64 arithmetic.
-struct FPair {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float t = __fadd_rn(hi, x);
-        const float bp = __fsub_rn(t, hi);
-        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
-        hi = t;
-    }
-    // x y added exactly: the product's rounding error from fmaf
-    __device__ __forceinline__ void add_prod(float x, float y) {
-        const float p = __fmul_rn(x, y);
-        add(p);
-        lo = __fadd_rn(lo, fmaf(x, y, -p));
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-    __device__ __forceinline__ void merge(const FPair &o) {
-        add(o.hi);
-        lo = __fadd_rn(lo, o.lo);
-    }
-    // the larger of two non-negative pairs (by hi, then lo)
-    __device__ __forceinline__ void take_max(const FPair &o) {
-        if (o.hi > hi || (o.hi == hi && o.lo > lo)) hi = o.hi, lo = o.lo;
-    }
-};
-
 // Per-block partial sums of mass, x/y momentum, e_T (Sec. 2.2) and the max of |u|^2.
 // float64 states: float64 arithmetic. float32 states: the large terms (rho, rho u, rho T,
 // 9/8 rho^2, |u|^2) enter as exact products and sums in float pairs, the small ones (the
@@ -178,52 +151,13 @@ __global__ void __launch_bounds__(256) diag_kernel(const __grid_constant__ DiagA
             const long long ro = (long long)y * a.ld;
             for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
                 const long long o = ro + x;
-                const float rho = prho[o], ux = pux[o], uy = puy[o], T = pT[o];
-                const float rx = prx[o], ry = pry[o];
-                S[0].add(rho);
-                S[1].add_prod(rho, ux);
-                S[2].add_prod(rho, uy);
-                FPair u2;  // |u|^2 exactly
-                u2.add_prod(ux, ux);
-                u2.add_prod(uy, uy);
-                S[3].add_prod(rho, T);
-                const float r2 = __fmul_rn(rho, rho), er2 = fmaf(rho, rho, -r2);  // rho^2 = r2 + er2
-                S[3].add_prod(-1.125f, r2);
-                S[3].lo = __fadd_rn(S[3].lo, fmaf(hK, fmaf(rx, rx, ry * ry), fmaf(-1.125f, er2, 0.5f * rho * u2.hi)));
-                S[4].take_max(u2);
+                diag_accumulate(S, prho[o], pux[o], puy[o], pT[o], prx[o], pry[o], hK);
             }
         }
-        // block reduction in float pairs (warp shuffles, then one warp over the warps' pairs);
-        // the block's pairs become float64 once
         __shared__ float wpart[32][5][2];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            for (int d = 16; d > 0; d >>= 1) {
-                FPair o;
-                o.hi = __shfl_down_sync(0xffffffffu, S[k].hi, d);
-                o.lo = __shfl_down_sync(0xffffffffu, S[k].lo, d);
-                if (k < 4) S[k].merge(o);
-                else S[k].take_max(o);
-            }
-            if (lane == 0) wpart[warp][k][0] = S[k].hi, wpart[warp][k][1] = S[k].lo;
-        }
+        diag_warp_reduce(S, wpart);
         __syncthreads();
-        if (warp == 0) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                FPair v;
-                if (lane < nw) v.hi = wpart[lane][k][0], v.lo = wpart[lane][k][1];
-                for (int d = 16; d > 0; d >>= 1) {
-                    FPair o;
-                    o.hi = __shfl_down_sync(0xffffffffu, v.hi, d);
-                    o.lo = __shfl_down_sync(0xffffffffu, v.lo, d);
-                    if (k < 4) v.merge(o);
-                    else v.take_max(o);
-                }
-                if (lane == 0) a.partial[blockIdx.x * 5 + k] = v.value();
-            }
-        }
+        diag_block_write(wpart, a.partial + blockIdx.x * 5);
     }
 }
 

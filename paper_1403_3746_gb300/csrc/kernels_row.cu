@@ -12,9 +12,9 @@
 
 namespace lbm {
 
-template <typename R, int LOG2N, bool SERIAL, bool RHO64>
+template <typename R, int LOG2N, bool SERIAL, bool RHO64, bool DIAG = false>
 __global__ void __launch_bounds__(MacroThreads<R, LOG2N>::value, MacroThreads<R, LOG2N>::min_blocks) macro_row_kernel(const __grid_constant__ MacroArgs<R> a) {
-    macro_rows<R, LOG2N, SERIAL, false, RHO64>(a, blockIdx.x);
+    macro_rows<R, LOG2N, SERIAL, false, RHO64, DIAG>(a, blockIdx.x);
 }
 
 template <typename R, int LOG2N, bool MOMENT_SPACE>
@@ -85,6 +85,15 @@ template <typename R, int LOG2N> static cudaError_t launch_macro_n(const MacroAr
         }
     }
     if (a.serial) return cudaErrorInvalidValue;
+    if (a.diag_partial && (sizeof(R) != 4 || a.r64)) return cudaErrorInvalidValue;
+    if constexpr (sizeof(R) == 4) {
+        if (a.diag_partial) {  // the diagnostics of the input state fused in
+            cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, false, false, true>);
+            if (e != cudaSuccess) return e;
+            macro_row_kernel<R, LOG2N, false, false, true><<<a.ny / a.rows, 2 * a.rows * F::G, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (sizeof(R) == 4) {  // the float64 density chain (LBM_MIXED_RHO64)
         if (a.r64) {
             cudaError_t e = allow_smem(macro_row_kernel<R, LOG2N, false, true>);

@@ -116,9 +116,20 @@ struct lbm_ctx {
     // pipelined diagnostics (lbm_diagnostics_begin / _end): two pinned host slots, each the
     // per-block partial sums and the error word of one request, and a ring of pending requests
     double *hpart = nullptr;
+    size_t dslot = 0;                 // doubles per slot: partial values, then the error word
+    int dnparts[2] = {0, 0};          // partial values (blocks) in each slot
     cudaEvent_t dev_ev[2] = {nullptr, nullptr};
     long long dsteps[2] = {0, 0};
     int dhead = 0, dcount = 0;
+    // a request fused into the next step: that step's first macro pass (which has the moments and
+    // the density derivatives of the requested state at hand) writes the partial values to fpart,
+    // one block per macro CTA; graph_diag is the step graph with that pass
+    int fuse_slot = -1;
+    int fuse_capture = -1;             // slot whose buffer the launches being issued write, or -1
+    double *fpart[2] = {nullptr, nullptr};            // per slot: the fused partial values
+    cudaGraphExec_t graph_diag[2] = {nullptr, nullptr};  // per slot: the step graph writing fpart[slot]
+    cudaStream_t dstream = nullptr;   // copies of fused partial values, off the stepping stream
+    cudaEvent_t fev[2] = {nullptr, nullptr};           // per slot: the fused step has written fpart
     int *err = nullptr;               // device error word of the bounded waits (tma::kErrTimeout)
     long long wait_cycles = 1LL << 31;  // budget of one device-side wait (about a second)
     int starve = 0;                   // fault-injection hook (lbm_fault_inject)
@@ -379,7 +390,11 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
         }
     }
     if (frc && (passes & PASS_MACRO)) {
-        const MacroArgs<R> a = macro_args<R>(c, c->geo.rows_macro);
+        MacroArgs<R> a = macro_args<R>(c, c->geo.rows_macro);
+        if (c->fuse_capture >= 0 && stage != 1) {  // the step's first macro pass: the state's diagnostics
+            a.diag_partial = c->fpart[c->fuse_capture];
+            a.diag_hK = (float)(0.5 * c->p.K);
+        }
         LaunchTimer t(c, LBM_K_MACRO);
         CU_TRY(launch_macro<R>(a, c->geo.macro_smem, c->stream));
     }
@@ -490,10 +505,15 @@ int capture_into(lbm_ctx *c, cudaStream_t s) {
     return rc;
 }
 
-int build_step_graph(lbm_ctx *c) {
+// One step's launches as a CUDA graph: c->graph, or for a fused diagnostics request in slot
+// `slot` (>= 0) c->graph_diag[slot], whose first macro pass also writes the diagnostics partial
+// values into fpart[slot].
+int build_step_graph(lbm_ctx *c, int slot = -1) {
     if (!c->cap) CU_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     CU_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+    c->fuse_capture = slot;
     const int rc = capture_into(c, c->cap);
+    c->fuse_capture = -1;
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
     if (rc) {
@@ -501,10 +521,20 @@ int build_step_graph(lbm_ctx *c) {
         return rc;
     }
     CU_TRY(e);
-    const cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+    const cudaError_t ei = cudaGraphInstantiate(slot >= 0 ? &c->graph_diag[slot] : &c->graph, g, 0);
     cudaGraphDestroy(g);
     CU_TRY(ei);
     return LBM_OK;
+}
+
+// Drops the step graphs (recaptured at the next step, e.g. with new launch shapes).
+void drop_graphs(lbm_ctx *c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    for (cudaGraphExec_t &g : c->graph_diag) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
 }
 
 // ---- autotuner: tile and CTA shapes by measurement ------------------------------------
@@ -560,10 +590,7 @@ template <typename R> int run_stage(lbm_ctx *c, int stage, int passes);
 // also changes what it leaves in L2 for the next pass. The steps advance the state, which the
 // caller saves and restores.
 int time_step(lbm_ctx *c, void *flush, size_t flush_bytes, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c);
     int rc = build_step_graph(c);
     if (rc) return rc;
     CU_TRY(cudaGraphLaunch(c->graph, c->stream));
@@ -612,10 +639,7 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
             if (saved) restore();
             cudaStreamSynchronize(c->stream);
         }
-        if (c->graph) {  // recaptured with the chosen shapes at the next step
-            cudaGraphExecDestroy(c->graph);
-            c->graph = nullptr;
-        }
+        drop_graphs(c);  // recaptured with the chosen shapes at the next step
         if (save) cudaFree(save);
         if (save_f) cudaFree(save_f);
         if (flush) cudaFree(flush);
@@ -744,7 +768,14 @@ void free_ctx(lbm_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    if (c->dstream) cudaStreamSynchronize(c->dstream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph_diag[k]) cudaGraphExecDestroy(c->graph_diag[k]);
+        if (c->fpart[k]) cudaFree(c->fpart[k]);
+        if (c->fev[k]) cudaEventDestroy(c->fev[k]);
+    }
+    if (c->dstream) cudaStreamDestroy(c->dstream);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : c->dev_ev)
@@ -1200,9 +1231,9 @@ int diagnostics_instance(lbm_ctx *c, int k, long long steps, double out[6]) {
 }
 
 // host reduction of one slot of per-block partial sums into out[0..4]
-int reduce_partials(const lbm_ctx *c, const double *part, double out[6]) {
+int reduce_partials(const lbm_ctx *c, const double *part, int nparts, double out[6]) {
     double s[4] = {0, 0, 0, 0}, mx = 0;
-    for (int b = 0; b < c->diag_blocks; ++b) {
+    for (int b = 0; b < nparts; ++b) {
         for (int j = 0; j < 4; ++j) s[j] += part[b * 5 + j];
         mx = std::max(mx, part[b * 5 + 4]);
     }
@@ -1336,20 +1367,31 @@ int lbm_create(int nx, int ny, const lbm_params *params, void *stream, lbm_handl
 
 void lbm_destroy(lbm_handle c) { free_ctx(c); }
 
+int diag_flush(lbm_ctx *c);
+int step_with_diag(lbm_ctx *c);
+
 int lbm_init(lbm_handle c, const double *rho, const double *ux, const double *uy, const double *T) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
-    return init_instance_host(c, 0, rho, ux, uy, T);
+    const int rc = diag_flush(c);
+    return rc ? rc : init_instance_host(c, 0, rho, ux, uy, T);
 }
 
 int lbm_init_device(lbm_handle c, const double *rho, const double *ux, const double *uy, const double *T) {
     if (!c || !rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "NULL argument");
-    return init_instance(c, 0, rho, ux, uy, T);
+    const int rc = diag_flush(c);
+    return rc ? rc : init_instance(c, 0, rho, ux, uy, T);
 }
 
 int lbm_step(lbm_handle c, int n) {
     if (!c || n < 0) return fail(LBM_ERR_ARG, "bad handle or n < 0");
     if (!c->all_initialized()) return fail(LBM_ERR_STATE, "lbm_step before lbm_init / lbm_set_f");
     if (n == 0) return LBM_OK;
+    if (c->fuse_slot >= 0) {  // a diagnostics request of the current state rides on this step
+        const int rc = step_with_diag(c);
+        if (rc) return rc;
+        ++c->steps;
+        if (--n == 0) return LBM_OK;
+    }
     if (c->timing) {  // direct launches, each between the timing events
         for (int s = 0; s < n; ++s) {
             int rc = run_step_launches(c);
@@ -1390,7 +1432,8 @@ int lbm_get_f(lbm_handle c, double *f16) {
 
 int lbm_set_f(lbm_handle c, const double *f16) {
     if (!c || !f16) return fail(LBM_ERR_ARG, "NULL argument");
-    return set_f_host(c, 0, f16);
+    const int rc = diag_flush(c);
+    return rc ? rc : set_f_host(c, 0, f16);
 }
 
 size_t lbm_state_bytes(int nx, int ny, int precision) {
@@ -1412,6 +1455,7 @@ int lbm_set_state(lbm_handle c, const void *blob, size_t bytes) {
     long long steps = 0;
     int rc = check_state(c, blob, bytes, &steps);
     if (rc) return rc;
+    if ((rc = diag_flush(c))) return rc;
     rc = set_state_host(c, 0, blob);
     if (rc) return rc;
     c->steps = steps;
@@ -1424,13 +1468,78 @@ int lbm_diagnostics(lbm_handle c, double out[6]) {
     return diagnostics_instance(c, 0, c->steps, out);
 }
 
+// A diagnostics request can be fused into the next step when that step's first macro pass
+// computes it: float32 passes (LBM_MIXED), the forcing chain on, one instance.
+static bool diag_fusable(const lbm_ctx *c) {
+    return c->mixed && !c->rho64 && !(c->p.flags & LBM_FLAG_NO_FORCE) && !c->geo.macro_serial && c->nb == 1;
+}
+
+// Queues the copy of `nparts` partial values from `dev` and the error word into slot `slot`, and
+// the slot's event.
+static int diag_copy_out(lbm_ctx *c, int slot, const double *dev, int nparts) {
+    double *h = c->hpart + slot * c->dslot;
+    CU_TRY(cudaMemcpyAsync(h, dev, (size_t)nparts * 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaMemcpyAsync(h + c->dslot - 1, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaEventRecord(c->dev_ev[slot], c->stream));
+    c->dnparts[slot] = nparts;
+    return LBM_OK;
+}
+
+// The standalone form of a request: the diagnostics of the current state into slot `slot`.
+static int diag_standalone(lbm_ctx *c, int slot) {
+    int rc = c->mixed ? diag_launch<float>(c, 0) : diag_launch<double>(c, 0);
+    if (rc) return rc;
+    return diag_copy_out(c, slot, c->partial, c->diag_blocks);
+}
+
+// A request still waiting for a step is computed now, before the state changes other than by
+// a step (init, set_f, set_state, autotune).
+int diag_flush(lbm_ctx *c) {
+    if (c->fuse_slot < 0) return LBM_OK;
+    const int slot = c->fuse_slot;
+    c->fuse_slot = -1;
+    return diag_standalone(c, slot);
+}
+
+// The fused request's step: the step graph whose first macro pass writes the partial values
+// into the slot's buffer; their copy to the host slot runs on a side stream after that step,
+// so the stepping stream goes on at once. The slot's previous copy has been waited for by the
+// lbm_diagnostics_end that freed the slot.
+int step_with_diag(lbm_ctx *c) {
+    const int slot = c->fuse_slot;
+    c->fuse_slot = -1;
+    if (c->timing) {
+        c->fuse_capture = slot;
+        const int rc = run_step_launches(c);
+        c->fuse_capture = -1;
+        if (rc) return rc;
+    } else {
+        if (!c->graph_diag[slot]) {
+            const int rc = build_step_graph(c, slot);
+            if (rc) return rc;
+        }
+        CU_TRY(cudaGraphLaunch(c->graph_diag[slot], c->stream));
+    }
+    CU_TRY(cudaEventRecord(c->fev[slot], c->stream));
+    CU_TRY(cudaStreamWaitEvent(c->dstream, c->fev[slot], 0));
+    double *h = c->hpart + slot * c->dslot;
+    const int nparts = (c->nb * c->ny) / c->geo.rows_macro;
+    CU_TRY(cudaMemcpyAsync(h, c->fpart[slot], (size_t)nparts * 5 * sizeof(double), cudaMemcpyDeviceToHost, c->dstream));
+    CU_TRY(cudaMemcpyAsync(h + c->dslot - 1, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->dstream));
+    CU_TRY(cudaEventRecord(c->dev_ev[slot], c->dstream));
+    c->dnparts[slot] = nparts;
+    return LBM_OK;
+}
+
 int lbm_diagnostics_begin(lbm_handle c) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
     if (!c->all_initialized()) return fail(LBM_ERR_STATE, "no state yet");
     if (c->dcount == 2) return fail(LBM_ERR_STATE, "two requests pending: call lbm_diagnostics_end first");
-    const size_t slot_doubles = (size_t)c->diag_blocks * 5 + 1;  // partials, then the error word
     if (!c->hpart) {
-        if (cudaHostAlloc(&c->hpart, 2 * slot_doubles * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+        // per slot: the partial values of the larger of the diagnostics kernel's blocks and the
+        // macro pass's CTAs (one row each at most), then the error word
+        c->dslot = (size_t)std::max(c->diag_blocks, c->nb * c->ny) * 5 + 1;
+        if (cudaHostAlloc(&c->hpart, 2 * c->dslot * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             c->hpart = nullptr;
             return fail(LBM_ERR_NOMEM, "no pinned host memory for the diagnostics slots");
@@ -1438,13 +1547,21 @@ int lbm_diagnostics_begin(lbm_handle c) {
         for (cudaEvent_t &e : c->dev_ev) CU_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     const int slot = (c->dhead + c->dcount) & 1;
-    double *h = c->hpart + slot * slot_doubles;
-    int rc = c->mixed ? diag_launch<float>(c, 0) : diag_launch<double>(c, 0);
-    if (rc) return rc;
-    CU_TRY(cudaMemcpyAsync(h, c->partial, (slot_doubles - 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CU_TRY(cudaMemcpyAsync(h + slot_doubles - 1, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CU_TRY(cudaEventRecord(c->dev_ev[slot], c->stream));
     c->dsteps[slot] = c->steps;
+    if (diag_fusable(c) && c->fuse_slot < 0) {  // computed by the next step (or at lbm_diagnostics_end)
+        if (!c->dstream) {
+            bool ok = cudaStreamCreateWithFlags(&c->dstream, cudaStreamNonBlocking) == cudaSuccess;
+            for (int k = 0; k < 2 && ok; ++k)
+                ok = cudaMalloc(&c->fpart[k], (size_t)c->nb * c->ny * 5 * sizeof(double)) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&c->fev[k], cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) return fail(LBM_ERR_NOMEM, "no device memory or stream for the fused diagnostics");
+        }
+        c->fuse_slot = slot;
+        ++c->dcount;
+        return LBM_OK;
+    }
+    const int rc = diag_standalone(c, slot);
+    if (rc) return rc;
     ++c->dcount;
     return LBM_OK;
 }
@@ -1452,20 +1569,23 @@ int lbm_diagnostics_begin(lbm_handle c) {
 int lbm_diagnostics_end(lbm_handle c, double out[6]) {
     if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");
     if (c->dcount == 0) return fail(LBM_ERR_STATE, "no diagnostics request pending");
-    const size_t slot_doubles = (size_t)c->diag_blocks * 5 + 1;
     const int slot = c->dhead;
+    if (slot == c->fuse_slot) {  // no step since the request: computed on its own now
+        const int rc = diag_flush(c);
+        if (rc) return rc;
+    }
     c->dhead ^= 1;
     --c->dcount;
     CU_TRY(cudaEventSynchronize(c->dev_ev[slot]));
-    const double *h = c->hpart + slot * slot_doubles;
+    const double *h = c->hpart + slot * c->dslot;
     int err = 0;
-    std::memcpy(&err, h + slot_doubles - 1, sizeof err);
+    std::memcpy(&err, h + c->dslot - 1, sizeof err);
     if (err) {
         CU_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
         return fail(LBM_ERR_TIMEOUT, "a bounded device-side wait gave up (error word %d) before this request", err);
     }
     out[5] = (double)c->dsteps[slot];
-    return reduce_partials(c, h, out);
+    return reduce_partials(c, h, c->dnparts[slot], out);
 }
 
 int lbm_synchronize(lbm_handle c) {
@@ -1501,10 +1621,7 @@ int lbm_set_pass_kinds(lbm_handle c, const int kinds[3]) {
     c->geo.flux_kind = kinds[1];
     c->geo.upd_cs = kinds[2];
     c->geo.upd_smem = upd_smem(c->geo.rows_upd, c->lx, c->fsize, c->geo.upd_cs);
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c);
     return LBM_OK;
 }
 
@@ -1513,10 +1630,7 @@ int lbm_fault_inject(lbm_handle c, int what, long long wait_cycles) {
     CU_TRY(cudaStreamSynchronize(c->stream));
     c->starve = what == LBM_FAULT_STARVE_COPIES ? 1 : 0;
     c->wait_cycles = wait_cycles > 0 ? wait_cycles : (1LL << 31);
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c);
     return LBM_OK;
 }
 
@@ -1613,17 +1727,16 @@ int lbm_set_geometry(lbm_handle c, const int geometry[4]) {
         if (geometry[2] != 1) c->geo.upd_cs = 1;
         c->geo.upd_smem = upd_smem(geometry[2], c->lx, es, c->geo.upd_cs);
     }
-    if (c->graph) {  // recaptured with the new shapes at the next step
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c);  // recaptured with the new shapes at the next step
     return LBM_OK;
 }
 
 int lbm_autotune(lbm_handle c, int geometry[4], double ms[4]) {
     if (!c) return fail(LBM_ERR_ARG, "NULL handle");
     float t[4] = {0, 0, 0, 0};
-    const int rc = autotune_ctx(c, t);
+    int rc = diag_flush(c);
+    if (rc) return rc;
+    rc = autotune_ctx(c, t);
     if (rc) return rc;
     if (ms)
         for (int k = 0; k < 4; ++k) ms[k] = t[k];

@@ -217,6 +217,10 @@ template <typename R> struct MacroArgs {
     // parameters in float64 for the terms evaluated in float64
     const double *r64;
     double K64, H64, q64, zeta64;
+    // diagnostics of the stage's input state fused into the pass (float32, nullptr otherwise):
+    // five float64 partial values per CTA (as the diagnostics kernel writes them), hK = K/2
+    double *diag_partial;
+    float diag_hK;
 };
 // fields of the float64 density chain (LBM_MIXED_RHO64): rho = the float64 sum of the stored f,
 // d_x rho, d_xx rho (row derivatives), d_y rho, d_yy rho (column derivatives)
@@ -304,6 +308,87 @@ struct MomArgs {
     double b;
     double T_iso;  // > 0: isothermal (stored as the temperature field)
 };
+
+// ---- diagnostics of float32 states: exact float-pair sums ----------------------------
+// A float32 value pair hi + lo (about 48 significant bits) and its exact-sum update (Knuth's
+// TwoSum for hi, the error into lo), for sums of float32 terms without float64 arithmetic
+// (GB300's float64 rate is 1/64 of float32).
+struct FPair {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(hi, x);
+        const float bp = __fsub_rn(t, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+        hi = t;
+    }
+    // x y added exactly: the product's rounding error from fmaf
+    __device__ __forceinline__ void add_prod(float x, float y) {
+        const float p = __fmul_rn(x, y);
+        add(p);
+        lo = __fadd_rn(lo, fmaf(x, y, -p));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ void merge(const FPair &o) {
+        add(o.hi);
+        lo = __fadd_rn(lo, o.lo);
+    }
+    // the larger of two non-negative pairs (by hi, then lo)
+    __device__ __forceinline__ void take_max(const FPair &o) {
+        if (o.hi > hi || (o.hi == hi && o.lo > lo)) hi = o.hi, lo = o.lo;
+    }
+};
+// One node's share of the diagnostics (Sec. 2.2): mass rho, momentum rho u, the energy density
+// e_T = rho T - 9/8 rho^2 + K/2 |grad rho|^2 + rho |u|^2 / 2, and |u|^2 for its maximum. The
+// large terms (rho, rho u, rho T, 9/8 rho^2, |u|^2) enter exactly as float pairs, the small
+// ones (the gradient and kinetic parts of e_T) in float32. hK = K/2.
+__device__ __forceinline__ void diag_accumulate(FPair S[5], float rho, float ux, float uy, float T, float rx, float ry,
+                                                float hK) {
+    S[0].add(rho);
+    S[1].add_prod(rho, ux);
+    S[2].add_prod(rho, uy);
+    FPair u2;  // |u|^2 exactly
+    u2.add_prod(ux, ux);
+    u2.add_prod(uy, uy);
+    S[3].add_prod(rho, T);
+    const float r2 = __fmul_rn(rho, rho), er2 = fmaf(rho, rho, -r2);  // rho^2 = r2 + er2
+    S[3].add_prod(-1.125f, r2);
+    S[3].lo = __fadd_rn(S[3].lo, fmaf(hK, fmaf(rx, rx, ry * ry), fmaf(-1.125f, er2, 0.5f * rho * u2.hi)));
+    S[4].take_max(u2);
+}
+// Block reduction, part 1 (every thread): each warp's pairs by shuffles into wpart[warp].
+__device__ __forceinline__ void diag_warp_reduce(FPair S[5], float (*wpart)[5][2]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        for (int d = 16; d > 0; d >>= 1) {
+            FPair o;
+            o.hi = __shfl_down_sync(0xffffffffu, S[k].hi, d);
+            o.lo = __shfl_down_sync(0xffffffffu, S[k].lo, d);
+            if (k < 4) S[k].merge(o);
+            else S[k].take_max(o);
+        }
+        if (lane == 0) wpart[warp][k][0] = S[k].hi, wpart[warp][k][1] = S[k].lo;
+    }
+}
+// Part 2 (after a CTA barrier; the first warp works): the warps' pairs into the block's five
+// float64 partial values (sums of mass, x and y momentum, e_T; the max of |u|^2).
+__device__ __forceinline__ void diag_block_write(const float (*wpart)[5][2], double *out) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (threadIdx.x >= 32) return;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        FPair v;
+        if (lane < nw) v.hi = wpart[lane][k][0], v.lo = wpart[lane][k][1];
+        for (int d = 16; d > 0; d >>= 1) {
+            FPair o;
+            o.hi = __shfl_down_sync(0xffffffffu, v.hi, d);
+            o.lo = __shfl_down_sync(0xffffffffu, v.lo, d);
+            if (k < 4) v.merge(o);
+            else v.take_max(o);
+        }
+        if (lane == 0) out[k] = v.value();
+    }
+}
 
 // rho, u, T, d_x rho, d_y rho: row y of each at p + y * ld
 struct DiagArgs {

@@ -103,8 +103,10 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
 // RHO64 (LBM_MIXED_RHO64): rho and its derivatives come from the float64 density chain
 // (a.r64) and the node loop's rho-dependent terms (P^w, Lambda, S, Q, the C numerator) are
 // evaluated in float64, then rounded to the path's type; d_y rho is also written to M_RY for the
-// update pass.
-template <typename R, int LOG2N, bool SERIAL, bool EXTRA = false, bool RHO64 = false>
+// update pass. DIAG (float32): the node loop also accumulates the diagnostics of the stage's
+// input state (the nodes' rho, u, T and the d_x rho, d_y rho it has at hand) and the CTA writes
+// its five partial values to a.diag_partial, as the diagnostics kernel would.
+template <typename R, int LOG2N, bool SERIAL, bool EXTRA = false, bool RHO64 = false, bool DIAG = false>
 __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
     using F = reg::LineFFT<R, LOG2N, true>;
     using CT = typename F::CT;
@@ -174,6 +176,8 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
     using D = std::conditional_t<RHO64, double, R>;  // type of the rho-dependent terms
     const D K = RHO64 ? (D)a.K64 : (D)a.K, H = RHO64 ? (D)a.H64 : (D)a.H, q = RHO64 ? (D)a.q64 : (D)a.q,
             zeta = RHO64 ? (D)a.zeta64 : (D)a.zeta;
+    static_assert(!DIAG || (sizeof(R) == 4 && !RHO64 && !SERIAL && !EXTRA), "fused diagnostics: float32 pass only");
+    FPair dS[DIAG ? 5 : 1];
     for (int idx = threadIdx.x; idx < nodes; idx += blockDim.x) {
         const int rr = idx / NX, x = idx % NX;
         R *mn = a.m + (size_t)(y0 + rr) * NF_M * NX + x;  // this node: field k at mn[k * NX]
@@ -199,6 +203,10 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
             ry = __ldcg(mn + M_RY * NX);
             ryy = __ldcg(mn + M_RYY * NX);
         }
+
+        if constexpr (DIAG)
+            diag_accumulate(dS, (float)rho, __ldcg(mn + M_UX * NX), __ldcg(mn + M_UY * NX), (float)T, (float)rx,
+                            (float)ry, a.diag_hK);
 
         const D lap = rxx + ryy;
         const D divu = dux_dx + duy_dy;
@@ -230,6 +238,12 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
         mn[M_DIVU * NX] = (R)divu;
         A1[x] = reg::mk<R>((R)Qx, (R)Sxx);  // round-2 lines, same node and thread as the reads above
         B1[x] = reg::mk<R>((R)Sxy, (R)divu);
+    }
+    if constexpr (DIAG) {
+        __shared__ float dwarp[32][5][2];
+        diag_warp_reduce(dS, dwarp);
+        __syncthreads();
+        diag_block_write(dwarp, a.diag_partial + (size_t)blk * 5);
     }
     __syncthreads();
 
