@@ -391,12 +391,24 @@ int run_stage(lbm_ctx *c, int stage, int passes = PASS_ALL) {
     }
     if (frc && (passes & PASS_MACRO)) {
         MacroArgs<R> a = macro_args<R>(c, c->geo.rows_macro);
-        if (c->fuse_capture >= 0 && stage != 1) {  // the step's first macro pass: the state's diagnostics
+        const bool fused = c->fuse_capture >= 0 && stage != 1;
+        if (fused) {  // the step's first macro pass: the state's diagnostics
             a.diag_partial = c->fpart[c->fuse_capture];
             a.diag_hK = (float)(0.5 * c->p.K);
         }
-        LaunchTimer t(c, LBM_K_MACRO);
-        CU_TRY(launch_macro<R>(a, c->geo.macro_smem, c->stream));
+        {
+            LaunchTimer t(c, LBM_K_MACRO);
+            CU_TRY(launch_macro<R>(a, c->geo.macro_smem, c->stream));
+        }
+        // the partial values are ready here: their copy can start while the step goes on (in a
+        // captured step an external event-record node, which streams outside the graph can wait on)
+        if (fused) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            CU_TRY(cudaStreamIsCapturing(c->stream, &cs));
+            CU_TRY(cs == cudaStreamCaptureStatusActive
+                       ? cudaEventRecordWithFlags(c->fev[c->fuse_capture], c->stream, cudaEventRecordExternal)
+                       : cudaEventRecord(c->fev[c->fuse_capture], c->stream));
+        }
     }
     if (frc && (passes & PASS_FLUX)) {
         ColArgs<R> a = col_args<R>(c, c->nb, c->geo.fluxW);
@@ -1502,9 +1514,10 @@ int diag_flush(lbm_ctx *c) {
 }
 
 // The fused request's step: the step graph whose first macro pass writes the partial values
-// into the slot's buffer; their copy to the host slot runs on a side stream after that step,
-// so the stepping stream goes on at once. The slot's previous copy has been waited for by the
-// lbm_diagnostics_end that freed the slot.
+// into the slot's buffer and then records the slot's event; their copy to the host slot runs on
+// a side stream from that event, while the rest of the step runs, so lbm_diagnostics_end
+// returns before the step ends and the caller can queue the next step in time. The slot's
+// previous copy has been waited for by the lbm_diagnostics_end that freed the slot.
 int step_with_diag(lbm_ctx *c) {
     const int slot = c->fuse_slot;
     c->fuse_slot = -1;
@@ -1520,7 +1533,6 @@ int step_with_diag(lbm_ctx *c) {
         }
         CU_TRY(cudaGraphLaunch(c->graph_diag[slot], c->stream));
     }
-    CU_TRY(cudaEventRecord(c->fev[slot], c->stream));
     CU_TRY(cudaStreamWaitEvent(c->dstream, c->fev[slot], 0));
     double *h = c->hpart + slot * c->dslot;
     const int nparts = (c->nb * c->ny) / c->geo.rows_macro;
