@@ -244,6 +244,24 @@ cudaError_t launch_rho64(const float *f, double *r64, int nx, int ny, cudaStream
     return cudaGetLastError();
 }
 
+// Validity of initial fields (0 < rho < 3, T > 0 and finite, u finite): the lowest index of a
+// node that fails, by atomicMin into *bad (left untouched when every node passes).
+__global__ void check_init_kernel(const double *rho, const double *ux, const double *uy, const double *T,
+                                  long long n, unsigned long long *bad) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
+         g += (long long)gridDim.x * blockDim.x) {
+        const double r = rho[g], t = T[g];
+        if (!(r > 0.0 && r < 3.0) || !(t > 0.0) || !isfinite(t) || !isfinite(ux[g]) || !isfinite(uy[g]))
+            atomicMin(bad, (unsigned long long)g);
+    }
+}
+
+cudaError_t launch_check_init(const double *rho, const double *ux, const double *uy, const double *T, long long n,
+                              unsigned long long *bad, cudaStream_t s) {
+    check_init_kernel<<<grid_for(n), 256, 0, s>>>(rho, ux, uy, T, n, bad);
+    return cudaGetLastError();
+}
+
 template <typename F> cudaError_t launch_init(const InitArgs &a, cudaStream_t s) {
     init_feq_kernel<F><<<grid_for((long long)a.nx * a.ny), 256, 0, s>>>(a);
     return cudaGetLastError();

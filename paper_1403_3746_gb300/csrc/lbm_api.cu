@@ -131,6 +131,7 @@ struct lbm_ctx {
     cudaStream_t dstream = nullptr;   // copies of fused partial values, off the stepping stream
     cudaEvent_t fev[2] = {nullptr, nullptr};           // per slot: the fused step has written fpart
     int *err = nullptr;               // device error word of the bounded waits (tma::kErrTimeout)
+    unsigned long long *bad = nullptr;  // lowest failing node of the last initial-field check
     long long wait_cycles = 1LL << 31;  // budget of one device-side wait (about a second)
     int starve = 0;                   // fault-injection hook (lbm_fault_inject)
     // per-axis tables
@@ -862,6 +863,7 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     if (c->rho64) parts.push_back({reinterpret_cast<void **>(&c->r64), (size_t)NR64 * c->n * nb * sizeof(double)});
     parts.push_back({reinterpret_cast<void **>(&c->partial), (size_t)c->diag_blocks * 5 * 8});
     parts.push_back({reinterpret_cast<void **>(&c->err), sizeof(int)});
+    parts.push_back({reinterpret_cast<void **>(&c->bad), sizeof(unsigned long long)});
     parts.push_back({reinterpret_cast<void **>(&c->tw64x), (size_t)nx * 16});
     parts.push_back({reinterpret_cast<void **>(&c->tw64y), (size_t)ny * 16});
     parts.push_back({reinterpret_cast<void **>(&c->tw32x), (size_t)nx * 8});
@@ -963,23 +965,22 @@ int init_instance(lbm_ctx *c, int k, const double *rho, const double *ux, const 
 
 int init_instance_host(lbm_ctx *c, int k, const double *rho, const double *ux, const double *uy, const double *T) {
     if (!rho || !ux || !uy || !T) return fail(LBM_ERR_ARG, "NULL argument");
-    for (long long g = 0; g < c->n; ++g) {
-        if (!(rho[g] > 0.0 && rho[g] < 3.0) || !(T[g] > 0.0) || !std::isfinite(T[g]) || !std::isfinite(ux[g]) ||
-            !std::isfinite(uy[g]))
-            return fail(LBM_ERR_ARG, "node %lld: need 0 < rho < 3, T > 0 and finite u", g);
-    }
     // stage the four float64 fields in the half-step buffer f1 (free outside a step;
-    // it holds at least 16 * 4 bytes per node >= 4 * 8)
+    // it holds at least 16 * 4 bytes per node >= 4 * 8), check them there, and only then
+    // replace the state
     const size_t bytes = (size_t)c->n * 8;
     double *st = static_cast<double *>(c->f1);
     CU_TRY(cudaMemcpyAsync(st, rho, bytes, cudaMemcpyHostToDevice, c->stream));
     CU_TRY(cudaMemcpyAsync(st + c->n, ux, bytes, cudaMemcpyHostToDevice, c->stream));
     CU_TRY(cudaMemcpyAsync(st + 2 * c->n, uy, bytes, cudaMemcpyHostToDevice, c->stream));
     CU_TRY(cudaMemcpyAsync(st + 3 * c->n, T, bytes, cudaMemcpyHostToDevice, c->stream));
-    int rc = init_instance(c, k, st, st + c->n, st + 2 * c->n, st + 3 * c->n);
-    if (rc) return rc;
-    CU_TRY(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    CU_TRY(cudaMemsetAsync(c->bad, 0xff, sizeof(unsigned long long), c->stream));
+    CU_TRY(launch_check_init(st, st + c->n, st + 2 * c->n, st + 3 * c->n, c->n, c->bad, c->stream));
+    unsigned long long bad = 0;
+    CU_TRY(cudaMemcpyAsync(&bad, c->bad, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));  // the host buffers are free from here on
+    if (bad != ~0ULL) return fail(LBM_ERR_ARG, "node %llu: need 0 < rho < 3, T > 0 and finite u", bad);
+    return init_instance(c, k, st, st + c->n, st + 2 * c->n, st + 3 * c->n);
 }
 
 // rho, u_x, u_y, T (macro fields 0..3) of instance k as dense float64 [ny][nx] device arrays

@@ -227,6 +227,9 @@ template <typename R> struct MacroArgs {
 enum Rho64Field { R64_RHO, R64_RX, R64_RXX, R64_RY, R64_RYY, NR64 };
 // rho in float64 as the sum of the 16 stored distributions of each node (f: [ny][16][nx])
 cudaError_t launch_rho64(const float *f, double *r64, int nx, int ny, cudaStream_t s);
+// initial-field validity: the lowest failing node index into *bad (untouched if none fails)
+cudaError_t launch_check_init(const double *rho, const double *ux, const double *uy, const double *T, long long n,
+                              unsigned long long *bad, cudaStream_t s);
 
 // ---- fused update row pass -----------------------------------------------------------
 // tables of the model read with compile-time indices by the node loop (kernel parameters, so
