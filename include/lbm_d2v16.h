@@ -41,7 +41,7 @@ extern "C" {
 #define LBM_ERR_NONFINITE (-4) /* a NaN or Inf was found in the state */
 #define LBM_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define LBM_ERR_STATE (-6)     /* call out of order (e.g. lbm_step before lbm_init) */
-#define LBM_ERR_UNSUPPORTED (-7) /* size or precision not supported by this build */
+#define LBM_ERR_UNSUPPORTED (-7) /* size or precision not supported by the library */
 
 /* precision of the hot path */
 #define LBM_FP64 0   /* every step in float64 (the plain method) */
