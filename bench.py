@@ -300,7 +300,7 @@ def large_run(lbm, torch, synthetic, steps, stream):
             ms = e0.elapsed_time(e1) / steps
             S[name] = sim.structure_factor(nbins)[0]
             out[name] = {"value": n / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
-                         "launch_shapes": list(sim.geometry())}
+                         "launch_shapes": list(sim.geometry()) + list(sim.pass_kinds())}
     out["mixed"]["step_frac_of_hbm_roofline"] = (ELEMS_PER_NODE_STEP * 4 * n / (out["mixed"]["ms_per_step"] * 1e-3)
                                                  / 1e9 / peaks()[0])
     k = int(np.argmax(S["fp64"][1:])) + 1

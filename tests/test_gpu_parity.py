@@ -279,6 +279,20 @@ def test_mixed_rho64_forcing_only(nx, ny):
     assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
 
 
+def test_mixed_droplet_128_against_oracle():
+    # a droplet of the error table's runs (128^2, R = 16, T = 0.9, phase-separation set) after 100
+    # steps, mixed path against the FP64 oracle directly (the table itself compares mixed with the
+    # FP64 GPU path over 10^4 steps); the same bounds as the slab
+    T = 0.9
+    rl, rv = oracle.coexistence(T)
+    fields = synthetic.droplet(128, 128, 16, rl, rv, T, width=2.0)
+    fo, mo = run_oracle(fields, 100)
+    fg, mg = run_gpu(fields, 100, **MIX)
+    ef, er, eu, eT = mixed_errors(fg, mg, fo, mo)
+    print(f"mixed droplet 128^2 x 100: f {ef:.2e}, rho {er:.2e}, |du| {eu:.2e}, T {eT:.2e}")
+    assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
+
+
 def test_mixed_rows_of_4096():
     # float32 rows of 4096: the update pass's 6 line buffers take 209 KB of shared memory
     fields = slab_fields(4096, 8)
