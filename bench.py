@@ -434,6 +434,15 @@ def profile_main(args):
             sim.step(2)
             sim.synchronize()
             out = {"profile": "large", "n": LARGE_N, "steps": 3, "launch_shapes": list(sim.geometry()) + list(sim.pass_kinds())}
+    elif args.profile == "tma":
+        fields = make_fields(lbm, synthetic)
+        with lbm.Simulation(N_GRID, N_GRID, p) as sim:
+            sim.init(*fields)
+            sim.set_pass_kinds((lbm.LBM_COL_TMA, lbm.LBM_COL_TMA, 1))
+            sim.step(1)
+            sim.step(2)
+            sim.synchronize()
+            out = {"profile": "tma", "n": N_GRID, "steps": 3, "launch_shapes": list(sim.geometry()) + list(sim.pass_kinds())}
     else:
         fields = make_fields(lbm, synthetic)
         with lbm.Simulation(N_GRID, N_GRID, p) as sim:
@@ -455,10 +464,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched form and the error table")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (for profiler runs, whose timing would mislead the tuner)")
-    ap.add_argument("--profile", choices=["large", "diag"], default=None,
+    ap.add_argument("--profile", choices=["large", "diag", "tma"], default=None,
                     help="a fixed short launch sequence for ncu launch lists (default shapes, no timing): "
                          "large = 4096^2 mixed spinodal, init + 1 + 2 steps; diag = 1024^2 mixed droplet, "
-                         "init + 1 step + 3 diagnostics requests")
+                         "init + 1 step + 3 diagnostics requests; tma = the 1024^2 droplet with both column "
+                         "passes in the TMA form (16-column tiles), init + 1 + 2 steps")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
