@@ -164,7 +164,9 @@ int lbm_diagnostics(lbm_handle h, double out[6]);
  * an asynchronous copy into a pinned host slot the handle owns (allocated at the first call).
  * For LBM_MIXED handles with the forcing chain on, a request is fused into the next lbm_step:
  * that step's first macroscopic pass, which holds the state's moments and density derivatives,
- * also sums the diagnostics (no launch of their own); if no step comes before the end, or the
+ * also sums the diagnostics (no launch of their own; their copy runs on a side stream the handle
+ * owns, after an event recorded on the handle's stream right after that pass, so the end returns
+ * while the rest of the step runs); if no step comes before the end, or the
  * state is replaced first (lbm_init, lbm_set_f, lbm_set_state, lbm_autotune), it is computed
  * on its own then, from the same state. The fused form agrees with lbm_diagnostics to rounding
  * (its d_x rho comes from the pass's own transform: the energy to ~1e-9). Other handles issue
