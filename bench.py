@@ -281,7 +281,7 @@ def large_run(lbm, torch, synthetic, steps, stream):
     same seed."""
     fields = synthetic.spinodal(LARGE_N, LARGE_N, 1.0, 0.01, 0.9, seed=5)
     n = LARGE_N * LARGE_N
-    nbins = 256
+    nbins = int(np.ceil(np.sqrt(2) * LARGE_N / 2)) + 2  # every shell of the box
     out = {"workload": f"spinodal quench {LARGE_N}x{LARGE_N}, rho = 1 +/- 1% (seed 5), T = 0.9", "steps": steps}
     S = {}
     for prec, name in ((lbm.LBM_MIXED, "mixed"), (lbm.LBM_FP64, "fp64")):

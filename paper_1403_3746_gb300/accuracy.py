@@ -20,7 +20,7 @@ import numpy as np
 
 import synthetic
 
-from . import Batch, LBM_FP64, LBM_MIXED, LBM_MIXED_RHO64, default_params, maxwell
+from . import Batch, LBM_FP64, LBM_MIXED, LBM_MIXED_RHO64, Simulation, default_params, maxwell
 
 PHASE = dict(tau=1e-4, dt=1e-4, dx=1 / 256, dy=1 / 256, K=5e-6, q=-0.004, b=2.0)
 
@@ -162,3 +162,29 @@ def laplace_check(radii=(12, 16, 24, 32), n=128, T=0.9, steps=100000, slab_steps
             r_eq = equimolar_radius(rho, float(rho[inner].mean()), float(rho[outer].mean()))
             rows.append({"R": R, "R_eq": r_eq, "dp": dp, "dp_R_over_sigma": dp * r_eq * kw["dx"] / sigma})
     return {"sigma": sigma, "T": T, "steps": steps, "rows": rows}
+
+
+def structure_factor_growth(n=4096, checkpoints=(500, 1000, 2000), nbins=None, seed=5, T=0.9):
+    """Growth of the structure factor S(k) of the density after a quench (Sec. 3.2's measure of
+    domain growth), LBM_MIXED against LBM_FP64 on the same seeded n x n spinodal field
+    (rho = 1 +/- 1%, u = 0, T), phase-separation set. Returns per checkpoint the FP64 peak
+    shell and height, the mixed peak height, and the relative L2 difference of the two S(k).
+    nbins: shells of |q| (default: every shell of the box, up to the corner of the spectrum)."""
+    nbins = nbins or int(np.ceil(np.sqrt(2) * n / 2)) + 2
+    fields = synthetic.spinodal(n, n, 1.0, 0.01, T, seed=seed)
+    S = {}
+    for prec in (LBM_FP64, LBM_MIXED):
+        with Simulation(n, n, default_params(precision=prec, **PHASE)) as s:
+            s.init(*fields)
+            done = 0
+            for c in checkpoints:
+                s.step(c - done)
+                done = c
+                S[(prec, c)] = s.structure_factor(nbins)[0]
+    rows = []
+    for c in checkpoints:
+        a, m = S[(LBM_FP64, c)], S[(LBM_MIXED, c)]
+        k = int(np.argmax(a[1:])) + 1
+        rows.append({"steps": c, "peak_shell": k, "peak_fp64": float(a[k]), "peak_mixed": float(m[k]),
+                     "rel_l2": float(np.linalg.norm(m - a) / np.linalg.norm(a))})
+    return {"n": n, "T": T, "seed": seed, "nbins": nbins, "rows": rows}
