@@ -271,6 +271,29 @@ def batch_path(lbm, torch, synthetic, precision, steps, warmup, stream, form=Non
     return out
 
 
+def batch_full_run(lbm, synthetic, steps=2000):
+    """The batched workload over its whole quench (2000 steps, graph form, LBM_MIXED): every
+    instance's mass drift and max |u| at the end, and whether every state stayed finite."""
+    p = lbm.default_params(precision=lbm.LBM_MIXED, **PARAMS)
+    temps = synthetic.quench_temperatures(4, len(BATCH_SIZES))
+    t0 = time.perf_counter()
+    with lbm.Batch([(n, n) for n in BATCH_SIZES], p) as b:
+        for k, n in enumerate(BATCH_SIZES):
+            b.init(k, *synthetic.spinodal(n, n, 1.0, 0.01, float(temps[k]), seed=4000 + k))
+        d0 = [b.diagnostics(k) for k in range(len(BATCH_SIZES))]
+        b.step(steps)
+        b.synchronize()
+        wall = time.perf_counter() - t0
+        try:
+            d1 = [b.diagnostics(k) for k in range(len(BATCH_SIZES))]
+            finite = True
+        except lbm.LbmError:  # a non-finite diagnostic
+            d1, finite = d0, False
+    drift = max(abs(a["mass"] / c["mass"] - 1) for a, c in zip(d1, d0))
+    return {"steps": steps, "wall_s": wall, "finite": finite, "mass_drift_max": drift,
+            "umax_max": max(a["umax"] for a in d1)}
+
+
 LARGE_N = 4096
 
 
@@ -536,7 +559,8 @@ def main():
             "mixed": batch_path(lbm, torch, synthetic, lbm.LBM_MIXED, kb, 3, stream),
             "mixed_persistent": batch_path(lbm, torch, synthetic, lbm.LBM_MIXED, kb, 3, stream,
                                            lbm.LBM_BATCH_PERSISTENT),
-            "fp64": batch_path(lbm, torch, synthetic, lbm.LBM_FP64, max(3, kb // 4), 3, stream)}
+            "fp64": batch_path(lbm, torch, synthetic, lbm.LBM_FP64, max(3, kb // 4), 3, stream),
+            "whole_quench_mixed": batch_full_run(lbm, synthetic)}
         if rank == 0:
             from paper_1403_3746_gb300 import accuracy
             tab = accuracy.error_table(rho64=True)
