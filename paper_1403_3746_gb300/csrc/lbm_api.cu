@@ -1521,7 +1521,6 @@ int diag_flush(lbm_ctx *c) {
 // previous copy has been waited for by the lbm_diagnostics_end that freed the slot.
 int step_with_diag(lbm_ctx *c) {
     const int slot = c->fuse_slot;
-    c->fuse_slot = -1;
     if (c->timing) {
         c->fuse_capture = slot;
         const int rc = run_step_launches(c);
@@ -1530,10 +1529,11 @@ int step_with_diag(lbm_ctx *c) {
     } else {
         if (!c->graph_diag[slot]) {
             const int rc = build_step_graph(c, slot);
-            if (rc) return rc;
+            if (rc) return rc;  // nothing launched: the request stays pending (computed on its own at the end)
         }
         CU_TRY(cudaGraphLaunch(c->graph_diag[slot], c->stream));
     }
+    c->fuse_slot = -1;
     CU_TRY(cudaStreamWaitEvent(c->dstream, c->fev[slot], 0));
     double *h = c->hpart + slot * c->dslot;
     const int nparts = (c->nb * c->ny) / c->geo.rows_macro;
