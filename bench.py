@@ -295,6 +295,7 @@ def batch_full_run(lbm, synthetic, steps=2000):
 
 
 LARGE_N = 4096
+TALL_NX = 256  # width of the tall grid of `--profile tall`
 
 
 def large_run(lbm, torch, synthetic, steps, stream):
@@ -457,6 +458,17 @@ def profile_main(args):
             sim.step(2)
             sim.synchronize()
             out = {"profile": "large", "n": LARGE_N, "steps": 3, "launch_shapes": list(sim.geometry()) + list(sim.pass_kinds())}
+    elif args.profile == "tall":
+        # 4096-point columns on a small grid (256 x 4096, about 0.3 GB): the column pass's
+        # 4-column tiles at a size one ncu capture of a single launch covers quickly
+        fields = synthetic.spinodal(TALL_NX, LARGE_N, 1.0, 0.01, 0.9, seed=5)
+        with lbm.Simulation(TALL_NX, LARGE_N, p) as sim:
+            sim.init(*fields)
+            sim.step(1)
+            sim.step(2)
+            sim.synchronize()
+            out = {"profile": "tall", "nx": TALL_NX, "ny": LARGE_N, "steps": 3,
+                   "launch_shapes": list(sim.geometry()) + list(sim.pass_kinds())}
     elif args.profile == "tma":
         fields = make_fields(lbm, synthetic)
         with lbm.Simulation(N_GRID, N_GRID, p) as sim:
@@ -487,11 +499,12 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched form and the error table")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (for profiler runs, whose timing would mislead the tuner)")
-    ap.add_argument("--profile", choices=["large", "diag", "tma"], default=None,
+    ap.add_argument("--profile", choices=["large", "diag", "tma", "tall"], default=None,
                     help="a fixed short launch sequence for ncu launch lists (default shapes, no timing): "
                          "large = 4096^2 mixed spinodal, init + 1 + 2 steps; diag = 1024^2 mixed droplet, "
                          "init + 1 step + 3 diagnostics requests; tma = the 1024^2 droplet with both column "
-                         "passes in the TMA form (16-column tiles), init + 1 + 2 steps")
+                         "passes in the TMA form (16-column tiles), init + 1 + 2 steps; tall = a 256 x 4096 "
+                         "mixed spinodal (4096-point columns), init + 1 + 2 steps")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)

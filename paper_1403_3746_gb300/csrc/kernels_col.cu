@@ -84,7 +84,8 @@ static cudaError_t launch_col_cs_t(const ColArgs<R> &a, int njobs, size_t smem, 
 template <typename R, int LOG2N, int CS> static cudaError_t launch_col_cs(const ColArgs<R> &a, int njobs, size_t smem,
                                                                            cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N, true, CS>;
-    if (smem < (size_t)(a.W / 2) * F::STRIDE * sizeof(typename F::CT)) return cudaErrorInvalidValue;
+    if (smem < (size_t)(a.W / 2) * col_line_stride(LOG2N, sizeof(R), CS) * sizeof(typename F::CT))
+        return cudaErrorInvalidValue;
     const int acc = jobs_acc(a, njobs);
     if (acc < 0) return cudaErrorInvalidValue;
     return acc ? launch_col_cs_t<R, LOG2N, CS, true>(a, njobs, smem, s)
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
         CT v[F::E];
 #pragma unroll
         for (int e = 0; e < F::E; ++e) v[e] = st[(size_t)(t + F::G * e) * L + l];  // row t + G e, columns 2l, 2l+1
-        CT *buf = st + l * F::STRIDE;
+        CT *buf = st + l * col_line_stride(LOG2N, sizeof(R), 1);
         F::template forward<reg::SyncCta>(v, buf, t, c.ay.tw);
         F::multiply(v, t, jb.order, jb.c, c.ay.k1, c.ay.k2);
         F::template inverse<reg::SyncCta>(v, buf, t, c.ay.tw);
@@ -198,7 +199,7 @@ size_t col_tma_smem(int nx, int ny, int W, size_t esize) {
     if (W < 2 || W > nx || (W * esize) % 16 != 0 || (W * esize) > 256) return 0;
     int l2 = 0;
     while ((1 << l2) < ny) ++l2;
-    const size_t lines = (size_t)(W / 2) * line_smem(l2) * 2 * esize;
+    const size_t lines = (size_t)(W / 2) * col_line_stride(l2, esize, 1) * 2 * esize;
     const size_t tile = (size_t)ny * W * esize;
     const size_t sb = (std::max(lines, tile) + 127) & ~(size_t)127;
     return 2 * sb + 32;
@@ -226,7 +227,8 @@ template <typename R, int LOG2N, bool ACC>
 static cudaError_t launch_col_tma_t(const ColTmaArgs<R> &a, size_t smem, cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N>;
     const int threads = (a.c.W / 2) * F::G;
-    if (threads > PassThreads<R>::value || a.stage_bytes < (unsigned)((a.c.W / 2) * F::STRIDE * sizeof(typename F::CT)))
+    if (threads > PassThreads<R>::value ||
+        a.stage_bytes < (unsigned)((a.c.W / 2) * col_line_stride(LOG2N, sizeof(R), 1) * sizeof(typename F::CT)))
         return cudaErrorNotSupported;
     cudaError_t e = allow_smem(col_tma_kernel<R, LOG2N, ACC>);
     if (e != cudaSuccess) return e;

@@ -2325,7 +2325,7 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     int W = (int)(128 / esize);
     if (W > nx) W = nx;
     const int maxt = max_threads(esize), colt = pass_threads(esize);
-    while (W > 2 && ((W / 2) * line_G(ly) > colt || (size_t)(W / 2) * line_smem(ly) * cs > 100 * 1024)) W >>= 1;
+    while (W > 2 && ((W / 2) * line_G(ly) > colt || col_smem(W, ly, esize) > 100 * 1024)) W >>= 1;
     g->colW = g->fluxW = W;
     g->col_smem = g->flux_smem = col_smem(W, ly, esize);
     // row kernels: rows per CTA, starting from about 512 nodes per CTA

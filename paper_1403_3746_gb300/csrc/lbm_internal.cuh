@@ -86,13 +86,32 @@ __host__ __device__ constexpr int col_cluster(int W, int log2n, size_t esize) {
 __host__ __device__ constexpr size_t upd_smem(int rows, int log2n, size_t esize, int cs) {
     return (size_t)6 * rows * (((1 << log2n) / cs) + (((1 << log2n) / cs) >> 4) + 2) * 2 * esize;
 }
+// Distance, in complex elements, between the line buffers of a column tile. The tile's L = W/2
+// lines share warps (line index fastest), and shared memory serves an 8-byte access per
+// half-warp and a 16-byte one per quarter-warp, in which each line's points cover 128/L
+// contiguous bytes (or a stride-17 pattern over as many banks). So each padded buffer (nl +
+// nl/16 elements for nl positions) is rounded up to 128 bytes and consecutive buffers start
+// 128/L bytes apart in bank space (one element at least): the lines of a half- or quarter-warp
+// take disjoint banks. The distance is a compile-time constant of each kernel (a run-time one
+// costs the transforms registers), set for the kernel's default tile: 128 bytes of a row,
+// halved until the tile's lines fit the CTAs of a cluster of cs; other widths stay correct.
+__host__ __device__ constexpr int log2_int(int v) { return v > 1 ? 1 + log2_int(v >> 1) : 0; }
+__host__ __device__ constexpr int col_tile_log2W(int log2n, size_t esize, int cs) {
+    int lw = log2_int((int)(128 / esize));
+    while (lw > 1 && (1 << (lw - 1)) * line_G(log2n) > cs * pass_threads(esize)) --lw;
+    return lw;
+}
+__host__ __device__ constexpr int col_line_stride(int log2n, size_t esize, int cs) {
+    const int nl = (1 << log2n) / cs, per128 = (int)(128 / (2 * esize));
+    const int base = (int)((((size_t)(nl + (nl >> 4)) * 2 * esize + 127) / 128) * per128);
+    const int off = per128 >> (col_tile_log2W(log2n, esize, cs) - 1);
+    return base + (off > 0 ? off : 1);
+}
 // shared memory of a direct column-pass CTA: W/2 line buffers of its share of each line
 __host__ __device__ constexpr size_t col_smem(int W, int log2n, size_t esize) {
     return col_cluster(W, log2n, esize) == 0
                ? 0
-               : (size_t)(W / 2) *
-                     (((1 << log2n) / col_cluster(W, log2n, esize)) + (((1 << log2n) / col_cluster(W, log2n, esize)) >> 4) + 2) *
-                     2 * esize;
+               : (size_t)(W / 2) * col_line_stride(log2n, esize, col_cluster(W, log2n, esize)) * 2 * esize;
 }
 // macroscopic row pass (two lines of G threads per row): float32 CTAs of max(128, 2 G)
 // threads; at 128 (nx <= 1024) seven are resident per SM (<= 72 registers per thread), so

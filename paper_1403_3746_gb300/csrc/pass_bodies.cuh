@@ -42,7 +42,7 @@ __device__ __forceinline__ void col_tile(const ColArgs<R> &a, int jobi, int z, i
     CT v[F::E];
 #pragma unroll
     for (int e = 0; e < F::E; ++e) v[e] = __ldcg(in + (size_t)(t + F::G * e) * rsi);  // L2 only: single use
-    CT *buf = sbuf + l * F::STRIDE;
+    CT *buf = sbuf + l * col_line_stride(LOG2N, sizeof(R), CS);
     F::template forward<reg::SyncCta>(v, buf, t, a.ay.tw);
     F::multiply(v, t, job.order, job.c, a.ay.k1, a.ay.k2);
     F::template inverse<reg::SyncCta>(v, buf, t, a.ay.tw);
