@@ -254,17 +254,21 @@ int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
  * than one CTA's threads split every line over a thread-block cluster of 2 or 4 CTAs that
  * exchange points through distributed shared memory); LBM_COL_TMA: a persistent grid whose CTAs
  * stage the next tile in shared memory with tiled bulk tensor copies (TMA) while they transform
- * the current one; LBM_COL_LOOKAHEAD: the direct form, each CTA first issuing bulk L2
+ * the current one; LBM_COL_TMA1: the same with one staging buffer per CTA (half the shared
+ * memory, so two CTAs per SM where two buffers leave one; a CTA's copy overlaps the other
+ * CTAs' transforms instead of its own); LBM_COL_LOOKAHEAD: the direct form, each CTA first issuing bulk L2
  * prefetches of the input rows of the CTA about one wave of resident CTAs after it, so that
  * DRAM streams while the resident CTAs transform. kinds[2]: CTAs per row of the update pass, 1
  * or 2 (a cluster of two splits each row's transforms and node loop; float32 rows of 2048 or
  * more, one row per cluster). lbm_autotune chooses them together with the tile widths and rows
  * per CTA. lbm_set_pass_kinds returns LBM_ERR_ARG for a choice the current shapes cannot take
- * (TMA and lookahead: rows of fewer than 16 bytes or cluster-split widths; TMA: staging buffers
- * beyond a CTA's shared memory); where a launch still cannot use TMA, the direct form runs. */
+ * (TMA forms and lookahead: rows of fewer than 16 bytes or cluster-split widths; TMA forms:
+ * staging buffers beyond a CTA's shared memory); where a launch still cannot use TMA, the
+ * direct form runs. */
 #define LBM_COL_DIRECT 0
 #define LBM_COL_TMA 1
 #define LBM_COL_LOOKAHEAD 2
+#define LBM_COL_TMA1 3
 int lbm_pass_kinds(lbm_handle h, int kinds[3]);
 int lbm_set_pass_kinds(lbm_handle h, const int kinds[3]);
 

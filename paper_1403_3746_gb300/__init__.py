@@ -27,6 +27,7 @@ KERNELS = {"col": 0, "macro": 1, "flux": 2, "update": 3, "rho64": 4}
 LBM_COL_DIRECT = 0
 LBM_COL_TMA = 1
 LBM_COL_LOOKAHEAD = 2
+LBM_COL_TMA1 = 3
 LBM_FAULT_NONE = 0
 LBM_FAULT_STARVE_COPIES = 1
 LBM_FAULT_WITHHOLD_COMPLETION = 2
@@ -351,7 +352,7 @@ class Simulation:
 
     def pass_kinds(self):
         """(column pass kind, flux column pass kind, update CTAs per row): each column kind
-        LBM_COL_DIRECT, LBM_COL_TMA or LBM_COL_LOOKAHEAD; 1 or 2."""
+        LBM_COL_DIRECT, LBM_COL_TMA, LBM_COL_LOOKAHEAD or LBM_COL_TMA1; 1 or 2."""
         k = (ctypes.c_int * 3)()
         _check(lib().lbm_pass_kinds(self._h, ctypes.cast(k, _P)))
         return tuple(k)

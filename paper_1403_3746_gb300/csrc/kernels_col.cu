@@ -105,13 +105,16 @@ template <typename R, int LOG2N> static cudaError_t launch_col_n(const ColArgs<R
 
 // ---------------------------------------------------------------------------------------
 // TMA-fed column pass. A persistent CTA walks the work items it + k gridDim (item = tile of W
-// columns of one job's field in one instance). Item k is staged in buffer k & 1: thread 0
-// arms that buffer's barrier with the tile's byte count and issues ny / boxr tiled copies of
-// (W x boxr) boxes; the copies of item k + 1 land while item k is transformed. Once every
-// thread has read its points of item k into registers, the same buffer serves as the line
-// buffers of item k's transforms (it is at least as large as both); after the CTA barrier
-// that ends item k it is handed back to the copy engine for item k + 2. Results are written
-// from registers, as in col_deriv_kernel, so every output value is bit for bit the same.
+// columns of one job's field in one instance). With two staging buffers (a.nstage = 2) item k
+// is staged in buffer k & 1: thread 0 arms that buffer's barrier with the tile's byte count and
+// issues ny / boxr tiled copies of (W x boxr) boxes; the copies of item k + 1 land while item k
+// is transformed. Once every thread has read its points of item k into registers, the same
+// buffer serves as the line buffers of item k's transforms (it is at least as large as both);
+// after the CTA barrier that ends item k it is handed back to the copy engine for item k + 2.
+// With one buffer (a.nstage = 1: half the shared memory, so two CTAs per SM where two buffers
+// leave one) item k + 1 is issued after item k, and the CTA's copy overlaps the transforms of
+// the other CTAs on its SM instead of its own. Results are written from registers, as in
+// col_deriv_kernel, so every output value is bit for bit the same.
 // ---------------------------------------------------------------------------------------
 template <typename R, int LOG2N, bool ACC>
 __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blocks)
@@ -122,8 +125,9 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
     const ColArgs<R> &c = a.c;
     const int W = c.W, L = W >> 1;
     const int l = threadIdx.x & (L - 1), t = threadIdx.x >> (c.log2W - 1);
-    unsigned char *stage0 = smem_raw, *stage1 = smem_raw + a.stage_bytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * (size_t)a.stage_bytes);
+    const int ns = a.nstage;  // 1 or 2
+    unsigned char *stage0 = smem_raw, *stage1 = smem_raw + (ns - 1) * (size_t)a.stage_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + ns * (size_t)a.stage_bytes);
     volatile int *flag = reinterpret_cast<volatile int *>(bar + 2);
     const int tiles = c.nx / W, nb = c.nb > 0 ? c.nb : 1;
     const unsigned tile_bytes = (unsigned)c.ny * (unsigned)W * (unsigned)sizeof(R);
@@ -148,13 +152,13 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
     __syncthreads();
     if (threadIdx.x == 0) {
         if (blockIdx.x < a.items) issue(blockIdx.x, 0), pend0 = true;
-        if (blockIdx.x + gridDim.x < a.items) issue(blockIdx.x + gridDim.x, 1), pend1 = true;
+        if (ns == 2 && blockIdx.x + gridDim.x < a.items) issue(blockIdx.x + gridDim.x, 1), pend1 = true;
     }
     int k = 0;
     for (int it = blockIdx.x; it < a.items; it += gridDim.x, ++k) {
-        const int b = k & 1;
+        const int b = ns == 2 ? k & 1 : 0;
         if (threadIdx.x == 0) {
-            bool ok = tma::bar_wait_bounded(&bar[b], (k >> 1) & 1, a.wait_cycles);
+            bool ok = tma::bar_wait_bounded(&bar[b], ns == 2 ? (k >> 1) & 1 : k & 1, a.wait_cycles);
             if (b) pend1 = false; else pend0 = false;
             if (!ok) {
                 atomicOr(a.err, tma::kErrTimeout);
@@ -187,22 +191,22 @@ __global__ void __launch_bounds__(PassThreads<R>::value, PassThreads<R>::min_blo
             out[(size_t)(t + F::G * e) * rso] = r;
         }
         reg::cta_barrier();  // every thread is done with this buffer
-        if (threadIdx.x == 0 && it + 2 * (int)gridDim.x < a.items) {
+        if (threadIdx.x == 0 && it + ns * (int)gridDim.x < a.items) {
             tma::fence_proxy_async_smem();
-            issue(it + 2 * gridDim.x, b);
+            issue(it + ns * gridDim.x, b);
             if (b) pend1 = true; else pend0 = true;
         }
     }
 }
 
-size_t col_tma_smem(int nx, int ny, int W, size_t esize) {
+size_t col_tma_smem(int nx, int ny, int W, size_t esize, int nstage) {
     if (W < 2 || W > nx || (W * esize) % 16 != 0 || (W * esize) > 256) return 0;
     int l2 = 0;
     while ((1 << l2) < ny) ++l2;
     const size_t lines = (size_t)(W / 2) * col_line_stride(l2, esize, 1) * 2 * esize;
     const size_t tile = (size_t)ny * W * esize;
     const size_t sb = (std::max(lines, tile) + 127) & ~(size_t)127;
-    return 2 * sb + 32;
+    return nstage == 1 || nstage == 2 ? (size_t)nstage * sb + 32 : 0;
 }
 
 namespace {
@@ -253,10 +257,10 @@ static cudaError_t launch_col_tma_n(const ColTmaArgs<R> &a, int njobs, size_t sm
 
 template <typename R>
 cudaError_t launch_col_tma(const ColArgs<R> &c, int njobs, int *err, long long wait_cycles, int starve,
-                           cudaStream_t s) {
+                           cudaStream_t s, int nstage) {
     if (njobs <= 0) return cudaSuccess;
     const size_t es = sizeof(R);
-    const size_t smem = col_tma_smem(c.nx, c.ny, c.W, es);
+    const size_t smem = col_tma_smem(c.nx, c.ny, c.W, es, nstage);
     if (smem == 0 || smem > kMaxCtaSmem || !err) return cudaErrorNotSupported;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
@@ -265,7 +269,8 @@ cudaError_t launch_col_tma(const ColArgs<R> &c, int njobs, int *err, long long w
     a.boxr = std::min(c.ny, 256);
     const int nb = c.nb > 0 ? c.nb : 1;
     a.items = njobs * (c.nx / c.W) * nb;
-    a.stage_bytes = (unsigned)((smem - 32) / 2);
+    a.nstage = nstage;
+    a.stage_bytes = (unsigned)((smem - 32) / nstage);
     a.err = err;
     a.wait_cycles = wait_cycles;
     a.starve = starve;
@@ -291,8 +296,8 @@ cudaError_t launch_col_tma(const ColArgs<R> &c, int njobs, int *err, long long w
     }
 }
 
-template cudaError_t launch_col_tma<double>(const ColArgs<double> &, int, int *, long long, int, cudaStream_t);
-template cudaError_t launch_col_tma<float>(const ColArgs<float> &, int, int *, long long, int, cudaStream_t);
+template cudaError_t launch_col_tma<double>(const ColArgs<double> &, int, int *, long long, int, cudaStream_t, int);
+template cudaError_t launch_col_tma<float>(const ColArgs<float> &, int, int *, long long, int, cudaStream_t, int);
 
 template <typename R>
 cudaError_t launch_col(const ColArgs<R> &a, int njobs, size_t smem, cudaStream_t s) {

@@ -243,8 +243,9 @@ enum { PASS_COL = 1, PASS_MACRO = 2, PASS_FLUX = 4, PASS_UPDATE = 8, PASS_ALL = 
 // serve the shape: rows narrower than 16 bytes, misaligned fields)
 template <typename R>
 cudaError_t launch_col_pass(const lbm_ctx *c, const ColArgs<R> &a, int nj, int kind, size_t direct_smem) {
-    if (kind == LBM_COL_TMA) {
-        const cudaError_t e = launch_col_tma<R>(a, nj, c->err, c->wait_cycles, c->starve, c->stream);
+    if (kind == LBM_COL_TMA || kind == LBM_COL_TMA1) {
+        const cudaError_t e =
+            launch_col_tma<R>(a, nj, c->err, c->wait_cycles, c->starve, c->stream, kind == LBM_COL_TMA1 ? 1 : 2);
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
     }
@@ -561,10 +562,11 @@ std::vector<int> col_candidates(const lbm_ctx *c) {
         if (col_cluster(W, c->ly, c->fsize) > 0 && col_smem(W, c->ly, c->fsize) <= 100 * 1024) out.push_back(W);
     return out;
 }
-// Whether the TMA-fed column kernel can take tiles of W columns: rows of at least 16 bytes,
-// aligned field rows, its staging buffers within a CTA's shared memory.
-bool col_tma_ok(const lbm_ctx *c, int W) {
-    const size_t sm = col_tma_smem(c->nx, c->ny, W, c->fsize);
+// Whether the TMA-fed column kernel can take tiles of W columns with `kind`'s staging buffers
+// (LBM_COL_TMA: two, LBM_COL_TMA1: one): rows of at least 16 bytes, aligned field rows, the
+// buffers within a CTA's shared memory.
+bool col_tma_ok(const lbm_ctx *c, int W, int kind) {
+    const size_t sm = col_tma_smem(c->nx, c->ny, W, c->fsize, kind == LBM_COL_TMA1 ? 1 : 2);
     return col_cluster(W, c->ly, c->fsize) == 1 && sm > 0 && sm <= kMaxCtaSmem && (c->nx * c->fsize) % 16 == 0;
 }
 // Whether the direct column kernel can prefetch tiles of W columns row by row: rows of at least
@@ -692,9 +694,9 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
         int &Kg = pass == PASS_COL ? c->geo.col_kind : c->geo.flux_kind;
         int bestW = Wg, bestK = Kg;
         float bt = 1e30f;
-        for (int kind : {LBM_COL_DIRECT, LBM_COL_TMA, LBM_COL_LOOKAHEAD}) {
+        for (int kind : {LBM_COL_DIRECT, LBM_COL_TMA, LBM_COL_LOOKAHEAD, LBM_COL_TMA1}) {
             for (int W : col_candidates(c)) {
-                if (kind == LBM_COL_TMA && !col_tma_ok(c, W)) continue;
+                if ((kind == LBM_COL_TMA || kind == LBM_COL_TMA1) && !col_tma_ok(c, W, kind)) continue;
                 if (kind == LBM_COL_LOOKAHEAD && !col_lookahead_ok(c, W)) continue;
                 Wg = W;
                 Kg = kind;
@@ -1618,10 +1620,11 @@ int lbm_pass_kinds(lbm_handle c, int kinds[3]) {
 int lbm_set_pass_kinds(lbm_handle c, const int kinds[3]) {
     if (!c || !kinds) return fail(LBM_ERR_ARG, "NULL argument");
     for (int j = 0; j < 2; ++j) {
-        if (kinds[j] != LBM_COL_DIRECT && kinds[j] != LBM_COL_TMA && kinds[j] != LBM_COL_LOOKAHEAD)
+        if (kinds[j] != LBM_COL_DIRECT && kinds[j] != LBM_COL_TMA && kinds[j] != LBM_COL_LOOKAHEAD &&
+            kinds[j] != LBM_COL_TMA1)
             return fail(LBM_ERR_ARG, "unknown pass kind");
         const int W = j == 0 ? c->geo.colW : c->geo.fluxW;
-        if (kinds[j] == LBM_COL_TMA && !col_tma_ok(c, W))
+        if ((kinds[j] == LBM_COL_TMA || kinds[j] == LBM_COL_TMA1) && !col_tma_ok(c, W, kinds[j]))
             return fail(LBM_ERR_ARG, "the TMA column pass cannot take %d-column tiles of %d x %d", W, c->nx, c->ny);
         if (kinds[j] == LBM_COL_LOOKAHEAD && !col_lookahead_ok(c, W))
             return fail(LBM_ERR_ARG, "the lookahead column pass cannot take %d-column tiles of %d x %d", W, c->nx, c->ny);
@@ -1727,7 +1730,9 @@ int lbm_set_geometry(lbm_handle c, const int geometry[4]) {
     c->geo.flux_smem = col_smem(geometry[3], c->ly, es);
     // a pass kind the new widths cannot take falls back to the direct form
     auto kind_ok = [c](int kind, int W) {
-        return kind == LBM_COL_TMA ? col_tma_ok(c, W) : kind == LBM_COL_LOOKAHEAD ? col_lookahead_ok(c, W) : true;
+        return kind == LBM_COL_TMA || kind == LBM_COL_TMA1 ? col_tma_ok(c, W, kind)
+               : kind == LBM_COL_LOOKAHEAD                ? col_lookahead_ok(c, W)
+                                                          : true;
     };
     if (!kind_ok(c->geo.col_kind, c->geo.colW)) c->geo.col_kind = LBM_COL_DIRECT;
     if (!kind_ok(c->geo.flux_kind, c->geo.fluxW)) c->geo.flux_kind = LBM_COL_DIRECT;

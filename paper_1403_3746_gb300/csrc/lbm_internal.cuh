@@ -215,15 +215,17 @@ template <typename R> struct ColTmaArgs {
     int *err;             // device error word (tma::kErrTimeout when a bounded wait gives up)
     long long wait_cycles;  // budget of one wait
     int starve;           // fault-injection hook: arm the barriers but issue no copies
+    int nstage;           // staging buffers: 2 (the next item's copies land during this one) or 1
 };
-// Shared memory of the TMA column pass for a tile of W columns of ny rows (two staging buffers
-// and two barriers); 0 if TMA cannot serve the shape.
-size_t col_tma_smem(int nx, int ny, int W, size_t esize);
-// Encodes the job tensor maps and launches on a persistent grid (at most `max_ctas` CTAs, 0 =
-// as many as fit); cudaErrorNotSupported when the shape or the driver cannot use TMA.
+// Shared memory of the TMA column pass for a tile of W columns of ny rows (nstage = 1 or 2
+// staging buffers, and two barriers); 0 if TMA cannot serve the shape.
+size_t col_tma_smem(int nx, int ny, int W, size_t esize, int nstage);
+// Encodes the job tensor maps and launches on a persistent grid of as many CTAs as fit (one per
+// item at most) with nstage (1 or 2) staging buffers each; cudaErrorNotSupported when the shape
+// or the driver cannot use TMA.
 template <typename R>
 cudaError_t launch_col_tma(const ColArgs<R> &a, int njobs, int *err, long long wait_cycles, int starve,
-                           cudaStream_t s);
+                           cudaStream_t s, int nstage);
 
 // ---- row pass of the macroscopic chain ---------------------------------------------
 template <typename R> struct MacroArgs {

@@ -1,7 +1,8 @@
-"""The TMA-fed column pass (LBM_COL_TMA) and the direct pass with L2 lookahead
-(LBM_COL_LOOKAHEAD) against the direct one: bit for bit the same states over every legal tile
-width, in both precisions, for single grids and stacked batch instances; the TMA pass's bounded
-waits end a starved launch with LBM_ERR_TIMEOUT instead of a hang."""
+"""The TMA-fed column pass with two or one staging buffers (LBM_COL_TMA, LBM_COL_TMA1) and the
+direct pass with L2 lookahead (LBM_COL_LOOKAHEAD) against the direct one: bit for bit the same
+states over every legal tile width, in both precisions, for single grids and stacked batch
+instances; the TMA pass's bounded waits end a starved launch with LBM_ERR_TIMEOUT instead of a
+hang."""
 import numpy as np
 import pytest
 
@@ -35,9 +36,9 @@ def _run(nx, ny, precision, W, kinds, steps=3):
         return s.get_f()
 
 
-@pytest.mark.parametrize("kind", [lbm.LBM_COL_TMA, lbm.LBM_COL_LOOKAHEAD])
+@pytest.mark.parametrize("kind", [lbm.LBM_COL_TMA, lbm.LBM_COL_LOOKAHEAD, lbm.LBM_COL_TMA1])
 @pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_MIXED])
-@pytest.mark.parametrize("nx,ny", [(64, 64), (256, 128), (32, 1024), (1024, 16)])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (256, 128), (32, 1024), (1024, 16), (16, 4096)])
 def test_column_pass_kinds_are_bitwise_the_direct_one(kind, precision, nx, ny):
     es = 8 if precision == lbm.LBM_FP64 else 4
     plan = lbm.launch_plan(nx, ny, precision)
@@ -72,14 +73,15 @@ def test_tma_in_a_batch_matches_separate_runs():
             assert np.array_equal(s.get_f(), got[k]), k
 
 
-def test_starved_copies_end_in_a_timeout_not_a_hang():
+@pytest.mark.parametrize("kind", [lbm.LBM_COL_TMA, lbm.LBM_COL_TMA1])
+def test_starved_copies_end_in_a_timeout_not_a_hang(kind):
     nx = ny = 128
     with lbm.Simulation(nx, ny, lbm.default_params(precision=lbm.LBM_MIXED)) as s:
         s.init(*_fields(nx, ny))
         s.step(2)
         blob = s.get_state()
         ref_next = None
-        s.set_pass_kinds((lbm.LBM_COL_TMA, lbm.LBM_COL_TMA))
+        s.set_pass_kinds((kind, kind))
         s.fault_inject(lbm.LBM_FAULT_STARVE_COPIES, 200000)  # about 0.1 ms per wait
         s.step(1)
         with pytest.raises(lbm.LbmError) as ei:
