@@ -458,16 +458,19 @@ def profile_main(args):
             sim.step(2)
             sim.synchronize()
             out = {"profile": "large", "n": LARGE_N, "steps": 3, "launch_shapes": list(sim.geometry()) + list(sim.pass_kinds())}
-    elif args.profile == "tall":
+    elif args.profile in ("tall", "tall-tma1"):
         # 4096-point columns on a small grid (256 x 4096, about 0.3 GB): the column pass's
-        # 4-column tiles at a size one ncu capture of a single launch covers quickly
+        # 4-column tiles at a size one ncu capture of a single launch covers quickly; "tall" in
+        # the direct form, "tall-tma1" in the default one there (TMA, one staging buffer)
         fields = synthetic.spinodal(TALL_NX, LARGE_N, 1.0, 0.01, 0.9, seed=5)
         with lbm.Simulation(TALL_NX, LARGE_N, p) as sim:
             sim.init(*fields)
+            if args.profile == "tall":
+                sim.set_pass_kinds((lbm.LBM_COL_DIRECT, lbm.LBM_COL_DIRECT, 1))
             sim.step(1)
             sim.step(2)
             sim.synchronize()
-            out = {"profile": "tall", "nx": TALL_NX, "ny": LARGE_N, "steps": 3,
+            out = {"profile": args.profile, "nx": TALL_NX, "ny": LARGE_N, "steps": 3,
                    "launch_shapes": list(sim.geometry()) + list(sim.pass_kinds())}
     elif args.profile == "tma":
         fields = make_fields(lbm, synthetic)
@@ -499,12 +502,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched form and the error table")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (for profiler runs, whose timing would mislead the tuner)")
-    ap.add_argument("--profile", choices=["large", "diag", "tma", "tall"], default=None,
+    ap.add_argument("--profile", choices=["large", "diag", "tma", "tall", "tall-tma1"], default=None,
                     help="a fixed short launch sequence for ncu launch lists (default shapes, no timing): "
                          "large = 4096^2 mixed spinodal, init + 1 + 2 steps; diag = 1024^2 mixed droplet, "
                          "init + 1 step + 3 diagnostics requests; tma = the 1024^2 droplet with both column "
                          "passes in the TMA form (16-column tiles), init + 1 + 2 steps; tall = a 256 x 4096 "
-                         "mixed spinodal (4096-point columns), init + 1 + 2 steps")
+                         "mixed spinodal (4096-point columns), direct column passes, init + 1 + 2 steps; "
+                         "tall-tma1 = the same in the default column form there (TMA, one staging buffer)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)

@@ -260,7 +260,10 @@ int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
  * prefetches of the input rows of the CTA about one wave of resident CTAs after it, so that
  * DRAM streams while the resident CTAs transform. kinds[2]: CTAs per row of the update pass, 1
  * or 2 (a cluster of two splits each row's transforms and node loop; float32 rows of 2048 or
- * more, one row per cluster). lbm_autotune chooses them together with the tile widths and rows
+ * more, one row per cluster). Defaults: LBM_COL_TMA1 for both column passes of LBM_MIXED and
+ * LBM_MIXED_RHO64 handles whose columns have 2048 or more points (where the shape allows it),
+ * LBM_COL_DIRECT otherwise; 2 CTAs per update row for float32 rows of 4096, 1 otherwise.
+ * lbm_autotune chooses them together with the tile widths and rows
  * per CTA. lbm_set_pass_kinds returns LBM_ERR_ARG for a choice the current shapes cannot take
  * (TMA forms and lookahead: rows of fewer than 16 bytes or cluster-split widths; TMA forms:
  * staging buffers beyond a CTA's shared memory); where a launch still cannot use TMA, the

@@ -151,7 +151,7 @@ struct Geometry {
     bool upd_ax = false;        // update pass takes d_x f from a separate row pass (Ax)
     bool macro_serial = false;  // macro pass transforms a row's two lines in turn
     int upd_cs = 1;             // update pass: CTAs per row (2: a cluster splits each row)
-    int col_kind = 0;           // column pass: LBM_COL_DIRECT, LBM_COL_TMA or LBM_COL_LOOKAHEAD (width colW)
+    int col_kind = 0;           // column pass: LBM_COL_DIRECT, LBM_COL_TMA, LBM_COL_LOOKAHEAD or LBM_COL_TMA1 (width colW)
     int flux_kind = 0;          // flux column pass: the same choice (width fluxW)
 };
 void pass_geometry(int nx, int ny, size_t esize, Geometry *g);

@@ -305,6 +305,20 @@ def test_mixed_rows_of_4096():
     assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
 
 
+@pytest.mark.parametrize("nx,ny", [(16, 2048), (8, 4096)])
+def test_mixed_columns_of_2048_and_4096(nx, ny):
+    # float32 columns of 2048+ points, where both column passes take the TMA form with one
+    # staging buffer per CTA by default (LBM_COL_TMA1); fields that vary along both axes
+    with lbm.Simulation(nx, ny, lib_params(**MIX)) as s:
+        assert s.pass_kinds()[:2] == (lbm.LBM_COL_TMA1, lbm.LBM_COL_TMA1)
+    fields = moving_fields(nx, ny)
+    fo, mo = run_oracle(fields, 3)
+    fg, mg = run_gpu(fields, 3, **MIX)
+    ef, er, eu, eT = mixed_errors(fg, mg, fo, mo)
+    print(f"mixed {nx}x{ny} x 3: f {ef:.2e}, rho {er:.2e}, |du| {eu:.2e}, T {eT:.2e}")
+    assert ef <= 2e-6 and er <= 2e-6 and eu <= 2e-6 and eT <= 2e-6
+
+
 def test_mixed_droplet_1024_one_step():
     # the benchmark workload: droplet R = 128, T = 0.9, phase-separation parameter set
     T = 0.9
