@@ -71,9 +71,8 @@ template <typename R, int LOG2N> static cudaError_t launch_update_n(const Update
 template <typename R, int LOG2N> static cudaError_t launch_macro_n(const MacroArgs<R> &a, size_t smem,
                                                                    cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N>;
-    // three line buffers per row, plus K rho d_x rho per node unless serial; refuse less
-    const size_t need = (size_t)3 * a.rows * F::STRIDE * sizeof(typename F::CT) +
-                        (a.serial ? 0 : (size_t)a.rows * F::N * sizeof(R));
+    // three line buffers per row; refuse less
+    const size_t need = (size_t)3 * a.rows * F::STRIDE * sizeof(typename F::CT);
     if (smem < need) return cudaErrorInvalidValue;
     if constexpr (sizeof(R) == 8 && LOG2N == 12) {  // the only shape that needs the serial form
         if (a.serial) {

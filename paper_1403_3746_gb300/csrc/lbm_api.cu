@@ -587,10 +587,8 @@ std::vector<int> upd_candidates(const lbm_ctx *c) {
 // Candidate rows per CTA of the macro pass (two lines per row within its thread bound).
 std::vector<int> macro_candidates(const lbm_ctx *c) {
     std::vector<int> out;
-    const size_t SM = (size_t)line_smem(c->lx) * 2 * c->fsize;
     for (int r = 1; r <= c->ny && r * c->nx <= 4096; r *= 2)
-        if (2 * r * line_G(c->lx) <= macro_threads(c->fsize, c->lx) &&
-            3 * r * SM + (size_t)r * c->nx * c->fsize <= kMaxCtaSmem)
+        if (2 * r * line_G(c->lx) <= macro_threads(c->fsize, c->lx) && macro_smem(r, c->lx, c->fsize) <= kMaxCtaSmem)
             out.push_back(r);
     return out;
 }
@@ -710,19 +708,18 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
         Sg = col_smem(bestW, c->ly, es);
         best_ms[pass == PASS_COL ? 0 : 3] = bt;
     }
-    const size_t SM = (size_t)line_smem(c->lx) * 2 * es;
     best_ms[1] = 0;
     if (frc && !c->geo.macro_serial) {
         int bestr = c->geo.rows_macro;
         float bt = 1e30f;
         for (int r : macro_candidates(c)) {
             c->geo.rows_macro = r;
-            c->geo.macro_smem = 3 * r * SM + (size_t)r * c->nx * es;
+            c->geo.macro_smem = macro_smem(r, c->lx, es);
             if ((rc = time_step(c, flush, flush_bytes, e0, e1, &t))) return done(rc);
             if (t < bt) bt = t, bestr = r;
         }
         c->geo.rows_macro = bestr;
-        c->geo.macro_smem = 3 * bestr * SM + (size_t)bestr * c->nx * es;
+        c->geo.macro_smem = macro_smem(bestr, c->lx, es);
         best_ms[1] = bt < 1e30f ? bt : 0.0f;
     }
     best_ms[2] = 0;
@@ -1723,7 +1720,7 @@ int lbm_set_geometry(lbm_handle c, const int geometry[4]) {
     if (c->geo.upd_ax ? geometry[2] != c->geo.rows_upd : !has(upd_candidates(c), geometry[2]))
         return fail(LBM_ERR_ARG, "update rows per CTA %d not valid", geometry[2]);
     CU_TRY(cudaStreamSynchronize(c->stream));
-    const size_t es = c->fsize, SMr = (size_t)line_smem(c->lx) * 2 * es;
+    const size_t es = c->fsize;
     c->geo.colW = geometry[0];
     c->geo.col_smem = col_smem(geometry[0], c->ly, es);
     c->geo.fluxW = geometry[3];
@@ -1738,7 +1735,7 @@ int lbm_set_geometry(lbm_handle c, const int geometry[4]) {
     if (!kind_ok(c->geo.flux_kind, c->geo.fluxW)) c->geo.flux_kind = LBM_COL_DIRECT;
     if (!c->geo.macro_serial) {
         c->geo.rows_macro = geometry[1];
-        c->geo.macro_smem = 3 * geometry[1] * SMr + (size_t)geometry[1] * c->nx * es;
+        c->geo.macro_smem = macro_smem(geometry[1], c->lx, es);
     }
     if (!c->geo.upd_ax) {
         c->geo.rows_upd = geometry[2];
@@ -2042,7 +2039,7 @@ static int batch_args(lbm_batch b, BatchArgs<float> &A, size_t &smem) {
         const int W = std::min(c->nx, 2 * T / Gy);
         int nrm = 1;
         while (2 * nrm <= c->ny && 2 * (2 * nrm) * Gx <= T &&
-               3 * (size_t)(2 * nrm) * line_smem(c->lx) * 2 * es + (size_t)(2 * nrm) * c->nx * es <= cap)
+               macro_smem(2 * nrm, c->lx, es) <= cap)
             nrm *= 2;
         int nru = 1;
         while (2 * nru <= c->ny && 2 * nru * c->nx <= 8 * T && upd_smem(2 * nru, c->lx, es, 1) <= cap) nru *= 2;
@@ -2065,7 +2062,7 @@ static int batch_args(lbm_batch b, BatchArgs<float> &A, size_t &smem) {
         G.inst0 = inst;
         inst += c->nb;
         smem = std::max(smem, col_smem(W, c->ly, es));
-        smem = std::max(smem, 3 * (size_t)nrm * line_smem(c->lx) * 2 * es + (size_t)nrm * c->nx * es);
+        smem = std::max(smem, macro_smem(nrm, c->lx, es));
         smem = std::max(smem, upd_smem(nru, c->lx, es, 1));
     }
     int q = 0;
@@ -2362,8 +2359,8 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
         g->upd_smem = upd_smem(1, lx, esize, 2);
     }
     r = r0;
-    // macro: 2 lines per row with 3 buffers, plus 1 value per node
-    auto macro_bytes = [&](int rr) { return 3 * (size_t)rr * SM + (size_t)rr * nx * esize; };
+    // macro: 2 lines per row with 3 buffers
+    auto macro_bytes = [&](int rr) { return macro_smem(rr, lx, esize); };
     const int mact = macro_threads(esize, lx);
     while (r > 1 && (2 * r * G > mact || macro_bytes(r) > 200 * 1024)) r >>= 1;
     g->rows_macro = r;

@@ -107,6 +107,10 @@ __host__ __device__ constexpr int col_line_stride(int log2n, size_t esize, int c
     const int off = per128 >> (col_tile_log2W(log2n, esize, cs) - 1);
     return base + (off > 0 ? off : 1);
 }
+// shared memory of a macroscopic row-pass CTA: three line buffers per row
+__host__ __device__ constexpr size_t macro_smem(int rows, int log2n, size_t esize) {
+    return (size_t)3 * rows * line_smem(log2n) * 2 * esize;
+}
 // shared memory of a direct column-pass CTA: W/2 line buffers of its share of each line
 __host__ __device__ constexpr size_t col_smem(int W, int log2n, size_t esize) {
     return col_cluster(W, log2n, esize) == 0
@@ -115,13 +119,15 @@ __host__ __device__ constexpr size_t col_smem(int W, int log2n, size_t esize) {
 }
 // macroscopic row pass (two lines of G threads per row): float32 CTAs of max(128, 2 G)
 // threads; at 128 (nx <= 1024) seven are resident per SM (<= 72 registers per thread), so
-// that 1024 rows fit in one wave of 152 SMs
+// that 1024 rows fit in one wave of 152 SMs; at 256 (nx = 2048) three (<= 85 registers: 2048^2
+// step 1.70 -> 1.56 ms against one); at 512 (nx = 4096) one (two at 64 registers spill, and
+// that macro pass took 620 instead of 535 us per launch at 4096^2)
 __host__ __device__ constexpr int macro_threads(size_t esize, int log2n) {
     return esize == 8 ? 384 : (2 * line_G(log2n) > 128 ? 2 * line_G(log2n) : 128);
 }
 template <typename R, int LOG2N> struct MacroThreads {
     static constexpr int value = macro_threads(sizeof(R), LOG2N);
-    static constexpr int min_blocks = sizeof(R) == 8 ? 1 : (value == 128 ? 7 : 1);
+    static constexpr int min_blocks = sizeof(R) == 8 ? 1 : value == 128 ? 7 : value == 256 ? 3 : 1;
 };
 // every supported line length 2^1 .. 2^12
 #define LBM_FOR_LOG2N(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)

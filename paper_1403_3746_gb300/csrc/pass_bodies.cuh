@@ -114,10 +114,10 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     CT *sb = reinterpret_cast<CT *>(smem_raw);
     const int NR = a.rows, nodes = NR * NX;
-    // per row three line buffers: A1, A2 (line A) and B1 (line B); then K rho d_x rho per node.
+    // per row three line buffers: A1, A2 (line A) and B1 (line B). K rho d_x rho of node x waits
+    // in A2[x].y between the rounds (d_xx T, the other half of A2, is not needed), unless SERIAL.
     // The partial numerator of C waits in its own global slot (M_CNUM) between the rounds.
-    CT *lines = sb;                                            // [NR][3 SM]
-    R *krx = reinterpret_cast<R *>(sb + (size_t)3 * NR * SM);  // [NR][NX] (not SERIAL)
+    CT *lines = sb;  // [NR][3 SM]
     const int y0 = blk * NR;
     const int slot = threadIdx.x / G, t = threadIdx.x % G;
     const bool active = !EXTRA || slot < (SERIAL ? NR : 2 * NR);
@@ -231,7 +231,7 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
         mn[M_CNUM * NX] = (R)((Pw - rT) * divu + L_gradu - zeta * divu * divu + D(1.125) * rho * rho * divu +
                               K * (-D(0.5) * grr * divu - r_gradu_r));
         if constexpr (SERIAL) mn[M_DSXY * NX] = (R)(K * rho * rx);
-        else krx[idx] = (R)(K * rho * rx);
+        else A2[x].y = (R)(K * rho * rx);  // this thread read A2[x].x above
         mn[M_QY * NX] = (R)Qy;
         mn[M_SXY * NX] = (R)Sxy;
         mn[M_SYY * NX] = (R)Syy;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void macro_rows(const MacroArgs<R> &a, int blk) {
                 mrow[M_DSXX * NX + x] = v[e].y;
             } else {
                 // - K rho d_x rho d_x(div u); the partial value was written by this CTA's node loop
-                const R k = SERIAL ? mrow[M_DSXY * NX + x] : krx[r * NX + x];
+                const R k = SERIAL ? mrow[M_DSXY * NX + x] : O2[x].y;
                 mrow[M_DSXY * NX + x] = v[e].x;
                 mrow[M_CNUM * NX + x] -= k * v[e].y;
             }
