@@ -41,11 +41,6 @@ int fail(int code, const char *fmt, ...) {
     } while (0)
 
 bool is_pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
-int ilog2(int n) {
-    int l = 0;
-    while ((1 << l) < n) ++l;
-    return l;
-}
 
 // Rows of the 16x16 matrix of moment functionals
 // 1; v_x, v_y; psi; v_x v_x, v_x v_y, v_y v_y; psi v_x, psi v_y; v_x^3, v_x^2 v_y, v_x v_y^2, v_y^3;
@@ -227,7 +222,7 @@ template <typename R> ColArgs<R> col_args(const lbm_ctx *c, int nb, int W) {
     a.nx = c->nx;
     a.ny = c->ny;
     a.W = W;
-    a.log2W = ilog2(W);
+    a.log2W = log2_int(W);
     a.nb = nb;
     a.ay = axis<R>(c, false);
     return a;
@@ -814,8 +809,8 @@ int create_ctx(int nx, int ny, int nb, const lbm_params *params, cudaStream_t st
     c->nx = nx;
     c->ny = ny;
     c->nb = nb;
-    c->lx = ilog2(nx);
-    c->ly = ilog2(ny);
+    c->lx = log2_int(nx);
+    c->ly = log2_int(ny);
     c->n = (long long)nx * ny;
     c->p = *params;
     c->stream = stream;
@@ -1681,7 +1676,7 @@ int lbm_launch_plan(int nx, int ny, int precision, int out[18]) {
     if (precision != LBM_FP64 && precision != LBM_MIXED && precision != LBM_MIXED_RHO64)
         return fail(LBM_ERR_ARG, "precision must be LBM_FP64, LBM_MIXED or LBM_MIXED_RHO64");
     const size_t es = precision == LBM_FP64 ? 8 : 4;
-    const int lx = ilog2(nx), ly = ilog2(ny);
+    const int lx = log2_int(nx), ly = log2_int(ny);
     Geometry g;
     pass_geometry(nx, ny, es, &g);
     const int v[18] = {g.colW, (g.colW / 2) * line_G(ly) / std::max(1, col_cluster(g.colW, ly, es)), (int)g.col_smem,
