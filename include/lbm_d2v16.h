@@ -239,7 +239,7 @@ int lbm_geometry(lbm_handle h, int geometry[4]);
  * [8] update shared memory, [9] 1 if the update takes d_x f from a separate row pass (then
  * [8] is 0); [10] rows per CTA, [11] CTA threads and [12] shared memory of the row-derivative
  * pass; limits: [13] CTA threads of the column and update passes, [14] CTA threads of the
- * macro pass, [15] shared memory per CTA; [16] CTAs per row of the update pass (a cluster of two
+ * macro pass, [15] shared memory per CTA; [16] CTAs per row of the update pass (a cluster of four
  * splits float32 rows of 4096), [17] CTAs per cluster of the column pass. LBM_ERR_ARG for sizes or precision outside the
  * library's range; LBM_ERR_UNSUPPORTED (out filled) if a pass would exceed [15]. */
 int lbm_launch_plan(int nx, int ny, int precision, int out[18]);
@@ -258,11 +258,11 @@ int lbm_autotune(lbm_handle h, int geometry[4], double ms[4]);
  * memory, so two CTAs per SM where two buffers leave one; a CTA's copy overlaps the other
  * CTAs' transforms instead of its own); LBM_COL_LOOKAHEAD: the direct form, each CTA first issuing bulk L2
  * prefetches of the input rows of the CTA about one wave of resident CTAs after it, so that
- * DRAM streams while the resident CTAs transform. kinds[2]: CTAs per row of the update pass, 1
- * or 2 (a cluster of two splits each row's transforms and node loop; float32 rows of 2048 or
- * more, one row per cluster). Defaults: LBM_COL_TMA1 for both column passes of LBM_MIXED and
+ * DRAM streams while the resident CTAs transform. kinds[2]: CTAs per row of the update pass, 1,
+ * 2 or 4 (a cluster of two or four splits each row's transforms and node loop; float32 rows of
+ * 2048 or more for two, of 4096 for four, one row per cluster). Defaults: LBM_COL_TMA1 for both column passes of LBM_MIXED and
  * LBM_MIXED_RHO64 handles whose columns have 2048 or more points (where the shape allows it),
- * LBM_COL_DIRECT otherwise; 2 CTAs per update row for float32 rows of 4096, 1 otherwise.
+ * LBM_COL_DIRECT otherwise; 4 CTAs per update row for float32 rows of 4096, 1 otherwise.
  * lbm_autotune chooses them together with the tile widths and rows
  * per CTA. lbm_set_pass_kinds returns LBM_ERR_ARG for a choice the current shapes cannot take
  * (TMA forms and lookahead: rows of fewer than 16 bytes or cluster-split widths; TMA forms:

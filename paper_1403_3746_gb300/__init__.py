@@ -352,7 +352,7 @@ class Simulation:
 
     def pass_kinds(self):
         """(column pass kind, flux column pass kind, update CTAs per row): each column kind
-        LBM_COL_DIRECT, LBM_COL_TMA, LBM_COL_LOOKAHEAD or LBM_COL_TMA1; 1 or 2."""
+        LBM_COL_DIRECT, LBM_COL_TMA, LBM_COL_LOOKAHEAD or LBM_COL_TMA1; 1, 2 or 4."""
         k = (ctypes.c_int * 3)()
         _check(lib().lbm_pass_kinds(self._h, ctypes.cast(k, _P)))
         return tuple(k)

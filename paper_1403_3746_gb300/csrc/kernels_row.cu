@@ -34,8 +34,9 @@ template <typename R, int LOG2N, int CS> static cudaError_t launch_update_cs(con
                                                                               cudaStream_t s) {
     using F = reg::LineFFT<R, LOG2N, true, CS>;
     constexpr bool MS = sizeof(R) == 4;  // float32: moment-space collision
-    cudaError_t e = CS == 1 ? allow_smem(update_row_kernel<R, LOG2N, MS>)
-                            : allow_smem(update_cluster_kernel<R, LOG2N, MS, CS>);
+    cudaError_t e;
+    if constexpr (CS == 1) e = allow_smem(update_row_kernel<R, LOG2N, MS>);
+    else e = allow_smem(update_cluster_kernel<R, LOG2N, MS, CS>);
     if (e != cudaSuccess) return e;
     // the in-kernel row transforms need 6 line buffers per row; refuse a launch without them
     const bool adv = !(a.flags & LBM_FLAG_NO_ADVECTION);
@@ -63,6 +64,9 @@ template <typename R, int LOG2N> static cudaError_t launch_update_n(const Update
                                                                     cudaStream_t s) {
     if constexpr (sizeof(R) == 4 && LOG2N >= 11) {
         if (a.cs == 2) return launch_update_cs<R, LOG2N, 2>(a, smem, s);
+    }
+    if constexpr (sizeof(R) == 4 && LOG2N >= 12) {
+        if (a.cs == 4) return launch_update_cs<R, LOG2N, 4>(a, smem, s);
     }
     if (a.cs != 1 && a.cs != 0) return cudaErrorInvalidValue;
     return launch_update_cs<R, LOG2N, 1>(a, smem, s);

@@ -569,8 +569,11 @@ bool col_tma_ok(const lbm_ctx *c, int W, int kind) {
 bool col_lookahead_ok(const lbm_ctx *c, int W) {
     return col_cluster(W, c->ly, c->fsize) == 1 && W * c->fsize >= 16 && (c->nx * c->fsize) % 16 == 0;
 }
-// Whether a cluster of two CTAs may split the update pass's rows: float32 rows of 2048 or more.
-bool upd_split_ok(const lbm_ctx *c) { return c->fsize == 4 && c->lx >= 11 && !c->geo.upd_ax; }
+// Whether a cluster of cs CTAs may split the update pass's rows: float32 rows of 2048 or more
+// in two, of 4096 in four.
+bool upd_split_ok(const lbm_ctx *c, int cs) {
+    return c->fsize == 4 && !c->geo.upd_ax && ((cs == 2 && c->lx >= 11) || (cs == 4 && c->lx >= 12));
+}
 // Candidate rows per CTA of the update pass (6 line buffers per row within a CTA's shared memory).
 std::vector<int> upd_candidates(const lbm_ctx *c) {
     std::vector<int> out;
@@ -721,8 +724,8 @@ template <typename R> int autotune_impl(lbm_ctx *c, float best_ms[4]) {
     if (!c->geo.upd_ax) {
         int bestr = c->geo.rows_upd, bestcs = c->geo.upd_cs;
         float bt = 1e30f;
-        for (int cs : {1, 2}) {
-            if (cs == 2 && !upd_split_ok(c)) continue;
+        for (int cs : {1, 2, 4}) {
+            if (cs > 1 && !upd_split_ok(c, cs)) continue;
             for (int r : upd_candidates(c)) {
                 if (cs > 1 && r != 1) continue;
                 c->geo.rows_upd = r;
@@ -1621,9 +1624,11 @@ int lbm_set_pass_kinds(lbm_handle c, const int kinds[3]) {
         if (kinds[j] == LBM_COL_LOOKAHEAD && !col_lookahead_ok(c, W))
             return fail(LBM_ERR_ARG, "the lookahead column pass cannot take %d-column tiles of %d x %d", W, c->nx, c->ny);
     }
-    if (kinds[2] != 1 && kinds[2] != 2) return fail(LBM_ERR_ARG, "update CTAs per row must be 1 or 2");
-    if (kinds[2] == 2 && !(upd_split_ok(c) && c->geo.rows_upd == 1))
-        return fail(LBM_ERR_ARG, "the update pass splits only float32 rows of 2048 or more, one row per cluster");
+    if (kinds[2] != 1 && kinds[2] != 2 && kinds[2] != 4) return fail(LBM_ERR_ARG, "update CTAs per row must be 1, 2 or 4");
+    if (kinds[2] > 1 && !(upd_split_ok(c, kinds[2]) && c->geo.rows_upd == 1))
+        return fail(LBM_ERR_ARG,
+                    "the update pass splits only float32 rows, of 2048 or more in two and of 4096 in four, one "
+                    "row per cluster");
     CU_TRY(cudaStreamSynchronize(c->stream));
     c->geo.col_kind = kinds[0];
     c->geo.flux_kind = kinds[1];
@@ -2346,12 +2351,13 @@ void pass_geometry(int nx, int ny, size_t esize, Geometry *g) {
     // its x-derivatives from a separate row pass instead (float32 at 4096 needs 209 KB and fits)
     g->upd_ax = g->upd_smem > kMaxCtaSmem;
     if (g->upd_ax) g->upd_smem = 0;
-    // float32 rows of 4096: a cluster of two CTAs splits each row (two CTAs per SM instead of one;
-    // update pass 4.84 -> 3.57 ms per step at 4096^2)
+    // float32 rows of 4096: a cluster of four CTAs splits each row (two CTAs per SM instead of
+    // the one that a whole row's 209 KB of line buffers leaves, and the six line transforms in
+    // one batch; update pass per 4096^2 step: 3.37 ms over four CTAs, 3.55 over two)
     g->upd_cs = 1;
     if (esize == 4 && lx >= 12 && r == 1) {
-        g->upd_cs = 2;
-        g->upd_smem = upd_smem(1, lx, esize, 2);
+        g->upd_cs = 4;
+        g->upd_smem = upd_smem(1, lx, esize, 4);
     }
     r = r0;
     // macro: 2 lines per row with 3 buffers

@@ -275,7 +275,7 @@ template <typename R> struct UpdateArgs {
     R *m;            // macroscopic block; moments of fs in, moments of fout out
     int nx, ny, rows;
     int lines_per_batch;  // line transforms in flight per batch (the other threads wait)
-    int cs;               // CTAs per row: 1, or 2 (a cluster splits the row; float32 rows of 2048+)
+    int cs;               // CTAs per row: 1, or 2 / 4 (a cluster splits the row; float32 rows of 2048+ / 4096)
     Axis<R> ax;
     R tau_inv, h, K, b, eta2;  // eta2 = eta0^2
     R cx[6];  // multiplier of row-transform line q: -h v_x of its first field (the second has -v_x)

@@ -605,7 +605,7 @@ __device__ __forceinline__ void update_node(const UpdateArgs<R> &a, const Update
     }
 }
 
-// CS = 1: a CTA owns `rows` whole rows. CS > 1 (float32 rows of 2048 or more, one row per
+// CS = 1: a CTA owns `rows` whole rows. CS > 1 (float32 rows of 2048 or more, 4096 for CS = 4, one row per
 // cluster): the CS CTAs of a cluster split the row's line transforms (fft_reg.cuh) and CTA
 // `rank` runs the node loop over its x-range [rank N/CS, (rank + 1) N/CS), whose derivatives the
 // transforms leave in its own shared memory.

@@ -114,11 +114,12 @@ def test_cluster_split_column_tiles_are_bitwise_the_plain_ones(precision, nx, ny
         assert np.array_equal(got, ref), (W, float(np.max(np.abs(got - ref))))
 
 
-@pytest.mark.parametrize("nx,ny", [(2048, 8), (4096, 8)])
-def test_cluster_split_update_rows_are_bitwise_the_plain_ones(nx, ny):
-    # float32 rows of 2048+: a cluster of two CTAs splits each row's line transforms and node loop
+@pytest.mark.parametrize("nx,ny,cs", [(2048, 8, 2), (4096, 8, 2), (4096, 8, 4)])
+def test_cluster_split_update_rows_are_bitwise_the_plain_ones(nx, ny, cs):
+    # float32 rows of 2048+ (4096 for four): a cluster of cs CTAs splits each row's line
+    # transforms and node loop
     ref = _run(nx, ny, lbm.LBM_MIXED, 4, (lbm.LBM_COL_DIRECT, lbm.LBM_COL_DIRECT, 1))
-    got = _run(nx, ny, lbm.LBM_MIXED, 4, (lbm.LBM_COL_DIRECT, lbm.LBM_COL_DIRECT, 2))
+    got = _run(nx, ny, lbm.LBM_MIXED, 4, (lbm.LBM_COL_DIRECT, lbm.LBM_COL_DIRECT, cs))
     assert np.array_equal(got, ref), float(np.max(np.abs(got - ref)))
     with lbm.Simulation(256, 8, lbm.default_params(precision=lbm.LBM_MIXED)) as s:
         s.init(*_fields(256, 8))

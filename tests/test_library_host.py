@@ -168,8 +168,8 @@ def test_launch_plan_of_every_size_fits_the_kernels(L, precision):
             special = es == 8 and nx == 4096
             assert pl["update_ax"] == (1 if special else 0), (nx, ny, pl)
             assert pl["macro_serial"] == (1 if special else 0), (nx, ny, pl)
-            # a cluster of two CTAs splits float32 rows of 4096 in the update pass
-            assert pl["update_ctas_per_row"] == (2 if (es == 4 and nx == 4096) else 1), (nx, ny, pl)
+            # a cluster of four CTAs splits float32 rows of 4096 in the update pass
+            assert pl["update_ctas_per_row"] == (4 if (es == 4 and nx == 4096) else 1), (nx, ny, pl)
             assert pl["col_ctas_per_cluster"] == 1
             if not pl["update_ax"]:
                 # six line buffers per row of the update CTA, each its share of the row
