@@ -56,6 +56,24 @@ def test_column_pass_kinds_are_bitwise_the_direct_one(kind, precision, nx, ny):
     assert tried >= 1
 
 
+def test_default_one_buffer_tma_in_a_batch_matches_separate_runs():
+    # columns of 2048 points take the one-buffer TMA form by default, here with three instances
+    # stacked in one size group (tensor maps over the stacked rows) next to a second group
+    sizes = [(16, 2048)] * 3 + [(32, 1024)] * 2
+    p = lbm.default_params(precision=lbm.LBM_MIXED)
+    with lbm.Batch(sizes, p) as b:
+        for k, (nx, ny) in enumerate(sizes):
+            b.init(k, *_fields(nx, ny, seed=70 + k))
+        b.step(3)
+        got = [b.get_f(k) for k in range(len(sizes))]
+    for k, (nx, ny) in enumerate(sizes):
+        with lbm.Simulation(nx, ny, p) as s:
+            s.init(*_fields(nx, ny, seed=70 + k))
+            s.set_pass_kinds((lbm.LBM_COL_DIRECT, lbm.LBM_COL_DIRECT))
+            s.step(3)
+            assert np.array_equal(s.get_f(), got[k]), k
+
+
 def test_tma_in_a_batch_matches_separate_runs():
     sizes = [(64, 64)] * 3 + [(128, 32)] * 2
     p = lbm.default_params(precision=lbm.LBM_MIXED)
