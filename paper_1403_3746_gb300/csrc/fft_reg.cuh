@@ -228,8 +228,9 @@ template <typename R, int LOG2N, bool PK = false, int CS = 1> struct LineFFT {
     static constexpr int NL = N / CS;                        // positions held by one CTA
     static constexpr int GL = G / CS;                        // threads of a line in one CTA
     static constexpr int SMEM = NL + (NL >> 4);              // padded line buffer, complex elements
-    // distance between consecutive line buffers: two extra elements shift each buffer by 16 or
-    // 32 bytes, so lines that share a warp (column tiles) do not collide on the same banks
+    // distance between consecutive line buffers of the row passes: two extra elements shift each
+    // buffer by 16 or 32 bytes (the column tiles, whose lines share warps, space their buffers by
+    // their line count instead: col_line_stride in lbm_internal.cuh)
     static constexpr int STRIDE = SMEM + 2;
     typedef C<R> CT;
 
