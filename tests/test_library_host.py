@@ -178,6 +178,33 @@ def test_launch_plan_of_every_size_fits_the_kernels(L, precision):
                 assert pl["update_smem"] == 6 * pl["update_rows"] * line
 
 
+@pytest.mark.parametrize("precision", [lbm.LBM_MIXED, lbm.LBM_FP64])
+def test_column_tile_line_buffers_take_disjoint_banks(L, precision):
+    # a column tile's L = W/2 lines share warps (line index fastest); an 8-byte (16-byte) shared
+    # access is served per half-warp (quarter-warp), where each line covers 128/L bytes, so
+    # consecutive line buffers must start 128/L bytes apart modulo 128 (one element at least)
+    # and hold the padded line (N + N/16 complex values)
+    es = 8 if precision == lbm.LBM_FP64 else 4
+    cs = 2 * es
+    for ly in range(1, 13):
+        ny = 1 << ly
+        nx = 4096 if precision == lbm.LBM_MIXED else 1024
+        pl = lbm.launch_plan(nx, ny, precision)
+        W, clu = pl["col_width"], pl["col_ctas_per_cluster"]
+        lines = W // 2
+        if lines < 2:
+            continue
+        stride = pl["col_smem"] // lines  # bytes per line buffer
+        assert pl["col_smem"] % lines == 0
+        part = ny // clu
+        assert stride >= (part + part // 16) * cs, (ny, pl)
+        assert stride % 128 == max(128 // lines, cs) % 128, (ny, W, stride)
+        # the lines of one half-warp (quarter-warp) start at distinct offsets modulo 128 bytes
+        per = 16 if es == 4 else 8  # lanes served together
+        group = min(lines, per)
+        assert len({(l * stride) % 128 for l in range(group)}) == group, (ny, W, stride)
+
+
 def test_launch_plan_rejects_bad_sizes(L):
     for nx, ny in ((3, 8), (8, 8192), (1, 2)):
         with pytest.raises(lbm.LbmError, match="power of two"):
